@@ -1,0 +1,349 @@
+/*
+ * gsb_oracle.c -- plain FP64 CPU reference for generalized ballistic simulated
+ * bifurcation (GbSB) and its relatives bSB and dSB.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the oracle that the CUDA library is
+ * checked against. Only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark may load it. It shares no code, header, table or constant with
+ * the CUDA library; the two are written independently from the paper
+ * (Goto, Hidaka, Tatsumura, "Edge-of-chaos enhanced quantum-inspired algorithm
+ * for combinatorial optimization", arXiv:2508.17655).
+ *
+ * Everything here is deliberately slow and literal: one replica at a time, one
+ * spin at a time, in double precision, in the order the paper states the
+ * update (Sec. II, Eqs. 3-7; Fig. 2 caption for the FP -> FX/JX -> FY -> wall
+ * order). Replicas are independent, so an OpenMP loop over replicas is the only
+ * parallelism.
+ *
+ * Readings of points the paper leaves open (each is also listed in the design doc):
+ *   - Eq. 5 writes t_{k+1}; it is read as t_{m+1}.
+ *   - The wall test is strict: |x| > 1. |x| == 1 keeps y.
+ *   - sgn(0) = +1, for spins and for the dSB coupling.
+ *   - Eq. 7 uses x(t_m) (the old position) and the denominator M - m for the
+ *     update that produces p(t_{m+1}); m runs over 0..M-1.
+ *   - Eq. 3 uses p(t_{m+1}) (the new bifurcation parameter), x(t_m) and the
+ *     coupling of x(t_m); Eq. 4 uses y(t_{m+1}).
+ *   - dSB (Sec. VI) replaces J x by J sgn(x) in Eq. 3 only; the p x term keeps x.
+ *   - The shared schedule of bSB/dSB is p(t_m) = 1 - m/M (Eq. 6) unless a
+ *     schedule array is passed.
+ *   - Energy and best-state evaluation: at every step m+1 that is a multiple of
+ *     eval_every, and always at m+1 == M; strict improvement, so the earliest
+ *     step wins a tie.
+ *
+ * Parity status per function:
+ *   orc_philox4x32_10 .... pinned (published known-answer vectors)
+ *   orc_init_uniform ..... pinned (range, symmetry of the integer map)
+ *   orc_energy_* / cut ... pinned (cut identity, closed-form graphs, brute force)
+ *   orc_bruteforce ....... pinned (closed-form max-cut graphs, exhaustive numpy)
+ *   orc_run .............. pinned (Eq. 10 closed form, A=0 -> bSB (Eq. 6),
+ *                          Eq. 7 product formula, time reversal, sign and
+ *                          gauge symmetry, ground states of small instances)
+ *   orc_lambda_extremes .. pinned (LAPACK eigvalsh on small matrices)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11. Ten rounds of the 4x32 Philox S-box with the published
+ * multipliers and Weyl key increments. */
+static void orc_mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+    uint64_t prod = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(prod >> 32);
+    *lo = (uint32_t)prod;
+}
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k[2] = {key_in[0], key_in[1]};
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k[0] += weyl0;
+            k[1] += weyl1;
+        }
+        uint32_t hi0, lo0, hi1, lo1;
+        orc_mulhilo32(mult0, c[0], &hi0, &lo0);
+        orc_mulhilo32(mult1, c[2], &hi1, &lo1);
+        uint32_t n0 = hi1 ^ c[1] ^ k[0];
+        uint32_t n2 = hi0 ^ c[3] ^ k[1];
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+    out[0] = c[0];
+    out[1] = c[1];
+    out[2] = c[2];
+    out[3] = c[3];
+}
+
+/* Uniform draw used for the initial conditions (App. A: x_i(0) uniform in
+ * (-0.1, 0.1)). Counter (i, r, stream, 0), key (seed low, seed high); the top
+ * 24 bits of the first output word give k in [-2^23, 2^23), and the value is
+ * k * (range * 2^-23) rounded once to FP32. The result is returned in double. */
+void orc_init_uniform(int32_t R, int32_t N, uint64_t seed, uint32_t stream, float range,
+                      double* out /* R*N, replica-major */) {
+    const float scale = range * 1.1920928955078125e-07f; /* exact: times 2^-23 */
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int32_t r = 0; r < R; ++r) {
+        for (int32_t i = 0; i < N; ++i) {
+            uint32_t ctr[4] = {(uint32_t)i, (uint32_t)r, stream, 0u};
+            uint32_t w[4];
+            orc_philox4x32_10(ctr, key, w);
+            int32_t kk = (int32_t)(w[0] >> 8) - 8388608;
+            volatile float xf = (float)kk * scale;
+            out[(int64_t)r * N + i] = (double)xf;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+static double orc_sgn(double v) { return v >= 0.0 ? 1.0 : -1.0; }
+
+/* f = J v for a dense row-major N x N matrix (the many-body term of Eq. 3). */
+static void orc_coupling_dense(int32_t N, const double* J, const double* v, double* f) {
+    for (int32_t i = 0; i < N; ++i) {
+        double acc = 0.0;
+        const double* row = J + (int64_t)i * N;
+        for (int32_t j = 0; j < N; ++j) acc += row[j] * v[j];
+        f[i] = acc;
+    }
+}
+
+/* f = J v for J stored as CSR (row pointers, column indices, values). */
+static void orc_coupling_csr(int32_t N, const int32_t* rowptr, const int32_t* col,
+                             const double* val, const double* v, double* f) {
+    for (int32_t i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) acc += val[k] * v[col[k]];
+        f[i] = acc;
+    }
+}
+
+static void orc_coupling(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
+                         const double* val, const double* v, double* f) {
+    if (J)
+        orc_coupling_dense(N, J, v, f);
+    else
+        orc_coupling_csr(N, rowptr, col, val, v, f);
+}
+
+/* Ising energy, Eq. 1: E = -1/2 sum_i sum_j J_ij s_i s_j. */
+double orc_energy(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
+                  const double* val, const int8_t* s) {
+    double* v = (double*)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double* f = (double*)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    for (int32_t i = 0; i < N; ++i) v[i] = (double)s[i];
+    orc_coupling(N, J, rowptr, col, val, v, f);
+    double e = 0.0;
+    for (int32_t i = 0; i < N; ++i) e += v[i] * f[i];
+    free(v);
+    free(f);
+    return -0.5 * e;
+}
+
+/* Energies of R spin vectors (R x N, replica-major). */
+void orc_energy_batch(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
+                      const double* val, int32_t R, const int8_t* s, double* e_out) {
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t r = 0; r < R; ++r)
+        e_out[r] = orc_energy(N, J, rowptr, col, val, s + (int64_t)r * N);
+}
+
+/* Cut value by its definition: with edge weights W = -J (Sec. III), the cut is
+ * the total weight of the edges {i, j}, i < j, whose endpoints have different
+ * spins. Dense J only. */
+double orc_cut_dense(int32_t N, const double* J, const int8_t* s) {
+    double cut = 0.0;
+    for (int32_t i = 0; i < N; ++i)
+        for (int32_t j = i + 1; j < N; ++j)
+            if (s[i] != s[j]) cut += -J[(int64_t)i * N + j];
+    return cut;
+}
+
+/* Exhaustive minimum of Eq. 1 over all 2^N spin vectors (N <= 30), visiting
+ * them in Gray-code order with s_0 fixed to +1 (E is invariant under s -> -s).
+ * Returns the minimum energy; writes one minimiser to s_best. */
+double orc_bruteforce(int32_t N, const double* J, int8_t* s_best) {
+    if (N <= 0) return 0.0;
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    double* h = (double*)malloc(sizeof(double) * (size_t)N);
+    for (int32_t i = 0; i < N; ++i) s[i] = 1;
+    for (int32_t i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int32_t j = 0; j < N; ++j) acc += J[(int64_t)i * N + j];
+        h[i] = acc; /* local field sum_j J_ij s_j */
+    }
+    double e = 0.0;
+    for (int32_t i = 0; i < N; ++i) e += h[i];
+    e *= -0.5;
+    double best = e;
+    memcpy(s_best, s, (size_t)N);
+    uint64_t count = (N > 1) ? (1ull << (N - 1)) : 1ull;
+    for (uint64_t g = 1; g < count; ++g) {
+        /* spin to flip: lowest set bit of g, offset by one (spin 0 is fixed) */
+        int32_t k = 1 + __builtin_ctzll(g);
+        /* flipping s_k changes E by 2 s_k h_k */
+        e += 2.0 * (double)s[k] * h[k];
+        double two_sk = 2.0 * (double)s[k];
+        s[k] = (int8_t)(-s[k]);
+        for (int32_t j = 0; j < N; ++j) h[j] -= two_sk * J[(int64_t)j * N + k];
+        if (e < best) {
+            best = e;
+            memcpy(s_best, s, (size_t)N);
+        }
+    }
+    free(s);
+    free(h);
+    return best;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The GbSB iteration for R independent replicas, steps m = m0 .. m0+nsteps-1
+ * of a run with M steps in total (Sec. II).
+ *
+ *   coupling: 0 -> J x   (bSB, GbSB; Eq. 3)
+ *             1 -> J sgn(x)   (dSB; Sec. VI)
+ *   control:  0 -> one shared bifurcation parameter: sched[m+1] if sched is
+ *                  given, else 1 - (m+1)/M (Eq. 6)
+ *             1 -> individual parameters p_i controlled by Eq. 7 with the
+ *                  replica's control strength A[r]
+ *
+ * x, y, p are R x N (replica-major) and updated in place. For control 0 the p
+ * array receives the shared value. Each evaluation step writes sgn(x) energy
+ * (Eq. 1) and keeps the strictly best one per replica in best_E, best_s,
+ * best_step (best_E must be initialised by the caller, e.g. to +inf).
+ * Returns 0, or -1 on bad arguments. */
+int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
+            const double* val, int32_t coupling, int32_t control, const double* A,
+            const double* sched, double c, double dt, int32_t M, int32_t m0, int32_t nsteps,
+            int32_t R, double* x, double* y, double* p, int32_t eval_every, double* best_E,
+            int8_t* best_s, int32_t* best_step, int32_t nthreads) {
+    if (N <= 0 || R <= 0 || M <= 0 || m0 < 0 || nsteps < 0 || m0 + nsteps > M) return -1;
+    if (!J && !(rowptr && col && val)) return -1;
+    if (control == 1 && !A) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t r = 0; r < R; ++r) {
+        double* xr = x + (int64_t)r * N;
+        double* yr = y + (int64_t)r * N;
+        double* pr = p + (int64_t)r * N;
+        double* v = (double*)malloc(sizeof(double) * (size_t)N);
+        double* f = (double*)malloc(sizeof(double) * (size_t)N);
+        int8_t* s = (int8_t*)malloc((size_t)N);
+        for (int32_t m = m0; m < m0 + nsteps; ++m) {
+            /* FP: bifurcation parameter(s) at t_{m+1}, from x(t_m) */
+            if (control == 1) {
+                const double a = A[r];
+                for (int32_t i = 0; i < N; ++i)
+                    pr[i] = pr[i] - (1.0 - a * xr[i] * xr[i]) * pr[i] / (double)(M - m);
+            } else {
+                double pnext = sched ? sched[m + 1] : 1.0 - (double)(m + 1) / (double)M;
+                for (int32_t i = 0; i < N; ++i) pr[i] = pnext;
+            }
+            /* JX: many-body term of x(t_m) or of its signs */
+            for (int32_t j = 0; j < N; ++j) v[j] = coupling ? orc_sgn(xr[j]) : xr[j];
+            orc_coupling(N, J, rowptr, col, val, v, f);
+            /* Eq. 3: momentum, with p(t_{m+1}) and x(t_m) */
+            for (int32_t i = 0; i < N; ++i) yr[i] = yr[i] - (pr[i] * xr[i] - c * f[i]) * dt;
+            /* Eq. 4: position, with y(t_{m+1}) */
+            for (int32_t i = 0; i < N; ++i) xr[i] = xr[i] + yr[i] * dt;
+            /* Eq. 5: perfectly inelastic walls at |x| = 1 */
+            for (int32_t i = 0; i < N; ++i) {
+                if (fabs(xr[i]) > 1.0) {
+                    xr[i] = orc_sgn(xr[i]);
+                    yr[i] = 0.0;
+                }
+            }
+            /* Ising energy of sgn x(t_{m+1}) and best-state keeping */
+            int32_t step = m + 1;
+            int is_eval = (step == M) || (eval_every > 0 && step % eval_every == 0);
+            if (is_eval && best_E) {
+                for (int32_t i = 0; i < N; ++i) s[i] = (int8_t)(xr[i] >= 0.0 ? 1 : -1);
+                double e = orc_energy(N, J, rowptr, col, val, s);
+                if (e < best_E[r]) {
+                    best_E[r] = e;
+                    if (best_s) memcpy(best_s + (int64_t)r * N, s, (size_t)N);
+                    if (best_step) best_step[r] = step;
+                }
+            }
+        }
+        free(v);
+        free(f);
+        free(s);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Extreme eigenvalues of a symmetric matrix by shifted power iteration (used
+ * for c = 1/lambda_max and Eq. 13, App. A). With sigma = 1.01 rho(J) (a
+ * bound just above the spectral radius), J + sigma I and sigma I - J are
+ * positive semidefinite and their dominant eigenvalues are lambda_max + sigma
+ * and sigma - lambda_min.
+ * Iterates until the Rayleigh quotient changes by less than tol (relative) or
+ * iters is reached. Dense or CSR. */
+static double orc_power_dominant(int32_t N, const double* J, const int32_t* rowptr,
+                                 const int32_t* col, const double* val, double sigma, double sign,
+                                 int32_t iters, double tol) {
+    double* v = (double*)malloc(sizeof(double) * (size_t)N);
+    double* f = (double*)malloc(sizeof(double) * (size_t)N);
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)N);
+    uint32_t key[2] = {12345u, 0u};
+    for (int32_t i = 0; i < N; ++i) {
+        uint32_t ctr[4] = {(uint32_t)i, 0u, 7u, 0u}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        v[i] = ((double)(w[0] >> 8) + 0.5) / 16777216.0 - 0.5;
+    }
+    double rq = 0.0;
+    for (int32_t it = 0; it < iters; ++it) {
+        double nrm = 0.0;
+        for (int32_t i = 0; i < N; ++i) nrm += v[i] * v[i];
+        nrm = sqrt(nrm);
+        for (int32_t i = 0; i < N; ++i) v[i] /= nrm;
+        orc_coupling(N, J, rowptr, col, val, v, f);
+        if (sign == 0.0) {
+            /* J^2 v: apply the coupling a second time */
+            memcpy(tmp, f, sizeof(double) * (size_t)N);
+            orc_coupling(N, J, rowptr, col, val, tmp, f);
+        }
+        double num = 0.0;
+        for (int32_t i = 0; i < N; ++i) {
+            f[i] = sigma * v[i] + (sign == 0.0 ? 1.0 : sign) * f[i];
+            num += v[i] * f[i];
+        }
+        double prev = rq;
+        rq = num;
+        memcpy(v, f, sizeof(double) * (size_t)N);
+        if (it > 10 && fabs(rq - prev) <= tol * fabs(rq)) break;
+    }
+    free(v);
+    free(f);
+    free(tmp);
+    return rq;
+}
+
+void orc_lambda_extremes(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
+                         const double* val, int32_t iters, double tol, double* lmax,
+                         double* lmin) {
+    /* spectral radius rho(J) from ||J^k v|| growth (power iteration with no
+     * shift, Rayleigh quotient of J^2), then shifts by 1.01 rho so that both
+     * shifted matrices are positive semidefinite */
+    double rho2 = orc_power_dominant(N, J, rowptr, col, val, 0.0, 0.0, iters, tol);
+    double sigma = 1.01 * sqrt(rho2 > 0.0 ? rho2 : 0.0) + 1e-300;
+    double top = orc_power_dominant(N, J, rowptr, col, val, sigma, 1.0, iters, tol);
+    double bot = orc_power_dominant(N, J, rowptr, col, val, sigma, -1.0, iters, tol);
+    *lmax = top - sigma;
+    *lmin = sigma - bot;
+}
