@@ -1,0 +1,172 @@
+/*
+ * gsb.h -- C ABI of libgsb: generalized ballistic simulated bifurcation (GbSB)
+ * and its relatives bSB / dSB on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Goto, Hidaka, Tatsumura, "Edge-of-chaos enhanced quantum-inspired
+ * algorithm for combinatorial optimization", arXiv:2508.17655.
+ *   - Problem: the Ising energy E = -1/2 sum_ij J_ij s_i s_j with J symmetric
+ *     and J_ii = 0 (Sec. II, Eq. 1); Max-Cut with edge weights W = -J (Sec. III).
+ *   - Per time step m = 0..M-1, for every replica and spin i (Sec. II; order of
+ *     the Fig. 2 caption):
+ *       FP (Eq. 7):  p_i <- p_i - (1 - A x_i^2) p_i / (M - m)        [GbSB]
+ *                    p   <- 1 - (m+1)/M, or a caller schedule      [bSB, dSB; Eq. 6]
+ *       JX:          f_i = sum_j J_ij v_j,  v = x (bSB/GbSB) or sgn x (dSB, Sec. VI)
+ *       FX (Eq. 3):  y_i <- y_i - (p_i x_i - c f_i) dt
+ *       FY (Eq. 4):  x_i <- x_i + y_i dt
+ *       wall (Eq. 5): if |x_i| > 1 then x_i <- sgn x_i, y_i <- 0
+ *   - Initial state (App. A): x_i(0) uniform in [-0.1, 0.1), y_i(0) = 0, p_i(0) = 1.
+ *   - c = 1/lambda_max and dt = D_t sqrt(2 / (1 - lambda_min/lambda_max)) with
+ *     D_t = 1.25 (App. A, Eq. 13) when the caller passes 0 for them.
+ *
+ * Conventions for every entry point:
+ *   - Return a gsb_status; GSB_OK is 0. No C++ exception crosses the ABI.
+ *     gsb_last_error() gives a message for the last failure on this thread.
+ *   - Pointers documented as "host" are caller-owned host memory, read or
+ *     written before the call returns (gsb_best and gsb_get_state block on the
+ *     run's stream first). Pointers documented as "device" are caller-owned
+ *     device memory on the current device.
+ *   - Handles (gsb_problem, gsb_run_state) are library-owned; they own their device
+ *     buffers. A handle must not be used from two threads at once.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Work is enqueued asynchronously on it.
+ *   - Spins are int8 +-1; sgn(0) = +1. Energies are double; for integer J they
+ *     are exact integers.
+ *   - Layouts: J dense is row-major N x N. Per-replica arrays of length R;
+ *     per-replica vectors (spins, x, y, p) are replica-major R x N.
+ */
+#ifndef GSB_H
+#define GSB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gsb_status {
+    GSB_OK = 0,
+    GSB_EINVAL = 1,       /* bad argument: size, null pointer, asymmetric J, nonzero diagonal */
+    GSB_ENOMEM = 2,       /* device allocation failed */
+    GSB_ECUDA = 3,        /* a CUDA runtime or driver call failed */
+    GSB_ETIMEOUT = 4,     /* a bounded device-side wait gave up (status word set by a kernel) */
+    GSB_EUNSUPPORTED = 5, /* valid request the library cannot serve (e.g. FP8 with non-integer J) */
+    GSB_ENUMERIC = 6,     /* a NaN or Inf reached the state */
+    GSB_ENODEV = 7        /* no usable sm_103 device */
+} gsb_status;
+
+/* Variant = (coupling, control). bSB and GbSB couple through x, dSB and GdSB
+ * through sgn x (Sec. VI). bSB and dSB share one parameter p (Eq. 6); GbSB and
+ * GdSB control individual parameters by Eq. 7. GdSB (Eq. 7 with sgn x
+ * coupling) is not in the paper; it is named there as a direction only. */
+typedef enum gsb_variant { GSB_BSB = 0, GSB_GBSB = 1, GSB_DSB = 2, GSB_GDSB = 3 } gsb_variant;
+
+/* Coupling arithmetic. */
+typedef enum gsb_precision {
+    GSB_PREC_AUTO = 0,   /* FP8 for sgn-x coupling with small integer J, BF16X3 for x coupling
+                            with small integer J, FP32 otherwise; CSR problems always use CSR */
+    GSB_PREC_FP32 = 1,   /* FP32 on CUDA cores (the plain form) */
+    GSB_PREC_FP8 = 2,    /* tcgen05 kind::f8f6f4, e4m3 J and sgn x, FP32 accumulate: exact for
+                            integer |J| <= 16; sgn-x coupling (dSB, GdSB) only */
+    GSB_PREC_BF16X3 = 3  /* tcgen05 kind::f16, J in bf16 (exact for integer |J| <= 256) and x
+                            split into three bf16 terms (x = hi + mid + lo exactly) */
+} gsb_precision;
+
+/* J storage passed to gsb_create. */
+typedef enum gsb_jformat {
+    GSB_J_DENSE_I8 = 0,  /* int8, N x N row-major */
+    GSB_J_DENSE_F32 = 1, /* float, N x N row-major */
+    GSB_J_CSR_F32 = 2    /* CSR: int32 rowptr[N+1], int32 col[nnz], float val[nnz]; every row's
+                            column indices strictly increasing */
+} gsb_jformat;
+
+/* gsb_create flags */
+#define GSB_CREATE_DEVICE_INPUT 0x1u /* J / rowptr / col / val / h are device pointers */
+#define GSB_CREATE_NO_VALIDATE 0x2u  /* skip the symmetry and zero-diagonal check */
+
+typedef struct gsb_problem gsb_problem;
+typedef struct gsb_run_state gsb_run_state;
+
+/* Run parameters. Zero-initialise, then set what you need; zero means the
+ * documented default. */
+typedef struct gsb_params {
+    int32_t variant;          /* gsb_variant */
+    int32_t M;                /* total steps of the run (t_M = M dt), >= 1 */
+    int32_t R;                /* replicas, >= 1 */
+    int32_t precision;        /* gsb_precision */
+    double c;                 /* > 0, or 0: 1/lambda_max (App. A) */
+    double dt;                /* > 0, or 0: Eq. 13 with D_t = 1.25 */
+    float A;                  /* control strength of Eq. 7 for every replica (GbSB, GdSB) */
+    const float* A_per_replica; /* host, length R, or NULL: per-replica control strengths */
+    const float* schedule;    /* host, length M+1, or NULL: p(t_m) for bSB / dSB (default Eq. 6) */
+    uint64_t seed;            /* Philox4x32-10 key for the initial conditions */
+    float x0_range;           /* 0: 0.1 (App. A) */
+    int32_t y0_uniform;       /* 0: y(0) = 0 (App. A); 1: y(0) uniform in [-x0_range, x0_range) */
+    int32_t eval_every;       /* 0: evaluate the energy at t_M only (Sec. III); k > 0: also
+                                 at every step that is a multiple of k */
+    int32_t steps_per_launch; /* 0: automatic; else steps fused per launch on paths that fuse */
+    const float* x0;          /* host, R x N, or NULL: explicit x(0) instead of the Philox draw */
+    const float* y0;          /* host, R x N, or NULL: explicit y(0) */
+    uint32_t flags;           /* GSB_RUN_* */
+} gsb_params;
+
+#define GSB_RUN_DEFER 0x1u /* gsb_run sets up the state but advances no step */
+
+/* Create a problem from a coupling matrix (Eq. 1). The library copies J into
+ * the device formats its kernels need (FP32, e4m3, bf16 and/or CSR), padded
+ * to its tile sizes. Validation (unless GSB_CREATE_NO_VALIDATE): square,
+ * symmetric, zero diagonal, finite -- else GSB_EINVAL. h (host or device,
+ * length N, nullable) adds a local field -h_i s_i to Eq. 1 (not in the paper):
+ * it is folded in exactly as an extra spin N coupled by J_{i,N} = h_i, and
+ * results are reported with that spin gauge-fixed to +1.
+ * Arguments not used by `format` must be NULL / 0. */
+gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* J,
+                      const int32_t* rowptr, const int32_t* col, const float* val, int64_t nnz,
+                      const float* h, uint32_t flags, void* stream);
+gsb_status gsb_destroy(gsb_problem* problem);
+
+/* Number of spins (including the auxiliary one when h was given) and the
+ * extreme eigenvalues of J used for c and dt (computed on the GPU by power
+ * iteration on first use; App. A). */
+gsb_status gsb_problem_info(gsb_problem* problem, int32_t* n_spins, double* lambda_max,
+                            double* lambda_min, void* stream);
+
+/* Start a run: allocate its device state, draw or upload x(0), y(0), set
+ * p(0) = 1, and (unless GSB_RUN_DEFER) enqueue all M steps on `stream`. */
+gsb_status gsb_run(gsb_problem* problem, const gsb_params* params, gsb_run_state** out, void* stream);
+
+/* Advance a run by nsteps (<= M - steps already done) on its stream. Runs
+ * split into several calls follow the same trajectory as one call. */
+gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps);
+
+/* Best state per replica (host outputs, each nullable): spins R x N int8,
+ * energies (Eq. 1), cut values (W_tot - E)/2 with W = -J (Sec. III), and the
+ * step m at which it was found. Blocks on the run's stream. Replicas that have
+ * not been evaluated yet report energy +inf and step -1. */
+gsb_status gsb_best(gsb_run_state* run, int8_t* spins, double* energies, double* cuts,
+                    int32_t* step_found);
+
+/* Current state, host outputs R x N each (nullable), and the number of steps
+ * done so far. For bSB/dSB, p holds the shared parameter in every entry. */
+gsb_status gsb_get_state(gsb_run_state* run, float* x, float* y, float* p, int32_t* steps_done);
+
+/* Ising energies (Eq. 1) of R caller spin vectors (host, R x N int8 +-1) into
+ * energies (host, length R). Evaluated on the GPU. */
+gsb_status gsb_energy(gsb_problem* problem, int32_t R, const int8_t* spins, double* energies,
+                      void* stream);
+
+gsb_status gsb_run_destroy(gsb_run_state* run);
+
+/* Message for the last non-OK status returned on the calling thread. */
+const char* gsb_last_error(void);
+
+/* Library version, and the number of kernels this library has launched in
+ * this process (a counter the host increments at every launch). */
+int32_t gsb_version(void);
+int64_t gsb_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSB_H */

@@ -1,0 +1,684 @@
+// gsb_api.cu -- the C ABI declared in include/gsb.h: problem set-up and
+// validation, run state, the host loop over time steps, results.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "gsb_internal.cuh"
+
+namespace gsb {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+gsb_status set_error(gsb_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+gsb_status cuda_error(cudaError_t err, const char* what) {
+    return set_error(err == cudaErrorMemoryAllocation ? GSB_ENOMEM : GSB_ECUDA,
+                     std::string(what) + ": " + cudaGetErrorString(err));
+}
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+gsb_status check_device(int* dev_out) {
+    int dev = 0;
+    GSB_CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    GSB_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return set_error(GSB_ENODEV, "libgsb is built for sm_103a (GB300); device " +
+                                         std::string(prop.name) + " is sm_" +
+                                         std::to_string(prop.major) + std::to_string(prop.minor));
+    *dev_out = dev;
+    return GSB_OK;
+}
+
+template <typename T>
+gsb_status dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return GSB_OK;
+    GSB_CUDA_TRY(cudaMalloc((void**)p, sizeof(T) * count));
+    return GSB_OK;
+}
+
+// J32 -> e4m3 and bf16 copies (exact for the integer ranges they are made for).
+__global__ void k_convert_J(const float* __restrict__ J, uint8_t* __restrict__ J8,
+                            __nv_bfloat16* __restrict__ J16, size_t n) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float v = J[k];
+    if (J8) J8[k] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    if (J16) J16[k] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_fill_f64(double* p, double v, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] = v;
+}
+__global__ void k_fill_i32(int32_t* p, int32_t v, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] = v;
+}
+
+bool is_integer(float v) { return v == nearbyintf(v); }
+
+void free_problem(gsb_problem* P) {
+    if (!P) return;
+    cudaFree(P->J32);
+    cudaFree(P->J8);
+    cudaFree(P->J16);
+    cudaFree(P->rowptr);
+    cudaFree(P->col);
+    cudaFree(P->val);
+    delete P;
+}
+
+gsb_status create_dense(gsb_problem* P, const float* Jh, const float* hh, bool validate,
+                        cudaStream_t s) {
+    const int Nu = P->N_user;
+    const int N = P->N;
+    const int Np = P->Np;
+    std::vector<float> Jp((size_t)Np * Np, 0.f);
+    for (int i = 0; i < Nu; ++i)
+        for (int j = 0; j < Nu; ++j) Jp[(size_t)i * Np + j] = Jh[(size_t)i * Nu + j];
+    if (hh) {
+        for (int i = 0; i < Nu; ++i) {
+            Jp[(size_t)i * Np + Nu] = hh[i];
+            Jp[(size_t)Nu * Np + i] = hh[i];
+        }
+    }
+    bool integer = true;
+    float mx = 0.f;
+    double sum = 0.0;
+    for (int i = 0; i < N; ++i) {
+        for (int j = 0; j < N; ++j) {
+            const float v = Jp[(size_t)i * Np + j];
+            if (validate) {
+                if (!isfinite(v)) return set_error(GSB_EINVAL, "J has a non-finite entry");
+                if (i == j && v != 0.f)
+                    return set_error(GSB_EINVAL, "J has a nonzero diagonal entry (Eq. 1 needs J_ii = 0)");
+                if (j > i && v != Jp[(size_t)j * Np + i])
+                    return set_error(GSB_EINVAL, "J is not symmetric (Eq. 1 needs J_ij = J_ji)");
+            }
+            integer = integer && is_integer(v);
+            mx = std::max(mx, fabsf(v));
+            sum += v;
+        }
+    }
+    P->integer_J = integer;
+    P->max_abs_J = mx;
+    P->W_tot = -0.5 * sum;
+    const size_t n = (size_t)Np * Np;
+    gsb_status st;
+    if ((st = dev_alloc(&P->J32, n)) != GSB_OK) return st;
+    GSB_CUDA_TRY(cudaMemcpyAsync(P->J32, Jp.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (integer && mx <= 16.f)
+        if ((st = dev_alloc(&P->J8, n)) != GSB_OK) return st;
+    if (integer && mx <= 256.f)
+        if ((st = dev_alloc(&P->J16, n)) != GSB_OK) return st;
+    if (P->J8 || P->J16) {
+        k_convert_J<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P->J32, P->J8, P->J16, n);
+        GSB_LAUNCH_CHECK("k_convert_J");
+    }
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));  // Jp goes out of scope
+    return GSB_OK;
+}
+
+gsb_status create_csr(gsb_problem* P, const int32_t* rp, const int32_t* ci, const float* vv,
+                      int64_t nnz, const float* hh, bool validate, cudaStream_t s) {
+    const int Nu = P->N_user;
+    const int N = P->N;
+    if (rp[0] != 0 || rp[Nu] != nnz) return set_error(GSB_EINVAL, "rowptr must run from 0 to nnz");
+    std::vector<int32_t> rowptr(N + 1, 0), col;
+    std::vector<float> val;
+    col.reserve(nnz + (hh ? 2 * Nu : 0));
+    val.reserve(col.capacity());
+    for (int i = 0; i < Nu; ++i) {
+        if (rp[i + 1] < rp[i]) return set_error(GSB_EINVAL, "rowptr is not monotone");
+        int prev = -1;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            if (j < 0 || j >= Nu) return set_error(GSB_EINVAL, "column index out of range");
+            if (j <= prev) return set_error(GSB_EINVAL, "column indices must increase within a row");
+            prev = j;
+            if (validate) {
+                if (!isfinite(vv[k])) return set_error(GSB_EINVAL, "J has a non-finite entry");
+                if (j == i && vv[k] != 0.f)
+                    return set_error(GSB_EINVAL, "J has a nonzero diagonal entry (Eq. 1 needs J_ii = 0)");
+                // symmetric partner (j, i) with the same value
+                const int32_t* b = ci + rp[j];
+                const int32_t* e = ci + rp[j + 1];
+                const int32_t* f = std::lower_bound(b, e, i);
+                if (f == e || *f != i || vv[rp[j] + (f - b)] != vv[k])
+                    return set_error(GSB_EINVAL, "J is not symmetric (Eq. 1 needs J_ij = J_ji)");
+            }
+            col.push_back(j);
+            val.push_back(vv[k]);
+        }
+        if (hh && hh[i] != 0.f) {
+            col.push_back(Nu);
+            val.push_back(hh[i]);
+        }
+        rowptr[i + 1] = (int32_t)col.size();
+    }
+    if (hh) {
+        for (int j = 0; j < Nu; ++j)
+            if (hh[j] != 0.f) {
+                col.push_back(j);
+                val.push_back(hh[j]);
+            }
+        rowptr[N] = (int32_t)col.size();
+    }
+    bool integer = true;
+    float mx = 0.f;
+    double sum = 0.0;
+    for (float v : val) {
+        integer = integer && is_integer(v);
+        mx = std::max(mx, fabsf(v));
+        sum += v;
+    }
+    P->integer_J = integer;
+    P->max_abs_J = mx;
+    P->W_tot = -0.5 * sum;
+    P->nnz = (int64_t)col.size();
+    gsb_status st;
+    if ((st = dev_alloc(&P->rowptr, (size_t)N + 1)) != GSB_OK) return st;
+    if ((st = dev_alloc(&P->col, std::max<size_t>(1, col.size()))) != GSB_OK) return st;
+    if ((st = dev_alloc(&P->val, std::max<size_t>(1, val.size()))) != GSB_OK) return st;
+    GSB_CUDA_TRY(cudaMemcpyAsync(P->rowptr, rowptr.data(), sizeof(int32_t) * (N + 1),
+                                 cudaMemcpyHostToDevice, s));
+    if (!col.empty()) {
+        GSB_CUDA_TRY(cudaMemcpyAsync(P->col, col.data(), sizeof(int32_t) * col.size(),
+                                     cudaMemcpyHostToDevice, s));
+        GSB_CUDA_TRY(cudaMemcpyAsync(P->val, val.data(), sizeof(float) * val.size(),
+                                     cudaMemcpyHostToDevice, s));
+    }
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    return GSB_OK;
+}
+
+template <typename T>
+std::vector<T> fetch(const T* p, size_t n, bool device) {
+    std::vector<T> v(n);
+    if (n == 0) return v;
+    if (device)
+        cudaMemcpy(v.data(), p, sizeof(T) * n, cudaMemcpyDeviceToHost);
+    else
+        memcpy(v.data(), p, sizeof(T) * n);
+    return v;
+}
+
+void free_run(gsb_run_state* r) {
+    if (!r) return;
+    if (r->tc) tc_free(r);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(r->x[b]);
+        cudaFree(r->s8[b]);
+        cudaFree(r->v8[b]);
+        cudaFree(r->v16[b]);
+    }
+    cudaFree(r->y);
+    cudaFree(r->p);
+    cudaFree(r->A);
+    cudaFree(r->sched);
+    cudaFree(r->e_acc);
+    cudaFree(r->best_e);
+    cudaFree(r->best_step);
+    cudaFree(r->best_s);
+    cudaFree(r->flag);
+    cudaFree(r->status);
+    delete r;
+}
+
+gsb_status evaluate(gsb_run_state* run, int step) {
+    if (run->path == kPathTcFp8 || run->path == kPathTcBf16x3) {
+        gsb_status st = tc_energy(run);
+        if (st != GSB_OK) return st;
+        return launch_best_keep(run, step);
+    }
+    GSB_CUDA_TRY(cudaMemsetAsync(run->e_acc, 0, sizeof(double) * run->Rp, run->stream));
+    gsb_status st = run->path == kPathCsr
+                        ? launch_csr_energy(run->prob, run->x[run->cur], run->Rp, run->e_acc,
+                                            run->stream)
+                        : launch_dense_f32_energy(run->prob, run->x[run->cur], run->Rp,
+                                                  run->e_acc, run->stream);
+    if (st != GSB_OK) return st;
+    return launch_best_keep(run, step);
+}
+
+bool is_eval_step(const gsb_run_state* run, int step) {
+    const int k = run->params.eval_every;
+    return step == run->params.M || (k > 0 && step % k == 0);
+}
+
+// Shared bifurcation parameter p(t_step) of bSB / dSB: the caller's schedule,
+// else Eq. 6, p(t_m) = 1 - m/M (evaluated in double, rounded once).
+float p_shared_at(const gsb_run_state* run, int step) {
+    if (!run->sched_host.empty()) return run->sched_host[step];
+    return (float)(1.0 - (double)step / (double)run->params.M);
+}
+
+}  // namespace
+
+bool run_is_eval_step(const gsb_run_state* run, int step) { return is_eval_step(run, step); }
+float run_p_shared(const gsb_run_state* run, int step) { return p_shared_at(run, step); }
+gsb_status run_evaluate(gsb_run_state* run, int step) { return evaluate(run, step); }
+
+}  // namespace gsb
+
+using namespace gsb;
+
+extern "C" {
+
+const char* gsb_last_error(void) { return g_last_error.c_str(); }
+int32_t gsb_version(void) { return 100; }
+int64_t gsb_launch_count(void) { return g_launches.load(); }
+
+gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* J,
+                      const int32_t* rowptr, const int32_t* col, const float* val, int64_t nnz,
+                      const float* h, uint32_t flags, void* stream) {
+    if (!out) return set_error(GSB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 1) return set_error(GSB_EINVAL, "N must be >= 1");
+    if (N > (1 << 20)) return set_error(GSB_EINVAL, "N too large");
+    int dev = 0;
+    gsb_status st = check_device(&dev);
+    if (st != GSB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool device_in = flags & GSB_CREATE_DEVICE_INPUT;
+    const bool validate = !(flags & GSB_CREATE_NO_VALIDATE);
+    gsb_problem* P = new gsb_problem();
+    P->device = dev;
+    P->N_user = N;
+    P->has_h = h != nullptr;
+    P->N = N + (h ? 1 : 0);
+    P->Np = round_up(P->N, kTile);
+    std::vector<float> hv;
+    if (h) hv = fetch(h, (size_t)N, device_in);
+    if (format == GSB_J_DENSE_I8 || format == GSB_J_DENSE_F32) {
+        if (!J || rowptr || col || val || nnz) {
+            free_problem(P);
+            return set_error(GSB_EINVAL, "dense formats take J only");
+        }
+        if ((int64_t)P->Np * P->Np > (int64_t)1 << 32) {
+            free_problem(P);
+            return set_error(GSB_EINVAL, "dense J too large; use CSR");
+        }
+        std::vector<float> Jf((size_t)N * N);
+        if (format == GSB_J_DENSE_I8) {
+            auto J8 = fetch((const int8_t*)J, (size_t)N * N, device_in);
+            for (size_t k = 0; k < Jf.size(); ++k) Jf[k] = (float)J8[k];
+        } else {
+            Jf = fetch((const float*)J, (size_t)N * N, device_in);
+        }
+        st = create_dense(P, Jf.data(), h ? hv.data() : nullptr, validate, s);
+    } else if (format == GSB_J_CSR_F32) {
+        if (J || !rowptr || (nnz > 0 && (!col || !val)) || nnz < 0) {
+            free_problem(P);
+            return set_error(GSB_EINVAL, "CSR format takes rowptr, col, val");
+        }
+        auto rp = fetch(rowptr, (size_t)N + 1, device_in);
+        auto ci = fetch(col, (size_t)nnz, device_in);
+        auto vv = fetch(val, (size_t)nnz, device_in);
+        P->csr = true;
+        st = create_csr(P, rp.data(), ci.data(), vv.data(), nnz, h ? hv.data() : nullptr,
+                        validate, s);
+    } else {
+        free_problem(P);
+        return set_error(GSB_EINVAL, "unknown J format");
+    }
+    if (st != GSB_OK) {
+        free_problem(P);
+        return st;
+    }
+    *out = P;
+    return GSB_OK;
+}
+
+gsb_status gsb_destroy(gsb_problem* problem) {
+    free_problem(problem);
+    return GSB_OK;
+}
+
+gsb_status gsb_problem_info(gsb_problem* P, int32_t* n_spins, double* lmax, double* lmin,
+                            void* stream) {
+    if (!P) return set_error(GSB_EINVAL, "problem is NULL");
+    if (n_spins) *n_spins = P->N;
+    if (lmax || lmin) {
+        gsb_status st = compute_lambda(P, (cudaStream_t)stream);
+        if (st != GSB_OK) return st;
+        if (lmax) *lmax = P->lambda_max;
+        if (lmin) *lmin = P->lambda_min;
+    }
+    return GSB_OK;
+}
+
+gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, void* stream) {
+    if (!P || !prm || !out) return set_error(GSB_EINVAL, "NULL argument");
+    *out = nullptr;
+    const gsb_params& Q = *prm;
+    if (Q.variant < GSB_BSB || Q.variant > GSB_GDSB) return set_error(GSB_EINVAL, "unknown variant");
+    if (Q.M < 1) return set_error(GSB_EINVAL, "M must be >= 1");
+    if (Q.R < 1 || Q.R > (1 << 22)) return set_error(GSB_EINVAL, "R out of range");
+    if (Q.c < 0 || Q.dt < 0 || !isfinite(Q.c) || !isfinite(Q.dt))
+        return set_error(GSB_EINVAL, "c and dt must be >= 0 and finite");
+    if (Q.eval_every < 0) return set_error(GSB_EINVAL, "eval_every must be >= 0");
+    if (Q.x0_range < 0) return set_error(GSB_EINVAL, "x0_range must be >= 0");
+    const bool sign = Q.variant == GSB_DSB || Q.variant == GSB_GDSB;
+    const bool control = Q.variant == GSB_GBSB || Q.variant == GSB_GDSB;
+    if (Q.schedule && control)
+        return set_error(GSB_EINVAL, "a schedule applies to bSB / dSB only (GbSB uses Eq. 7)");
+    int path = kPathDenseF32;
+    if (P->csr) {
+        if (Q.precision != GSB_PREC_AUTO)
+            return set_error(GSB_EUNSUPPORTED, "CSR problems run on the CSR path only");
+        path = kPathCsr;
+    } else {
+        switch (Q.precision) {
+            case GSB_PREC_AUTO:
+                if (!tc_available())
+                    path = kPathDenseF32;
+                else if (sign && P->J8)
+                    path = kPathTcFp8;
+                else if (!sign && P->J16)
+                    path = kPathTcBf16x3;
+                else
+                    path = kPathDenseF32;
+                break;
+            case GSB_PREC_FP32: path = kPathDenseF32; break;
+            case GSB_PREC_FP8:
+                if (!sign)
+                    return set_error(GSB_EUNSUPPORTED, "FP8 serves the sgn-x coupling (dSB, GdSB)");
+                if (!P->J8)
+                    return set_error(GSB_EUNSUPPORTED, "FP8 needs integer J with |J| <= 16");
+                path = kPathTcFp8;
+                break;
+            case GSB_PREC_BF16X3:
+                if (!P->J16)
+                    return set_error(GSB_EUNSUPPORTED, "BF16X3 needs integer J with |J| <= 256");
+                path = kPathTcBf16x3;
+                break;
+            default: return set_error(GSB_EINVAL, "unknown precision");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double c = Q.c, dt = Q.dt;
+    if (c == 0.0 || dt == 0.0) {
+        gsb_status st = compute_lambda(P, s);
+        if (st != GSB_OK) return st;
+        if (!(P->lambda_max > 0.0))
+            return set_error(GSB_EINVAL, "lambda_max <= 0: set c and dt explicitly");
+        if (c == 0.0) c = 1.0 / P->lambda_max;  // App. A
+        if (dt == 0.0) dt = 1.25 * sqrt(2.0 / (1.0 - P->lambda_min / P->lambda_max));  // Eq. 13
+    }
+    gsb_run_state* run = new gsb_run_state();
+    run->prob = P;
+    run->params = Q;
+    run->params.A_per_replica = nullptr;
+    run->params.schedule = nullptr;
+    run->params.x0 = nullptr;
+    run->params.y0 = nullptr;
+    run->path = path;
+    run->stream = s;
+    run->N = P->N;
+    run->Np = P->Np;
+    run->R = Q.R;
+    run->Rp = round_up(Q.R, kTile);
+    run->c = (float)c;
+    run->dt = (float)dt;
+    run->sign_coupling = sign;
+    run->control = control;
+    const size_t nst = (size_t)run->Np * run->Rp;
+    gsb_status st = GSB_OK;
+    auto fail = [&](gsb_status e) {
+        free_run(run);
+        return e;
+    };
+    if ((st = dev_alloc(&run->x[0], nst)) || (st = dev_alloc(&run->y, nst))) return fail(st);
+    if (path != kPathTcFp8 && path != kPathTcBf16x3)
+        if ((st = dev_alloc(&run->x[1], nst))) return fail(st);
+    if (control)
+        if ((st = dev_alloc(&run->p, nst))) return fail(st);
+    if (path == kPathCsr && sign)
+        if ((st = dev_alloc(&run->s8[0], nst)) || (st = dev_alloc(&run->s8[1], nst)))
+            return fail(st);
+    if ((st = dev_alloc(&run->A, run->Rp)) || (st = dev_alloc(&run->e_acc, run->Rp)) ||
+        (st = dev_alloc(&run->best_e, run->Rp)) || (st = dev_alloc(&run->best_step, run->Rp)) ||
+        (st = dev_alloc(&run->flag, run->Rp)) || (st = dev_alloc(&run->best_s, nst)) ||
+        (st = dev_alloc(&run->status, 1)))
+        return fail(st);
+    {
+        std::vector<float> Ah(run->Rp, 0.f);
+        for (int r = 0; r < Q.R; ++r) Ah[r] = Q.A_per_replica ? Q.A_per_replica[r] : Q.A;
+        if (cudaMemcpyAsync(run->A, Ah.data(), sizeof(float) * run->Rp, cudaMemcpyHostToDevice,
+                            s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "copy A"));
+    }
+    if (Q.schedule) run->sched_host.assign(Q.schedule, Q.schedule + Q.M + 1);
+    GSB_CUDA_TRY(cudaMemsetAsync(run->status, 0, sizeof(int), s));
+    GSB_CUDA_TRY(cudaMemsetAsync(run->best_s, 0, nst, s));
+    k_fill_f64<<<(run->Rp + 255) / 256, 256, 0, s>>>(run->best_e,
+                                                     std::numeric_limits<double>::infinity(),
+                                                     run->Rp);
+    k_fill_i32<<<(run->Rp + 255) / 256, 256, 0, s>>>(run->best_step, -1, run->Rp);
+    count_launch(2);
+    // initial state
+    float *x0d = nullptr, *y0d = nullptr;
+    const size_t nrm = (size_t)Q.R * P->N;
+    if (Q.x0 || Q.y0) {
+        if (P->has_h) return fail(set_error(GSB_EINVAL, "explicit x0/y0 with h: pass N+1 columns is unsupported"));
+    }
+    if (Q.x0) {
+        if ((st = dev_alloc(&x0d, nrm))) return fail(st);
+        GSB_CUDA_TRY(cudaMemcpyAsync(x0d, Q.x0, sizeof(float) * nrm, cudaMemcpyHostToDevice, s));
+    }
+    if (Q.y0) {
+        if ((st = dev_alloc(&y0d, nrm))) return fail(st);
+        GSB_CUDA_TRY(cudaMemcpyAsync(y0d, Q.y0, sizeof(float) * nrm, cudaMemcpyHostToDevice, s));
+    }
+    st = launch_init_state(run, x0d, y0d);
+    if (x0d || y0d) {
+        cudaStreamSynchronize(s);
+        cudaFree(x0d);
+        cudaFree(y0d);
+    }
+    if (st != GSB_OK) return fail(st);
+    if (path == kPathTcFp8 || path == kPathTcBf16x3) {
+        if ((st = tc_setup(run)) != GSB_OK) return fail(st);
+    }
+    *out = run;
+    if (!(Q.flags & GSB_RUN_DEFER)) {
+        st = gsb_run_steps(run, Q.M);
+        if (st != GSB_OK) {
+            *out = nullptr;
+            gsb_run_destroy(run);
+            return st;
+        }
+    }
+    return GSB_OK;
+}
+
+gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps) {
+    if (!run) return set_error(GSB_EINVAL, "run is NULL");
+    if (nsteps < 0 || run->steps_done + nsteps > run->params.M)
+        return set_error(GSB_EINVAL, "nsteps exceeds the remaining steps of the run");
+    const int M = run->params.M;
+    if (run->path == kPathTcFp8 || run->path == kPathTcBf16x3) {
+        gsb_status st = tc_steps(run, run->steps_done, nsteps);
+        if (st == GSB_OK) run->steps_done += nsteps;
+        return st;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        const int m = run->steps_done;
+        StepScalars sc;
+        sc.m = m;
+        sc.M = M;
+        sc.c = run->c;
+        sc.dt = run->dt;
+        sc.p_next = p_shared_at(run, m + 1);
+        gsb_status st = run->path == kPathCsr ? launch_csr_step(run, sc)
+                                              : launch_dense_f32_step(run, sc);
+        if (st != GSB_OK) return st;
+        run->steps_done = m + 1;
+        if (is_eval_step(run, m + 1)) {
+            if ((st = evaluate(run, m + 1)) != GSB_OK) return st;
+        }
+    }
+    return GSB_OK;
+}
+
+
+static gsb_status check_status_word(gsb_run_state* run) {
+    int st = 0;
+    GSB_CUDA_TRY(cudaMemcpyAsync(&st, run->status, sizeof(int), cudaMemcpyDeviceToHost, run->stream));
+    GSB_CUDA_TRY(cudaStreamSynchronize(run->stream));
+    if (st & kDevTimeout) return set_error(GSB_ETIMEOUT, "a device-side wait timed out");
+    if (st & kDevBounds) return set_error(GSB_ECUDA, "a kernel detected an out-of-range index");
+    if (st & kDevNumeric) return set_error(GSB_ENUMERIC, "NaN or Inf in the state");
+    return GSB_OK;
+}
+
+gsb_status gsb_best(gsb_run_state* run, int8_t* spins, double* energies, double* cuts,
+                    int32_t* step_found) {
+    if (!run) return set_error(GSB_EINVAL, "run is NULL");
+    gsb_status st = check_status_word(run);
+    if (st != GSB_OK) return st;
+    const int R = run->R, N = run->N, Nu = run->prob->N_user;
+    std::vector<double> e(R);
+    std::vector<int32_t> stp(R);
+    GSB_CUDA_TRY(cudaMemcpyAsync(e.data(), run->best_e, sizeof(double) * R, cudaMemcpyDeviceToHost,
+                                 run->stream));
+    GSB_CUDA_TRY(cudaMemcpyAsync(stp.data(), run->best_step, sizeof(int32_t) * R,
+                                 cudaMemcpyDeviceToHost, run->stream));
+    std::vector<int8_t> s;
+    if (spins) {
+        int8_t* tmp = nullptr;
+        if ((st = dev_alloc(&tmp, (size_t)R * N))) return st;
+        st = launch_transpose_i8_to_host_layout(run->best_s, tmp, run->Np, run->Rp, N, R,
+                                                run->stream);
+        if (st == GSB_OK) {
+            s.resize((size_t)R * N);
+            if (cudaMemcpyAsync(s.data(), tmp, (size_t)R * N, cudaMemcpyDeviceToHost,
+                                run->stream) != cudaSuccess)
+                st = cuda_error(cudaGetLastError(), "copy best spins");
+        }
+        cudaStreamSynchronize(run->stream);
+        cudaFree(tmp);
+        if (st != GSB_OK) return st;
+    }
+    GSB_CUDA_TRY(cudaStreamSynchronize(run->stream));
+    for (int r = 0; r < R; ++r) {
+        if (energies) energies[r] = e[r];
+        if (cuts) cuts[r] = isfinite(e[r]) ? 0.5 * (run->prob->W_tot - e[r]) : -INFINITY;
+        if (step_found) step_found[r] = stp[r];
+        if (spins) {
+            const int8_t* src = &s[(size_t)r * N];
+            // gauge-fix the auxiliary spin of the h augmentation to +1
+            const int8_t g = (run->prob->has_h && src[Nu] < 0) ? -1 : 1;
+            for (int i = 0; i < Nu; ++i) spins[(size_t)r * Nu + i] = (int8_t)(g * src[i]);
+        }
+    }
+    return GSB_OK;
+}
+
+gsb_status gsb_get_state(gsb_run_state* run, float* x, float* y, float* p, int32_t* steps_done) {
+    if (!run) return set_error(GSB_EINVAL, "run is NULL");
+    gsb_status st = GSB_OK;
+    const int R = run->R, N = run->N;
+    if (run->path == kPathTcFp8 || run->path == kPathTcBf16x3) {
+        // the fused path keeps x, y, p in its own buffers; they are synced after every call
+    }
+    float* tmp = nullptr;
+    if ((st = dev_alloc(&tmp, (size_t)R * N))) return st;
+    struct Item {
+        const float* src;
+        float* dst;
+    } items[3] = {{run->x[run->cur], x}, {run->y, y}, {run->control ? run->p : nullptr, p}};
+    for (auto& it : items) {
+        if (!it.dst) continue;
+        if (it.src) {
+            st = launch_transpose_to_host_layout(it.src, tmp, run->Np, run->Rp, N, R, run->stream);
+            if (st != GSB_OK) break;
+            if (cudaMemcpyAsync(it.dst, tmp, sizeof(float) * R * N, cudaMemcpyDeviceToHost,
+                                run->stream) != cudaSuccess ||
+                cudaStreamSynchronize(run->stream) != cudaSuccess) {
+                st = cuda_error(cudaGetLastError(), "copy state");
+                break;
+            }
+        } else {
+            const float pv = run->steps_done == 0 ? 1.f : run_p_shared(run, run->steps_done);
+            for (size_t k = 0; k < (size_t)R * N; ++k) it.dst[k] = pv;
+        }
+    }
+    cudaFree(tmp);
+    if (st != GSB_OK) return st;
+    if (steps_done) *steps_done = run->steps_done;
+    return check_status_word(run);
+}
+
+gsb_status gsb_energy(gsb_problem* P, int32_t R, const int8_t* spins, double* energies,
+                      void* stream) {
+    if (!P || !spins || !energies || R < 1) return set_error(GSB_EINVAL, "bad argument");
+    if (P->has_h) return set_error(GSB_EUNSUPPORTED, "gsb_energy takes problems without h");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Rp = round_up(R, kTile);
+    const size_t nst = (size_t)P->Np * Rp;
+    int8_t* sd = nullptr;
+    float* xd = nullptr;
+    double* acc = nullptr;
+    gsb_status st = GSB_OK;
+    if ((st = dev_alloc(&sd, (size_t)R * P->N)) || (st = dev_alloc(&xd, nst)) ||
+        (st = dev_alloc(&acc, Rp))) {
+        cudaFree(sd);
+        cudaFree(xd);
+        cudaFree(acc);
+        return st;
+    }
+    std::vector<double> h(R);
+    do {
+        if (cudaMemcpyAsync(sd, spins, (size_t)R * P->N, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "copy spins");
+            break;
+        }
+        if ((st = launch_spins_to_state(sd, xd, P->N, R, P->Np, Rp, s)) != GSB_OK) break;
+        if (cudaMemsetAsync(acc, 0, sizeof(double) * Rp, s) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "memset");
+            break;
+        }
+        st = P->csr ? launch_csr_energy(P, xd, Rp, acc, s)
+                    : launch_dense_f32_energy(P, xd, Rp, acc, s);
+        if (st != GSB_OK) break;
+        if (cudaMemcpyAsync(h.data(), acc, sizeof(double) * R, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "copy energies");
+            break;
+        }
+        for (int r = 0; r < R; ++r) energies[r] = -0.5 * h[r];
+    } while (0);
+    cudaStreamSynchronize(s);
+    cudaFree(sd);
+    cudaFree(xd);
+    cudaFree(acc);
+    return st;
+}
+
+gsb_status gsb_run_destroy(gsb_run_state* run) {
+    if (!run) return GSB_OK;
+    cudaStreamSynchronize(run->stream);
+    free_run(run);
+    return GSB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// gsb_internal.cuh -- types and helpers shared by the libgsb translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gsb.h"
+
+namespace gsb {
+
+// Padding unit of the spin (row) dimension and of the replica dimension: one
+// tcgen05 accumulator tile is 128 spins (TMEM lanes) by 128 replicas (columns).
+constexpr int kTile = 128;
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+enum Path : int {
+    kPathDenseF32 = 0,  // FP32 CUDA-core coupling (the plain form)
+    kPathCsr = 1,       // CSR coupling
+    kPathTcFp8 = 2,     // tcgen05 e4m3, sgn x coupling
+    kPathTcBf16x3 = 3,  // tcgen05 bf16, x split in three terms
+};
+
+// Device status word bits (written by kernels, read by the host).
+enum DevStatus : int {
+    kDevOk = 0,
+    kDevTimeout = 1,
+    kDevNumeric = 2,
+    kDevBounds = 4,
+};
+
+// Per-step scalars of Eqs. 3-7 shared by every kernel of a step.
+struct StepScalars {
+    int m;        // step index; the step produces t_{m+1}
+    int M;        // total steps
+    float c;      // coupling constant
+    float dt;     // time step
+    float p_next; // shared p(t_{m+1}) for bSB / dSB (ignored with individual control)
+};
+
+}  // namespace gsb
+
+struct gsb_problem {
+    int device = 0;
+    int N = 0;       // spins, including the auxiliary spin when h was given
+    int N_user = 0;  // caller's N
+    bool has_h = false;
+    bool csr = false;
+    int Np = 0;      // N padded to kTile
+    bool integer_J = false;
+    float max_abs_J = 0.f;
+    double W_tot = 0.0;  // sum_{i<j} W_ij with W = -J (Sec. III)
+    // dense device copies, Np x Np row-major, zero padded
+    float* J32 = nullptr;
+    uint8_t* J8 = nullptr;         // e4m3, when integer and |J| <= 16
+    __nv_bfloat16* J16 = nullptr;  // bf16, when integer and |J| <= 256
+    // CSR device copy (N rows)
+    int32_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    float* val = nullptr;
+    int64_t nnz = 0;
+    // App. A setup
+    bool have_lambda = false;
+    double lambda_max = 0.0, lambda_min = 0.0;
+};
+
+struct gsb_run_state {
+    gsb_problem* prob = nullptr;
+    gsb_params params{};
+    int path = 0;
+    cudaStream_t stream = nullptr;
+    int R = 0, Rp = 0, Np = 0, N = 0;
+    int steps_done = 0;
+    float c = 0.f, dt = 0.f;
+    bool sign_coupling = false;
+    bool control = false;
+    // state, spin-major [Np][Rp]
+    float* x[2] = {nullptr, nullptr};
+    int cur = 0;
+    float* y = nullptr;
+    float* p = nullptr;       // individual parameters (GbSB / GdSB)
+    int8_t* s8[2] = {nullptr, nullptr};  // sgn x for the CSR sgn coupling
+    float* A = nullptr;       // [Rp]
+    float* sched = nullptr;   // [M+1] or null
+    // tcgen05 operands, replica-major [Rp][Np] (K-major B operand)
+    uint8_t* v8[2] = {nullptr, nullptr};
+    __nv_bfloat16* v16[2] = {nullptr, nullptr};  // three planes each: [3][Rp][Np]
+    // energy bookkeeping
+    double* e_acc = nullptr;    // [Rp] sum_i s_i (J s)_i
+    double* best_e = nullptr;   // [Rp]
+    int32_t* best_step = nullptr;
+    int8_t* best_s = nullptr;   // [Np][Rp]
+    int32_t* flag = nullptr;    // [Rp]
+    int* status = nullptr;      // device status word
+    void* tc = nullptr;         // tcgen05 path state (tensor maps, barriers)
+    std::vector<float> sched_host;  // caller schedule p(t_m), m = 0..M (bSB / dSB)
+};
+
+namespace gsb {
+
+// Error reporting (thread-local message, set by the API layer).
+gsb_status set_error(gsb_status st, const std::string& msg);
+gsb_status cuda_error(cudaError_t err, const char* what);
+void count_launch(int n = 1);
+
+#define GSB_CUDA_TRY(call)                                     \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return ::gsb::cuda_error(e_, #call); \
+    } while (0)
+
+#define GSB_LAUNCH_CHECK(what)                                 \
+    do {                                                       \
+        ::gsb::count_launch();                                 \
+        cudaError_t e_ = cudaGetLastError();                   \
+        if (e_ != cudaSuccess) return ::gsb::cuda_error(e_, what); \
+    } while (0)
+
+// ---- kernels' host-side launchers (defined in the .cu files) ----
+// init / util
+gsb_status launch_init_state(gsb_run_state* run, const float* x0_dev_rm, const float* y0_dev_rm);
+gsb_status launch_sign_extract(gsb_run_state* run);
+gsb_status launch_transpose_to_host_layout(const float* src_sm, float* dst_rm, int Np, int Rp,
+                                           int N, int R, cudaStream_t s);
+gsb_status launch_transpose_i8_to_host_layout(const int8_t* src_sm, int8_t* dst_rm, int Np,
+                                              int Rp, int N, int R, cudaStream_t s);
+gsb_status launch_spins_to_state(const int8_t* spins_rm, float* x_sm, int N, int R, int Np,
+                                 int Rp, cudaStream_t s);
+// dense FP32 path
+gsb_status launch_dense_f32_step(gsb_run_state* run, const StepScalars& sc);
+gsb_status launch_dense_f32_energy(const gsb_problem* prob, const float* x_sm, int Rp,
+                                   double* e_acc, cudaStream_t s);
+// CSR path
+gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc);
+gsb_status launch_csr_energy(const gsb_problem* prob, const float* x_sm, int Rp, double* e_acc,
+                             cudaStream_t s);
+// best keeping
+gsb_status launch_best_keep(gsb_run_state* run, int step);
+// power iteration (App. A)
+gsb_status compute_lambda(gsb_problem* prob, cudaStream_t s);
+// tcgen05 path
+bool tc_available();
+gsb_status tc_setup(gsb_run_state* run);
+gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps);
+gsb_status tc_energy(gsb_run_state* run);
+void tc_free(gsb_run_state* run);
+// host loop helpers shared with the tcgen05 path
+bool run_is_eval_step(const gsb_run_state* run, int step);
+float run_p_shared(const gsb_run_state* run, int step);
+gsb_status run_evaluate(gsb_run_state* run, int step);
+
+}  // namespace gsb

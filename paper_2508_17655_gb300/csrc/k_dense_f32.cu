@@ -1,0 +1,188 @@
+// k_dense_f32.cu -- the plain FP32 form of one dense time step: the many-body
+// term f = J v (v = x or sgn x) as a CUDA-core SGEMM over all replicas at once,
+// with Eqs. 3-7 fused into its epilogue; and the Ising energy (Eq. 1) of sgn x
+// by the same SGEMM with a reducing epilogue.
+//
+// Layouts: J row-major [Np][Np] (zero padded), state spin-major [Np][Rp].
+// One CTA computes a 128-spin x 128-replica tile; 256 threads, 8 x 8
+// accumulators each (rows {4ty..4ty+3, 64+4ty..}, columns {4tx.., 64+4tx..}).
+#include "gsb_update.cuh"
+
+namespace gsb {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 8;
+
+struct F32Smem {
+    float A[2][BK][BM + 4];  // J tile, transposed (k-major)
+    float B[2][BK][BN];      // v tile
+};
+
+template <bool SIGN>
+__device__ __forceinline__ float4 vload(const float* p) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    if (SIGN) {
+        v.x = sgnf(v.x);
+        v.y = sgnf(v.y);
+        v.z = sgnf(v.z);
+        v.w = sgnf(v.w);
+    }
+    return v;
+}
+
+// acc[a][b] += sum_k J[row_a][k] v[k][col_b] over the full K = Np.
+template <bool SIGN>
+__device__ __forceinline__ void sgemm_tile(const float* __restrict__ J,
+                                           const float* __restrict__ X, int Np, int Rp, int i0,
+                                           int r0, float (&acc)[8][8], F32Smem& sm) {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int a_row = tid >> 1, a_k = (tid & 1) * 4;
+    const int b_k = tid >> 5, b_c = (tid & 31) * 4;
+    const float* Ap = J + (size_t)(i0 + a_row) * Np + a_k;
+    const float* Bp = X + (size_t)b_k * Rp + r0 + b_c;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+
+    float4 ra = *reinterpret_cast<const float4*>(Ap);
+    float4 rb = vload<SIGN>(Bp);
+    auto stash = [&](int buf) {
+        sm.A[buf][a_k + 0][a_row] = ra.x;
+        sm.A[buf][a_k + 1][a_row] = ra.y;
+        sm.A[buf][a_k + 2][a_row] = ra.z;
+        sm.A[buf][a_k + 3][a_row] = ra.w;
+        *reinterpret_cast<float4*>(&sm.B[buf][b_k][b_c]) = rb;
+    };
+    stash(0);
+    __syncthreads();
+    const int nk = Np / BK;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < nk) {
+            ra = *reinterpret_cast<const float4*>(Ap + (size_t)(kt + 1) * BK);
+            rb = vload<SIGN>(Bp + (size_t)(kt + 1) * BK * Rp);
+        }
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[buf][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[buf][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&sm.B[buf][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&sm.B[buf][k][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        if (kt + 1 < nk) stash(buf ^ 1);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int row_of(int a, int ty) { return a < 4 ? ty * 4 + a : 64 + ty * 4 + (a - 4); }
+
+template <bool SIGN, bool CONTROL>
+__global__ void __launch_bounds__(256) k_dense_f32_step(
+    const float* __restrict__ J, int Np, int Rp, const float* __restrict__ xc,
+    float* __restrict__ xn, float* __restrict__ y, float* __restrict__ p,
+    const float* __restrict__ A, float c, float dt, float p_shared, float inv_rem) {
+    __shared__ __align__(16) F32Smem sm;
+    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
+    float acc[8][8];
+    sgemm_tile<SIGN>(J, xc, Np, Rp, i0, r0, acc, sm);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int cols[2] = {r0 + tx * 4, r0 + 64 + tx * 4};
+    float av[8];
+    if (CONTROL) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 t = *reinterpret_cast<const float4*>(A + cols[h]);
+            av[h * 4 + 0] = t.x; av[h * 4 + 1] = t.y; av[h * 4 + 2] = t.z; av[h * 4 + 3] = t.w;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const size_t rowoff = (size_t)(i0 + row_of(a, ty)) * Rp;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const size_t o = rowoff + cols[h];
+            float4 x4 = *reinterpret_cast<const float4*>(xc + o);
+            float4 y4 = *reinterpret_cast<float4*>(y + o);
+            float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (CONTROL) p4 = *reinterpret_cast<float4*>(p + o);
+            float* xs = &x4.x; float* ys = &y4.x; float* ps = &p4.x;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                sb_update<CONTROL>(xs[q], ys[q], ps[q], acc[a][h * 4 + q],
+                                   CONTROL ? av[h * 4 + q] : 0.f, c, dt, p_shared, inv_rem);
+            *reinterpret_cast<float4*>(xn + o) = x4;
+            *reinterpret_cast<float4*>(y + o) = y4;
+            if (CONTROL) *reinterpret_cast<float4*>(p + o) = p4;
+        }
+    }
+}
+
+// e_acc[r] += sum_i s_i (J s)_i over this tile's 128 spins (s = sgn x).
+__global__ void __launch_bounds__(256) k_dense_f32_energy(const float* __restrict__ J, int Np,
+                                                          int Rp, const float* __restrict__ x,
+                                                          double* __restrict__ e_acc) {
+    __shared__ __align__(16) F32Smem sm;
+    __shared__ float red[16][BN + 1];
+    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
+    float acc[8][8];
+    sgemm_tile<true>(J, x, Np, Rp, i0, r0, acc, sm);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int col = b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4);
+        float part = 0.f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const float si = sgnf(x[(size_t)(i0 + row_of(a, ty)) * Rp + r0 + col]);
+            part = fmaf(si, acc[a][b], part);
+        }
+        red[ty][col] = part;
+    }
+    __syncthreads();
+    if (threadIdx.x < BN) {
+        double s = 0.0;
+        for (int t = 0; t < 16; ++t) s += (double)red[t][threadIdx.x];
+        atomicAdd(&e_acc[r0 + threadIdx.x], s);
+    }
+}
+
+}  // namespace
+
+gsb_status launch_dense_f32_step(gsb_run_state* run, const StepScalars& sc) {
+    const gsb_problem* P = run->prob;
+    dim3 grid(run->Rp / BN, run->Np / BM);
+    const float* xc = run->x[run->cur];
+    float* xn = run->x[run->cur ^ 1];
+    const float inv_rem = 1.0f / (float)(sc.M - sc.m);
+#define GSB_F32_LAUNCH(S, C)                                                                  \
+    k_dense_f32_step<S, C><<<grid, 256, 0, run->stream>>>(P->J32, run->Np, run->Rp, xc, xn,   \
+                                                          run->y, run->p, run->A, sc.c, sc.dt, \
+                                                          sc.p_next, inv_rem)
+    if (run->sign_coupling) {
+        if (run->control) GSB_F32_LAUNCH(true, true); else GSB_F32_LAUNCH(true, false);
+    } else {
+        if (run->control) GSB_F32_LAUNCH(false, true); else GSB_F32_LAUNCH(false, false);
+    }
+#undef GSB_F32_LAUNCH
+    GSB_LAUNCH_CHECK("k_dense_f32_step");
+    run->cur ^= 1;
+    return GSB_OK;
+}
+
+gsb_status launch_dense_f32_energy(const gsb_problem* P, const float* x, int Rp, double* e_acc,
+                                   cudaStream_t s) {
+    dim3 grid(Rp / BN, P->Np / BM);
+    k_dense_f32_energy<<<grid, 256, 0, s>>>(P->J32, P->Np, Rp, x, e_acc);
+    GSB_LAUNCH_CHECK("k_dense_f32_energy");
+    return GSB_OK;
+}
+
+}  // namespace gsb

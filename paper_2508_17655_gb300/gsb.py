@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libgsb (include/gsb.h). Argument marshalling only:
+every step of the method runs in the library's CUDA kernels.
+
+The library must exist (``paper_2508_17655_gb300.build.build()``); importing
+this module without it raises, there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# enums / flags of include/gsb.h
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENUMERIC, ENODEV = range(8)
+BSB, GBSB, DSB, GDSB = range(4)
+PREC_AUTO, PREC_FP32, PREC_FP8, PREC_BF16X3 = range(4)
+J_DENSE_I8, J_DENSE_F32, J_CSR_F32 = range(3)
+CREATE_DEVICE_INPUT, CREATE_NO_VALIDATE = 0x1, 0x2
+RUN_DEFER = 0x1
+
+VARIANT = {"bsb": BSB, "gbsb": GBSB, "dsb": DSB, "gdsb": GDSB}
+PRECISION = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp8": PREC_FP8, "bf16x3": PREC_BF16X3}
+
+
+class gsb_params(ctypes.Structure):
+    _fields_ = [
+        ("variant", ctypes.c_int32),
+        ("M", ctypes.c_int32),
+        ("R", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("c", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("A", ctypes.c_float),
+        ("A_per_replica", ctypes.POINTER(ctypes.c_float)),
+        ("schedule", ctypes.POINTER(ctypes.c_float)),
+        ("seed", ctypes.c_uint64),
+        ("x0_range", ctypes.c_float),
+        ("y0_uniform", ctypes.c_int32),
+        ("eval_every", ctypes.c_int32),
+        ("steps_per_launch", ctypes.c_int32),
+        ("x0", ctypes.POINTER(ctypes.c_float)),
+        ("y0", ctypes.POINTER(ctypes.c_float)),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class GsbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libgsb status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgsb.so is not built ({path}); run "
+                               "paper_2508_17655_gb300.build.build() first")
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _LIB = L
+    return _LIB
+
+
+def _declare(L):
+    st = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.gsb_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int32, _vp,
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), fp,
+                             ctypes.c_int64, fp, ctypes.c_uint32, _vp]
+    L.gsb_create.restype = st
+    L.gsb_destroy.argtypes = [_vp]
+    L.gsb_destroy.restype = st
+    L.gsb_problem_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), _vp]
+    L.gsb_problem_info.restype = st
+    L.gsb_run.argtypes = [_vp, ctypes.POINTER(gsb_params), ctypes.POINTER(_vp), _vp]
+    L.gsb_run.restype = st
+    L.gsb_run_steps.argtypes = [_vp, ctypes.c_int32]
+    L.gsb_run_steps.restype = st
+    L.gsb_best.argtypes = [_vp, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
+    L.gsb_best.restype = st
+    L.gsb_get_state.argtypes = [_vp, fp, fp, fp, ctypes.POINTER(ctypes.c_int32)]
+    L.gsb_get_state.restype = st
+    L.gsb_energy.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int8),
+                             ctypes.POINTER(ctypes.c_double), _vp]
+    L.gsb_energy.restype = st
+    L.gsb_run_destroy.argtypes = [_vp]
+    L.gsb_run_destroy.restype = st
+    L.gsb_last_error.argtypes = []
+    L.gsb_last_error.restype = ctypes.c_char_p
+    L.gsb_version.restype = ctypes.c_int32
+    L.gsb_launch_count.restype = ctypes.c_int64
+
+
+def _check(status):
+    if status != OK:
+        raise GsbError(status, lib().gsb_last_error().decode())
+
+
+def _p(a, ctype):
+    if a is None:
+        return ctypes.cast(None, ctypes.POINTER(ctype))
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def launch_count():
+    return int(lib().gsb_launch_count())
+
+
+class Problem:
+    """Device-resident coupling matrix (Eq. 1), dense or CSR."""
+
+    def __init__(self, handle, N):
+        self.handle = handle
+        self.N = N
+
+    @classmethod
+    def dense(cls, J, h=None, stream=None, validate=True):
+        J = np.asarray(J)
+        N = J.shape[0]
+        if J.dtype == np.int8:
+            fmt, Jc = J_DENSE_I8, np.ascontiguousarray(J)
+        else:
+            fmt, Jc = J_DENSE_F32, np.ascontiguousarray(J, dtype=np.float32)
+        hc = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
+        out = _vp()
+        _check(lib().gsb_create(ctypes.byref(out), N, fmt, Jc.ctypes.data_as(_vp), None, None,
+                                None, 0, _p(hc, ctypes.c_float),
+                                0 if validate else CREATE_NO_VALIDATE, _stream_handle(stream)))
+        return cls(out, N)
+
+    @classmethod
+    def csr(cls, N, rowptr, col, val, h=None, stream=None, validate=True):
+        rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col, dtype=np.int32)
+        vv = np.ascontiguousarray(val, dtype=np.float32)
+        hc = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
+        out = _vp()
+        _check(lib().gsb_create(ctypes.byref(out), N, J_CSR_F32, None, _p(rp, ctypes.c_int32),
+                                _p(ci, ctypes.c_int32), _p(vv, ctypes.c_float), len(ci),
+                                _p(hc, ctypes.c_float), 0 if validate else CREATE_NO_VALIDATE,
+                                _stream_handle(stream)))
+        return cls(out, N)
+
+    def info(self, stream=None):
+        n = ctypes.c_int32()
+        lmax = ctypes.c_double()
+        lmin = ctypes.c_double()
+        _check(lib().gsb_problem_info(self.handle, ctypes.byref(n), ctypes.byref(lmax),
+                                      ctypes.byref(lmin), _stream_handle(stream)))
+        return n.value, lmax.value, lmin.value
+
+    def energy(self, spins, stream=None):
+        s = np.ascontiguousarray(spins, dtype=np.int8)
+        if s.ndim == 1:
+            s = s[None]
+        out = np.zeros(s.shape[0], dtype=np.float64)
+        _check(lib().gsb_energy(self.handle, s.shape[0], _p(s, ctypes.c_int8),
+                                _p(out, ctypes.c_double), _stream_handle(stream)))
+        return out
+
+    def run(self, variant, M, R, *, c=0.0, dt=0.0, A=0.0, seed=0, precision="auto",
+            eval_every=0, x0=None, y0=None, y0_uniform=False, x0_range=0.0, schedule=None,
+            steps_per_launch=0, defer=False, stream=None):
+        return Run(self, variant, M, R, c=c, dt=dt, A=A, seed=seed, precision=precision,
+                   eval_every=eval_every, x0=x0, y0=y0, y0_uniform=y0_uniform,
+                   x0_range=x0_range, schedule=schedule, steps_per_launch=steps_per_launch,
+                   defer=defer, stream=stream)
+
+    def close(self):
+        if self.handle:
+            lib().gsb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Run:
+    """One GbSB / bSB / dSB run of R replicas over M steps (Sec. II)."""
+
+    def __init__(self, problem, variant, M, R, *, c, dt, A, seed, precision, eval_every, x0, y0,
+                 y0_uniform, x0_range, schedule, steps_per_launch, defer, stream):
+        self.problem = problem
+        self.R = int(R)
+        self.N = problem.N
+        prm = gsb_params()
+        prm.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+        prm.M = int(M)
+        prm.R = int(R)
+        prm.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        prm.c = float(c)
+        prm.dt = float(dt)
+        keep = []
+        A_arr = np.asarray(A, dtype=np.float32)
+        if A_arr.ndim == 0:
+            prm.A = float(A_arr)
+        else:
+            a = np.ascontiguousarray(A_arr)
+            keep.append(a)
+            prm.A_per_replica = _p(a, ctypes.c_float)
+        if schedule is not None:
+            s = np.ascontiguousarray(schedule, dtype=np.float32)
+            keep.append(s)
+            prm.schedule = _p(s, ctypes.c_float)
+        prm.seed = int(seed)
+        prm.x0_range = float(x0_range)
+        prm.y0_uniform = int(bool(y0_uniform))
+        prm.eval_every = int(eval_every)
+        prm.steps_per_launch = int(steps_per_launch)
+        if x0 is not None:
+            xa = np.ascontiguousarray(x0, dtype=np.float32)
+            keep.append(xa)
+            prm.x0 = _p(xa, ctypes.c_float)
+        if y0 is not None:
+            ya = np.ascontiguousarray(y0, dtype=np.float32)
+            keep.append(ya)
+            prm.y0 = _p(ya, ctypes.c_float)
+        prm.flags = RUN_DEFER if defer else 0
+        out = _vp()
+        _check(lib().gsb_run(problem.handle, ctypes.byref(prm), ctypes.byref(out),
+                             _stream_handle(stream)))
+        self.handle = out
+
+    def steps(self, n):
+        _check(lib().gsb_run_steps(self.handle, int(n)))
+
+    def best(self):
+        spins = np.zeros((self.R, self.N), dtype=np.int8)
+        e = np.zeros(self.R, dtype=np.float64)
+        cut = np.zeros(self.R, dtype=np.float64)
+        step = np.zeros(self.R, dtype=np.int32)
+        _check(lib().gsb_best(self.handle, _p(spins, ctypes.c_int8), _p(e, ctypes.c_double),
+                              _p(cut, ctypes.c_double), _p(step, ctypes.c_int32)))
+        return {"s": spins, "E": e, "cut": cut, "step": step}
+
+    def state(self):
+        """Current x, y, p (R x n_spins, host) and the steps done so far."""
+        x = np.zeros((self.R, self._n_state()), dtype=np.float32)
+        y = np.zeros_like(x)
+        p = np.zeros_like(x)
+        done = ctypes.c_int32()
+        _check(lib().gsb_get_state(self.handle, _p(x, ctypes.c_float), _p(y, ctypes.c_float),
+                                   _p(p, ctypes.c_float), ctypes.byref(done)))
+        return {"x": x, "y": y, "p": p, "steps": done.value}
+
+    def _n_state(self):
+        n = ctypes.c_int32()
+        _check(lib().gsb_problem_info(self.problem.handle, ctypes.byref(n), None, None, None))
+        return n.value
+
+    def close(self):
+        if self.handle:
+            lib().gsb_run_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

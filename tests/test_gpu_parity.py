@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Integer work (energies, cuts, J s for integer J, best-state bookkeeping) is
+compared bit-exactly; FP32 trajectories over the first 50 steps to
+max|gpu - oracle| <= 1e-5 max|oracle| (x, y and p each)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2508_17655_gb300 import gsb, inputs as I
+from tests._parity import RTOL_TRAJ, assert_traj_close, spins
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["bsb", "gbsb", "dsb", "gdsb"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2508_17655_gb300 import build
+    build.build()
+
+
+def _oracle_traj(J, variant, x0, y0, *, c, dt, M, A, nsteps, sched=None):
+    return O.run(J, variant, x0, y0, c=c, dt=dt, M=M, A=A, nsteps=nsteps, sched=sched)
+
+
+# ------------------------------------------------------------------ init (App. A)
+
+@pytest.mark.parametrize("R,N", [(1, 1), (3, 130), (200, 300)])
+def test_initial_state_matches_philox_draw(R, N):
+    J = I.sk_pm1(N, 5) if N > 1 else np.zeros((1, 1), np.int8)
+    P = gsb.Problem.dense(J)
+    run = P.run("gbsb", M=10, R=R, c=0.1, dt=0.5, seed=1234567890123, defer=True,
+                precision="fp32", y0_uniform=True)
+    st = run.state()
+    np.testing.assert_array_equal(st["x"], O.init_uniform(R, N, 1234567890123).astype(np.float32))
+    np.testing.assert_array_equal(st["y"], O.init_uniform(R, N, 1234567890123, stream=1).astype(np.float32))
+    np.testing.assert_array_equal(st["p"], np.ones((R, N), np.float32))
+
+
+# ------------------------------------------------------------------ energy (Eq. 1)
+
+@pytest.mark.parametrize("N,R", [(1, 1), (7, 3), (300, 129), (1000, 64)])
+def test_energy_bit_exact_dense(N, R):
+    J = I.sk_pm1(N, 11) if N > 1 else np.zeros((1, 1), np.int8)
+    S = (np.random.default_rng(N).integers(0, 2, size=(R, N)) * 2 - 1).astype(np.int8)
+    P = gsb.Problem.dense(J)
+    e = P.energy(S)
+    np.testing.assert_array_equal(e, O.energy(J.astype(np.float64), S))
+
+
+def test_energy_bit_exact_csr():
+    N, R = 2000, 130
+    rp, col, val = I.er_graph(N, 20, "pm1", 3)
+    S = (np.random.default_rng(1).integers(0, 2, size=(R, N)) * 2 - 1).astype(np.int8)
+    P = gsb.Problem.csr(N, rp, col, val)
+    np.testing.assert_array_equal(P.energy(S), O.energy(O.Coupling(N, rowptr=rp, col=col, val=val), S))
+
+
+# ------------------------------------------------------------------ trajectories
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("N,R", [(300, 200), (130, 1)])
+def test_dense_f32_trajectory_50_steps(variant, N, R):
+    J = I.sk_pm1(N, 21)
+    c, dt, M, A = 1 / (2 * math.sqrt(N)), 1.25, 400, 0.25
+    P = gsb.Problem.dense(J)
+    run = P.run(variant, M=M, R=R, c=c, dt=dt, A=A, seed=9, precision="fp32", defer=True)
+    run.steps(50)
+    st = run.state()
+    x0 = O.init_uniform(R, N, 9)
+    ref = _oracle_traj(J.astype(np.float64), variant, x0, 0 * x0, c=c, dt=dt, M=M, A=A, nsteps=50)
+    assert_traj_close(st["x"], ref["x"], what="x")
+    assert_traj_close(st["y"], ref["y"], what="y")
+    assert_traj_close(st["p"], ref["p"], what="p")
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("weights", ["+1", "pm1"])
+def test_csr_trajectory_50_steps(variant, weights):
+    N, R = 1000, 130
+    rp, col, val = I.er_graph(N, 20, weights, 5)
+    C = O.Coupling(N, rowptr=rp, col=col, val=val)
+    lmax, lmin = O.lambda_extremes(C)
+    c, dt, M, A = 1 / lmax, O.dt_from_lambda(lmax, lmin), 500, 0.2
+    P = gsb.Problem.csr(N, rp, col, val)
+    run = P.run(variant, M=M, R=R, c=c, dt=dt, A=A, seed=3, defer=True)
+    run.steps(50)
+    st = run.state()
+    x0 = O.init_uniform(R, N, 3)
+    ref = _oracle_traj(C, variant, x0, 0 * x0, c=c, dt=dt, M=M, A=A, nsteps=50)
+    assert_traj_close(st["x"], ref["x"], what="x")
+    assert_traj_close(st["y"], ref["y"], what="y")
+    assert_traj_close(st["p"], ref["p"], what="p")
+
+
+def test_gaussian_couplings_and_schedule():
+    """Real-valued J (SK N(0, 1/N)), explicit x0/y0, caller schedule."""
+    N, R, M = 257, 33, 60
+    J = I.sk_gauss(N, 4)
+    rng = np.random.default_rng(2)
+    x0 = rng.uniform(-0.1, 0.1, size=(R, N)).astype(np.float32)
+    y0 = rng.uniform(-0.1, 0.1, size=(R, N)).astype(np.float32)
+    sched = np.linspace(1.0, 0.0, M + 1) ** 2
+    P = gsb.Problem.dense(J)
+    for variant in ("bsb", "dsb"):
+        run = P.run(variant, M=M, R=R, c=0.5, dt=0.9, x0=x0, y0=y0, schedule=sched,
+                    precision="fp32", defer=True)
+        run.steps(50)
+        st = run.state()
+        ref = O.run(J.astype(np.float64), variant, x0.astype(np.float64), y0.astype(np.float64),
+                    c=0.5, dt=0.9, M=M, sched=sched.astype(np.float32).astype(np.float64), nsteps=50)
+        assert_traj_close(st["x"], ref["x"], what=variant + " x")
+
+
+def test_per_replica_control_strength():
+    N, R, M = 200, 16, 300
+    J = I.sk_pm1(N, 31)
+    A = np.linspace(0.0, 0.45, R).astype(np.float32)
+    c = 1 / (2 * math.sqrt(N))
+    run = gsb.Problem.dense(J).run("gbsb", M=M, R=R, c=c, dt=1.25, A=A, seed=4, precision="fp32",
+                                   defer=True)
+    run.steps(50)
+    x0 = O.init_uniform(R, N, 4)
+    ref = O.run(J.astype(np.float64), "gbsb", x0, 0 * x0, c=c, dt=1.25, M=M, A=A.astype(np.float64),
+                nsteps=50)
+    assert_traj_close(run.state()["p"], ref["p"], what="p")
+
+
+# ------------------------------------------------------------------ bookkeeping
+
+@pytest.mark.parametrize("path", ["fp32", "csr"])
+def test_best_state_bookkeeping_is_exact(path):
+    """Energies reported are the exact energies of the reported spins; cuts
+    follow cut = (W_tot - E)/2; the step found is an evaluation step."""
+    N, R, M = 400, 70, 200
+    if path == "csr":
+        rp, col, val = I.er_graph(N, 12, "pm1", 8)
+        P = gsb.Problem.csr(N, rp, col, val)
+        Jo = O.Coupling(N, rowptr=rp, col=col, val=val)
+        run = P.run("gdsb", M=M, R=R, c=0.2, dt=0.8, A=0.2, seed=2, eval_every=7)
+    else:
+        J = I.sk_pm1(N, 8)
+        P = gsb.Problem.dense(J)
+        Jo = J.astype(np.float64)
+        run = P.run("gbsb", M=M, R=R, c=1 / (2 * math.sqrt(N)), dt=1.25, A=0.2, seed=2,
+                    eval_every=7, precision="fp32")
+    b = run.best()
+    np.testing.assert_array_equal(b["E"], O.energy(Jo, b["s"]))
+    np.testing.assert_array_equal(b["cut"], (O.total_weight(Jo) - b["E"]) / 2)
+    assert np.all((b["step"] % 7 == 0) | (b["step"] == M))
+
+
+def test_short_run_best_matches_oracle_where_spins_agree():
+    N, R, M = 300, 96, 40
+    J = I.sk_pm1(N, 12)
+    c = 1 / (2 * math.sqrt(N))
+    run = gsb.Problem.dense(J).run("gdsb", M=M, R=R, c=c, dt=1.25, A=0.3, seed=5, eval_every=1,
+                                   precision="fp32")
+    b = run.best()
+    x0 = O.init_uniform(R, N, 5)
+    ref = O.run(J.astype(np.float64), "gdsb", x0, 0 * x0, c=c, dt=1.25, M=M, A=0.3, eval_every=1)
+    same = np.all(b["s"] == ref["best"]["s"], axis=1)
+    assert same.mean() > 0.9
+    np.testing.assert_array_equal(b["E"][same], ref["best"]["E"][same])
+    np.testing.assert_array_equal(b["step"][same], ref["best"]["step"][same])
+
+
+def test_resume_in_chunks_is_bit_identical():
+    N, R, M = 256, 128, 90
+    J = I.sk_pm1(N, 13)
+    P = gsb.Problem.dense(J)
+    kw = dict(M=M, R=R, c=0.05, dt=1.0, A=0.3, seed=6, eval_every=10, precision="fp32")
+    one = P.run("gbsb", **kw)
+    two = P.run("gbsb", defer=True, **kw)
+    for n in (1, 29, 30, 30):
+        two.steps(n)
+    a, b = one.state(), two.state()
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["y"], b["y"])
+    assert np.array_equal(one.best()["E"], two.best()["E"])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_sign_symmetry_on_gpu(variant):
+    N, R, M = 200, 64, 300
+    J = I.sk_pm1(N, 14)
+    x0 = O.init_uniform(R, N, 7).astype(np.float32)
+    P = gsb.Problem.dense(J)
+    kw = dict(M=M, R=R, c=1 / (2 * math.sqrt(N)), dt=1.25, A=0.25, precision="fp32")
+    a = P.run(variant, x0=x0, **kw).state()
+    b = P.run(variant, x0=-x0, **kw).state()
+    assert np.array_equal(a["x"], -b["x"]) and np.array_equal(a["y"], -b["y"])
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_degenerate_sizes():
+    # N = 1 (no coupling), R = 1, M = 1
+    P = gsb.Problem.dense(np.zeros((1, 1), np.float32))
+    run = P.run("gbsb", M=1, R=1, c=1.0, dt=0.5, seed=1, precision="fp32")
+    b = run.best()
+    assert b["E"][0] == 0.0 and b["step"][0] == 1
+    # N = 2 ferromagnet: both spins aligned at the end
+    P = gsb.Problem.dense(np.array([[0, 1], [1, 0]], np.float32))
+    b = P.run("gbsb", M=200, R=5, c=1.0, dt=0.5, A=0.0, seed=1, precision="fp32").best()
+    assert np.all(b["E"] == -1.0)
+
+
+def test_local_field_augmentation():
+    """h folded in as an auxiliary spin: reported energies equal
+    -1/2 s^T J s - h^T s of the reported spins (s_aux gauge-fixed to +1)."""
+    N, R = 50, 40
+    J = I.sk_pm1(N, 15).astype(np.float32)
+    h = np.random.default_rng(3).integers(-2, 3, size=N).astype(np.float32)
+    P = gsb.Problem.dense(J, h=h)
+    assert P.info()[0] == N + 1
+    b = P.run("gbsb", M=300, R=R, c=1 / (2 * math.sqrt(N)), dt=1.0, A=0.2, seed=3,
+              precision="fp32").best()
+    s = b["s"].astype(np.float64)
+    want = -0.5 * np.einsum("ri,ij,rj->r", s, J.astype(np.float64), s) - s @ h.astype(np.float64)
+    np.testing.assert_array_equal(b["E"], want)
+
+
+def test_invalid_inputs_are_rejected():
+    with pytest.raises(gsb.GsbError) as e:
+        gsb.Problem.dense(np.array([[0, 1], [2, 0]], np.float32))
+    assert e.value.status == gsb.EINVAL
+    with pytest.raises(gsb.GsbError) as e:
+        gsb.Problem.dense(np.array([[1, 1], [1, 0]], np.float32))
+    assert e.value.status == gsb.EINVAL
+    P = gsb.Problem.dense(I.sk_gauss(8, 1))
+    with pytest.raises(gsb.GsbError) as e:
+        P.run("dsb", M=10, R=4, c=1, dt=1, precision="fp8")
+    assert e.value.status == gsb.EUNSUPPORTED
+    with pytest.raises(gsb.GsbError) as e:
+        P.run("gbsb", M=0, R=4, c=1, dt=1)
+    assert e.value.status == gsb.EINVAL
+
+
+def test_lambda_and_auto_parameters_match_oracle():
+    N = 500
+    rp, col, val = I.er_graph(N, 10, "+1", 6)
+    C = O.Coupling(N, rowptr=rp, col=col, val=val)
+    lmax, lmin = O.lambda_extremes(C)
+    n, gl, gm = gsb.Problem.csr(N, rp, col, val).info()
+    assert n == N
+    assert abs(gl - lmax) <= 1e-6 * abs(lmax) and abs(gm - lmin) <= 1e-6 * abs(lmin)
