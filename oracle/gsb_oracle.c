@@ -220,12 +220,17 @@ double orc_bruteforce(int32_t N, const double* J, int8_t* s_best) {
  * array receives the shared value. Each evaluation step writes sgn(x) energy
  * (Eq. 1) and keeps the strictly best one per replica in best_E, best_s,
  * best_step (best_E must be initialised by the caller, e.g. to +inf).
+ * margin (nullable, length R) receives, per replica, the smallest distance of
+ * any floating-point decision from its threshold over this segment: | |x| - 1 |
+ * before the wall test of Eq. 5, and |x| where sgn x enters the coupling. It
+ * only observes the iteration; a decision closer than rounding error to its
+ * threshold may go either way in another precision.
  * Returns 0, or -1 on bad arguments. */
 int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
             const double* val, int32_t coupling, int32_t control, const double* A,
             const double* sched, double c, double dt, int32_t M, int32_t m0, int32_t nsteps,
             int32_t R, double* x, double* y, double* p, int32_t eval_every, double* best_E,
-            int8_t* best_s, int32_t* best_step, int32_t nthreads) {
+            int8_t* best_s, int32_t* best_step, int32_t nthreads, double* margin) {
     if (N <= 0 || R <= 0 || M <= 0 || m0 < 0 || nsteps < 0 || m0 + nsteps > M) return -1;
     if (!J && !(rowptr && col && val)) return -1;
     if (control == 1 && !A) return -1;
@@ -242,6 +247,7 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
         double* v = (double*)malloc(sizeof(double) * (size_t)N);
         double* f = (double*)malloc(sizeof(double) * (size_t)N);
         int8_t* s = (int8_t*)malloc((size_t)N);
+        double mrg = INFINITY;
         for (int32_t m = m0; m < m0 + nsteps; ++m) {
             /* FP: bifurcation parameter(s) at t_{m+1}, from x(t_m) */
             if (control == 1) {
@@ -253,7 +259,10 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
                 for (int32_t i = 0; i < N; ++i) pr[i] = pnext;
             }
             /* JX: many-body term of x(t_m) or of its signs */
-            for (int32_t j = 0; j < N; ++j) v[j] = coupling ? orc_sgn(xr[j]) : xr[j];
+            for (int32_t j = 0; j < N; ++j) {
+                v[j] = coupling ? orc_sgn(xr[j]) : xr[j];
+                if (coupling && fabs(xr[j]) < mrg) mrg = fabs(xr[j]);
+            }
             orc_coupling(N, J, rowptr, col, val, v, f);
             /* Eq. 3: momentum, with p(t_{m+1}) and x(t_m) */
             for (int32_t i = 0; i < N; ++i) yr[i] = yr[i] - (pr[i] * xr[i] - c * f[i]) * dt;
@@ -261,6 +270,8 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
             for (int32_t i = 0; i < N; ++i) xr[i] = xr[i] + yr[i] * dt;
             /* Eq. 5: perfectly inelastic walls at |x| = 1 */
             for (int32_t i = 0; i < N; ++i) {
+                /* a wall test is a near-tie unless x was not moved (y == 0) */
+                if (yr[i] != 0.0 && fabs(fabs(xr[i]) - 1.0) < mrg) mrg = fabs(fabs(xr[i]) - 1.0);
                 if (fabs(xr[i]) > 1.0) {
                     xr[i] = orc_sgn(xr[i]);
                     yr[i] = 0.0;
@@ -279,6 +290,7 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
                 }
             }
         }
+        if (margin) margin[r] = mrg;
         free(v);
         free(f);
         free(s);

@@ -1,11 +1,378 @@
-// k_dense_tc.cu -- tcgen05 (5th-generation tensor core) path: placeholder
-// until the fused kernel lands.
-#include "gsb_internal.cuh"
+// k_dense_tc.cu -- dense time step on the sm_103a tensor cores.
+//
+// One CTA owns a tile of 128 spins (rows of J, TMEM lanes) x 128 replicas
+// (TMEM columns). The many-body term F = J V over the full K = Np is a chain
+// of tcgen05.mma into one FP32 TMEM accumulator, fed by a TMA ring of
+// 128-byte-swizzled K slices of J and V. The epilogue warps read F back with
+// tcgen05.ld and apply Eqs. 7, 3, 4, 5 to their spin (one TMEM lane per
+// thread), then write the next step's V operand.
+//
+//   KIND 0 (GSB_PREC_FP8):    J and V = sgn x in e4m3, kind::f8f6f4. Exact:
+//                             products are +-J_ij, partial sums are integers
+//                             far below 2^24 (|J| <= 16, N < 2^20).
+//   KIND 1 (GSB_PREC_BF16X3): J in bf16 (exact for integer |J| <= 256) and
+//                             x = hi + mid + lo, three bf16 planes that sum to
+//                             the FP32 x exactly; three kind::f16 MMAs per K
+//                             slice accumulate J hi + J mid + J lo in FP32.
+//
+// Warp roles (192 threads): warp 0 lane 0 issues TMA, warp 1 owns TMEM and
+// its lane 0 issues MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes
+// 32 (w % 4) .. +31, as tcgen05.ld requires).
+#include <cudaTypedefs.h>
+
+#include "gsb_update.cuh"
+#include "tc_ptx.cuh"
 
 namespace gsb {
-bool tc_available() { return false; }
-gsb_status tc_setup(gsb_run_state*) { return set_error(GSB_EUNSUPPORTED, "tcgen05 path not built"); }
-gsb_status tc_steps(gsb_run_state*, int, int) { return set_error(GSB_EUNSUPPORTED, "tcgen05 path not built"); }
-gsb_status tc_energy(gsb_run_state*) { return set_error(GSB_EUNSUPPORTED, "tcgen05 path not built"); }
-void tc_free(gsb_run_state*) {}
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128;   // spins per tile
+constexpr int BN = 128;   // replicas per tile
+constexpr int KB = 128;   // bytes of K per pipeline stage (one swizzle row)
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 128;
+
+template <int KIND>
+struct Cfg;
+template <>
+struct Cfg<0> {
+    static constexpr int kElem = 1, kPlanes = 1, kStages = 6;
+};
+template <>
+struct Cfg<1> {
+    static constexpr int kElem = 2, kPlanes = 3, kStages = 3;
+};
+
+template <int KIND>
+__host__ __device__ constexpr int stage_a_bytes() { return BM * KB; }
+template <int KIND>
+__host__ __device__ constexpr int stage_b_bytes() { return Cfg<KIND>::kPlanes * BN * KB; }
+template <int KIND>
+__host__ __device__ constexpr int smem_bytes() {
+    return 1024 /*alignment slack*/ + Cfg<KIND>::kStages * (stage_a_bytes<KIND>() + stage_b_bytes<KIND>()) + 256;
+}
+
+__device__ __forceinline__ uint8_t e4m3_sign(float x) { return x >= 0.f ? 0x38 : 0xB8; }  // +-1.0
+
+// x = hi + mid + lo, each a bf16; exact for finite FP32 x.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16& mid,
+                                       __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(hi);
+    mid = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(mid);
+    lo = __float2bfloat16_rn(r2);
+}
+
+template <int KIND, bool CONTROL>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_step(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              int Np, int Rp, float* __restrict__ x, float* __restrict__ y,
+              float* __restrict__ p, const float* __restrict__ A, void* __restrict__ vnext,
+              float c, float dt, float p_shared, float inv_rem, int* status) {
+    constexpr int S = Cfg<KIND>::kStages;
+    constexpr int PL = Cfg<KIND>::kPlanes;
+    constexpr int SA = stage_a_bytes<KIND>();
+    constexpr int SB = stage_b_bytes<KIND>();
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + S * SA;
+    uint64_t* full = (uint64_t*)(sB + S * SB);
+    uint64_t* empty = full + S;
+    uint64_t* accf = empty + S;
+    uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
+    const int nk = Np * Cfg<KIND>::kElem / KB;
+    constexpr int kElemsPerSlice = KB / Cfg<KIND>::kElem;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        fence_barrier_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kc = 0; kc < nk; ++kc) {
+                const int s = kc % S;
+                const uint32_t ph = (uint32_t)(kc / S) & 1u;
+                if (kc >= S && !mbar_wait(&empty[s], ph ^ 1u, status)) break;
+                mbar_arrive_expect_tx(&full[s], SA + SB);
+                tma_load_2d(sA + s * SA, &tmA, &full[s], kc * kElemsPerSlice, i0);
+#pragma unroll
+                for (int q = 0; q < PL; ++q)
+                    tma_load_2d(sB + s * SB + q * BN * KB, &tmB, &full[s], kc * kElemsPerSlice,
+                                q * Rp + r0);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_make(KIND == 0 ? 0u : 1u, BM, BN);
+            bool ok = true;
+            for (int kc = 0; kc < nk && ok; ++kc) {
+                const int s = kc % S;
+                const uint32_t ph = (uint32_t)(kc / S) & 1u;
+                if (!mbar_wait(&full[s], ph, status)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t a0 = smem_u32(sA + s * SA);
+                const uint32_t b0 = smem_u32(sB + s * SB);
+#pragma unroll
+                for (int k = 0; k < KB / 32; ++k) {  // 32 bytes of K per MMA
+                    const uint64_t ad = sdesc_sw128(a0 + k * 32);
+#pragma unroll
+                    for (int q = 0; q < PL; ++q) {
+                        const uint64_t bd = sdesc_sw128(b0 + q * BN * KB + k * 32);
+                        const uint32_t acc = (kc | k | q) != 0;
+                        if (KIND == 0)
+                            mma_f8f6f4(tmem, ad, bd, idesc, acc);
+                        else
+                            mma_f16(tmem, ad, bd, idesc, acc);
+                    }
+                }
+                mma_commit(&empty[s]);
+            }
+            if (ok) mma_commit(accf);
+        }
+    } else {
+        // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const int i = i0 + row;
+        // tcgen05.ld is warp-collective: proceed only if every lane saw the accumulator
+        const bool ready = __all_sync(0xffffffffu, mbar_wait(accf, 0, status));
+        if (ready) {
+            fence_after_sync();
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+            for (int cb = 0; cb < BN; cb += 16) {
+                float f[16];
+                tmem_ld16(taddr + cb, f);
+                const size_t o = (size_t)i * Rp + r0 + cb;
+                float xs[16], ys[16], ps[16], as[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 a = *reinterpret_cast<const float4*>(x + o + 4 * q);
+                    const float4 b = *reinterpret_cast<const float4*>(y + o + 4 * q);
+                    xs[4 * q] = a.x; xs[4 * q + 1] = a.y; xs[4 * q + 2] = a.z; xs[4 * q + 3] = a.w;
+                    ys[4 * q] = b.x; ys[4 * q + 1] = b.y; ys[4 * q + 2] = b.z; ys[4 * q + 3] = b.w;
+                    if (CONTROL) {
+                        const float4 pp = *reinterpret_cast<const float4*>(p + o + 4 * q);
+                        const float4 aa = *reinterpret_cast<const float4*>(A + r0 + cb + 4 * q);
+                        ps[4 * q] = pp.x; ps[4 * q + 1] = pp.y; ps[4 * q + 2] = pp.z; ps[4 * q + 3] = pp.w;
+                        as[4 * q] = aa.x; as[4 * q + 1] = aa.y; as[4 * q + 2] = aa.z; as[4 * q + 3] = aa.w;
+                    } else {
+                        ps[4 * q] = ps[4 * q + 1] = ps[4 * q + 2] = ps[4 * q + 3] = 0.f;
+                        as[4 * q] = as[4 * q + 1] = as[4 * q + 2] = as[4 * q + 3] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    sb_update<CONTROL>(xs[k], ys[k], ps[k], f[k], as[k], c, dt, p_shared, inv_rem);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    *reinterpret_cast<float4*>(x + o + 4 * q) =
+                        make_float4(xs[4 * q], xs[4 * q + 1], xs[4 * q + 2], xs[4 * q + 3]);
+                    *reinterpret_cast<float4*>(y + o + 4 * q) =
+                        make_float4(ys[4 * q], ys[4 * q + 1], ys[4 * q + 2], ys[4 * q + 3]);
+                    if (CONTROL)
+                        *reinterpret_cast<float4*>(p + o + 4 * q) =
+                            make_float4(ps[4 * q], ps[4 * q + 1], ps[4 * q + 2], ps[4 * q + 3]);
+                }
+                // next step's operand, replica-major [plane][Rp][Np]
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const size_t vo = (size_t)(r0 + cb + k) * Np + i;
+                    if (KIND == 0) {
+                        reinterpret_cast<uint8_t*>(vnext)[vo] = e4m3_sign(xs[k]);
+                    } else {
+                        __nv_bfloat16 h, m, l;
+                        split3(xs[k], h, m, l);
+                        __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(vnext);
+                        const size_t plane = (size_t)Rp * Np;
+                        v[vo] = h;
+                        v[plane + vo] = m;
+                        v[2 * plane + vo] = l;
+                    }
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// V(t_0) from x(t_0): spin-major x [Np][Rp] -> replica-major operand planes.
+template <int KIND>
+__global__ void k_tc_prep(const float* __restrict__ x, void* __restrict__ v, int Np, int Rp) {
+    __shared__ float tile[32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y)
+        tile[k][threadIdx.x] = x[(size_t)(i0 + k) * Rp + r0 + threadIdx.x];
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, i = i0 + threadIdx.x;
+        const float xv = tile[threadIdx.x][k];
+        const size_t vo = (size_t)r * Np + i;
+        if (KIND == 0) {
+            reinterpret_cast<uint8_t*>(v)[vo] = e4m3_sign(xv);
+        } else {
+            __nv_bfloat16 h, m, l;
+            split3(xv, h, m, l);
+            __nv_bfloat16* vb = reinterpret_cast<__nv_bfloat16*>(v);
+            const size_t plane = (size_t)Rp * Np;
+            vb[vo] = h;
+            vb[plane + vo] = m;
+            vb[2 * plane + vo] = l;
+        }
+    }
+}
+
+struct TcState {
+    CUtensorMap tmA;
+    CUtensorMap tmB[2];
+    int vcur = 0;
+    int kind = 0;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2D K-major tensor map: inner dimension K (contiguous), outer rows; box of
+// one 128-byte K slice by 128 rows, 128-byte swizzle.
+gsb_status make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, int elem_bytes,
+                    uint64_t inner, uint64_t outer) {
+    auto encode = get_encode();
+    if (!encode) return set_error(GSB_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * (cuuint64_t)elem_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(KB / elem_bytes), 128u};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = encode(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(GSB_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return GSB_OK;
+}
+
+template <int KIND, bool CONTROL>
+gsb_status launch_step(gsb_run_state* run, TcState* T, float p_shared, float inv_rem) {
+    auto kern = k_tc_step<KIND, CONTROL>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          smem_bytes<KIND>()));
+        attr_set = true;
+    }
+    dim3 grid(run->Rp / BN, run->Np / BM);
+    void* vnext = KIND == 0 ? (void*)run->v8[T->vcur ^ 1] : (void*)run->v16[T->vcur ^ 1];
+    kern<<<grid, kThreads, smem_bytes<KIND>(), run->stream>>>(
+        T->tmA, T->tmB[T->vcur], run->Np, run->Rp, run->x[0], run->y, run->p, run->A, vnext,
+        run->c, run->dt, p_shared, inv_rem, run->status);
+    GSB_LAUNCH_CHECK("k_tc_step");
+    T->vcur ^= 1;
+    return GSB_OK;
+}
+
+}  // namespace
+
+bool tc_available() { return true; }
+
+gsb_status tc_setup(gsb_run_state* run) {
+    const gsb_problem* P = run->prob;
+    TcState* T = new TcState();
+    run->tc = T;
+    T->kind = run->path == kPathTcFp8 ? 0 : 1;
+    const size_t n = (size_t)run->Np * run->Rp;
+    gsb_status st;
+    if (T->kind == 0) {
+        for (int b = 0; b < 2; ++b) GSB_CUDA_TRY(cudaMalloc(&run->v8[b], n));
+        if ((st = make_map(&T->tmA, P->J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P->Np, P->Np))) return st;
+        for (int b = 0; b < 2; ++b)
+            if ((st = make_map(&T->tmB[b], run->v8[b], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, run->Np,
+                               run->Rp)))
+                return st;
+    } else {
+        for (int b = 0; b < 2; ++b) GSB_CUDA_TRY(cudaMalloc(&run->v16[b], 3 * n * sizeof(__nv_bfloat16)));
+        if ((st = make_map(&T->tmA, P->J16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, P->Np, P->Np)))
+            return st;
+        for (int b = 0; b < 2; ++b)
+            if ((st = make_map(&T->tmB[b], run->v16[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                               run->Np, 3 * (uint64_t)run->Rp)))
+                return st;
+    }
+    dim3 grid(run->Np / 32, run->Rp / 32), block(32, 8);
+    if (T->kind == 0)
+        k_tc_prep<0><<<grid, block, 0, run->stream>>>(run->x[0], run->v8[0], run->Np, run->Rp);
+    else
+        k_tc_prep<1><<<grid, block, 0, run->stream>>>(run->x[0], run->v16[0], run->Np, run->Rp);
+    GSB_LAUNCH_CHECK("k_tc_prep");
+    T->vcur = 0;
+    return GSB_OK;
+}
+
+gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps) {
+    TcState* T = (TcState*)run->tc;
+    for (int m = m0; m < m0 + nsteps; ++m) {
+        const float p_shared = run_p_shared(run, m + 1);
+        const float inv_rem = 1.0f / (float)(run->params.M - m);
+        gsb_status st;
+        if (T->kind == 0)
+            st = run->control ? launch_step<0, true>(run, T, p_shared, inv_rem)
+                              : launch_step<0, false>(run, T, p_shared, inv_rem);
+        else
+            st = run->control ? launch_step<1, true>(run, T, p_shared, inv_rem)
+                              : launch_step<1, false>(run, T, p_shared, inv_rem);
+        if (st != GSB_OK) return st;
+        run->steps_done = m + 1;
+        if (run_is_eval_step(run, m + 1))
+            if ((st = run_evaluate(run, m + 1)) != GSB_OK) return st;
+    }
+    run->steps_done = m0;  // the caller adds nsteps
+    return GSB_OK;
+}
+
+gsb_status tc_energy(gsb_run_state* run) {
+    GSB_CUDA_TRY(cudaMemsetAsync(run->e_acc, 0, sizeof(double) * run->Rp, run->stream));
+    return launch_dense_f32_energy(run->prob, run->x[0], run->Rp, run->e_acc, run->stream);
+}
+
+void tc_free(gsb_run_state* run) {
+    delete (TcState*)run->tc;
+    run->tc = nullptr;
+}
+
 }  // namespace gsb
