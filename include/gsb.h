@@ -63,13 +63,18 @@ typedef enum gsb_variant { GSB_BSB = 0, GSB_GBSB = 1, GSB_DSB = 2, GSB_GDSB = 3 
 
 /* Coupling arithmetic. */
 typedef enum gsb_precision {
-    GSB_PREC_AUTO = 0,   /* FP8 for sgn-x coupling with small integer J, BF16X3 for x coupling
-                            with small integer J, FP32 otherwise; CSR problems always use CSR */
+    GSB_PREC_AUTO = 0,   /* FP8 for sgn-x coupling with integer |J| <= 16, FX32 for x coupling
+                            with integer J (128 max_i sum_j |J_ij| < 2^24), FP32 otherwise;
+                            CSR problems always use CSR */
     GSB_PREC_FP32 = 1,   /* FP32 on CUDA cores (the plain form) */
     GSB_PREC_FP8 = 2,    /* tcgen05 kind::f8f6f4, e4m3 J and sgn x, FP32 accumulate: exact for
                             integer |J| <= 16; sgn-x coupling (dSB, GdSB) only */
-    GSB_PREC_BF16X3 = 3  /* tcgen05 kind::f16, J in bf16 (exact for integer |J| <= 256) and x
-                            split into three bf16 terms (x = hi + mid + lo exactly) */
+    GSB_PREC_FX32 = 3    /* tcgen05 kind::f16 with integer J in bf16 and x as 32-bit fixed point
+                            rint(x 2^30) in four signed base-256 bf16 digits; each digit plane
+                            accumulates exactly, the planes are combined in int64 and rounded
+                            once: the coupling is the correctly rounded J x (x exact for
+                            |x| >= 2^-7, else rounded at 2^-31). Needs integer J with
+                            128 max_i sum_j |J_ij| < 2^24 */
 } gsb_precision;
 
 /* J storage passed to gsb_create. */

@@ -99,8 +99,11 @@ gsb_status create_dense(gsb_problem* P, const float* Jh, const float* hh, bool v
     }
     bool integer = true;
     float mx = 0.f;
-    double sum = 0.0;
+    double sum = 0.0, max_row = 0.0;
     for (int i = 0; i < N; ++i) {
+        double row = 0.0;
+        for (int j = 0; j < N; ++j) row += fabs((double)Jp[(size_t)i * Np + j]);
+        max_row = std::max(max_row, row);
         for (int j = 0; j < N; ++j) {
             const float v = Jp[(size_t)i * Np + j];
             if (validate) {
@@ -117,6 +120,7 @@ gsb_status create_dense(gsb_problem* P, const float* Jh, const float* hh, bool v
     }
     P->integer_J = integer;
     P->max_abs_J = mx;
+    P->max_row_abs = max_row;
     P->W_tot = -0.5 * sum;
     const size_t n = (size_t)Np * Np;
     gsb_status st;
@@ -124,7 +128,9 @@ gsb_status create_dense(gsb_problem* P, const float* Jh, const float* hh, bool v
     GSB_CUDA_TRY(cudaMemcpyAsync(P->J32, Jp.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
     if (integer && mx <= 16.f)
         if ((st = dev_alloc(&P->J8, n)) != GSB_OK) return st;
-    if (integer && mx <= 256.f)
+    // FX32 digit planes: every partial sum |sum_j J_ij d_j| <= 128 max row sum stays
+    // an exact FP32 integer
+    if (integer && mx <= 256.f && 128.0 * max_row < 16777216.0)
         if ((st = dev_alloc(&P->J16, n)) != GSB_OK) return st;
     if (P->J8 || P->J16) {
         k_convert_J<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P->J32, P->J8, P->J16, n);
@@ -181,14 +187,20 @@ gsb_status create_csr(gsb_problem* P, const int32_t* rp, const int32_t* ci, cons
     }
     bool integer = true;
     float mx = 0.f;
-    double sum = 0.0;
+    double sum = 0.0, max_row = 0.0;
     for (float v : val) {
         integer = integer && is_integer(v);
         mx = std::max(mx, fabsf(v));
         sum += v;
     }
+    for (int i = 0; i < N; ++i) {
+        double row = 0.0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) row += fabs((double)val[k]);
+        max_row = std::max(max_row, row);
+    }
     P->integer_J = integer;
     P->max_abs_J = mx;
+    P->max_row_abs = max_row;
     P->W_tot = -0.5 * sum;
     P->nnz = (int64_t)col.size();
     gsb_status st;
@@ -241,7 +253,7 @@ void free_run(gsb_run_state* r) {
 }
 
 gsb_status evaluate(gsb_run_state* run, int step) {
-    if (run->path == kPathTcFp8 || run->path == kPathTcBf16x3) {
+    if (run->path == kPathTcFp8 || run->path == kPathTcFx32) {
         gsb_status st = tc_energy(run);
         if (st != GSB_OK) return st;
         return launch_best_keep(run, step);
@@ -391,7 +403,7 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
                 else if (sign && P->J8)
                     path = kPathTcFp8;
                 else if (!sign && P->J16)
-                    path = kPathTcBf16x3;
+                    path = kPathTcFx32;
                 else
                     path = kPathDenseF32;
                 break;
@@ -403,10 +415,11 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
                     return set_error(GSB_EUNSUPPORTED, "FP8 needs integer J with |J| <= 16");
                 path = kPathTcFp8;
                 break;
-            case GSB_PREC_BF16X3:
+            case GSB_PREC_FX32:
                 if (!P->J16)
-                    return set_error(GSB_EUNSUPPORTED, "BF16X3 needs integer J with |J| <= 256");
-                path = kPathTcBf16x3;
+                    return set_error(GSB_EUNSUPPORTED,
+                                     "FX32 needs integer J with 128 max_i sum_j |J_ij| < 2^24");
+                path = kPathTcFx32;
                 break;
             default: return set_error(GSB_EINVAL, "unknown precision");
         }
@@ -445,7 +458,7 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
         return e;
     };
     if ((st = dev_alloc(&run->x[0], nst)) || (st = dev_alloc(&run->y, nst))) return fail(st);
-    if (path != kPathTcFp8 && path != kPathTcBf16x3)
+    if (path != kPathTcFp8 && path != kPathTcFx32)
         if ((st = dev_alloc(&run->x[1], nst))) return fail(st);
     if (control)
         if ((st = dev_alloc(&run->p, nst))) return fail(st);
@@ -494,7 +507,7 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
         cudaFree(y0d);
     }
     if (st != GSB_OK) return fail(st);
-    if (path == kPathTcFp8 || path == kPathTcBf16x3) {
+    if (path == kPathTcFp8 || path == kPathTcFx32) {
         if ((st = tc_setup(run)) != GSB_OK) return fail(st);
     }
     *out = run;
@@ -514,7 +527,7 @@ gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps) {
     if (nsteps < 0 || run->steps_done + nsteps > run->params.M)
         return set_error(GSB_EINVAL, "nsteps exceeds the remaining steps of the run");
     const int M = run->params.M;
-    if (run->path == kPathTcFp8 || run->path == kPathTcBf16x3) {
+    if (run->path == kPathTcFp8 || run->path == kPathTcFx32) {
         gsb_status st = tc_steps(run, run->steps_done, nsteps);
         if (st == GSB_OK) run->steps_done += nsteps;
         return st;
@@ -596,7 +609,7 @@ gsb_status gsb_get_state(gsb_run_state* run, float* x, float* y, float* p, int32
     if (!run) return set_error(GSB_EINVAL, "run is NULL");
     gsb_status st = GSB_OK;
     const int R = run->R, N = run->N;
-    if (run->path == kPathTcFp8 || run->path == kPathTcBf16x3) {
+    if (run->path == kPathTcFp8 || run->path == kPathTcFx32) {
         // the fused path keeps x, y, p in its own buffers; they are synced after every call
     }
     float* tmp = nullptr;

@@ -23,7 +23,7 @@ enum Path : int {
     kPathDenseF32 = 0,  // FP32 CUDA-core coupling (the plain form)
     kPathCsr = 1,       // CSR coupling
     kPathTcFp8 = 2,     // tcgen05 e4m3, sgn x coupling
-    kPathTcBf16x3 = 3,  // tcgen05 bf16, x split in three terms
+    kPathTcFx32 = 3,    // tcgen05 bf16, x as 32-bit fixed point in four digit planes
 };
 
 // Device status word bits (written by kernels, read by the host).
@@ -54,11 +54,12 @@ struct gsb_problem {
     int Np = 0;      // N padded to kTile
     bool integer_J = false;
     float max_abs_J = 0.f;
+    double max_row_abs = 0.0;  // max_i sum_j |J_ij|
     double W_tot = 0.0;  // sum_{i<j} W_ij with W = -J (Sec. III)
     // dense device copies, Np x Np row-major, zero padded
     float* J32 = nullptr;
     uint8_t* J8 = nullptr;         // e4m3, when integer and |J| <= 16
-    __nv_bfloat16* J16 = nullptr;  // bf16, when integer and |J| <= 256
+    __nv_bfloat16* J16 = nullptr;  // bf16, when integer and 128 max row sum |J| < 2^24
     // CSR device copy (N rows)
     int32_t* rowptr = nullptr;
     int32_t* col = nullptr;
@@ -89,7 +90,7 @@ struct gsb_run_state {
     float* sched = nullptr;   // [M+1] or null
     // tcgen05 operands, replica-major [Rp][Np] (K-major B operand)
     uint8_t* v8[2] = {nullptr, nullptr};
-    __nv_bfloat16* v16[2] = {nullptr, nullptr};  // three planes each: [3][Rp][Np]
+    __nv_bfloat16* v16[2] = {nullptr, nullptr};  // four digit planes each: [4][Rp][Np]
     // energy bookkeeping
     double* e_acc = nullptr;    // [Rp] sum_i s_i (J s)_i
     double* best_e = nullptr;   // [Rp]

@@ -6,6 +6,12 @@
 // replicas, so every gathered row of v is one coalesced 512-byte (x) or
 // 128-byte (sgn x, int8) access. The warp loads up to 32 nonzeros of its row at
 // once (one per lane) and broadcasts them with __shfl_sync.
+//
+// With integer J the x coupling is exact: each gathered x_j becomes the 32-bit
+// fixed-point integer q_j = rint(x_j 2^30) (equal to x_j 2^30 for
+// |x_j| >= 2^-7), sum_k J_ik q_k is accumulated in int64, and 2^-30 times it is
+// rounded once to FP32. The sgn x coupling of integer J is an integer sum
+// already (exact in FP32).
 #include "gsb_update.cuh"
 
 namespace gsb {
@@ -15,7 +21,7 @@ namespace {
 constexpr int kWarpsPerBlock = 8;
 constexpr int kReplicasPerWarp = 128;
 
-template <bool SIGN>
+template <bool SIGN, bool EXACT>
 __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowptr,
                                                const int32_t* __restrict__ col,
                                                const float* __restrict__ val,
@@ -24,6 +30,7 @@ __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowpt
                                                int rlane) {
     const int lane = threadIdx.x & 31;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    long long qa[4] = {0, 0, 0, 0};
     const int beg = rowptr[i], end = rowptr[i + 1];
     for (int kb = beg; kb < end; kb += 32) {
         const int k = kb + lane;
@@ -39,6 +46,13 @@ __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowpt
                 acc.y = fmaf(w, (float)s.y, acc.y);
                 acc.z = fmaf(w, (float)s.z, acc.z);
                 acc.w = fmaf(w, (float)s.w, acc.w);
+            } else if (EXACT) {
+                const float4 v = *reinterpret_cast<const float4*>(xv + (size_t)j * Rp + rlane);
+                const long long wi = (long long)__float2int_rn(w);
+                qa[0] += wi * __float2int_rn(v.x * 1073741824.0f);
+                qa[1] += wi * __float2int_rn(v.y * 1073741824.0f);
+                qa[2] += wi * __float2int_rn(v.z * 1073741824.0f);
+                qa[3] += wi * __float2int_rn(v.w * 1073741824.0f);
             } else {
                 const float4 v = *reinterpret_cast<const float4*>(xv + (size_t)j * Rp + rlane);
                 acc.x = fmaf(w, v.x, acc.x);
@@ -48,10 +62,15 @@ __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowpt
             }
         }
     }
+    if (!SIGN && EXACT) {
+        const double s = 9.313225746154785e-10;  // 2^-30
+        acc = make_float4((float)((double)qa[0] * s), (float)((double)qa[1] * s),
+                          (float)((double)qa[2] * s), (float)((double)qa[3] * s));
+    }
     return acc;
 }
 
-template <bool SIGN, bool CONTROL>
+template <bool SIGN, bool CONTROL, bool EXACT>
 __global__ void __launch_bounds__(256) k_csr_step(
     const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const float* __restrict__ val, int N, int Rp, const float* __restrict__ xc,
@@ -61,7 +80,7 @@ __global__ void __launch_bounds__(256) k_csr_step(
     const int i = blockIdx.y * kWarpsPerBlock + (threadIdx.x >> 5);
     if (i >= N) return;
     const int rlane = blockIdx.x * kReplicasPerWarp + (threadIdx.x & 31) * 4;
-    const float4 f = row_coupling<SIGN>(rowptr, col, val, xc, sc, Rp, i, rlane);
+    const float4 f = row_coupling<SIGN, EXACT>(rowptr, col, val, xc, sc, Rp, i, rlane);
     const size_t o = (size_t)i * Rp + rlane;
     float4 x4 = *reinterpret_cast<const float4*>(xc + o);
     float4 y4 = *reinterpret_cast<const float4*>(y + o);
@@ -148,15 +167,19 @@ gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc) {
     dim3 grid(run->Rp / kReplicasPerWarp, (run->N + kWarpsPerBlock - 1) / kWarpsPerBlock);
     const int cur = run->cur;
     const float inv_rem = 1.0f / (float)(sc.M - sc.m);
-#define GSB_CSR_LAUNCH(S, C)                                                                 \
-    k_csr_step<S, C><<<grid, 256, 0, run->stream>>>(                                         \
+#define GSB_CSR_LAUNCH(S, C, E)                                                              \
+    k_csr_step<S, C, E><<<grid, 256, 0, run->stream>>>(                                      \
         P->rowptr, P->col, P->val, run->N, run->Rp, run->x[cur], run->s8[cur],               \
         run->x[cur ^ 1], run->s8[cur ^ 1], run->y, run->p, run->A, sc.c, sc.dt, sc.p_next,   \
         inv_rem)
+    // exact fixed-point x coupling when J is integer and 2^30 sum_k |J_ik| fits in int64
+    const bool exact = P->integer_J && P->max_row_abs < 4294967296.0;
     if (run->sign_coupling) {
-        if (run->control) GSB_CSR_LAUNCH(true, true); else GSB_CSR_LAUNCH(true, false);
+        if (run->control) GSB_CSR_LAUNCH(true, true, false); else GSB_CSR_LAUNCH(true, false, false);
+    } else if (exact) {
+        if (run->control) GSB_CSR_LAUNCH(false, true, true); else GSB_CSR_LAUNCH(false, false, true);
     } else {
-        if (run->control) GSB_CSR_LAUNCH(false, true); else GSB_CSR_LAUNCH(false, false);
+        if (run->control) GSB_CSR_LAUNCH(false, true, false); else GSB_CSR_LAUNCH(false, false, false);
     }
 #undef GSB_CSR_LAUNCH
     GSB_LAUNCH_CHECK("k_csr_step");

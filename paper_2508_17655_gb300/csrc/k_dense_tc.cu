@@ -10,10 +10,17 @@
 //   KIND 0 (GSB_PREC_FP8):    J and V = sgn x in e4m3, kind::f8f6f4. Exact:
 //                             products are +-J_ij, partial sums are integers
 //                             far below 2^24 (|J| <= 16, N < 2^20).
-//   KIND 1 (GSB_PREC_BF16X3): J in bf16 (exact for integer |J| <= 256) and
-//                             x = hi + mid + lo, three bf16 planes that sum to
-//                             the FP32 x exactly; three kind::f16 MMAs per K
-//                             slice accumulate J hi + J mid + J lo in FP32.
+//   KIND 1 (GSB_PREC_FX32):   J in bf16 (integer) and x as the 32-bit fixed
+//                             point integer q = rint(x 2^30), written as four
+//                             signed base-256 digits d_0..d_3 (bf16, exact).
+//                             Digit plane k accumulates D_k = J d_k in its own
+//                             128-column TMEM accumulator; every partial sum
+//                             is an integer below 2^24 (128 sum_j |J_ij| <
+//                             2^24), so D_k is exact whatever order the tensor
+//                             core adds in. The epilogue forms
+//                             sum_k 256^k D_k exactly in int64 and rounds
+//                             2^-30 times it once to FP32: f is the correctly
+//                             rounded J x_q, and x_q = x for |x| >= 2^-7.
 //
 // Warp roles (192 threads): warp 0 lane 0 issues TMA, warp 1 owns TMEM and
 // its lane 0 issues MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes
@@ -33,17 +40,18 @@ constexpr int BM = 128;   // spins per tile
 constexpr int BN = 128;   // replicas per tile
 constexpr int KB = 128;   // bytes of K per pipeline stage (one swizzle row)
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 128;
 
 template <int KIND>
 struct Cfg;
 template <>
 struct Cfg<0> {
     static constexpr int kElem = 1, kPlanes = 1, kStages = 6;
+    static constexpr uint32_t kTmemCols = 128;
 };
 template <>
 struct Cfg<1> {
-    static constexpr int kElem = 2, kPlanes = 3, kStages = 3;
+    static constexpr int kElem = 2, kPlanes = 4, kStages = 2;
+    static constexpr uint32_t kTmemCols = 512;  // one 128-column accumulator per digit plane
 };
 
 template <int KIND>
@@ -57,14 +65,26 @@ __host__ __device__ constexpr int smem_bytes() {
 
 __device__ __forceinline__ uint8_t e4m3_sign(float x) { return x >= 0.f ? 0x38 : 0xB8; }  // +-1.0
 
-// x = hi + mid + lo, each a bf16; exact for finite FP32 x.
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16& mid,
-                                       __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(hi);
-    mid = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(mid);
-    lo = __float2bfloat16_rn(r2);
+// x as four signed base-256 digits of q = rint(x 2^30), |x| <= 1:
+// q = d0 + 256 d1 + 65536 d2 + 16777216 d3, d0..d2 in [-128, 127], |d3| <= 64.
+// x 2^30 is exact in FP32 (a power-of-two scaling), so q = x 2^30 exactly
+// whenever |x| >= 2^-7.
+__device__ __forceinline__ void fx32_digits(float x, __nv_bfloat16 (&d)[4]) {
+    int q = __float2int_rn(x * 1073741824.0f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int dk = ((q + 128) & 255) - 128;
+        d[k] = __int2bfloat16_rn(dk);
+        q = (q - dk) >> 8;  // exact: q - dk is a multiple of 256
+    }
+    d[3] = __int2bfloat16_rn(q);
+}
+
+// f = 2^-30 sum_k 256^k D_k, from exact integer accumulators, rounded once.
+__device__ __forceinline__ float fx32_combine(float d0, float d1, float d2, float d3) {
+    const long long v = (long long)d0 + ((long long)d1 << 8) + ((long long)d2 << 16) +
+                        ((long long)d3 << 24);
+    return (float)((double)v * 9.313225746154785e-10);  // 2^-30
 }
 
 template <int KIND, bool CONTROL>
@@ -101,6 +121,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
     }
+    constexpr uint32_t kTmemCols = Cfg<KIND>::kTmemCols;
     if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
     fence_before_sync();
     __syncthreads();
@@ -141,11 +162,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int q = 0; q < PL; ++q) {
                         const uint64_t bd = sdesc_sw128(b0 + q * BN * KB + k * 32);
-                        const uint32_t acc = (kc | k | q) != 0;
+                        const uint32_t acc = (kc | k) != 0;
                         if (KIND == 0)
                             mma_f8f6f4(tmem, ad, bd, idesc, acc);
-                        else
-                            mma_f16(tmem, ad, bd, idesc, acc);
+                        else  // digit plane q into accumulator columns [128 q, 128 q + 128)
+                            mma_f16(tmem + q * BN, ad, bd, idesc, acc);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -166,6 +187,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int cb = 0; cb < BN; cb += 16) {
                 float f[16];
                 tmem_ld16(taddr + cb, f);
+                if (KIND == 1) {
+                    float d1[16], d2[16], d3[16];
+                    tmem_ld16(taddr + BN + cb, d1);
+                    tmem_ld16(taddr + 2 * BN + cb, d2);
+                    tmem_ld16(taddr + 3 * BN + cb, d3);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) f[k] = fx32_combine(f[k], d1[k], d2[k], d3[k]);
+                }
                 const size_t o = (size_t)i * Rp + r0 + cb;
                 float xs[16], ys[16], ps[16], as[16];
 #pragma unroll
@@ -204,13 +233,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (KIND == 0) {
                         reinterpret_cast<uint8_t*>(vnext)[vo] = e4m3_sign(xs[k]);
                     } else {
-                        __nv_bfloat16 h, m, l;
-                        split3(xs[k], h, m, l);
+                        __nv_bfloat16 d[4];
+                        fx32_digits(xs[k], d);
                         __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(vnext);
                         const size_t plane = (size_t)Rp * Np;
-                        v[vo] = h;
-                        v[plane + vo] = m;
-                        v[2 * plane + vo] = l;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[q * plane + vo] = d[q];
                     }
                 }
             }
@@ -239,13 +267,12 @@ __global__ void k_tc_prep(const float* __restrict__ x, void* __restrict__ v, int
         if (KIND == 0) {
             reinterpret_cast<uint8_t*>(v)[vo] = e4m3_sign(xv);
         } else {
-            __nv_bfloat16 h, m, l;
-            split3(xv, h, m, l);
+            __nv_bfloat16 d[4];
+            fx32_digits(xv, d);
             __nv_bfloat16* vb = reinterpret_cast<__nv_bfloat16*>(v);
             const size_t plane = (size_t)Rp * Np;
-            vb[vo] = h;
-            vb[plane + vo] = m;
-            vb[2 * plane + vo] = l;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vb[q * plane + vo] = d[q];
         }
     }
 }
@@ -326,12 +353,12 @@ gsb_status tc_setup(gsb_run_state* run) {
                                run->Rp)))
                 return st;
     } else {
-        for (int b = 0; b < 2; ++b) GSB_CUDA_TRY(cudaMalloc(&run->v16[b], 3 * n * sizeof(__nv_bfloat16)));
+        for (int b = 0; b < 2; ++b) GSB_CUDA_TRY(cudaMalloc(&run->v16[b], 4 * n * sizeof(__nv_bfloat16)));
         if ((st = make_map(&T->tmA, P->J16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, P->Np, P->Np)))
             return st;
         for (int b = 0; b < 2; ++b)
             if ((st = make_map(&T->tmB[b], run->v16[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                               run->Np, 3 * (uint64_t)run->Rp)))
+                               run->Np, 4 * (uint64_t)run->Rp)))
                 return st;
     }
     dim3 grid(run->Np / 32, run->Rp / 32), block(32, 8);

@@ -16,13 +16,13 @@ from . import build as _build
 # enums / flags of include/gsb.h
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENUMERIC, ENODEV = range(8)
 BSB, GBSB, DSB, GDSB = range(4)
-PREC_AUTO, PREC_FP32, PREC_FP8, PREC_BF16X3 = range(4)
+PREC_AUTO, PREC_FP32, PREC_FP8, PREC_FX32 = range(4)
 J_DENSE_I8, J_DENSE_F32, J_CSR_F32 = range(3)
 CREATE_DEVICE_INPUT, CREATE_NO_VALIDATE = 0x1, 0x2
 RUN_DEFER = 0x1
 
 VARIANT = {"bsb": BSB, "gbsb": GBSB, "dsb": DSB, "gdsb": GDSB}
-PRECISION = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp8": PREC_FP8, "bf16x3": PREC_BF16X3}
+PRECISION = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp8": PREC_FP8, "fx32": PREC_FX32}
 
 
 class gsb_params(ctypes.Structure):
