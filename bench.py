@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the GbSB hot path on GB300 (one JSON line on stdout).
+
+Workload (the dense precision-form configuration): a complete graph with
+N = 2000 spins and i.i.d. +-1 couplings (symmetric, zero diagonal, seed 0),
+R = 1024 replicas, M = 2000 time steps, the control strength A of Eq. 7 swept
+over 8 values (128 replicas each), coupling J sgn(x) on the FP8 tensor cores
+(tcgen05 kind::f8f6f4, exact), c = 1/(2 sqrt N) and dt = 1.25 (App. A), energy
+and best state at t_M (Sec. III). One bench step = one complete run of all M
+steps for all R replicas. Metric: spin updates per second (N R M / time).
+
+Also reported: the paper's own GbSB (x coupling, exact FX32 tensor-core
+path) and the plain FP32 CUDA-core form on the same workload, TTS99 against
+the target energy fixed by long oracle runs (tests/golden/targets.json), the
+roofline of the step kernel, the end-to-end figure through the C ABI with
+host buffers, and the FP64 oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gsb,reference}]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SPINS, R_REPLICAS, M_STEPS = 2000, 1024, 2000
+A_VALUES = [0.0, 0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35]
+DT = 1.25
+METRIC = "GSB spin-updates/s & TTS99 at N=2000 ±1 complete graph; fused vs plain FP32"
+WORKLOAD = ("N=2000 +-1 complete graph (seed 0), R=1024 replicas, M=2000 steps, "
+            "A swept over 8 values x 128 replicas, J.sgn(x) + Eq. 7 control on FP8 tcgen05")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gsb", "reference"], default="gsb")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain-FP32 / GbSB / TTS legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            P = json.load(f)
+        return P, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def target_energy():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "targets.json")) as f:
+            return json.load(f)["sk_pm1_N2000_seed0"]["E_target"]
+    except (OSError, KeyError):
+        return None
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="gsb_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [t.strip() for t in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+
+def oracle_sample(seconds_hint=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    R_s replicas at the middle control strength for the first M_s of the
+    M = 2000 steps, on all host cores. Returns (spin-updates/s, cores, sample)."""
+    import numpy as np
+    import oracle as O
+    from paper_2508_17655_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    J = I.sk_pm1(N_SPINS, 0).astype(np.float64)
+    c = 1.0 / (2.0 * math.sqrt(N_SPINS))
+    Rs = max(8, 2 * cores)
+    Ms = 20
+    x0 = O.init_uniform(Rs, N_SPINS, 1)
+    t = time.perf_counter()
+    O.run(J, "gdsb", x0, 0 * x0, c=c, dt=DT, M=M_STEPS, A=0.2, nsteps=Ms, nthreads=cores)
+    dt1 = time.perf_counter() - t
+    Ms = max(20, min(M_STEPS, int(Ms * seconds_hint / max(dt1, 1e-3))))
+    t = time.perf_counter()
+    O.run(J, "gdsb", x0, 0 * x0, c=c, dt=DT, M=M_STEPS, A=0.2, nsteps=Ms, nthreads=cores)
+    el = time.perf_counter() - t
+    value = N_SPINS * Rs * Ms / el
+    sample = (f"{Rs} replicas x first {Ms} of {M_STEPS} steps of the same run (A=0.2, GdSB), "
+              f"N=2000, FP64, {el:.1f} s")
+    return value, cores, sample, el
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def gpu_arm(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2508_17655_gb300 import build, gsb, inputs as I
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(0)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", 0))
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    J = I.sk_pm1(N_SPINS, 0)
+    c = 1.0 / (2.0 * math.sqrt(N_SPINS))
+    A = np.repeat(np.array(A_VALUES, np.float32), R_REPLICAS // len(A_VALUES))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    P = gsb.Problem.dense(J, stream=stream.cuda_stream)
+
+    def timed_runs(variant, precision, K, W, seed0):
+        run = P.run(variant, M=M_STEPS, R=R_REPLICAS, c=c, dt=DT, A=A, seed=seed0,
+                    precision=precision, defer=True, profile=True, stream=stream.cuda_stream)
+        for w in range(W):
+            run.restart(seed0 + 1 + w)
+        times, kern_ms, kern_n, energies = [], 0.0, 0, []
+        launches0 = gsb.launch_count()
+        for k in range(K):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run.restart(seed0 + 100 + k)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            ms, n = run.kernel_time()
+            kern_ms += ms
+            kern_n += n
+            energies.append(run.best()["E"])
+        launches = gsb.launch_count() - launches0
+        run.close()
+        return times, kern_ms, kern_n, np.concatenate(energies), launches
+
+    # headline: GdSB on FP8 tensor cores
+    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0)) as clk:
+        times, kern_ms, kern_n, energies, launches = timed_runs("gdsb", "fp8", args.steps,
+                                                                 args.warmup, 1000 * rank)
+    clocks = clk.summary()
+    total_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = N_SPINS * R_REPLICAS * M_STEPS * args.steps * world
+    value = units / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    Pk, how = peaks()
+    fp8_peak = 2.0 * Pk["bf16_tflops_sustained"]  # e4m3 dense = 2x bf16 (nominal ratio)
+    avg_launch_s = (kern_ms / kern_n) / 1e3
+    flops_launch = 2.0 * N_SPINS * N_SPINS * R_REPLICAS  # algorithmic: J sgn(X), N = 2000
+    achieved = flops_launch / avg_launch_s / 1e12
+    roofline = {"bound": "tensor", "kernel": "k_tc_step<0,true> (e4m3 J.sgn(x) + Eqs. 3-7)",
+                "achieved": round(achieved, 1), "peak": round(fp8_peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / fp8_peak, 4), "traffic": None,
+                "peak_source": f"{how}: 2 x bf16 sustained (e4m3/bf16 nominal ratio)",
+                "avg_launch_us": round(avg_launch_s * 1e6, 3),
+                "algorithmic_flop_per_launch": flops_launch}
+
+    out = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3",
+           "data": "synthetic (seeded +-1 complete graph shaped like K2000; x0 by Philox)",
+           "config": {"workload": WORKLOAD, "N": N_SPINS, "R": R_REPLICAS, "M": M_STEPS,
+                      "A_values": A_VALUES, "variant": "gdsb", "precision": "fp8",
+                      "c": c, "dt": DT, "l2": "flushed (512 MB write) before every timed step",
+                      "parallelism": f"replicas only, {world} GPU(s)"},
+           "roofline": roofline, "clocks": clocks, "gpu_launches": launches}
+
+    if rank == 0 and not args.no_extras:
+        E = target_energy()
+        out["success"] = success_report(energies, A, args.steps, E, ms_per_step)
+        # the paper's GbSB (x coupling) on the exact FX32 tensor-core path
+        t2, km2, kn2, e2, _ = timed_runs("gbsb", "fx32", 2, 1, 7000)
+        fx_ms = sum(t2) / len(t2)
+        out["gbsb_fx32"] = {"value": N_SPINS * R_REPLICAS * M_STEPS / (fx_ms / 1e3),
+                            "ms_per_step": fx_ms, "avg_launch_us": 1e3 * km2 / kn2,
+                            "tensor_frac_bf16": (4 * 2.0 * N_SPINS ** 2 * R_REPLICAS /
+                                                 (km2 / kn2 / 1e3) / 1e12) /
+                                                Pk["bf16_tflops_sustained"],
+                            "success": success_report(e2, A, 2, E, fx_ms)}
+        # the plain FP32 form, same workload (one run)
+        t3, km3, kn3, e3, _ = timed_runs("gdsb", "fp32", 1, 1, 9000)
+        out["plain_fp32"] = {"value": N_SPINS * R_REPLICAS * M_STEPS / (t3[0] / 1e3),
+                             "ms_per_step": t3[0], "avg_launch_us": 1e3 * km3 / kn3}
+        out["fused_vs_plain"] = value / world / out["plain_fp32"]["value"]
+        out["e2e"] = e2e_leg(gsb, J, c, A, max(1, min(args.steps, 3)))
+    if rank == 0 and "e2e" not in out:
+        out["e2e"] = e2e_leg(gsb, J, c, A, 1)
+    if rank == 0:
+        v, cores, sample, _ = oracle_sample()
+        out["cpu_baseline"] = {"value": v, "unit": "spin-updates/s", "cores": cores,
+                               "kind": "oracle", "sample": sample}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def success_report(energies, A, runs, E_target, run_ms):
+    """P_S per control strength against the oracle target energy, with the 99 %
+    Clopper-Pearson interval, and TTS99 for a batch of the 128 replicas of
+    that strength: P_batch = 1 - (1 - P_S)^128, TTS = T log(0.01)/log(1 - P_batch)
+    (Sec. VI), T = run time (all 8 strengths share one run)."""
+    import numpy as np
+    import oracle as O
+    rep = {"target_E": E_target, "runs": runs}
+    if E_target is None:
+        rep["note"] = "no target file"
+        return rep
+    A_all = np.tile(A, runs)
+    per = []
+    for a in A_VALUES:
+        e = energies[A_all == np.float32(a)]
+        k = int(np.sum(e <= E_target + 1e-9))
+        n = len(e)
+        ps = k / n
+        lo, hi = O.clopper_pearson(k, n, 0.99)
+        pb = 1.0 - (1.0 - ps) ** (R_REPLICAS // len(A_VALUES))
+        tts = O.tts(pb, run_ms / 1e3)
+        per.append({"A": a, "P_S": ps, "P_S_ci99": [lo, hi], "n": n,
+                    "mean_E": float(np.mean(e)), "min_E": float(np.min(e)),
+                    "TTS99_s": tts if math.isfinite(tts) else None})
+    rep["per_A"] = per
+    return rep
+
+
+def e2e_leg(gsb, J, c, A, K):
+    """Same metric through the public C ABI with host buffers: create the
+    problem from host J (int8), run, read best spins / energies / cuts back."""
+    import numpy as np
+    times = []
+    for k in range(K):
+        t = time.perf_counter()
+        P = gsb.Problem.dense(J)
+        run = P.run("gdsb", M=M_STEPS, R=R_REPLICAS, c=c, dt=DT, A=A, seed=5000 + k,
+                    precision="fp8")
+        b = run.best()
+        run.close()
+        P.close()
+        times.append(time.perf_counter() - t)
+    el = sum(times) / K
+    h2d = J.nbytes + A.nbytes
+    d2h = b["s"].nbytes + b["E"].nbytes + b["cut"].nbytes + b["step"].nbytes
+    return {"value": N_SPINS * R_REPLICAS * M_STEPS / el, "unit": "spin-updates/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": el * 1e3, "how": "host wall clock around gsb_create + gsb_run + gsb_best"}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    per_step = []
+    info = None
+    for w in range(args.warmup + args.steps):
+        v, cores, sample, el = oracle_sample(seconds_hint=8.0)
+        if w >= args.warmup:
+            per_step.append((v, el))
+            info = (cores, sample)
+    value = statistics.mean(v for v, _ in per_step)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * statistics.mean(el for _, el in per_step),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "N": N_SPINS, "R": R_REPLICAS,
+                                           "M": M_STEPS, "reference": "FP64 CPU oracle"},
+           "cpu_baseline": {"kind": "oracle", "cores": info[0], "sample": info[1],
+                            "value": value, "unit": "spin-updates/s"},
+           "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if world > 1:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        ids = vis.split(",") if vis else [str(i) for i in range(world)]
+        os.environ["CUDA_VISIBLE_DEVICES"] = ids[local % len(ids)]
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+    else:
+        gpu_arm(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

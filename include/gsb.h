@@ -115,7 +115,8 @@ typedef struct gsb_params {
     uint32_t flags;           /* GSB_RUN_* */
 } gsb_params;
 
-#define GSB_RUN_DEFER 0x1u /* gsb_run sets up the state but advances no step */
+#define GSB_RUN_DEFER 0x1u   /* gsb_run sets up the state but advances no step */
+#define GSB_RUN_PROFILE 0x2u /* record CUDA events around every launch of the step kernel */
 
 /* Create a problem from a coupling matrix (Eq. 1). The library copies J into
  * the device formats its kernels need (FP32, e4m3, bf16 and/or CSR), padded
@@ -143,6 +144,17 @@ gsb_status gsb_run(gsb_problem* problem, const gsb_params* params, gsb_run_state
 /* Advance a run by nsteps (<= M - steps already done) on its stream. Runs
  * split into several calls follow the same trajectory as one call. */
 gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps);
+
+/* Start the same run again from step 0 with another seed, reusing its device
+ * buffers: x(0), y(0) drawn as in gsb_run (explicit x0/y0 are not kept),
+ * p(0) = 1, best states cleared. flags: GSB_RUN_DEFER as in gsb_params.
+ * Enqueued on the run's stream; allocates nothing. */
+gsb_status gsb_run_restart(gsb_run_state* run, uint64_t seed, uint32_t flags);
+
+/* With GSB_RUN_PROFILE: total device time (ms, from CUDA events on the run's
+ * stream) and number of launches of the run's step kernel since the last
+ * gsb_run / gsb_run_restart. Blocks on the run's stream. */
+gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches);
 
 /* Best state per replica (host outputs, each nullable): spins R x N int8,
  * energies (Eq. 1), cut values (W_tot - E)/2 with W = -J (Sec. III), and the

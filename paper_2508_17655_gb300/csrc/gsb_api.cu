@@ -249,6 +249,7 @@ void free_run(gsb_run_state* r) {
     cudaFree(r->best_s);
     cudaFree(r->flag);
     cudaFree(r->status);
+    for (cudaEvent_t e : r->prof_events) cudaEventDestroy(e);
     delete r;
 }
 
@@ -268,6 +269,21 @@ gsb_status evaluate(gsb_run_state* run, int step) {
     return launch_best_keep(run, step);
 }
 
+// Clear the status word and the best-state record; zero the profile.
+gsb_status reset_bookkeeping(gsb_run_state* run) {
+    cudaStream_t s = run->stream;
+    GSB_CUDA_TRY(cudaMemsetAsync(run->status, 0, sizeof(int), s));
+    GSB_CUDA_TRY(cudaMemsetAsync(run->best_s, 0, (size_t)run->Np * run->Rp, s));
+    k_fill_f64<<<(run->Rp + 255) / 256, 256, 0, s>>>(run->best_e,
+                                                     std::numeric_limits<double>::infinity(),
+                                                     run->Rp);
+    k_fill_i32<<<(run->Rp + 255) / 256, 256, 0, s>>>(run->best_step, -1, run->Rp);
+    GSB_LAUNCH_CHECK("k_fill");
+    run->prof_used = 0;
+    run->steps_done = 0;
+    return GSB_OK;
+}
+
 bool is_eval_step(const gsb_run_state* run, int step) {
     const int k = run->params.eval_every;
     return step == run->params.M || (k > 0 && step % k == 0);
@@ -281,6 +297,26 @@ float p_shared_at(const gsb_run_state* run, int step) {
 }
 
 }  // namespace
+
+gsb_status prof_begin(gsb_run_state* run) {
+    if (!(run->params.flags & GSB_RUN_PROFILE)) return GSB_OK;
+    if (run->prof_used + 2 > run->prof_events.size()) {
+        for (int k = 0; k < 2; ++k) {
+            cudaEvent_t e;
+            GSB_CUDA_TRY(cudaEventCreate(&e));
+            run->prof_events.push_back(e);
+        }
+    }
+    GSB_CUDA_TRY(cudaEventRecord(run->prof_events[run->prof_used], run->stream));
+    return GSB_OK;
+}
+
+gsb_status prof_end(gsb_run_state* run) {
+    if (!(run->params.flags & GSB_RUN_PROFILE)) return GSB_OK;
+    GSB_CUDA_TRY(cudaEventRecord(run->prof_events[run->prof_used + 1], run->stream));
+    run->prof_used += 2;
+    return GSB_OK;
+}
 
 bool run_is_eval_step(const gsb_run_state* run, int step) { return is_eval_step(run, step); }
 float run_p_shared(const gsb_run_state* run, int step) { return p_shared_at(run, step); }
@@ -479,13 +515,7 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
             return fail(cuda_error(cudaGetLastError(), "copy A"));
     }
     if (Q.schedule) run->sched_host.assign(Q.schedule, Q.schedule + Q.M + 1);
-    GSB_CUDA_TRY(cudaMemsetAsync(run->status, 0, sizeof(int), s));
-    GSB_CUDA_TRY(cudaMemsetAsync(run->best_s, 0, nst, s));
-    k_fill_f64<<<(run->Rp + 255) / 256, 256, 0, s>>>(run->best_e,
-                                                     std::numeric_limits<double>::infinity(),
-                                                     run->Rp);
-    k_fill_i32<<<(run->Rp + 255) / 256, 256, 0, s>>>(run->best_step, -1, run->Rp);
-    count_launch(2);
+    if ((st = reset_bookkeeping(run))) return fail(st);
     // initial state
     float *x0d = nullptr, *y0d = nullptr;
     const size_t nrm = (size_t)Q.R * P->N;
@@ -540,9 +570,11 @@ gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps) {
         sc.c = run->c;
         sc.dt = run->dt;
         sc.p_next = p_shared_at(run, m + 1);
-        gsb_status st = run->path == kPathCsr ? launch_csr_step(run, sc)
-                                              : launch_dense_f32_step(run, sc);
+        gsb_status st = prof_begin(run);
         if (st != GSB_OK) return st;
+        st = run->path == kPathCsr ? launch_csr_step(run, sc) : launch_dense_f32_step(run, sc);
+        if (st != GSB_OK) return st;
+        if ((st = prof_end(run)) != GSB_OK) return st;
         run->steps_done = m + 1;
         if (is_eval_step(run, m + 1)) {
             if ((st = evaluate(run, m + 1)) != GSB_OK) return st;
@@ -685,6 +717,32 @@ gsb_status gsb_energy(gsb_problem* P, int32_t R, const int8_t* spins, double* en
     cudaFree(xd);
     cudaFree(acc);
     return st;
+}
+
+gsb_status gsb_run_restart(gsb_run_state* run, uint64_t seed, uint32_t flags) {
+    if (!run) return set_error(GSB_EINVAL, "run is NULL");
+    run->params.seed = seed;
+    gsb_status st = reset_bookkeeping(run);
+    if (st != GSB_OK) return st;
+    if ((st = launch_init_state(run, nullptr, nullptr)) != GSB_OK) return st;
+    if (run->path == kPathTcFp8 || run->path == kPathTcFx32)
+        if ((st = tc_prepare(run)) != GSB_OK) return st;
+    if (flags & GSB_RUN_DEFER) return GSB_OK;
+    return gsb_run_steps(run, run->params.M);
+}
+
+gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches) {
+    if (!run) return set_error(GSB_EINVAL, "run is NULL");
+    GSB_CUDA_TRY(cudaStreamSynchronize(run->stream));
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < run->prof_used; k += 2) {
+        float t = 0.f;
+        GSB_CUDA_TRY(cudaEventElapsedTime(&t, run->prof_events[k], run->prof_events[k + 1]));
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = (int64_t)(run->prof_used / 2);
+    return GSB_OK;
 }
 
 gsb_status gsb_run_destroy(gsb_run_state* run) {

@@ -100,6 +100,9 @@ struct gsb_run_state {
     int* status = nullptr;      // device status word
     void* tc = nullptr;         // tcgen05 path state (tensor maps, barriers)
     std::vector<float> sched_host;  // caller schedule p(t_m), m = 0..M (bSB / dSB)
+    // GSB_RUN_PROFILE: event pairs around step-kernel launches
+    std::vector<cudaEvent_t> prof_events;
+    size_t prof_used = 0;
 };
 
 namespace gsb {
@@ -147,9 +150,13 @@ gsb_status compute_lambda(gsb_problem* prob, cudaStream_t s);
 // tcgen05 path
 bool tc_available();
 gsb_status tc_setup(gsb_run_state* run);
+gsb_status tc_prepare(gsb_run_state* run);
 gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps);
 gsb_status tc_energy(gsb_run_state* run);
 void tc_free(gsb_run_state* run);
+// GSB_RUN_PROFILE bracketing of a step-kernel launch
+gsb_status prof_begin(gsb_run_state* run);
+gsb_status prof_end(gsb_run_state* run);
 // host loop helpers shared with the tcgen05 path
 bool run_is_eval_step(const gsb_run_state* run, int step);
 float run_p_shared(const gsb_run_state* run, int step);

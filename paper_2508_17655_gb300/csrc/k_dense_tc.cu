@@ -361,6 +361,12 @@ gsb_status tc_setup(gsb_run_state* run) {
                                run->Np, 4 * (uint64_t)run->Rp)))
                 return st;
     }
+    return tc_prepare(run);
+}
+
+// V(t_0) from the current x (after the initial state is drawn).
+gsb_status tc_prepare(gsb_run_state* run) {
+    TcState* T = (TcState*)run->tc;
     dim3 grid(run->Np / 32, run->Rp / 32), block(32, 8);
     if (T->kind == 0)
         k_tc_prep<0><<<grid, block, 0, run->stream>>>(run->x[0], run->v8[0], run->Np, run->Rp);
@@ -376,7 +382,8 @@ gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps) {
     for (int m = m0; m < m0 + nsteps; ++m) {
         const float p_shared = run_p_shared(run, m + 1);
         const float inv_rem = 1.0f / (float)(run->params.M - m);
-        gsb_status st;
+        gsb_status st = prof_begin(run);
+        if (st != GSB_OK) return st;
         if (T->kind == 0)
             st = run->control ? launch_step<0, true>(run, T, p_shared, inv_rem)
                               : launch_step<0, false>(run, T, p_shared, inv_rem);
@@ -384,6 +391,7 @@ gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps) {
             st = run->control ? launch_step<1, true>(run, T, p_shared, inv_rem)
                               : launch_step<1, false>(run, T, p_shared, inv_rem);
         if (st != GSB_OK) return st;
+        if ((st = prof_end(run)) != GSB_OK) return st;
         run->steps_done = m + 1;
         if (run_is_eval_step(run, m + 1))
             if ((st = run_evaluate(run, m + 1)) != GSB_OK) return st;

@@ -19,7 +19,7 @@ BSB, GBSB, DSB, GDSB = range(4)
 PREC_AUTO, PREC_FP32, PREC_FP8, PREC_FX32 = range(4)
 J_DENSE_I8, J_DENSE_F32, J_CSR_F32 = range(3)
 CREATE_DEVICE_INPUT, CREATE_NO_VALIDATE = 0x1, 0x2
-RUN_DEFER = 0x1
+RUN_DEFER, RUN_PROFILE = 0x1, 0x2
 
 VARIANT = {"bsb": BSB, "gbsb": GBSB, "dsb": DSB, "gdsb": GDSB}
 PRECISION = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp8": PREC_FP8, "fx32": PREC_FX32}
@@ -99,6 +99,11 @@ def _declare(L):
     L.gsb_energy.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int8),
                              ctypes.POINTER(ctypes.c_double), _vp]
     L.gsb_energy.restype = st
+    L.gsb_run_restart.argtypes = [_vp, ctypes.c_uint64, ctypes.c_uint32]
+    L.gsb_run_restart.restype = st
+    L.gsb_kernel_time.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_int64)]
+    L.gsb_kernel_time.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
     L.gsb_run_destroy.restype = st
     L.gsb_last_error.argtypes = []
@@ -184,11 +189,11 @@ class Problem:
 
     def run(self, variant, M, R, *, c=0.0, dt=0.0, A=0.0, seed=0, precision="auto",
             eval_every=0, x0=None, y0=None, y0_uniform=False, x0_range=0.0, schedule=None,
-            steps_per_launch=0, defer=False, stream=None):
+            steps_per_launch=0, defer=False, profile=False, stream=None):
         return Run(self, variant, M, R, c=c, dt=dt, A=A, seed=seed, precision=precision,
                    eval_every=eval_every, x0=x0, y0=y0, y0_uniform=y0_uniform,
                    x0_range=x0_range, schedule=schedule, steps_per_launch=steps_per_launch,
-                   defer=defer, stream=stream)
+                   defer=defer, profile=profile, stream=stream)
 
     def close(self):
         if self.handle:
@@ -206,7 +211,7 @@ class Run:
     """One GbSB / bSB / dSB run of R replicas over M steps (Sec. II)."""
 
     def __init__(self, problem, variant, M, R, *, c, dt, A, seed, precision, eval_every, x0, y0,
-                 y0_uniform, x0_range, schedule, steps_per_launch, defer, stream):
+                 y0_uniform, x0_range, schedule, steps_per_launch, defer, profile, stream):
         self.problem = problem
         self.R = int(R)
         self.N = problem.N
@@ -242,7 +247,7 @@ class Run:
             ya = np.ascontiguousarray(y0, dtype=np.float32)
             keep.append(ya)
             prm.y0 = _p(ya, ctypes.c_float)
-        prm.flags = RUN_DEFER if defer else 0
+        prm.flags = (RUN_DEFER if defer else 0) | (RUN_PROFILE if profile else 0)
         out = _vp()
         _check(lib().gsb_run(problem.handle, ctypes.byref(prm), ctypes.byref(out),
                              _stream_handle(stream)))
@@ -250,6 +255,16 @@ class Run:
 
     def steps(self, n):
         _check(lib().gsb_run_steps(self.handle, int(n)))
+
+    def restart(self, seed, defer=False):
+        _check(lib().gsb_run_restart(self.handle, int(seed), RUN_DEFER if defer else 0))
+
+    def kernel_time(self):
+        """(total ms, launches) of the step kernel since the last (re)start."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(lib().gsb_kernel_time(self.handle, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def best(self):
         spins = np.zeros((self.R, self.N), dtype=np.int8)
