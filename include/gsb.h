@@ -109,7 +109,9 @@ typedef struct gsb_params {
     int32_t y0_uniform;       /* 0: y(0) = 0 (App. A); 1: y(0) uniform in [-x0_range, x0_range) */
     int32_t eval_every;       /* 0: evaluate the energy at t_M only (Sec. III); k > 0: also
                                  at every step that is a multiple of k */
-    int32_t steps_per_launch; /* 0: automatic; else steps fused per launch on paths that fuse */
+    int32_t steps_per_launch; /* 0: as many as possible (up to the next energy evaluation);
+                                 1: one step per launch; k: at most k steps per launch, on
+                                 the paths that fuse steps (the persistent FP8 kernel) */
     const float* x0;          /* host, R x N, or NULL: explicit x(0) instead of the Philox draw */
     const float* y0;          /* host, R x N, or NULL: explicit y(0) */
     uint32_t flags;           /* GSB_RUN_* */
@@ -152,9 +154,11 @@ gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps);
 gsb_status gsb_run_restart(gsb_run_state* run, uint64_t seed, uint32_t flags);
 
 /* With GSB_RUN_PROFILE: total device time (ms, from CUDA events on the run's
- * stream) and number of launches of the run's step kernel since the last
- * gsb_run / gsb_run_restart. Blocks on the run's stream. */
-gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches);
+ * stream) of the run's step-kernel launches since the last gsb_run /
+ * gsb_run_restart, how many launches that was, and how many time steps they
+ * covered (a persistent launch covers many). Each output is nullable. Blocks
+ * on the run's stream. */
+gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches, int64_t* steps);
 
 /* Best state per replica (host outputs, each nullable): spins R x N int8,
  * energies (Eq. 1), cut values (W_tot - E)/2 with W = -J (Sec. III), and the

@@ -280,6 +280,7 @@ gsb_status reset_bookkeeping(gsb_run_state* run) {
     k_fill_i32<<<(run->Rp + 255) / 256, 256, 0, s>>>(run->best_step, -1, run->Rp);
     GSB_LAUNCH_CHECK("k_fill");
     run->prof_used = 0;
+    run->prof_steps = 0;
     run->steps_done = 0;
     return GSB_OK;
 }
@@ -311,10 +312,11 @@ gsb_status prof_begin(gsb_run_state* run) {
     return GSB_OK;
 }
 
-gsb_status prof_end(gsb_run_state* run) {
+gsb_status prof_end(gsb_run_state* run, int steps) {
     if (!(run->params.flags & GSB_RUN_PROFILE)) return GSB_OK;
     GSB_CUDA_TRY(cudaEventRecord(run->prof_events[run->prof_used + 1], run->stream));
     run->prof_used += 2;
+    run->prof_steps += steps;
     return GSB_OK;
 }
 
@@ -574,7 +576,7 @@ gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps) {
         if (st != GSB_OK) return st;
         st = run->path == kPathCsr ? launch_csr_step(run, sc) : launch_dense_f32_step(run, sc);
         if (st != GSB_OK) return st;
-        if ((st = prof_end(run)) != GSB_OK) return st;
+        if ((st = prof_end(run, 1)) != GSB_OK) return st;
         run->steps_done = m + 1;
         if (is_eval_step(run, m + 1)) {
             if ((st = evaluate(run, m + 1)) != GSB_OK) return st;
@@ -731,7 +733,7 @@ gsb_status gsb_run_restart(gsb_run_state* run, uint64_t seed, uint32_t flags) {
     return gsb_run_steps(run, run->params.M);
 }
 
-gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches) {
+gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches, int64_t* steps) {
     if (!run) return set_error(GSB_EINVAL, "run is NULL");
     GSB_CUDA_TRY(cudaStreamSynchronize(run->stream));
     double total = 0.0;
@@ -742,6 +744,7 @@ gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches) {
     }
     if (ms) *ms = total;
     if (launches) *launches = (int64_t)(run->prof_used / 2);
+    if (steps) *steps = run->prof_steps;
     return GSB_OK;
 }
 

@@ -103,6 +103,7 @@ struct gsb_run_state {
     // GSB_RUN_PROFILE: event pairs around step-kernel launches
     std::vector<cudaEvent_t> prof_events;
     size_t prof_used = 0;
+    int64_t prof_steps = 0;  // time steps covered by the recorded launches
 };
 
 namespace gsb {
@@ -156,7 +157,7 @@ gsb_status tc_energy(gsb_run_state* run);
 void tc_free(gsb_run_state* run);
 // GSB_RUN_PROFILE bracketing of a step-kernel launch
 gsb_status prof_begin(gsb_run_state* run);
-gsb_status prof_end(gsb_run_state* run);
+gsb_status prof_end(gsb_run_state* run, int steps);
 // host loop helpers shared with the tcgen05 path
 bool run_is_eval_step(const gsb_run_state* run, int step);
 float run_p_shared(const gsb_run_state* run, int step);

@@ -252,6 +252,230 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form of the FP8 step: one cooperative launch runs many steps.
+// Each CTA keeps its tile's x, y (and p) in TMEM next to the accumulator
+// (columns [0,128) F, [128,256) x, [256,384) y, [384,512) p), so a step moves
+// no state through global memory: only the 16 KB of the next V tile leave the
+// SM. The CTAs that share a replica block (one grid column) then meet at a
+// counter in global memory (release add / acquire poll, bounded) before any
+// of them loads that block's next V. J does not change, so the producer issues
+// the first ring slots' J tiles before it waits.
+//
+// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2-9 epilogue (warp w
+// reads TMEM lanes 32 (w % 4).., columns 64 ((w - 2) / 4) .. +63).
+constexpr int kThreadsP = 320;
+constexpr int kEpiThreadsP = 256;
+constexpr int kStagesP = 6;
+
+__host__ __device__ constexpr int smem_bytes_persist() {
+    return 1024 + kStagesP * 2 * BM * KB + 256 + BN * 4;
+}
+
+template <bool CONTROL>
+__global__ void __launch_bounds__(kThreadsP, 1)
+    k_tc_persist(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmV0,
+                 const __grid_constant__ CUtensorMap tmV1, int Np, int Rp, float* __restrict__ x,
+                 float* __restrict__ y, float* __restrict__ p, const float* __restrict__ A,
+                 uint8_t* __restrict__ v0, uint8_t* __restrict__ v1, float c, float dt,
+                 const float* __restrict__ p_sched, int M, int m0, int nsteps,
+                 uint32_t* __restrict__ counters, int* status) {
+    constexpr int S = kStagesP;
+    constexpr int SA = BM * KB, SB = BN * KB;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + S * SA;
+    uint64_t* full = (uint64_t*)(sB + S * SB);
+    uint64_t* empty = full + S;
+    uint64_t* accf = empty + S;
+    uint64_t* acce = accf + 1;
+    uint32_t* tmem_slot = (uint32_t*)(acce + 1);
+    float* sAv = (float*)(smem + S * (SA + SB) + 256);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
+    const int nk = Np / KB;
+    const uint32_t nI = gridDim.y;
+    uint32_t* ctr = counters + blockIdx.x;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_init(acce, 1);
+        tmem_slot[1] = 0u;  // epilogue abort flag
+        fence_barrier_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmV0);
+        tma_prefetch_desc(&tmV1);
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + BN) sAv[threadIdx.x - 64] = A[r0 + threadIdx.x - 64];
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;  // ring slot counter across steps
+            const int pre = nk < S ? nk : S;
+            bool ok = true;
+            for (int s = 0; s < nsteps && ok; ++s) {
+                const CUtensorMap* tv = ((m0 + s) & 1) ? &tmV1 : &tmV0;
+                // J slices for the first ring slots: independent of the other CTAs
+                for (int kc = 0; kc < pre && ok; ++kc) {
+                    const uint32_t gg = g + kc, st = gg % S, ph = (gg / S) & 1u;
+                    if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) ok = false;
+                    if (!ok) break;
+                    mbar_arrive_expect_tx(&full[st], SA + SB);
+                    tma_load_2d(sA + st * SA, &tmA, &full[st], kc * KB, i0);
+                }
+                if (!ok) break;
+                // V of this step is complete once every CTA of the replica block published it
+                if (s > 0) {
+                    if (!wait_counter(ctr, nI * (uint32_t)s, status)) break;
+                    fence_proxy_async();
+                }
+                for (int kc = 0; kc < pre; ++kc) {
+                    const uint32_t st = (g + kc) % S;
+                    tma_load_2d(sB + st * SB, tv, &full[st], kc * KB, r0);
+                }
+                for (int kc = pre; kc < nk && ok; ++kc) {
+                    const uint32_t gg = g + kc, st = gg % S, ph = (gg / S) & 1u;
+                    if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) ok = false;
+                    if (!ok) break;
+                    mbar_arrive_expect_tx(&full[st], SA + SB);
+                    tma_load_2d(sA + st * SA, &tmA, &full[st], kc * KB, i0);
+                    tma_load_2d(sB + st * SB, tv, &full[st], kc * KB, r0);
+                }
+                g += nk;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_make(0u, BM, BN);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int s = 0; s < nsteps && ok; ++s) {
+                if (s > 0 && !mbar_wait(acce, (uint32_t)(s - 1) & 1u, status)) break;
+                fence_after_sync();
+                for (int kc = 0; kc < nk; ++kc, ++g) {
+                    const uint32_t st = g % S, ph = (g / S) & 1u;
+                    if (!mbar_wait(&full[st], ph, status)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+                    const uint32_t a0 = smem_u32(sA + st * SA), b0 = smem_u32(sB + st * SB);
+#pragma unroll
+                    for (int k = 0; k < KB / 32; ++k)
+                        mma_f8f6f4(tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
+                                   (kc | k) != 0);
+                    mma_commit(&empty[st]);
+                }
+                if (ok) mma_commit(accf);
+            }
+        }
+    } else {
+        const int ew = warp - 2;
+        const int quarter = warp & 3;
+        const int c0 = (ew >> 2) * 64;
+        const int i = i0 + quarter * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+        // state of this thread's spin, columns c0 .. c0+63, into TMEM
+#pragma unroll 1
+        for (int cb = c0; cb < c0 + 64; cb += 16) {
+            const size_t o = (size_t)i * Rp + r0 + cb;
+            float v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = x[o + k];
+            tmem_st16(tl + 128 + cb, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = y[o + k];
+            tmem_st16(tl + 256 + cb, v);
+            if (CONTROL) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) v[k] = p[o + k];
+                tmem_st16(tl + 384 + cb, v);
+            }
+        }
+        tmem_wait_st();
+        // Every epilogue warp passes the same named barriers: a timeout in one of
+        // them is published in *abort and all of them leave after the barrier.
+        volatile uint32_t* abort_flag = tmem_slot + 1;
+        for (int s = 0; s < nsteps; ++s) {
+            const int m = m0 + s;
+            bool ok = *abort_flag == 0u;
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(accf, (uint32_t)s & 1u, status));
+            if (!ok) {
+                *abort_flag = 1u;
+                named_barrier_sync(1, kEpiThreadsP);
+                break;
+            }
+            fence_after_sync();
+            const float inv_rem = __frcp_rn((float)(M - m));
+            const float p_shared = CONTROL ? 0.f : p_sched[s];
+            uint8_t* vn = (m & 1) ? v0 : v1;  // V(t_{m+1}) goes to buffer (m + 1) & 1
+#pragma unroll 1
+            for (int cb = c0; cb < c0 + 64; cb += 16) {
+                float f[16], xs[16], ys[16], ps[16];
+                tmem_ld16(tl + cb, f);
+                tmem_ld16(tl + 128 + cb, xs);
+                tmem_ld16(tl + 256 + cb, ys);
+                if (CONTROL) tmem_ld16(tl + 384 + cb, ps);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if (!CONTROL) ps[k] = 0.f;
+                    sb_update<CONTROL>(xs[k], ys[k], ps[k], f[k], CONTROL ? sAv[cb + k] : 0.f,
+                                       c, dt, p_shared, inv_rem);
+                }
+                tmem_st16(tl + 128 + cb, xs);
+                tmem_st16(tl + 256 + cb, ys);
+                if (CONTROL) tmem_st16(tl + 384 + cb, ps);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) vn[(size_t)(r0 + cb + k) * Np + i] = e4m3_sign(xs[k]);
+            }
+            tmem_wait_st();
+            fence_before_sync();
+            __threadfence();
+            fence_proxy_async();
+            named_barrier_sync(1, kEpiThreadsP);
+            if (*abort_flag) break;
+            if (ew == 0 && lane == 0) {
+                mbar_arrive(acce);
+                red_release_add(ctr, 1u);
+            }
+        }
+        // state back to global memory
+#pragma unroll 1
+        for (int cb = c0; cb < c0 + 64; cb += 16) {
+            const size_t o = (size_t)i * Rp + r0 + cb;
+            float v[16];
+            tmem_ld16(tl + 128 + cb, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) x[o + k] = v[k];
+            tmem_ld16(tl + 256 + cb, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) y[o + k] = v[k];
+            if (CONTROL) {
+                tmem_ld16(tl + 384 + cb, v);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) p[o + k] = v[k];
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // V(t_0) from x(t_0): spin-major x [Np][Rp] -> replica-major operand planes.
 template <int KIND>
 __global__ void k_tc_prep(const float* __restrict__ x, void* __restrict__ v, int Np, int Rp) {
@@ -282,6 +506,9 @@ struct TcState {
     CUtensorMap tmB[2];
     int vcur = 0;
     int kind = 0;
+    bool persistent = false;     // the cooperative multi-step kernel fits the grid
+    uint32_t* counters = nullptr;  // one per replica block
+    float* p_sched = nullptr;      // p(t_{m+1}) for m = 0..M-1 (shared schedule)
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -361,6 +588,30 @@ gsb_status tc_setup(gsb_run_state* run) {
                                run->Np, 4 * (uint64_t)run->Rp)))
                 return st;
     }
+    if (T->kind == 0) {
+        // co-residency of the whole grid (one CTA per SM) decides the persistent form
+        int dev = 0, sms = 0, per_sm = 0;
+        GSB_CUDA_TRY(cudaGetDevice(&dev));
+        GSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        auto kern = run->control ? (const void*)k_tc_persist<true> : (const void*)k_tc_persist<false>;
+        GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          smem_bytes_persist()));
+        GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsP,
+                                                                   smem_bytes_persist()));
+        const long grid = (long)(run->Rp / BN) * (run->Np / BM);
+        int coop = 0;
+        GSB_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        T->persistent = coop && per_sm >= 1 && grid <= (long)per_sm * sms &&
+                        run->params.steps_per_launch != 1;
+        if (T->persistent) {
+            GSB_CUDA_TRY(cudaMalloc(&T->counters, sizeof(uint32_t) * (run->Rp / BN)));
+            std::vector<float> ps(run->params.M);
+            for (int m = 0; m < run->params.M; ++m) ps[m] = run_p_shared(run, m + 1);
+            GSB_CUDA_TRY(cudaMalloc(&T->p_sched, sizeof(float) * run->params.M));
+            GSB_CUDA_TRY(cudaMemcpy(T->p_sched, ps.data(), sizeof(float) * run->params.M,
+                                    cudaMemcpyHostToDevice));
+        }
+    }
     return tc_prepare(run);
 }
 
@@ -377,8 +628,54 @@ gsb_status tc_prepare(gsb_run_state* run) {
     return GSB_OK;
 }
 
+// Persistent launch over steps [m0, m0 + n): cooperative, one CTA per tile.
+template <bool CONTROL>
+gsb_status launch_persist(gsb_run_state* run, TcState* T, int m0, int n) {
+    const int nrb = run->Rp / BN;
+    GSB_CUDA_TRY(cudaMemsetAsync(T->counters, 0, sizeof(uint32_t) * nrb, run->stream));
+    dim3 grid(nrb, run->Np / BM);
+    int Np = run->Np, Rp = run->Rp, M = run->params.M;
+    float c = run->c, dt = run->dt;
+    const float* ps = T->p_sched + m0;
+    void* args[] = {(void*)&T->tmA, (void*)&T->tmB[0], (void*)&T->tmB[1], &Np, &Rp,
+                    (void*)&run->x[0], (void*)&run->y, (void*)&run->p, (void*)&run->A,
+                    (void*)&run->v8[0], (void*)&run->v8[1], &c, &dt, (void*)&ps, &M, &m0, &n,
+                    (void*)&T->counters, (void*)&run->status};
+    GSB_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_tc_persist<CONTROL>, grid,
+                                             dim3(kThreadsP), args, smem_bytes_persist(),
+                                             run->stream));
+    count_launch();
+    T->vcur = (m0 + n) & 1;
+    return GSB_OK;
+}
+
 gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps) {
     TcState* T = (TcState*)run->tc;
+    if (T->persistent) {
+        // one launch per stretch of steps between energy evaluations
+        int m = m0;
+        const int end = m0 + nsteps;
+        const int spl = run->params.steps_per_launch;
+        while (m < end) {
+            int stop = end;
+            for (int k = m + 1; k <= end; ++k)
+                if (run_is_eval_step(run, k)) {
+                    stop = k;
+                    break;
+                }
+            if (spl > 0 && stop - m > spl) stop = m + spl;
+            gsb_status st = prof_begin(run);
+            if (st != GSB_OK) return st;
+            st = run->control ? launch_persist<true>(run, T, m, stop - m)
+                              : launch_persist<false>(run, T, m, stop - m);
+            if (st != GSB_OK) return st;
+            if ((st = prof_end(run, stop - m)) != GSB_OK) return st;
+            m = stop;
+            if (run_is_eval_step(run, m))
+                if ((st = run_evaluate(run, m)) != GSB_OK) return st;
+        }
+        return GSB_OK;
+    }
     for (int m = m0; m < m0 + nsteps; ++m) {
         const float p_shared = run_p_shared(run, m + 1);
         const float inv_rem = 1.0f / (float)(run->params.M - m);
@@ -391,12 +688,10 @@ gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps) {
             st = run->control ? launch_step<1, true>(run, T, p_shared, inv_rem)
                               : launch_step<1, false>(run, T, p_shared, inv_rem);
         if (st != GSB_OK) return st;
-        if ((st = prof_end(run)) != GSB_OK) return st;
-        run->steps_done = m + 1;
+        if ((st = prof_end(run, 1)) != GSB_OK) return st;
         if (run_is_eval_step(run, m + 1))
             if ((st = run_evaluate(run, m + 1)) != GSB_OK) return st;
     }
-    run->steps_done = m0;  // the caller adds nsteps
     return GSB_OK;
 }
 
@@ -406,7 +701,12 @@ gsb_status tc_energy(gsb_run_state* run) {
 }
 
 void tc_free(gsb_run_state* run) {
-    delete (TcState*)run->tc;
+    TcState* T = (TcState*)run->tc;
+    if (T) {
+        cudaFree(T->counters);
+        cudaFree(T->p_sched);
+    }
+    delete T;
     run->tc = nullptr;
 }
 

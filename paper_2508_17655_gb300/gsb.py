@@ -102,7 +102,7 @@ def _declare(L):
     L.gsb_run_restart.argtypes = [_vp, ctypes.c_uint64, ctypes.c_uint32]
     L.gsb_run_restart.restype = st
     L.gsb_kernel_time.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
-                                  ctypes.POINTER(ctypes.c_int64)]
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.gsb_kernel_time.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
     L.gsb_run_destroy.restype = st
@@ -260,11 +260,13 @@ class Run:
         _check(lib().gsb_run_restart(self.handle, int(seed), RUN_DEFER if defer else 0))
 
     def kernel_time(self):
-        """(total ms, launches) of the step kernel since the last (re)start."""
+        """(total ms, launches, steps covered) of the step kernel since the last (re)start."""
         ms = ctypes.c_double()
         n = ctypes.c_int64()
-        _check(lib().gsb_kernel_time(self.handle, ctypes.byref(ms), ctypes.byref(n)))
-        return ms.value, n.value
+        k = ctypes.c_int64()
+        _check(lib().gsb_kernel_time(self.handle, ctypes.byref(ms), ctypes.byref(n),
+                                     ctypes.byref(k)))
+        return ms.value, n.value, k.value
 
     def best(self):
         spins = np.zeros((self.R, self.N), dtype=np.int8)

@@ -333,3 +333,24 @@ def test_lambda_and_auto_parameters_match_oracle():
     n, gl, gm = gsb.Problem.csr(N, rp, col, val).info()
     assert n == N
     assert abs(gl - lmax) <= 1e-6 * abs(lmax) and abs(gm - lmin) <= 1e-6 * abs(lmin)
+
+
+@pytest.mark.parametrize("variant", ["dsb", "gdsb"])
+def test_fp8_persistent_matches_per_step_launches_bit_exact(variant):
+    """The persistent FP8 kernel (state in TMEM, many steps per launch) and the
+    one-step-per-launch FP8 kernel do the same arithmetic: identical bits."""
+    N, R, M = 300, 200, 120
+    J = I.sk_pm1(N, 41)
+    P = gsb.Problem.dense(J)
+    kw = dict(M=M, R=R, c=f32(1 / (2 * math.sqrt(N))), dt=1.25, A=0.3, seed=8, precision="fp8",
+              eval_every=25)
+    outs = []
+    for spl in (1, 0, 7):
+        run = P.run(variant, steps_per_launch=spl, **kw)
+        outs.append((run.state(), run.best()))
+    for st, b in outs[1:]:
+        for k in ("x", "y", "p"):
+            assert np.array_equal(st[k], outs[0][0][k]), k
+        assert np.array_equal(b["E"], outs[0][1]["E"])
+        assert np.array_equal(b["s"], outs[0][1]["s"])
+        assert np.array_equal(b["step"], outs[0][1]["step"])
