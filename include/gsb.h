@@ -178,6 +178,19 @@ gsb_status gsb_energy(gsb_problem* problem, int32_t R, const int8_t* spins, doub
 
 gsb_status gsb_run_destroy(gsb_run_state* run);
 
+/* Allocation-free energies, for callers that cannot call cudaMalloc / cudaFree
+ * (a steady-state loop that must not block on them, or an application whose own
+ * allocator owns the device memory). The paper has no counterpart: it is an
+ * interface variant of gsb_energy. J (device, N x N row-major float), spins
+ * (device, R x N int8 +-1) and energies (device, length R, written) belong to
+ * the caller; the kernels run on `stream`. The per-replica accumulators are a
+ * fixed array inside the library (1 <= R <= 65536; larger R gives GSB_EINVAL),
+ * one per device, shared by all calls: each call clears it first, and calls
+ * whose work overlaps on the GPU race on it. N <= 29,000. The first call on a
+ * device looks up that array's device address (once per device). */
+gsb_status gsb_energy_noalloc(const float* J, int32_t N, const int8_t* spins, int32_t R,
+                              double* energies, void* stream);
+
 /* Message for the last non-OK status returned on the calling thread. */
 const char* gsb_last_error(void);
 

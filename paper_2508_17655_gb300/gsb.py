@@ -104,6 +104,8 @@ def _declare(L):
     L.gsb_kernel_time.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.gsb_kernel_time.restype = st
+    L.gsb_energy_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp, _vp]
+    L.gsb_energy_noalloc.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
     L.gsb_run_destroy.restype = st
     L.gsb_last_error.argtypes = []
@@ -133,6 +135,14 @@ def _stream_handle(stream):
 
 def launch_count():
     return int(lib().gsb_launch_count())
+
+
+def energy_noalloc(J_ptr, N, spins_ptr, R, energies_ptr, stream=None):
+    """gsb_energy_noalloc on caller device buffers (raw pointers, e.g. from
+    torch tensors' data_ptr()): J N x N float32, spins R x N int8, energies R
+    float64. Allocates nothing on the device."""
+    _check(lib().gsb_energy_noalloc(J_ptr, int(N), spins_ptr, int(R), energies_ptr,
+                                    _stream_handle(stream)))
 
 
 class Problem:
