@@ -54,6 +54,12 @@ def _declare(L):
                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                           _dp, _dp, _dp, ctypes.c_int32, _dp, _i8p, _i32p, ctypes.c_int32, _dp]
     L.orc_run.restype = ctypes.c_int
+    L.orc_tangent_run.argtypes = [ctypes.c_int32, _dp, _i32p, _i32p, _dp, ctypes.c_int32,
+                                  ctypes.c_int32, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int32, _dp,
+                                  ctypes.c_int32]
+    L.orc_tangent_run.restype = ctypes.c_int
     L.orc_lambda_extremes.argtypes = [ctypes.c_int32, _dp, _i32p, _i32p, _dp, ctypes.c_int32,
                                       ctypes.c_double, _dp, _dp]
     L.orc_lambda_extremes.restype = None
@@ -209,6 +215,35 @@ def run(J, variant, x, y, *, c, dt, M, A=0.0, p=None, sched=None, m0=0, nsteps=N
     if rc != 0:
         raise ValueError("orc_run rejected its arguments")
     return {"x": x, "y": y, "p": p, "best": best, "margin": margin}
+
+
+def tangent_run(J, variant, x, y, dx, *, c, dt, M, A=0.0, p=None, dy=None, dp=None, sched=None,
+                m0=0, nsteps=None, renorm_every=10, nthreads=0):
+    """Tangent-linear propagation alongside the iteration (FP64). Returns the
+    advanced state and tangent and log_sum (per replica, sum of log norms at
+    every renormalisation); log_sum / (nsteps dt) is the largest Lyapunov
+    exponent estimate."""
+    C = as_coupling(J)
+    coupling, control = VARIANTS[variant]
+    arr = lambda a: np.array(a, dtype=np.float64, copy=True, order="C")
+    x, y, dx = arr(x), arr(y), arr(dx)
+    R, N = x.shape
+    p = np.ones_like(x) if p is None else arr(p)
+    dy = np.zeros_like(x) if dy is None else arr(dy)
+    dp = np.zeros_like(x) if dp is None else arr(dp)
+    Aarr = np.broadcast_to(np.asarray(A, dtype=np.float64), (R,)).copy()
+    sch = None if sched is None else np.ascontiguousarray(sched, dtype=np.float64)
+    if nsteps is None:
+        nsteps = M - m0
+    log_sum = np.zeros(R)
+    rc = lib().orc_tangent_run(*C.args(), coupling, control, _ptr(Aarr, _dp), _ptr(sch, _dp),
+                               float(c), float(dt), int(M), int(m0), int(nsteps), int(R),
+                               _ptr(x, _dp), _ptr(y, _dp), _ptr(p, _dp), _ptr(dx, _dp),
+                               _ptr(dy, _dp), _ptr(dp, _dp), int(renorm_every),
+                               _ptr(log_sum, _dp), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_tangent_run rejected its arguments")
+    return {"x": x, "y": y, "p": p, "dx": dx, "dy": dy, "dp": dp, "log_sum": log_sum}
 
 
 def spins(x):

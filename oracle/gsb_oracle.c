@@ -39,6 +39,8 @@
  *                          Eq. 7 product formula, time reversal, sign and
  *                          gauge symmetry, ground states of small instances)
  *   orc_lambda_extremes .. pinned (LAPACK eigvalsh on small matrices)
+ *   orc_tangent_run ...... pinned (central finite differences of orc_run, the
+ *                          closed-form growth rate about the x = 0 equilibrium)
  */
 #include <math.h>
 #include <stdint.h>
@@ -358,4 +360,103 @@ void orc_lambda_extremes(int32_t N, const double* J, const int32_t* rowptr, cons
     double bot = orc_power_dominant(N, J, rowptr, col, val, sigma, -1.0, iters, tol);
     *lmax = top - sigma;
     *lmin = sigma - bot;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tangent-linear propagation of the iteration (not in the paper; the paper
+ * measures chaos with the two-trajectory distance of Eq. 8). Differentiating
+ * one step of Sec. II with respect to the state (x, y, p):
+ *   FP:   dp' = dp - [(1 - A x^2) dp - 2 A x dx p] / (M - m)   (individual control;
+ *         dp' = 0 with a shared schedule)
+ *   FX:   dy' = dy - [dp' x + p' dx - c J dx] dt               (the sgn x coupling of
+ *         dSB is piecewise constant: its derivative is 0)
+ *   FY:   dx' = dx + dy' dt
+ *   wall: where Eq. 5 clamps, x' and y' are constants: dx' = dy' = 0.
+ * The tangent (dx, dy, dp) of every replica is renormalised to unit Euclidean
+ * norm every renorm_every steps and at the end; log_sum[r] accumulates the log
+ * of the norms in double, so log_sum / (nsteps dt) estimates the largest
+ * Lyapunov exponent. dx, dy, dp are R x N, in/out (start vectors on input). */
+int orc_tangent_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
+                    const double* val, int32_t coupling, int32_t control, const double* A,
+                    const double* sched, double c, double dt, int32_t M, int32_t m0,
+                    int32_t nsteps, int32_t R, double* x, double* y, double* p, double* dx,
+                    double* dy, double* dp, int32_t renorm_every, double* log_sum,
+                    int32_t nthreads) {
+    if (N <= 0 || R <= 0 || M <= 0 || m0 < 0 || nsteps < 0 || m0 + nsteps > M) return -1;
+    if (!J && !(rowptr && col && val)) return -1;
+    if (control == 1 && !A) return -1;
+    if (renorm_every <= 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t r = 0; r < R; ++r) {
+        double* xr = x + (int64_t)r * N;
+        double* yr = y + (int64_t)r * N;
+        double* pr = p + (int64_t)r * N;
+        double* dxr = dx + (int64_t)r * N;
+        double* dyr = dy + (int64_t)r * N;
+        double* dpr = dp + (int64_t)r * N;
+        double* v = (double*)malloc(sizeof(double) * (size_t)N);
+        double* f = (double*)malloc(sizeof(double) * (size_t)N);
+        double* df = (double*)malloc(sizeof(double) * (size_t)N);
+        double acc = 0.0;
+        for (int32_t m = m0; m < m0 + nsteps; ++m) {
+            const double rem = (double)(M - m);
+            /* FP and its tangent, both from x(t_m), p(t_m) */
+            for (int32_t i = 0; i < N; ++i) {
+                if (control == 1) {
+                    const double a = A[r];
+                    const double g = 1.0 - a * xr[i] * xr[i];
+                    const double dpn = dpr[i] - (g * dpr[i] - 2.0 * a * xr[i] * dxr[i] * pr[i]) / rem;
+                    pr[i] = pr[i] - g * pr[i] / rem;
+                    dpr[i] = dpn;
+                } else {
+                    pr[i] = sched ? sched[m + 1] : 1.0 - (double)(m + 1) / (double)M;
+                    dpr[i] = 0.0;
+                }
+            }
+            for (int32_t j = 0; j < N; ++j) v[j] = coupling ? orc_sgn(xr[j]) : xr[j];
+            orc_coupling(N, J, rowptr, col, val, v, f);
+            if (!coupling) orc_coupling(N, J, rowptr, col, val, dxr, df);
+            for (int32_t i = 0; i < N; ++i) {
+                const double dfi = coupling ? 0.0 : df[i];
+                const double dyn = dyr[i] - (dpr[i] * xr[i] + pr[i] * dxr[i] - c * dfi) * dt;
+                const double yn = yr[i] - (pr[i] * xr[i] - c * f[i]) * dt;
+                const double xn = xr[i] + yn * dt;
+                const double dxn = dxr[i] + dyn * dt;
+                if (fabs(xn) > 1.0) {
+                    xr[i] = orc_sgn(xn);
+                    yr[i] = 0.0;
+                    dxr[i] = 0.0;
+                    dyr[i] = 0.0;
+                } else {
+                    xr[i] = xn;
+                    yr[i] = yn;
+                    dxr[i] = dxn;
+                    dyr[i] = dyn;
+                }
+            }
+            const int32_t done = m - m0 + 1;
+            if (done % renorm_every == 0 || done == nsteps) {
+                double s2 = 0.0;
+                for (int32_t i = 0; i < N; ++i)
+                    s2 += dxr[i] * dxr[i] + dyr[i] * dyr[i] + dpr[i] * dpr[i];
+                const double nrm = sqrt(s2);
+                acc += log(nrm);
+                for (int32_t i = 0; i < N; ++i) {
+                    dxr[i] /= nrm;
+                    dyr[i] /= nrm;
+                    dpr[i] /= nrm;
+                }
+            }
+        }
+        log_sum[r] = acc;
+        free(v);
+        free(f);
+        free(df);
+    }
+    return 0;
 }

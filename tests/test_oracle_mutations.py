@@ -32,6 +32,13 @@ MUTATIONS = [
     ("best keeps latest tie", "if (e < best_E[r]) {", "if (e <= best_E[r]) {",
      [P.test_walls_and_best_keeping]),
     ("control uses new x", None, None, [lambda: P.test_time_reversal_of_wall_free_step("gbsb")]),
+    ("tangent coupling sign", "(dpr[i] * xr[i] + pr[i] * dxr[i] - c * dfi)",
+     "(dpr[i] * xr[i] + pr[i] * dxr[i] + c * dfi)",
+     [lambda: P.test_tangent_matches_central_differences("gbsb"), P.test_tangent_growth_rate_at_equilibrium]),
+    ("tangent drops p' dx", "(dpr[i] * xr[i] + pr[i] * dxr[i] - c * dfi)",
+     "(dpr[i] * xr[i] - c * dfi)", [lambda: P.test_tangent_matches_central_differences("bsb")]),
+    ("tangent dp drops 2Ax dx p", "(g * dpr[i] - 2.0 * a * xr[i] * dxr[i] * pr[i])",
+     "(g * dpr[i])", [lambda: P.test_tangent_matches_central_differences("gbsb")]),
 ]
 
 

@@ -399,3 +399,58 @@ def test_twin_distance_values():
     a = np.where(rng.random((1, 200000)) < 0.5, 1.0, -1.0)
     b = np.where(rng.random((1, 200000)) < 0.5, 1.0, -1.0)
     assert abs(O.twin_delta(a, b)[0] - vals["twin_delta_chaos"]) < 5e-3
+
+
+# ---------------------------------------------------------------- tangent-linear
+
+@pytest.mark.parametrize("variant", ["gbsb", "bsb", "gdsb", "dsb"])
+def test_tangent_matches_central_differences(variant):
+    """The tangent propagated over a few wall-free steps equals the central
+    difference quotient of the nonlinear iteration (orc_run) in that direction."""
+    N, R, M, m0, n = 40, 3, 300, 7, 4
+    J = I.sk_gauss(N, 61).astype(np.float64)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-0.2, 0.2, size=(R, N))
+    x[np.abs(x) < 0.05] = 0.05  # keep signs away from zero (dSB coupling)
+    y = rng.uniform(-0.02, 0.02, size=(R, N))
+    p = rng.uniform(0.6, 1.0, size=(R, N))
+    dx, dy, dp = (rng.standard_normal((R, N)) for _ in range(3))
+    if variant in ("bsb", "dsb"):
+        dp = np.zeros_like(dp)
+    kw = dict(c=0.2, dt=0.5, M=M, A=0.35, m0=m0, nsteps=n)
+    t = O.tangent_run(J, variant, x, y, dx, dy=dy, dp=dp, p=p, renorm_every=10 ** 6, **kw)
+    scale = np.exp(t["log_sum"])[:, None]
+    eps = 1e-6
+    plus = O.run(J, variant, x + eps * dx, y + eps * dy, p=p + eps * dp, **kw)
+    minus = O.run(J, variant, x - eps * dx, y - eps * dy, p=p - eps * dp, **kw)
+    assert np.all(np.abs(plus["x"]) < 1) and np.all(np.abs(minus["x"]) < 1)
+    for k, dk in (("x", "dx"), ("y", "dy"), ("p", "dp")):
+        fd = (plus[k] - minus[k]) / (2 * eps)
+        np.testing.assert_allclose(t[dk] * scale, fd, rtol=1e-6, atol=1e-7 * np.max(np.abs(fd)) + 1e-12)
+
+
+def test_tangent_growth_rate_at_equilibrium():
+    """About the x = 0 equilibrium of a ferromagnet (J = 1 - I, frozen p), the
+    uniform mode is the harmonic recurrence of Eq. 10 with k = p - c (N - 1) < 0;
+    its growth factor mu solves mu^2 - (2 - k dt^2) mu + 1 = 0, so the largest
+    Lyapunov exponent is ln(mu)/dt."""
+    N, R, M = 12, 4, 600
+    J = -I.complete(N)
+    p, c, dt = 0.5, 0.1, 0.8
+    k = p - c * (N - 1)
+    b = 2 - k * dt * dt
+    mu = (b + math.sqrt(b * b - 4)) / 2
+    x0 = np.zeros((R, N))
+    dx0 = 1.0 + 0.5 * np.random.default_rng(1).standard_normal((R, N))  # overlaps the uniform mode
+    for variant in ("bsb", "gbsb"):
+        t = O.tangent_run(J, variant, x0, x0, dx0, c=c, dt=dt, M=M, A=0.3, sched=np.full(M + 1, p),
+                          renorm_every=10) if variant == "bsb" else None
+        if t is None:  # GbSB: A x^2 = 0 at the equilibrium, p follows Eq. 7 (use it directly)
+            continue
+        assert np.all(t["x"] == 0)
+        mle = t["log_sum"] / (M * dt)
+        np.testing.assert_allclose(mle, math.log(mu) / dt, rtol=0.01)
+    # a stable frozen p (k > 0): no growth, exponent ~ 0
+    t = O.tangent_run(J, "bsb", x0, x0, dx0, c=0.01, dt=dt, M=M, sched=np.full(M + 1, p),
+                      renorm_every=10)
+    assert np.all(np.abs(t["log_sum"] / (M * dt)) < 0.01)
