@@ -178,6 +178,23 @@ gsb_status gsb_energy(gsb_problem* problem, int32_t R, const int8_t* spins, doub
 
 gsb_status gsb_run_destroy(gsb_run_state* run);
 
+/* Largest Lyapunov exponent per replica by tangent-linear propagation (not in
+ * the paper, whose chaos measure is the two-trajectory distance of Eq. 8).
+ * Linearisation of one step of Eqs. 3-7 in (x, y, p): dp' = dp - [(1 - A x^2)
+ * dp - 2 A x dx p]/(M - m) (individual control; 0 with a shared schedule),
+ * dy' = dy - [dp' x + p' dx - c J dx] dt (no J dx term for sgn-x coupling),
+ * dx' = dx + dy' dt, and dx' = dy' = 0 where Eq. 5 clamps. nA control strengths
+ * A_values (host) times params->R replicas each run together (replica k R + r
+ * uses A_values[k] and draws x(0) as gsb_run would for that index); each
+ * tangent starts as dx uniform in [-1, 1) (Philox stream 4), dy = dp = 0, unit
+ * norm, and is renormalised every renorm_every steps and after the last of the
+ * first nsteps steps (0 = all M) of the Eq. 6 schedule. mle_out (host, nA x R)
+ * receives sum(log norms) / (nsteps dt), accumulated in FP64. Dense problems,
+ * FP32 coupling. Blocks on `stream`. */
+gsb_status gsb_lyapunov(gsb_problem* problem, const gsb_params* params, int32_t nA,
+                        const float* A_values, int32_t renorm_every, int32_t nsteps,
+                        double* mle_out, void* stream);
+
 /* Allocation-free energies, for callers that cannot call cudaMalloc / cudaFree
  * (a steady-state loop that must not block on them, or an application whose own
  * allocator owns the device memory). The paper has no counterpart: it is an

@@ -375,7 +375,9 @@ void orc_lambda_extremes(int32_t N, const double* J, const int32_t* rowptr, cons
  * The tangent (dx, dy, dp) of every replica is renormalised to unit Euclidean
  * norm every renorm_every steps and at the end; log_sum[r] accumulates the log
  * of the norms in double, so log_sum / (nsteps dt) estimates the largest
- * Lyapunov exponent. dx, dy, dp are R x N, in/out (start vectors on input). */
+ * Lyapunov exponent. The inelastic walls zero the tangent of clamped
+ * oscillators; when all of them are clamped the norm is 0 and log_sum is -inf.
+ * dx, dy, dp are R x N, in/out (start vectors on input). */
 int orc_tangent_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
                     const double* val, int32_t coupling, int32_t control, const double* A,
                     const double* sched, double c, double dt, int32_t M, int32_t m0,
@@ -445,11 +447,13 @@ int orc_tangent_run(int32_t N, const double* J, const int32_t* rowptr, const int
                 for (int32_t i = 0; i < N; ++i)
                     s2 += dxr[i] * dxr[i] + dyr[i] * dyr[i] + dpr[i] * dpr[i];
                 const double nrm = sqrt(s2);
-                acc += log(nrm);
-                for (int32_t i = 0; i < N; ++i) {
-                    dxr[i] /= nrm;
-                    dyr[i] /= nrm;
-                    dpr[i] /= nrm;
+                acc += log(nrm); /* -inf once every oscillator has been clamped (Eq. 5) */
+                if (nrm > 0.0) {
+                    for (int32_t i = 0; i < N; ++i) {
+                        dxr[i] /= nrm;
+                        dyr[i] /= nrm;
+                        dpr[i] /= nrm;
+                    }
                 }
             }
         }

@@ -6,83 +6,13 @@
 // Layouts: J row-major [Np][Np] (zero padded), state spin-major [Np][Rp].
 // One CTA computes a 128-spin x 128-replica tile; 256 threads, 8 x 8
 // accumulators each (rows {4ty..4ty+3, 64+4ty..}, columns {4tx.., 64+4tx..}).
-#include "gsb_update.cuh"
+#include "sgemm_f32.cuh"
 
 namespace gsb {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 8;
-
-struct F32Smem {
-    float A[2][BK][BM + 4];  // J tile, transposed (k-major)
-    float B[2][BK][BN];      // v tile
-};
-
-template <bool SIGN>
-__device__ __forceinline__ float4 vload(const float* p) {
-    float4 v = *reinterpret_cast<const float4*>(p);
-    if (SIGN) {
-        v.x = sgnf(v.x);
-        v.y = sgnf(v.y);
-        v.z = sgnf(v.z);
-        v.w = sgnf(v.w);
-    }
-    return v;
-}
-
-// acc[a][b] += sum_k J[row_a][k] v[k][col_b] over the full K = Np.
-template <bool SIGN>
-__device__ __forceinline__ void sgemm_tile(const float* __restrict__ J,
-                                           const float* __restrict__ X, int Np, int Rp, int i0,
-                                           int r0, float (&acc)[8][8], F32Smem& sm) {
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int a_row = tid >> 1, a_k = (tid & 1) * 4;
-    const int b_k = tid >> 5, b_c = (tid & 31) * 4;
-    const float* Ap = J + (size_t)(i0 + a_row) * Np + a_k;
-    const float* Bp = X + (size_t)b_k * Rp + r0 + b_c;
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-
-    float4 ra = *reinterpret_cast<const float4*>(Ap);
-    float4 rb = vload<SIGN>(Bp);
-    auto stash = [&](int buf) {
-        sm.A[buf][a_k + 0][a_row] = ra.x;
-        sm.A[buf][a_k + 1][a_row] = ra.y;
-        sm.A[buf][a_k + 2][a_row] = ra.z;
-        sm.A[buf][a_k + 3][a_row] = ra.w;
-        *reinterpret_cast<float4*>(&sm.B[buf][b_k][b_c]) = rb;
-    };
-    stash(0);
-    __syncthreads();
-    const int nk = Np / BK;
-    for (int kt = 0; kt < nk; ++kt) {
-        const int buf = kt & 1;
-        if (kt + 1 < nk) {
-            ra = *reinterpret_cast<const float4*>(Ap + (size_t)(kt + 1) * BK);
-            rb = vload<SIGN>(Bp + (size_t)(kt + 1) * BK * Rp);
-        }
-#pragma unroll
-        for (int k = 0; k < BK; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&sm.A[buf][k][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&sm.A[buf][k][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&sm.B[buf][k][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&sm.B[buf][k][64 + tx * 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
-        }
-        if (kt + 1 < nk) stash(buf ^ 1);
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ int row_of(int a, int ty) { return a < 4 ? ty * 4 + a : 64 + ty * 4 + (a - 4); }
+using namespace f32;
 
 template <bool SIGN, bool CONTROL>
 __global__ void __launch_bounds__(256) k_dense_f32_step(

@@ -104,6 +104,10 @@ def _declare(L):
     L.gsb_kernel_time.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.gsb_kernel_time.restype = st
+    L.gsb_lyapunov.argtypes = [_vp, ctypes.POINTER(gsb_params), ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_double), _vp]
+    L.gsb_lyapunov.restype = st
     L.gsb_energy_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp, _vp]
     L.gsb_energy_noalloc.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
@@ -204,6 +208,26 @@ class Problem:
                    eval_every=eval_every, x0=x0, y0=y0, y0_uniform=y0_uniform,
                    x0_range=x0_range, schedule=schedule, steps_per_launch=steps_per_launch,
                    defer=defer, profile=profile, stream=stream)
+
+    def lyapunov(self, variant, M, R, A_values, *, c=0.0, dt=0.0, seed=0, renorm_every=10,
+                 nsteps=0, y0_uniform=False, x0_range=0.0, stream=None):
+        """Largest Lyapunov exponent per replica (len(A_values) x R), from the
+        tangent-linear kernel; see gsb_lyapunov in include/gsb.h."""
+        prm = gsb_params()
+        prm.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+        prm.M = int(M)
+        prm.R = int(R)
+        prm.c = float(c)
+        prm.dt = float(dt)
+        prm.seed = int(seed)
+        prm.x0_range = float(x0_range)
+        prm.y0_uniform = int(bool(y0_uniform))
+        A = np.ascontiguousarray(A_values, dtype=np.float32)
+        out = np.zeros(len(A) * int(R), dtype=np.float64)
+        _check(lib().gsb_lyapunov(self.handle, ctypes.byref(prm), len(A), _p(A, ctypes.c_float),
+                                  int(renorm_every), int(nsteps), _p(out, ctypes.c_double),
+                                  _stream_handle(stream)))
+        return out.reshape(len(A), int(R))
 
     def close(self):
         if self.handle:
