@@ -60,6 +60,11 @@ def _declare(L):
                                   _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int32, _dp,
                                   ctypes.c_int32]
     L.orc_tangent_run.restype = ctypes.c_int
+    L.orc_relaxed_energy_grad.argtypes = [ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int32,
+                                          _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, _dp, _dp, _dp, _dp,
+                                          _dp, ctypes.c_int32]
+    L.orc_relaxed_energy_grad.restype = ctypes.c_int
     L.orc_lambda_extremes.argtypes = [ctypes.c_int32, _dp, _i32p, _i32p, _dp, ctypes.c_int32,
                                       ctypes.c_double, _dp, _dp]
     L.orc_lambda_extremes.restype = None
@@ -244,6 +249,34 @@ def tangent_run(J, variant, x, y, dx, *, c, dt, M, A=0.0, p=None, dy=None, dp=No
     if rc != 0:
         raise ValueError("orc_tangent_run rejected its arguments")
     return {"x": x, "y": y, "p": p, "dx": dx, "dy": dy, "dp": dp, "log_sum": log_sum}
+
+
+def relaxed_energy(J, variant, x0, *, c, dt, M, W, A=0.0):
+    """E = -1/2 x(t_W)^T J x(t_W) after W steps from x(0) = x0, y(0) = 0,
+    p(0) = 1 (forward only, via orc_run)."""
+    J = np.asarray(J, dtype=np.float64)
+    x0 = np.asarray(x0, dtype=np.float64)
+    o = run(J, variant, x0, 0 * x0, c=c, dt=dt, M=M, A=A, nsteps=W)
+    xW = o["x"]
+    return -0.5 * np.einsum("ri,ij,rj->r", xW, J, xW), o["margin"]
+
+
+def relaxed_energy_grad(J, variant, x0, *, c, dt, M, W, A=0.0, nthreads=0):
+    """Reverse-mode gradient of the relaxed energy: (E, dE/dx0, dE/dA, dE/ddt)."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    coupling, control = VARIANTS[variant]
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    R, N = x0.shape
+    Aarr = np.broadcast_to(np.asarray(A, dtype=np.float64), (R,)).copy()
+    E, gA, gdt = np.zeros(R), np.zeros(R), np.zeros(R)
+    gx = np.zeros_like(x0)
+    rc = lib().orc_relaxed_energy_grad(N, _ptr(J, _dp), coupling, control, _ptr(Aarr, _dp),
+                                       float(c), float(dt), int(M), int(W), int(R),
+                                       _ptr(x0, _dp), _ptr(E, _dp), _ptr(gx, _dp),
+                                       _ptr(gA, _dp), _ptr(gdt, _dp), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_relaxed_energy_grad rejected its arguments")
+    return E, gx, gA, gdt
 
 
 def spins(x):

@@ -41,6 +41,8 @@
  *   orc_lambda_extremes .. pinned (LAPACK eigvalsh on small matrices)
  *   orc_tangent_run ...... pinned (central finite differences of orc_run, the
  *                          closed-form growth rate about the x = 0 equilibrium)
+ *   orc_relaxed_energy_grad pinned (central finite differences of the forward
+ *                          energy, the dot-product identity with the tangent)
  */
 #include <math.h>
 #include <stdint.h>
@@ -461,6 +463,143 @@ int orc_tangent_run(int32_t N, const double* J, const int32_t* rowptr, const int
         free(v);
         free(f);
         free(df);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Relaxed energy and its gradient by reverse-mode differentiation (not in the
+ * paper). Starting from x(0) = x0, y(0) = 0, p(0) = 1, the first W steps of an
+ * M-step run are taken (Sec. II) and E = -1/2 x(t_W)^T J x(t_W) (Eq. 1 with the
+ * continuous x in place of s). Each step is differentiated backwards in the
+ * reverse of its forward order (wall, FY, FX, JX, FP):
+ *   wall:  where clamped, x' and y' are constants: lx~ = ly~ = 0
+ *   FY:    x~ = x + y~ dt          -> lx += lx~, ly~ += lx~ dt, gdt += lx~ y~
+ *   FX:    y~ = y - (p' x - c f) dt -> ly = ly~, lp' += -ly~ x dt,
+ *                                      lx += -ly~ p' dt, lf = ly~ c dt,
+ *                                      gdt += -ly~ (p' x - c f)
+ *   JX:    f = J x (J symmetric)   -> lx += J lf   (0 for the sgn coupling)
+ *   FP:    p' = p - g p / (M - m), g = 1 - A x^2
+ *                                  -> lp = lp' (1 - g / (M - m)),
+ *                                     lg = -lp' p / (M - m), gA += -lg x^2,
+ *                                     lx += -2 A x lg
+ * with lx(t_W) = -J x(t_W). Outputs per replica: E, dE/dx0 (R x N), dE/dA,
+ * dE/ddt. All states of the window are stored (plain, memory O(W N)). */
+int orc_relaxed_energy_grad(int32_t N, const double* J, int32_t coupling, int32_t control,
+                            const double* A, double c, double dt, int32_t M, int32_t W,
+                            int32_t R, const double* x0, double* E, double* gx0, double* gA,
+                            double* gdt, int32_t nthreads) {
+    if (N <= 0 || R <= 0 || M <= 0 || W < 0 || W > M || !J) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t r = 0; r < R; ++r) {
+        const size_t sz = (size_t)N;
+        double* xs = (double*)malloc(sizeof(double) * sz * (size_t)(W + 1));
+        double* ys = (double*)malloc(sizeof(double) * sz * (size_t)(W + 1));
+        double* ps = (double*)malloc(sizeof(double) * sz * (size_t)(W + 1));
+        double* v = (double*)malloc(sizeof(double) * sz);
+        double* f = (double*)malloc(sizeof(double) * sz);
+        double* lx = (double*)malloc(sizeof(double) * sz);
+        double* ly = (double*)malloc(sizeof(double) * sz);
+        double* lp = (double*)malloc(sizeof(double) * sz);
+        double* lf = (double*)malloc(sizeof(double) * sz);
+        double* Jlf = (double*)malloc(sizeof(double) * sz);
+        const double a = control == 1 ? A[r] : 0.0;
+        for (int32_t i = 0; i < N; ++i) {
+            xs[i] = x0[(int64_t)r * N + i];
+            ys[i] = 0.0;
+            ps[i] = 1.0;
+        }
+        /* forward, storing every state */
+        for (int32_t m = 0; m < W; ++m) {
+            const double* x = xs + sz * m;
+            const double* y = ys + sz * m;
+            const double* p = ps + sz * m;
+            double* xn = xs + sz * (m + 1);
+            double* yn = ys + sz * (m + 1);
+            double* pn = ps + sz * (m + 1);
+            for (int32_t i = 0; i < N; ++i)
+                pn[i] = control == 1 ? p[i] - (1.0 - a * x[i] * x[i]) * p[i] / (double)(M - m)
+                                     : 1.0 - (double)(m + 1) / (double)M;
+            for (int32_t j = 0; j < N; ++j) v[j] = coupling ? orc_sgn(x[j]) : x[j];
+            orc_coupling_dense(N, J, v, f);
+            for (int32_t i = 0; i < N; ++i) {
+                const double yt = y[i] - (pn[i] * x[i] - c * f[i]) * dt;
+                const double xt = x[i] + yt * dt;
+                if (fabs(xt) > 1.0) {
+                    xn[i] = orc_sgn(xt);
+                    yn[i] = 0.0;
+                } else {
+                    xn[i] = xt;
+                    yn[i] = yt;
+                }
+            }
+        }
+        /* E and its adjoint seed */
+        const double* xW = xs + sz * W;
+        orc_coupling_dense(N, J, xW, f);
+        double e = 0.0;
+        for (int32_t i = 0; i < N; ++i) {
+            e += xW[i] * f[i];
+            lx[i] = -f[i];
+            ly[i] = 0.0;
+            lp[i] = 0.0;
+        }
+        E[r] = -0.5 * e;
+        double sA = 0.0, sdt = 0.0;
+        /* backward */
+        for (int32_t m = W - 1; m >= 0; --m) {
+            const double* x = xs + sz * m;
+            const double* y = ys + sz * m;
+            const double* p = ps + sz * m;
+            const double* pn = ps + sz * (m + 1);
+            const double rem = (double)(M - m);
+            for (int32_t j = 0; j < N; ++j) v[j] = coupling ? orc_sgn(x[j]) : x[j];
+            orc_coupling_dense(N, J, v, f);
+            for (int32_t i = 0; i < N; ++i) {
+                const double yt = y[i] - (pn[i] * x[i] - c * f[i]) * dt;
+                const double xt = x[i] + yt * dt;
+                const int clamped = fabs(xt) > 1.0;
+                const double lxt = clamped ? 0.0 : lx[i];
+                double lyt = clamped ? 0.0 : ly[i];
+                /* FY */
+                double lxi = lxt;
+                lyt += lxt * dt;
+                sdt += lxt * yt;
+                /* FX */
+                const double lyi = lyt;
+                double lpn = lp[i] - lyt * x[i] * dt;
+                lxi += -lyt * pn[i] * dt;
+                lf[i] = coupling ? 0.0 : lyt * c * dt;
+                sdt += -lyt * (pn[i] * x[i] - c * f[i]);
+                /* FP */
+                double lpi = lpn;
+                if (control == 1) {
+                    const double g = 1.0 - a * x[i] * x[i];
+                    lpi = lpn * (1.0 - g / rem);
+                    const double lg = -lpn * p[i] / rem;
+                    sA += -lg * x[i] * x[i];
+                    lxi += -2.0 * a * x[i] * lg;
+                }
+                lx[i] = lxi;
+                ly[i] = lyi;
+                lp[i] = lpi;
+            }
+            /* JX */
+            if (!coupling) {
+                orc_coupling_dense(N, J, lf, Jlf);
+                for (int32_t i = 0; i < N; ++i) lx[i] += Jlf[i];
+            }
+        }
+        for (int32_t i = 0; i < N; ++i) gx0[(int64_t)r * N + i] = lx[i];
+        gA[r] = sA;
+        gdt[r] = sdt;
+        free(xs); free(ys); free(ps); free(v); free(f);
+        free(lx); free(ly); free(lp); free(lf); free(Jlf);
     }
     return 0;
 }

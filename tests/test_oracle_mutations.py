@@ -37,6 +37,15 @@ MUTATIONS = [
      [lambda: P.test_tangent_matches_central_differences("gbsb"), P.test_tangent_growth_rate_at_equilibrium]),
     ("tangent drops p' dx", "(dpr[i] * xr[i] + pr[i] * dxr[i] - c * dfi)",
      "(dpr[i] * xr[i] - c * dfi)", [lambda: P.test_tangent_matches_central_differences("bsb")]),
+    ("adjoint drops J lf", "for (int32_t i = 0; i < N; ++i) lx[i] += Jlf[i];",
+     "for (int32_t i = 0; i < N; ++i) lx[i] += 0.0 * Jlf[i];",
+     [lambda: P.test_adjoint_matches_central_differences("gbsb"),
+      P.test_adjoint_dot_product_identity_with_tangent]),
+    ("adjoint dt term sign", "sdt += -lyt * (pn[i] * x[i] - c * f[i]);",
+     "sdt += lyt * (pn[i] * x[i] - c * f[i]);",
+     [lambda: P.test_adjoint_matches_central_differences("bsb")]),
+    ("adjoint control factor", "lpi = lpn * (1.0 - g / rem);", "lpi = lpn;",
+     [lambda: P.test_adjoint_matches_central_differences("gbsb")]),
     ("tangent dp drops 2Ax dx p", "(g * dpr[i] - 2.0 * a * xr[i] * dxr[i] * pr[i])",
      "(g * dpr[i])", [lambda: P.test_tangent_matches_central_differences("gbsb")]),
 ]

@@ -454,3 +454,53 @@ def test_tangent_growth_rate_at_equilibrium():
     t = O.tangent_run(J, "bsb", x0, x0, dx0, c=0.01, dt=dt, M=M, sched=np.full(M + 1, p),
                       renorm_every=10)
     assert np.all(np.abs(t["log_sum"] / (M * dt)) < 0.01)
+
+
+# ---------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("variant", ["gbsb", "bsb", "gdsb", "dsb"])
+def test_adjoint_matches_central_differences(variant):
+    """dE/dx0 (along random directions), dE/dA and dE/ddt of the relaxed energy
+    E = -1/2 x(t_W)^T J x(t_W) equal central differences of the forward
+    iteration, away from wall events and sign changes."""
+    N, R, M, W = 30, 3, 200, 25
+    J = I.sk_gauss(N, 71).astype(np.float64)
+    rng = np.random.default_rng(9)
+    x0 = rng.uniform(-0.3, 0.3, size=(R, N))
+    x0[np.abs(x0) < 0.05] = 0.05
+    c, dt, A = 0.4, 0.6, 0.3
+    E, gx, gA, gdt = O.relaxed_energy_grad(J, variant, x0, c=c, dt=dt, M=M, W=W, A=A)
+    E2, margin = O.relaxed_energy(J, variant, x0, c=c, dt=dt, M=M, W=W, A=A)
+    np.testing.assert_allclose(E, E2, rtol=1e-13)
+    ok = margin > 1e-4  # no wall test or sign within reach of the difference step
+    assert ok.sum() >= 2
+    h = 1e-6
+    u = rng.standard_normal((R, N))
+    fd_x = (O.relaxed_energy(J, variant, x0 + h * u, c=c, dt=dt, M=M, W=W, A=A)[0]
+            - O.relaxed_energy(J, variant, x0 - h * u, c=c, dt=dt, M=M, W=W, A=A)[0]) / (2 * h)
+    np.testing.assert_allclose(np.sum(gx * u, axis=1)[ok], fd_x[ok], rtol=1e-6, atol=1e-8)
+    fd_dt = (O.relaxed_energy(J, variant, x0, c=c, dt=dt + h, M=M, W=W, A=A)[0]
+             - O.relaxed_energy(J, variant, x0, c=c, dt=dt - h, M=M, W=W, A=A)[0]) / (2 * h)
+    np.testing.assert_allclose(gdt[ok], fd_dt[ok], rtol=1e-6, atol=1e-8)
+    fd_A = (O.relaxed_energy(J, variant, x0, c=c, dt=dt, M=M, W=W, A=A + h)[0]
+            - O.relaxed_energy(J, variant, x0, c=c, dt=dt, M=M, W=W, A=A - h)[0]) / (2 * h)
+    np.testing.assert_allclose(gA[ok], fd_A[ok], rtol=1e-6, atol=1e-8)
+    if variant in ("bsb", "dsb"):
+        assert np.all(gA == 0.0)
+
+
+def test_adjoint_dot_product_identity_with_tangent():
+    """<dE/dx0, u> = <dE/dx(t_W), TLM u> with dE/dx(t_W) = -J x(t_W): the
+    reverse sweep is the transpose of the tangent-linear map."""
+    N, R, M, W = 35, 4, 300, 40
+    J = I.sk_gauss(N, 72).astype(np.float64)
+    rng = np.random.default_rng(10)
+    x0 = rng.uniform(-0.2, 0.2, size=(R, N))
+    u = rng.standard_normal((R, N))
+    kw = dict(c=0.3, dt=0.5, M=M, A=0.25)
+    E, gx, _, _ = O.relaxed_energy_grad(J, "gbsb", x0, W=W, **kw)
+    t = O.tangent_run(J, "gbsb", x0, 0 * x0, u, nsteps=W, renorm_every=10 ** 6, **kw)
+    du = t["dx"] * np.exp(t["log_sum"])[:, None]
+    lhs = np.sum(gx * u, axis=1)
+    rhs = np.sum(-(t["x"] @ J) * du, axis=1)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-10)
