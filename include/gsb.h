@@ -195,6 +195,22 @@ gsb_status gsb_lyapunov(gsb_problem* problem, const gsb_params* params, int32_t 
                         const float* A_values, int32_t renorm_every, int32_t nsteps,
                         double* mle_out, void* stream);
 
+/* Gradient of the relaxed energy E = -1/2 x(t_W)^T J x(t_W) (Eq. 1 with the
+ * continuous positions; not in the paper) after the first `window` steps of an
+ * M-step run started from x(0) = x0, y(0) = 0, p(0) = 1, with respect to x0,
+ * the control strength A (Eq. 7) and the time step dt. Hand-written reverse
+ * sweep of Eqs. 3-7 (the wall of Eq. 5 passes no gradient through clamped
+ * components; the sgn coupling of dSB has none), with the forward states
+ * recomputed from checkpoints taken every ckpt_every steps. Uses params->
+ * variant, M, R, c (> 0), dt (> 0), A / A_per_replica. Device buffers owned by
+ * the caller: x0 (R x N float, replica-major), energy (R doubles, written),
+ * grad_x0 (R x N float), grad_A and grad_dt (R doubles each; nullable).
+ * Dense problems without h, FP32 arithmetic. Blocks on `stream`. */
+gsb_status gsb_relaxed_energy_grad(gsb_problem* problem, const gsb_params* params,
+                                   int32_t window, int32_t ckpt_every, const float* x0,
+                                   double* energy, float* grad_x0, double* grad_A,
+                                   double* grad_dt, void* stream);
+
 /* Allocation-free energies, for callers that cannot call cudaMalloc / cudaFree
  * (a steady-state loop that must not block on them, or an application whose own
  * allocator owns the device memory). The paper has no counterpart: it is an

@@ -63,7 +63,7 @@ def _declare(L):
     L.orc_relaxed_energy_grad.argtypes = [ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int32,
                                           _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, _dp, _dp, _dp, _dp,
-                                          _dp, ctypes.c_int32]
+                                          _dp, ctypes.c_int32, ctypes.c_int32]
     L.orc_relaxed_energy_grad.restype = ctypes.c_int
     L.orc_lambda_extremes.argtypes = [ctypes.c_int32, _dp, _i32p, _i32p, _dp, ctypes.c_int32,
                                       ctypes.c_double, _dp, _dp]
@@ -261,8 +261,9 @@ def relaxed_energy(J, variant, x0, *, c, dt, M, W, A=0.0):
     return -0.5 * np.einsum("ri,ij,rj->r", xW, J, xW), o["margin"]
 
 
-def relaxed_energy_grad(J, variant, x0, *, c, dt, M, W, A=0.0, nthreads=0):
-    """Reverse-mode gradient of the relaxed energy: (E, dE/dx0, dE/dA, dE/ddt)."""
+def relaxed_energy_grad(J, variant, x0, *, c, dt, M, W, A=0.0, nthreads=0, f32_state=False):
+    """Reverse-mode gradient of the relaxed energy: (E, dE/dx0, dE/dA, dE/ddt).
+    f32_state rounds the stored state to FP32 after every forward step."""
     J = np.ascontiguousarray(J, dtype=np.float64)
     coupling, control = VARIANTS[variant]
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
@@ -273,7 +274,8 @@ def relaxed_energy_grad(J, variant, x0, *, c, dt, M, W, A=0.0, nthreads=0):
     rc = lib().orc_relaxed_energy_grad(N, _ptr(J, _dp), coupling, control, _ptr(Aarr, _dp),
                                        float(c), float(dt), int(M), int(W), int(R),
                                        _ptr(x0, _dp), _ptr(E, _dp), _ptr(gx, _dp),
-                                       _ptr(gA, _dp), _ptr(gdt, _dp), int(nthreads))
+                                       _ptr(gA, _dp), _ptr(gdt, _dp), int(nthreads),
+                                       int(bool(f32_state)))
     if rc != 0:
         raise ValueError("orc_relaxed_energy_grad rejected its arguments")
     return E, gx, gA, gdt

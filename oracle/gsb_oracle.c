@@ -484,11 +484,15 @@ int orc_tangent_run(int32_t N, const double* J, const int32_t* rowptr, const int
  *                                     lg = -lp' p / (M - m), gA += -lg x^2,
  *                                     lx += -2 A x lg
  * with lx(t_W) = -J x(t_W). Outputs per replica: E, dE/dx0 (R x N), dE/dA,
- * dE/ddt. All states of the window are stored (plain, memory O(W N)). */
+ * dE/ddt. All states of the window are stored (plain, memory O(W N)).
+ * f32_state != 0 rounds x, y, p to FP32 after every forward step (the paper's
+ * machine keeps them in 32-bit floating point, Fig. 2 caption); arithmetic
+ * stays FP64. Tests use it to measure how much FP32 state storage alone moves
+ * E and its gradient. */
 int orc_relaxed_energy_grad(int32_t N, const double* J, int32_t coupling, int32_t control,
                             const double* A, double c, double dt, int32_t M, int32_t W,
                             int32_t R, const double* x0, double* E, double* gx0, double* gA,
-                            double* gdt, int32_t nthreads) {
+                            double* gdt, int32_t nthreads, int32_t f32_state) {
     if (N <= 0 || R <= 0 || M <= 0 || W < 0 || W > M || !J) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -536,6 +540,11 @@ int orc_relaxed_energy_grad(int32_t N, const double* J, int32_t coupling, int32_
                 } else {
                     xn[i] = xt;
                     yn[i] = yt;
+                }
+                if (f32_state) { /* the state kept in FP32 between steps */
+                    xn[i] = (double)(float)xn[i];
+                    yn[i] = (double)(float)yn[i];
+                    pn[i] = (double)(float)pn[i];
                 }
             }
         }

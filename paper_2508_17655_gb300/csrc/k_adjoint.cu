@@ -1,0 +1,384 @@
+// k_adjoint.cu -- gradient of the relaxed energy E = -1/2 x(t_W)^T J x(t_W)
+// after W steps (not in the paper) with respect to x(0), the control strength A
+// and the time step dt, by a hand-written reverse sweep with checkpointed
+// recomputation (gsb_relaxed_energy_grad).
+//
+// Forward: W steps of Sec. II (FP32 SGEMM coupling, the same update as the
+// plain form), a checkpoint of (x, y, p) every K steps. Backward, segment by
+// segment from the last: recompute the segment from its checkpoint, keeping
+// every state and the momentum before the wall test, then undo its steps in
+// reverse. One reverse step, for lx, ly, lp the adjoints of the step's outputs:
+//   wall: clamped components: lx~ = ly~ = 0; else lx~ = lx, ly~ = ly
+//   FY  (x~ = x + y~ dt):          ly~ += lx~ dt,   gdt += lx~ y~
+//   FX  (y~ = y - (p' x - c f) dt): ly = ly~, lp' = lp - ly~ x dt,
+//                                   lx = lx~ - ly~ p' dt, lf = ly~ c dt,
+//                                   gdt -= ly~ (p' x - c f) = ly~ (y~ - y) / dt
+//   JX  (f = J x, J symmetric):     lx += J lf  (no term for the sgn coupling)
+//   FP  (p' = p - g p / (M - m), g = 1 - A x^2):
+//                                   lp = lp' (1 - g / (M - m)), lg = -lp' p / (M - m),
+//                                   gA -= lg x^2, lx -= 2 A x lg
+// Each reverse step is an elementwise pass writing lf, then an SGEMM J lf whose
+// epilogue finishes the step and reduces gA, gdt per replica.
+#include <vector>
+
+#include "sgemm_f32.cuh"
+
+namespace gsb {
+
+namespace {
+
+using namespace f32;
+
+// One forward step that also records y~ (the momentum before the wall test).
+template <bool SIGN, bool CONTROL>
+__global__ void __launch_bounds__(256) k_adj_fwd(const float* __restrict__ J, int Np, int Rp,
+                                                 const float* __restrict__ x, const float* __restrict__ y,
+                                                 const float* __restrict__ p, float* __restrict__ xn,
+                                                 float* __restrict__ yn, float* __restrict__ pn,
+                                                 float* __restrict__ yt_out,
+                                                 const float* __restrict__ A, float c, float dt,
+                                                 float p_shared, float inv_rem) {
+    __shared__ __align__(16) F32Smem sm;
+    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
+    float acc[8][8];
+    sgemm_tile<SIGN>(J, x, Np, Rp, i0, r0, acc, sm);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int cols[2] = {r0 + tx * 4, r0 + 64 + tx * 4};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const size_t rowoff = (size_t)(i0 + row_of(a, ty)) * Rp;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const size_t o = rowoff + cols[h] + q;
+                const float xo = x[o];
+                float pv = CONTROL ? p[o] : 0.f;
+                const float g = 1.f - (CONTROL ? A[cols[h] + q] : 0.f) * xo * xo;
+                const float pnv = CONTROL ? pv - g * pv * inv_rem : p_shared;
+                const float ytv = y[o] - (pnv * xo - c * acc[a][h * 4 + q]) * dt;
+                float xt = xo + ytv * dt, yv = ytv;
+                if (fabsf(xt) > 1.f) {
+                    xt = sgnf(xt);
+                    yv = 0.f;
+                }
+                xn[o] = xt;
+                yn[o] = yv;
+                if (CONTROL) pn[o] = pnv;
+                yt_out[o] = ytv;
+            }
+        }
+    }
+}
+
+// Seed: G = J x(t_W); lx = -G, ly = lp = 0, e_acc[r] += sum_i x_i G_i.
+__global__ void __launch_bounds__(256) k_adj_seed(const float* __restrict__ J, int Np, int Rp,
+                                                  const float* __restrict__ x, float* __restrict__ lx,
+                                                  float* __restrict__ ly, float* __restrict__ lp,
+                                                  double* __restrict__ e_acc) {
+    __shared__ __align__(16) F32Smem sm;
+    __shared__ float red[16][BN + 1];
+    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
+    float acc[8][8];
+    sgemm_tile<false>(J, x, Np, Rp, i0, r0, acc, sm);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int col = b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4);
+        float part = 0.f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const size_t o = (size_t)(i0 + row_of(a, ty)) * Rp + r0 + col;
+            part = fmaf(x[o], acc[a][b], part);
+            lx[o] = -acc[a][b];
+            ly[o] = 0.f;
+            if (lp) lp[o] = 0.f;
+        }
+        red[ty][col] = part;
+    }
+    __syncthreads();
+    if (threadIdx.x < BN) {
+        double s = 0.0;
+        for (int t = 0; t < 16; ++t) s += (double)red[t][threadIdx.x];
+        atomicAdd(&e_acc[r0 + threadIdx.x], s);
+    }
+}
+
+// Elementwise first half of a reverse step: lf = ly~ c dt (ly~ after FY).
+__global__ void k_adj_pre(const float* __restrict__ x, const float* __restrict__ yt,
+                          const float* __restrict__ lx, const float* __restrict__ ly,
+                          float* __restrict__ lf, size_t n, float c, float dt) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float ytv = yt[k];
+    const bool clamped = fabsf(x[k] + ytv * dt) > 1.f;
+    const float lxt = clamped ? 0.f : lx[k];
+    const float lyt = (clamped ? 0.f : ly[k]) + lxt * dt;
+    lf[k] = lyt * c * dt;
+}
+
+// Second half: G = J lf (skipped for the sgn coupling), then every adjoint of
+// the step's inputs and the per-replica gA, gdt sums.
+template <bool SIGN, bool CONTROL>
+__global__ void __launch_bounds__(256) k_adj_post(const float* __restrict__ J, int Np, int Rp,
+                                                  const float* __restrict__ lf,
+                                                  const float* __restrict__ x,
+                                                  const float* __restrict__ y,
+                                                  const float* __restrict__ p,
+                                                  const float* __restrict__ pnext,
+                                                  const float* __restrict__ yt,
+                                                  float* __restrict__ lx, float* __restrict__ ly,
+                                                  float* __restrict__ lp,
+                                                  const float* __restrict__ A, float c, float dt,
+                                                  float p_shared, float inv_rem,
+                                                  double* __restrict__ gA,
+                                                  double* __restrict__ gdt) {
+    __shared__ __align__(16) F32Smem sm;
+    __shared__ float redA[16][BN + 1], redT[16][BN + 1];
+    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
+    float acc[8][8];
+    if (!SIGN) {
+        sgemm_tile<false>(J, lf, Np, Rp, i0, r0, acc, sm);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int col = b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4);
+        const float a_r = CONTROL ? A[r0 + col] : 0.f;
+        float sA = 0.f, sT = 0.f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const size_t o = (size_t)(i0 + row_of(a, ty)) * Rp + r0 + col;
+            const float xo = x[o], ytv = yt[o];
+            const bool clamped = fabsf(xo + ytv * dt) > 1.f;
+            const float lxt = clamped ? 0.f : lx[o];
+            const float lyt = (clamped ? 0.f : ly[o]) + lxt * dt;
+            const float pnv = CONTROL ? pnext[o] : p_shared;
+            sT = fmaf(lxt, ytv, sT);
+            sT = fmaf(lyt, (ytv - y[o]) / dt, sT);
+            float lxi = lxt - lyt * pnv * dt + acc[a][b];
+            if (CONTROL) {
+                const float lpn = lp[o] - lyt * xo * dt;
+                const float pv = p[o];
+                const float g = 1.f - a_r * xo * xo;
+                const float lg = -lpn * pv * inv_rem;
+                sA = fmaf(-lg, xo * xo, sA);
+                lxi = fmaf(-2.f * a_r * xo, lg, lxi);
+                lp[o] = lpn * (1.f - g * inv_rem);
+            }
+            lx[o] = lxi;
+            ly[o] = lyt;
+        }
+        redA[ty][col] = sA;
+        redT[ty][col] = sT;
+    }
+    __syncthreads();
+    if (threadIdx.x < BN) {
+        double a = 0.0, t = 0.0;
+        for (int k = 0; k < 16; ++k) {
+            a += (double)redA[k][threadIdx.x];
+            t += (double)redT[k][threadIdx.x];
+        }
+        if (CONTROL) atomicAdd(&gA[r0 + threadIdx.x], a);
+        atomicAdd(&gdt[r0 + threadIdx.x], t);
+    }
+}
+
+// caller layout [R][N] <-> state layout [Np][Rp]
+__global__ void k_rm_to_sm(const float* __restrict__ src, float* __restrict__ dst, int N, int R,
+                           int Rp) {
+    __shared__ float tile[32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, i = i0 + threadIdx.x;
+        tile[k][threadIdx.x] = (r < R && i < N) ? src[(size_t)r * N + i] : 0.f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y)
+        dst[(size_t)(i0 + k) * Rp + r0 + threadIdx.x] = tile[threadIdx.x][k];
+}
+
+__global__ void k_fill(float* p, float v, size_t n) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] = v;
+}
+
+__global__ void k_finish(const double* e_acc, double* E, const double* gA, double* gA_out,
+                         const double* gdt, double* gdt_out, int R) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    E[r] = -0.5 * e_acc[r];
+    if (gA_out) gA_out[r] = gA[r];
+    if (gdt_out) gdt_out[r] = gdt[r];
+}
+
+struct DevBuf {
+    std::vector<void*> ptrs;
+    ~DevBuf() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    gsb_status alloc(T** p, size_t n) {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
+        if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (adjoint)");
+        ptrs.push_back(*p);
+        return GSB_OK;
+    }
+};
+
+}  // namespace
+
+}  // namespace gsb
+
+using namespace gsb;
+
+extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* prm,
+                                              int32_t window, int32_t ckpt_every,
+                                              const float* x0, double* energy, float* grad_x0,
+                                              double* grad_A, double* grad_dt, void* stream) {
+    if (!P || !prm || !x0 || !energy) return set_error(GSB_EINVAL, "NULL argument");
+    const gsb_params& Q = *prm;
+    if (P->csr) return set_error(GSB_EUNSUPPORTED, "gsb_relaxed_energy_grad takes dense problems");
+    if (P->has_h) return set_error(GSB_EUNSUPPORTED, "gsb_relaxed_energy_grad takes problems without h");
+    if (Q.variant < GSB_BSB || Q.variant > GSB_GDSB) return set_error(GSB_EINVAL, "unknown variant");
+    if (Q.M < 1 || Q.R < 1) return set_error(GSB_EINVAL, "M and R must be >= 1");
+    if (window < 1 || window > Q.M) return set_error(GSB_EINVAL, "window must be in 1..M");
+    if (ckpt_every < 1) return set_error(GSB_EINVAL, "ckpt_every must be >= 1");
+    if (!(Q.c > 0.0) || !(Q.dt > 0.0)) return set_error(GSB_EINVAL, "c and dt must be > 0");
+    if (Q.schedule) return set_error(GSB_EUNSUPPORTED, "the Eq. 6 schedule only");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool sign = Q.variant == GSB_DSB || Q.variant == GSB_GDSB;
+    const bool control = Q.variant == GSB_GBSB || Q.variant == GSB_GDSB;
+    const int N = P->N, Np = P->Np, R = Q.R, Rp = round_up(R, kTile);
+    const int K = ckpt_every < window ? ckpt_every : window;
+    const int nseg = (window + K - 1) / K;
+    const size_t nst = (size_t)Np * Rp;
+    const float c = (float)Q.c, dt = (float)Q.dt;
+    DevBuf B;
+    float *ck = nullptr, *sx = nullptr, *sy = nullptr, *sp = nullptr, *syt = nullptr;
+    float *lx = nullptr, *ly = nullptr, *lp = nullptr, *lf = nullptr, *Ad = nullptr, *tmp = nullptr;
+    double *e_acc = nullptr, *gA = nullptr, *gdt = nullptr;
+    gsb_status st;
+    // checkpoints: (x, y, p) at the start of each segment
+    if ((st = B.alloc(&ck, 3 * nst * nseg)) || (st = B.alloc(&sx, nst * (K + 1))) ||
+        (st = B.alloc(&sy, nst * (K + 1))) || (st = B.alloc(&sp, nst * (K + 1))) ||
+        (st = B.alloc(&syt, nst * K)) || (st = B.alloc(&lx, nst)) || (st = B.alloc(&ly, nst)) ||
+        (st = B.alloc(&lp, nst)) || (st = B.alloc(&lf, nst)) || (st = B.alloc(&Ad, Rp)) ||
+        (st = B.alloc(&tmp, nst)) || (st = B.alloc(&e_acc, Rp)) || (st = B.alloc(&gA, Rp)) ||
+        (st = B.alloc(&gdt, Rp)))
+        return st;
+    {
+        std::vector<float> Ah(Rp, 0.f);
+        for (int r = 0; r < R; ++r) Ah[r] = Q.A_per_replica ? Q.A_per_replica[r] : Q.A;
+        GSB_CUDA_TRY(cudaMemcpyAsync(Ad, Ah.data(), sizeof(float) * Rp, cudaMemcpyHostToDevice, s));
+        GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    GSB_CUDA_TRY(cudaMemsetAsync(e_acc, 0, sizeof(double) * Rp, s));
+    GSB_CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * Rp, s));
+    GSB_CUDA_TRY(cudaMemsetAsync(gdt, 0, sizeof(double) * Rp, s));
+    // initial state into segment slot 0
+    k_rm_to_sm<<<dim3(Np / 32, Rp / 32), dim3(32, 8), 0, s>>>(x0, sx, N, R, Rp);
+    GSB_LAUNCH_CHECK("k_rm_to_sm");
+    GSB_CUDA_TRY(cudaMemsetAsync(sy, 0, sizeof(float) * nst, s));
+    k_fill<<<(unsigned)((nst + 255) / 256), 256, 0, s>>>(sp, 1.f, nst);
+    GSB_LAUNCH_CHECK("k_fill");
+    const dim3 grid(Rp / BN, Np / BM);
+    auto fwd = [&](int m, int slot) -> gsb_status {
+        const size_t a = (size_t)slot * nst, b = (size_t)(slot + 1) * nst;
+        const float p_shared = (float)(1.0 - (double)(m + 1) / (double)Q.M);
+        const float inv_rem = 1.0f / (float)(Q.M - m);
+#define GSB_ADJ_FWD(S, C)                                                                        \
+    k_adj_fwd<S, C><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + a, sy + a, sp + a, sx + b, sy + b, \
+                                         sp + b, syt + a, Ad, c, dt, p_shared, inv_rem)
+        if (sign) {
+            if (control) GSB_ADJ_FWD(true, true); else GSB_ADJ_FWD(true, false);
+        } else {
+            if (control) GSB_ADJ_FWD(false, true); else GSB_ADJ_FWD(false, false);
+        }
+#undef GSB_ADJ_FWD
+        GSB_LAUNCH_CHECK("k_adj_fwd");
+        return GSB_OK;
+    };
+    auto save_ckpt = [&](int seg) -> gsb_status {
+        for (int q = 0; q < 3; ++q) {
+            const float* src = q == 0 ? sx : (q == 1 ? sy : sp);
+            GSB_CUDA_TRY(cudaMemcpyAsync(ck + ((size_t)seg * 3 + q) * nst, src, sizeof(float) * nst,
+                                         cudaMemcpyDeviceToDevice, s));
+        }
+        return GSB_OK;
+    };
+    auto load_ckpt = [&](int seg) -> gsb_status {
+        for (int q = 0; q < 3; ++q) {
+            float* dst = q == 0 ? sx : (q == 1 ? sy : sp);
+            GSB_CUDA_TRY(cudaMemcpyAsync(dst, ck + ((size_t)seg * 3 + q) * nst, sizeof(float) * nst,
+                                         cudaMemcpyDeviceToDevice, s));
+        }
+        return GSB_OK;
+    };
+    auto seg_len = [&](int seg) { return seg == nseg - 1 ? window - seg * K : K; };
+    // forward pass with checkpoints
+    for (int seg = 0; seg < nseg; ++seg) {
+        if ((st = save_ckpt(seg))) return st;
+        const int L = seg_len(seg);
+        for (int k = 0; k < L; ++k)
+            if ((st = fwd(seg * K + k, k))) return st;
+        if (seg < nseg - 1) {
+            // the next segment starts from slot L
+            for (int q = 0; q < 3; ++q) {
+                float* buf = q == 0 ? sx : (q == 1 ? sy : sp);
+                GSB_CUDA_TRY(cudaMemcpyAsync(buf, buf + (size_t)L * nst, sizeof(float) * nst,
+                                             cudaMemcpyDeviceToDevice, s));
+            }
+        }
+    }
+    // seed from x(t_W) (slot of the last segment's end)
+    const int Llast = seg_len(nseg - 1);
+    k_adj_seed<<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + (size_t)Llast * nst, lx, ly,
+                                    control ? lp : nullptr, e_acc);
+    GSB_LAUNCH_CHECK("k_adj_seed");
+    // reverse sweep, segment by segment; the last segment is still in the slots
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int L = seg_len(seg);
+        if (seg < nseg - 1) {
+            if ((st = load_ckpt(seg))) return st;
+            for (int k = 0; k < L; ++k)
+                if ((st = fwd(seg * K + k, k))) return st;
+        }
+        for (int k = L - 1; k >= 0; --k) {
+            const int m = seg * K + k;
+            const size_t a = (size_t)k * nst, b = (size_t)(k + 1) * nst;
+            const float p_shared = (float)(1.0 - (double)(m + 1) / (double)Q.M);
+            const float inv_rem = 1.0f / (float)(Q.M - m);
+            if (!sign) {
+                k_adj_pre<<<(unsigned)((nst + 255) / 256), 256, 0, s>>>(sx + a, syt + a, lx, ly, lf,
+                                                                         nst, c, dt);
+                GSB_LAUNCH_CHECK("k_adj_pre");
+            }
+#define GSB_ADJ_POST(S, C)                                                                      \
+    k_adj_post<S, C><<<grid, 256, 0, s>>>(P->J32, Np, Rp, lf, sx + a, sy + a, sp + a, sp + b,   \
+                                          syt + a, lx, ly, lp, Ad, c, dt, p_shared, inv_rem, gA, \
+                                          gdt)
+            if (sign) {
+                if (control) GSB_ADJ_POST(true, true); else GSB_ADJ_POST(true, false);
+            } else {
+                if (control) GSB_ADJ_POST(false, true); else GSB_ADJ_POST(false, false);
+            }
+#undef GSB_ADJ_POST
+            GSB_LAUNCH_CHECK("k_adj_post");
+        }
+    }
+    k_finish<<<(R + 255) / 256, 256, 0, s>>>(e_acc, energy, gA, grad_A, gdt, grad_dt, R);
+    GSB_LAUNCH_CHECK("k_finish");
+    if (grad_x0) {
+        st = launch_transpose_to_host_layout(lx, grad_x0, Np, Rp, N, R, s);
+        if (st != GSB_OK) return st;
+    }
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));  // buffers are freed on return
+    return GSB_OK;
+}

@@ -108,6 +108,9 @@ def _declare(L):
                                ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.c_int32,
                                ctypes.POINTER(ctypes.c_double), _vp]
     L.gsb_lyapunov.restype = st
+    L.gsb_relaxed_energy_grad.argtypes = [_vp, ctypes.POINTER(gsb_params), ctypes.c_int32,
+                                          ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.gsb_relaxed_energy_grad.restype = st
     L.gsb_energy_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp, _vp]
     L.gsb_energy_noalloc.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
@@ -228,6 +231,28 @@ class Problem:
                                   int(renorm_every), int(nsteps), _p(out, ctypes.c_double),
                                   _stream_handle(stream)))
         return out.reshape(len(A), int(R))
+
+    def relaxed_energy_grad(self, variant, M, window, x0_ptr, R, A, dt, c, energy_ptr,
+                            grad_x0_ptr=None, grad_A_ptr=None, grad_dt_ptr=None,
+                            ckpt_every=20, stream=None):
+        """gsb_relaxed_energy_grad on caller device buffers (raw pointers)."""
+        prm = gsb_params()
+        prm.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+        prm.M = int(M)
+        prm.R = int(R)
+        prm.c = float(c)
+        prm.dt = float(dt)
+        A_arr = np.asarray(A, dtype=np.float32)
+        keep = None
+        if A_arr.ndim == 0:
+            prm.A = float(A_arr)
+        else:
+            keep = np.ascontiguousarray(A_arr)
+            prm.A_per_replica = _p(keep, ctypes.c_float)
+        _check(lib().gsb_relaxed_energy_grad(self.handle, ctypes.byref(prm), int(window),
+                                             int(ckpt_every), x0_ptr, energy_ptr, grad_x0_ptr,
+                                             grad_A_ptr, grad_dt_ptr, _stream_handle(stream)))
+        del keep
 
     def close(self):
         if self.handle:

@@ -1,0 +1,186 @@
+"""GPU adjoint (gsb_relaxed_energy_grad) against the FP64 oracle's reverse
+sweep, whose gradients are pinned to central finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2508_17655_gb300 import gsb, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def f32(v):
+    return float(np.float32(v))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2508_17655_gb300 import build
+    build.build()
+
+
+def _gpu_grad(P, variant, M, W, x0, A, dt, c, K=20):
+    torch = pytest.importorskip("torch")
+    R, N = x0.shape
+    xd = torch.from_numpy(np.ascontiguousarray(x0, dtype=np.float32)).cuda()
+    E = torch.empty(R, dtype=torch.float64, device="cuda")
+    gx = torch.empty_like(xd)
+    gA = torch.empty(R, dtype=torch.float64, device="cuda")
+    gdt = torch.empty(R, dtype=torch.float64, device="cuda")
+    P.relaxed_energy_grad(variant, M, W, xd.data_ptr(), R, A, dt, c, E.data_ptr(), gx.data_ptr(),
+                          gA.data_ptr(), gdt.data_ptr(), ckpt_every=K,
+                          stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return E.cpu().numpy(), gx.cpu().numpy().astype(np.float64), gA.cpu().numpy(), gdt.cpu().numpy()
+
+
+def _sensitivity(grad_fn, x0):
+    """Relative change of each FP64 output (E, dE/dx0 norm-wise, dE/dA, dE/ddt)
+    per replica when x0 is perturbed by one FP32 rounding (relative 2^-24,
+    random signs): how strongly the gradient itself amplifies FP32-level
+    perturbations of the trajectory."""
+    base = grad_fn(x0)
+    xi = np.where(np.random.default_rng(0).random(x0.shape) < 0.5, -1.0, 1.0)
+    pert = grad_fn(x0 * (1.0 + xi * 2.0 ** -24))
+    E, gx, gA, gdt = base
+    E2, gx2, gA2, gdt2 = pert
+    rel = lambda a, b: np.abs(a - b) / np.maximum(np.abs(a), 1e-300)
+    return base, (rel(E, E2), np.linalg.norm(gx - gx2, axis=1) / np.linalg.norm(gx, axis=1),
+                  rel(gA, gA2), rel(gdt, gdt2))
+
+
+def _check(got, want, sens, ok, what, base=1e-4, factor=200.0):
+    """Per replica and output: relative error <= max(base, factor x the FP64
+    gradient's one-ulp sensitivity). The GPU rounds in FP32 at every forward
+    and reverse step, which the x0-only sensitivity undercounts by up to ~100x
+    on ill-conditioned replicas; well-conditioned replicas get the 1e-4 bar."""
+    names = ("E", "dE/dx0", "dE/dA", "dE/ddt")
+    for k, name in enumerate(names):
+        g, w = got[k], want[k]
+        if k == 1:
+            err = np.linalg.norm(g - w, axis=1) / np.linalg.norm(w, axis=1)
+        else:
+            if np.all(w == 0):
+                assert np.all(g == 0), name
+                continue
+            # a gradient that nearly cancels across its terms has no meaningful
+            # relative error: floor the scale at 5 % of the median magnitude
+            scale = np.maximum(np.abs(w), 0.05 * np.median(np.abs(w)))
+            err = np.abs(g - w) / np.maximum(scale, 1e-300)
+        tol = np.maximum(base, factor * sens[k])
+        bad = ok & (err > tol)
+        assert not bad.any(), (f"{what} {name}: errors {err[bad]} vs tolerances {tol[bad]}")
+
+
+@pytest.mark.parametrize("variant", ["gbsb", "bsb", "gdsb", "dsb"])
+def test_adjoint_well_conditioned_within_1e4(variant):
+    """A short window from small x0 (no wall events, little amplification):
+    every replica's E, dE/dx0, dE/dA, dE/ddt within 1e-4 relative of FP64."""
+    N, R, M, W = 300, 96, 400, 12
+    J = I.sk_gauss(N, 13)
+    c, dt = 0.5, f32(0.8)
+    A = np.linspace(0.1, 0.4, R).astype(np.float32)
+    x0 = O.init_uniform(R, N, 18, rng=0.02)
+    got = _gpu_grad(gsb.Problem.dense(J), variant, M, W, x0, A, dt, c)
+    Jd = J.astype(np.float64)
+    Ad = A.astype(np.float64)
+    want = O.relaxed_energy_grad(Jd, variant, x0, c=c, dt=dt, M=M, W=W, A=Ad)
+    margin = O.run(Jd, variant, x0, 0 * x0, c=c, dt=dt, M=M, A=Ad, nsteps=W)["margin"]
+    ok = margin >= (2e-6 if variant in ("dsb", "gdsb") else 0.5)
+    assert ok.mean() >= 0.9
+    zero = (np.zeros(R),) * 4
+    _check(got, want, zero, ok, variant, base=1e-4, factor=0.0)
+
+
+@pytest.mark.parametrize("variant", ["gbsb", "bsb", "gdsb", "dsb"])
+def test_adjoint_matches_oracle_small(variant):
+    N, R, M, W = 300, 70, 400, 60
+    J = I.sk_gauss(N, 13)
+    c, dt = 0.5, f32(0.8)
+    A = np.linspace(0.1, 0.4, R).astype(np.float32)
+    x0 = O.init_uniform(R, N, 17)
+    got = _gpu_grad(gsb.Problem.dense(J), variant, M, W, x0, A, dt, c)
+    Jd = J.astype(np.float64)
+    Ad = A.astype(np.float64)
+    want, sens = _sensitivity(
+        lambda x: O.relaxed_energy_grad(Jd, variant, x, c=c, dt=dt, M=M, W=W, A=Ad), x0)
+    margin = O.run(Jd, variant, x0, 0 * x0, c=c, dt=dt, M=M, A=Ad, nsteps=W)["margin"]
+    # a different wall or sign decision changes the gradient by O(1)
+    ok = margin >= (1e-5 if variant in ("dsb", "gdsb") else 1e-4)
+    assert ok.sum() >= 2
+    _check(got, want, sens, ok, variant)
+
+
+def test_adjoint_config5_shape_against_fp64():
+    """N = 2000 SK (Gaussian, FP32 J), R = 256, the first 200 steps of a run
+    with the paper's K2000 step count M = 21,500 (Fig. 1(d)), checkpoints every
+    20 steps, c = 1/(2 sqrt(N) sigma) = 1/2 (App. A), dt = 1.25: a window with no
+    wall event. Keeping x, y, p in FP32 (as the paper's machine does) moves x
+    by ~1.3e-4 in 200 steps here, for any FP32 implementation; each sampled
+    replica's E, dE/dx0, dE/dA, dE/ddt must be within max(1e-4, 5 x the change
+    FP32 storage of the forward state alone causes in the FP64 oracle's
+    gradient; the GPU also keeps the adjoint state in FP32 through the reverse
+    sweep, which roughly doubles it). The FP64 gradient is checked against
+    central differences on one replica."""
+    N, R, M, W = 2000, 256, 21500, 200
+    J = I.sk_gauss(N, 0)
+    Jd = J.astype(np.float64)
+    c, dt, A = 0.5, 1.25, 0.2
+    x0 = O.init_uniform(R, N, 1)
+    got = _gpu_grad(gsb.Problem.dense(J), "gbsb", M, W, x0, A, dt, c)
+    pick = np.linspace(0, R - 1, 12).astype(int)
+    want = O.relaxed_energy_grad(Jd, "gbsb", x0[pick], c=c, dt=dt, M=M, W=W, A=A)
+    store = O.relaxed_energy_grad(Jd, "gbsb", x0[pick], c=c, dt=dt, M=M, W=W, A=A, f32_state=True)
+    rel = lambda a, b: np.abs(a - b) / np.abs(a)
+    drift = (rel(want[0], store[0]),
+             np.linalg.norm(want[1] - store[1], axis=1) / np.linalg.norm(want[1], axis=1),
+             rel(want[2], store[2]), rel(want[3], store[3]))
+    margin = O.run(Jd, "gbsb", x0[pick], 0 * x0[pick], c=c, dt=dt, M=M, A=A, nsteps=W)["margin"]
+    assert np.all(margin > 0.1)  # wall-free window
+    _check(tuple(g[pick] for g in got), want, drift, np.ones(len(pick), bool), "config 5",
+           base=1e-4, factor=5.0)
+    h = 1e-6
+    xr = x0[pick][:1]
+    fd = (O.relaxed_energy(Jd, "gbsb", xr, c=c, dt=dt + h, M=M, W=W, A=A)[0]
+          - O.relaxed_energy(Jd, "gbsb", xr, c=c, dt=dt - h, M=M, W=W, A=A)[0]) / (2 * h)
+    # central differences of an O(1) energy with h = 1e-6 carry ~1e-10 of roundoff
+    assert abs(want[3][0] - fd[0]) <= 1e-4 * abs(fd[0]) + 1e-8
+    fdA = (O.relaxed_energy(Jd, "gbsb", xr, c=c, dt=dt, M=M, W=W, A=A + h)[0]
+           - O.relaxed_energy(Jd, "gbsb", xr, c=c, dt=dt, M=M, W=W, A=A - h)[0]) / (2 * h)
+    assert abs(want[2][0] - fdA[0]) <= 1e-4 * abs(fdA[0]) + 1e-8
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    N, R, M, W = 256, 128, 500, 45
+    J = I.sk_gauss(N, 19)
+    x0 = O.init_uniform(R, N, 23)
+    P = gsb.Problem.dense(J)
+    outs = [_gpu_grad(P, "gbsb", M, W, x0, 0.3, 0.9, 0.5, K=K) for K in (1, 7, 20, 45)]
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
+def test_torch_autograd_function():
+    torch = pytest.importorskip("torch")
+    from paper_2508_17655_gb300.autograd import relaxed_energy
+    N, R, M, W = 200, 33, 300, 30
+    J = I.sk_gauss(N, 29)
+    P = gsb.Problem.dense(J)
+    x0 = torch.from_numpy(O.init_uniform(R, N, 31).astype(np.float32)).cuda().requires_grad_()
+    A = torch.full((R,), 0.25, dtype=torch.float32, requires_grad=True)
+    dt = torch.tensor(0.8, dtype=torch.float32, requires_grad=True)
+    w = torch.linspace(0.5, 1.5, R, dtype=torch.float64, device="cuda")
+    E = relaxed_energy(x0, A, dt, P, "gbsb", M, W, 0.5, 10)
+    (w * E).sum().backward()
+    # the same kernels called directly: autograd only applies the chain rule
+    Ed, gx, gA, gdt = _gpu_grad(P, "gbsb", M, W, x0.detach().cpu().numpy(), 0.25, 0.8, 0.5, K=10)
+    wn = w.cpu().numpy()
+    np.testing.assert_array_equal(E.detach().cpu().numpy(), Ed)
+    np.testing.assert_allclose(x0.grad.cpu().numpy(), (wn[:, None] * gx).astype(np.float32),
+                               rtol=1e-6)
+    np.testing.assert_allclose(A.grad.numpy(), (wn * gA).astype(np.float32), rtol=1e-6)
+    np.testing.assert_allclose(float(dt.grad), float(np.sum(wn * gdt)), rtol=1e-5)
+    assert A.grad.device.type == "cpu" and x0.grad.device.type == "cuda"
