@@ -211,6 +211,32 @@ gsb_status gsb_relaxed_energy_grad(gsb_problem* problem, const gsb_params* param
                                    double* energy, float* grad_x0, double* grad_A,
                                    double* grad_dt, void* stream);
 
+/* Batched runs: n independent instances (each its own dense problem and
+ * parameters; uneven N and R) advanced together, one launch per time step
+ * over a work list of tiles of all instances (the paper solves several
+ * instances at once on one machine, N_batch, Sec. VI). Every instance gets an
+ * ordinary run handle in runs_out[k] (query it with gsb_best / gsb_get_state,
+ * free it with gsb_run_destroy) and follows exactly the trajectory gsb_run
+ * would give it on the FP32 path. Energies are evaluated at t_M
+ * (eval_every must be 0). An autotuner picks the tile (128 or 64 spins x
+ * replicas) and the number of steps captured per CUDA graph on the run's first
+ * steps; info (nullable) reports the choice; info->force_tile = 128 or 64
+ * skips the tile probe; info->max_steps > 0 stops every instance after that
+ * many steps (continue each with gsb_run_steps). Blocks on `stream` until
+ * every instance is done. */
+typedef struct gsb_batch_info {
+    int32_t force_tile;       /* in: 0 = autotune, 128 or 64 */
+    int32_t max_steps;        /* in: 0 = run every instance to its M */
+    int32_t tile;             /* out: tile used */
+    int32_t steps_per_graph;  /* out: steps captured per graph launch */
+    int32_t tiles;            /* out: tiles per step */
+    double ms_step_tile128;   /* out: probe time per step, tile 128 (-1 if not probed) */
+    double ms_step_tile64;    /* out: probe time per step, tile 64 (-1 if not probed) */
+} gsb_batch_info;
+
+gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems, const gsb_params* params,
+                         gsb_run_state** runs_out, gsb_batch_info* info, void* stream);
+
 /* Allocation-free energies, for callers that cannot call cudaMalloc / cudaFree
  * (a steady-state loop that must not block on them, or an application whose own
  * allocator owns the device memory). The paper has no counterpart: it is an

@@ -1,0 +1,389 @@
+// k_batch.cu -- many independent instances of uneven size stepped together
+// (gsb_batch_run). The paper runs several instances per machine at once and
+// keeps the better result (N_batch, Sec. VI); here every instance is an
+// ordinary run (its own J, replicas, parameters, state buffers), and one
+// launch per time step covers all of them through a device work list of
+// tiles (instance, spin block, replica block). Tiles that only hold padding
+// are never listed. Each tile is the plain FP32 SGEMM tile with Eqs. 3-7 in its
+// epilogue, summing over K in the same order as the single-run kernel, so a
+// batched instance follows exactly the trajectory it would follow alone.
+//
+// The step index lives in device memory and a one-thread kernel advances it,
+// so a chunk of steps is captured once as a CUDA graph and replayed. An
+// autotuner times the two tile sizes (128 and 64 spins x replicas) and the
+// graph chunk lengths on the run's first steps and keeps the fastest.
+#include <algorithm>
+#include <vector>
+
+#include "sgemm_f32.cuh"
+
+namespace gsb {
+
+namespace {
+
+using namespace f32;
+
+struct BatchInst {
+    const float* J;
+    float* x0;
+    float* x1;
+    float* y;
+    float* p;
+    const float* A;
+    int Np, Rp, M, flags;  // flags: 1 = sgn-x coupling, 2 = individual control
+    int stop;              // steps this batch advances the instance (<= M)
+    float c, dt;
+    const float* sched;    // p(t_m), m = 0..M (device) or null
+};
+
+struct BatchTile {
+    int inst, i0, r0, work;
+};
+
+// 64 x 64 tile: 256 threads, 4 x 4 accumulators each (rows 4ty.., columns 4tx..).
+struct Smem64 {
+    float A[2][BK][64 + 4];
+    float B[2][BK][64];
+};
+
+template <bool SIGN>
+__device__ __forceinline__ void sgemm_tile64(const float* __restrict__ J, const float* __restrict__ X,
+                                             int Np, int Rp, int i0, int r0, float (&acc)[4][4],
+                                             Smem64& sm) {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int a_row = tid >> 2, a_k = (tid & 3) * 2;
+    const int b_k = tid >> 5, b_c = (tid & 31) * 2;
+    const float* Ap = J + (size_t)(i0 + a_row) * Np + a_k;
+    const float* Bp = X + (size_t)b_k * Rp + r0 + b_c;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    auto ldb = [&](const float* q) {
+        float2 v = *reinterpret_cast<const float2*>(q);
+        if (SIGN) {
+            v.x = sgnf(v.x);
+            v.y = sgnf(v.y);
+        }
+        return v;
+    };
+    float2 ra = *reinterpret_cast<const float2*>(Ap);
+    float2 rb = ldb(Bp);
+    auto stash = [&](int buf) {
+        sm.A[buf][a_k + 0][a_row] = ra.x;
+        sm.A[buf][a_k + 1][a_row] = ra.y;
+        *reinterpret_cast<float2*>(&sm.B[buf][b_k][b_c]) = rb;
+    };
+    stash(0);
+    __syncthreads();
+    const int nk = Np / BK;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < nk) {
+            ra = *reinterpret_cast<const float2*>(Ap + (size_t)(kt + 1) * BK);
+            rb = ldb(Bp + (size_t)(kt + 1) * BK * Rp);
+        }
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            const float4 a = *reinterpret_cast<const float4*>(&sm.A[buf][k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&sm.B[buf][k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        if (kt + 1 < nk) stash(buf ^ 1);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void batch_update4(const BatchInst& I, const float* xc, float* xn,
+                                              size_t o, int r, const float* f, bool control,
+                                              float p_shared, float inv_rem) {
+    float4 x4 = *reinterpret_cast<const float4*>(xc + o);
+    float4 y4 = *reinterpret_cast<float4*>(I.y + o);
+    float4 p4 = control ? *reinterpret_cast<float4*>(I.p + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float* xs = &x4.x;
+    float* ys = &y4.x;
+    float* ps = &p4.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (control)
+            sb_update<true>(xs[q], ys[q], ps[q], f[q], I.A[r + q], I.c, I.dt, p_shared, inv_rem);
+        else
+            sb_update<false>(xs[q], ys[q], ps[q], f[q], 0.f, I.c, I.dt, p_shared, inv_rem);
+    }
+    *reinterpret_cast<float4*>(xn + o) = x4;
+    *reinterpret_cast<float4*>(I.y + o) = y4;
+    if (control) *reinterpret_cast<float4*>(I.p + o) = p4;
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) k_batch_step(const BatchInst* __restrict__ insts,
+                                                    const BatchTile* __restrict__ tiles,
+                                                    const int* __restrict__ m_dev) {
+    const int m = *m_dev;
+    const BatchTile t = tiles[blockIdx.x];
+    const BatchInst I = insts[t.inst];
+    if (m >= I.stop) return;  // this instance has finished its steps
+    const bool odd = m & 1;
+    const float* xc = odd ? I.x1 : I.x0;
+    float* xn = odd ? I.x0 : I.x1;
+    const bool sign = I.flags & 1, control = I.flags & 2;
+    // same scalars as the single-run path: p(t_{m+1}) from the caller schedule
+    // or Eq. 6 (double, rounded once), 1/(M - m) rounded once
+    const float p_shared =
+        I.sched ? I.sched[m + 1] : (float)(1.0 - (double)(m + 1) / (double)I.M);
+    const float inv_rem = __frcp_rn((float)(I.M - m));
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (T == 128) {
+        __shared__ __align__(16) F32Smem sm;
+        float acc[8][8];
+        if (sign)
+            sgemm_tile<true>(I.J, xc, I.Np, I.Rp, t.i0, t.r0, acc, sm);
+        else
+            sgemm_tile<false>(I.J, xc, I.Np, I.Rp, t.i0, t.r0, acc, sm);
+        const int cols[2] = {t.r0 + tx * 4, t.r0 + 64 + tx * 4};
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const size_t rowoff = (size_t)(t.i0 + row_of(a, ty)) * I.Rp;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                batch_update4(I, xc, xn, rowoff + cols[h], cols[h], &acc[a][h * 4], control,
+                              p_shared, inv_rem);
+        }
+    } else {
+        __shared__ __align__(16) Smem64 sm;
+        float acc[4][4];
+        if (sign)
+            sgemm_tile64<true>(I.J, xc, I.Np, I.Rp, t.i0, t.r0, acc, sm);
+        else
+            sgemm_tile64<false>(I.J, xc, I.Np, I.Rp, t.i0, t.r0, acc, sm);
+        const int col = t.r0 + tx * 4;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            batch_update4(I, xc, xn, (size_t)(t.i0 + ty * 4 + a) * I.Rp + col, col, acc[a],
+                          control, p_shared, inv_rem);
+    }
+}
+
+__global__ void k_batch_advance(int* m_dev) { *m_dev += 1; }
+
+struct BatchState {
+    int n = 0;
+    BatchInst* d_inst = nullptr;
+    BatchTile* d_tiles[2] = {nullptr, nullptr};  // tile lists for T = 128, 64
+    int ntiles[2] = {0, 0};
+    float** d_sched = nullptr;
+    std::vector<float*> scheds;
+    int* d_m = nullptr;
+    ~BatchState() {
+        cudaFree(d_inst);
+        cudaFree(d_tiles[0]);
+        cudaFree(d_tiles[1]);
+        cudaFree(d_m);
+        for (float* s : scheds) cudaFree(s);
+    }
+};
+
+gsb_status launch_batch_step(BatchState& B, int which, cudaStream_t s) {
+    if (B.ntiles[which] == 0) return GSB_OK;
+    if (which == 0)
+        k_batch_step<128><<<B.ntiles[0], 256, 0, s>>>(B.d_inst, B.d_tiles[0], B.d_m);
+    else
+        k_batch_step<64><<<B.ntiles[1], 256, 0, s>>>(B.d_inst, B.d_tiles[1], B.d_m);
+    GSB_LAUNCH_CHECK("k_batch_step");
+    k_batch_advance<<<1, 1, 0, s>>>(B.d_m);
+    GSB_LAUNCH_CHECK("k_batch_advance");
+    return GSB_OK;
+}
+
+}  // namespace
+
+}  // namespace gsb
+
+using namespace gsb;
+
+extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
+                                    const gsb_params* params, gsb_run_state** runs_out,
+                                    gsb_batch_info* info, void* stream) {
+    if (n < 1 || !problems || !params || !runs_out) return set_error(GSB_EINVAL, "NULL argument or n < 1");
+    for (int k = 0; k < n; ++k) runs_out[k] = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the batched steps run (and are captured) on a stream of their own, after
+    // everything already queued on the caller's stream
+    struct OwnStream {
+        cudaStream_t s = nullptr;
+        ~OwnStream() {
+            if (s) cudaStreamDestroy(s);
+        }
+    } own;
+    GSB_CUDA_TRY(cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking));
+    gsb_status st = GSB_OK;
+    int M_max = 0;
+    auto cleanup = [&](gsb_status e) {
+        for (int k = 0; k < n; ++k) {
+            gsb_run_destroy(runs_out[k]);
+            runs_out[k] = nullptr;
+        }
+        return e;
+    };
+    for (int k = 0; k < n; ++k) {
+        if (!problems[k] || problems[k]->csr)
+            return cleanup(set_error(GSB_EUNSUPPORTED, "gsb_batch_run takes dense problems"));
+        if (params[k].eval_every != 0)
+            return cleanup(set_error(GSB_EUNSUPPORTED, "batched runs evaluate at t_M only"));
+        gsb_params q = params[k];
+        if (q.precision != GSB_PREC_AUTO && q.precision != GSB_PREC_FP32)
+            return cleanup(set_error(GSB_EUNSUPPORTED, "batched runs use FP32 coupling"));
+        q.precision = GSB_PREC_FP32;
+        q.flags |= GSB_RUN_DEFER;
+        if ((st = gsb_run(problems[k], &q, &runs_out[k], stream)) != GSB_OK) return cleanup(st);
+        M_max = std::max(M_max, (info && info->max_steps > 0) ? std::min(q.M, info->max_steps) : q.M);
+    }
+    BatchState B;
+    B.n = n;
+    std::vector<BatchInst> insts(n);
+    std::vector<BatchTile> tiles[2];
+    for (int k = 0; k < n; ++k) {
+        gsb_run_state* r = runs_out[k];
+        BatchInst& I = insts[k];
+        I.J = r->prob->J32;
+        I.x0 = r->x[0];
+        I.x1 = r->x[1];
+        I.y = r->y;
+        I.p = r->p;
+        I.A = r->A;
+        I.Np = r->Np;
+        I.Rp = r->Rp;
+        I.M = r->params.M;
+        I.stop = (info && info->max_steps > 0 && info->max_steps < I.M) ? info->max_steps : I.M;
+        I.flags = (r->sign_coupling ? 1 : 0) | (r->control ? 2 : 0);
+        I.c = r->c;
+        I.dt = r->dt;
+        I.sched = nullptr;
+        if (!r->sched_host.empty()) {
+            float* d = nullptr;
+            GSB_CUDA_TRY(cudaMalloc(&d, sizeof(float) * r->sched_host.size()));
+            B.scheds.push_back(d);
+            GSB_CUDA_TRY(cudaMemcpyAsync(d, r->sched_host.data(), sizeof(float) * r->sched_host.size(),
+                                         cudaMemcpyHostToDevice, s));
+            I.sched = d;
+        }
+        for (int w = 0; w < 2; ++w) {
+            const int T = w == 0 ? 128 : 64;
+            for (int i0 = 0; i0 < r->N; i0 += T)
+                for (int r0 = 0; r0 < r->R; r0 += T) tiles[w].push_back({k, i0, r0, r->Np});
+        }
+    }
+    for (int w = 0; w < 2; ++w) {
+        // longest K first, so the big tiles start early
+        std::stable_sort(tiles[w].begin(), tiles[w].end(),
+                         [](const BatchTile& a, const BatchTile& b) { return a.work > b.work; });
+        B.ntiles[w] = (int)tiles[w].size();
+        GSB_CUDA_TRY(cudaMalloc(&B.d_tiles[w], sizeof(BatchTile) * tiles[w].size()));
+        GSB_CUDA_TRY(cudaMemcpyAsync(B.d_tiles[w], tiles[w].data(), sizeof(BatchTile) * tiles[w].size(),
+                                     cudaMemcpyHostToDevice, s));
+    }
+    GSB_CUDA_TRY(cudaMalloc(&B.d_inst, sizeof(BatchInst) * n));
+    GSB_CUDA_TRY(cudaMemcpyAsync(B.d_inst, insts.data(), sizeof(BatchInst) * n,
+                                 cudaMemcpyHostToDevice, s));
+    GSB_CUDA_TRY(cudaMalloc(&B.d_m, sizeof(int)));
+    GSB_CUDA_TRY(cudaMemsetAsync(B.d_m, 0, sizeof(int), s));
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaStream_t caller = s;
+    s = own.s;
+
+    // autotune the tile on the first steps (both sizes give the same bits)
+    const int force = info ? info->force_tile : 0;
+    cudaEvent_t e0, e1;
+    GSB_CUDA_TRY(cudaEventCreate(&e0));
+    GSB_CUDA_TRY(cudaEventCreate(&e1));
+    int m = 0;
+    double ms_tile[2] = {-1.0, -1.0};
+    int which = force == 64 ? 1 : 0;
+    const int probe = 2;
+    if (!force && M_max >= 2 * probe + 2) {
+        for (int w = 0; w < 2; ++w) {
+            GSB_CUDA_TRY(cudaEventRecord(e0, s));
+            for (int k = 0; k < probe; ++k)
+                if ((st = launch_batch_step(B, w, s))) return cleanup(st);
+            GSB_CUDA_TRY(cudaEventRecord(e1, s));
+            GSB_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            GSB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            ms_tile[w] = t / probe;
+            m += probe;
+        }
+        which = ms_tile[1] >= 0 && ms_tile[1] < ms_tile[0] ? 1 : 0;
+    }
+    // graph chunk length: capture G steps once, replay; G tuned among a few sizes
+    int chunk = 1;
+    double best_ms = 1e300;
+    const int cands[3] = {16, 64, 256};
+    cudaGraphExec_t exec = nullptr;
+    for (int ci = 0; ci < 3 && m < M_max; ++ci) {
+        const int G = std::min(cands[ci], M_max - m);
+        cudaGraph_t g;
+        GSB_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < G; ++k)
+            if ((st = launch_batch_step(B, which, s))) {
+                cudaStreamEndCapture(s, &g);
+                return cleanup(st);
+            }
+        GSB_CUDA_TRY(cudaStreamEndCapture(s, &g));
+        cudaGraphExec_t ex;
+        GSB_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+        cudaGraphDestroy(g);
+        GSB_CUDA_TRY(cudaEventRecord(e0, s));
+        GSB_CUDA_TRY(cudaGraphLaunch(ex, s));
+        GSB_CUDA_TRY(cudaEventRecord(e1, s));
+        GSB_CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.f;
+        GSB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        m += G;
+        if (t / G < best_ms) {
+            best_ms = t / G;
+            chunk = G;
+            if (exec) cudaGraphExecDestroy(exec);
+            exec = ex;
+        } else {
+            cudaGraphExecDestroy(ex);
+        }
+        if (G < cands[ci]) break;
+    }
+    // the remaining steps: full chunks by graph replay, the tail step by step
+    while (exec && m + chunk <= M_max) {
+        GSB_CUDA_TRY(cudaGraphLaunch(exec, s));
+        m += chunk;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    while (m < M_max) {
+        if ((st = launch_batch_step(B, which, s))) return cleanup(st);
+        ++m;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    s = caller;
+    // record how far each run got; evaluate the ones that reached t_M
+    for (int k = 0; k < n; ++k) {
+        gsb_run_state* r = runs_out[k];
+        const int stop = insts[k].stop;
+        r->steps_done = stop;
+        r->cur = stop & 1;
+        if (stop == r->params.M)
+            if ((st = run_evaluate(r, r->params.M)) != GSB_OK) return cleanup(st);
+    }
+    if (info) {
+        info->tile = which == 0 ? 128 : 64;
+        info->steps_per_graph = chunk;
+        info->ms_step_tile128 = ms_tile[0];
+        info->ms_step_tile64 = ms_tile[1];
+        info->tiles = B.ntiles[which];
+    }
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    return GSB_OK;
+}

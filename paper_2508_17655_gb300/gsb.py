@@ -47,6 +47,18 @@ class gsb_params(ctypes.Structure):
     ]
 
 
+class gsb_batch_info(ctypes.Structure):
+    _fields_ = [
+        ("force_tile", ctypes.c_int32),
+        ("max_steps", ctypes.c_int32),
+        ("tile", ctypes.c_int32),
+        ("steps_per_graph", ctypes.c_int32),
+        ("tiles", ctypes.c_int32),
+        ("ms_step_tile128", ctypes.c_double),
+        ("ms_step_tile64", ctypes.c_double),
+    ]
+
+
 class GsbError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"libgsb status {status}: {msg}")
@@ -111,6 +123,9 @@ def _declare(L):
     L.gsb_relaxed_energy_grad.argtypes = [_vp, ctypes.POINTER(gsb_params), ctypes.c_int32,
                                           ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gsb_relaxed_energy_grad.restype = st
+    L.gsb_batch_run.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), ctypes.POINTER(gsb_params),
+                                ctypes.POINTER(_vp), ctypes.POINTER(gsb_batch_info), _vp]
+    L.gsb_batch_run.restype = st
     L.gsb_energy_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp, _vp]
     L.gsb_energy_noalloc.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
@@ -142,6 +157,58 @@ def _stream_handle(stream):
 
 def launch_count():
     return int(lib().gsb_launch_count())
+
+
+def _make_params(variant, M, R, *, c=0.0, dt=0.0, A=0.0, seed=0, precision="auto",
+                 eval_every=0, y0_uniform=False, x0_range=0.0):
+    prm = gsb_params()
+    prm.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+    prm.M = int(M)
+    prm.R = int(R)
+    prm.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    prm.c = float(c)
+    prm.dt = float(dt)
+    prm.A = float(A)
+    prm.seed = int(seed)
+    prm.eval_every = int(eval_every)
+    prm.y0_uniform = int(bool(y0_uniform))
+    prm.x0_range = float(x0_range)
+    return prm
+
+
+class _BatchRun(object):
+    """A run handle produced by gsb_batch_run (same queries as Run)."""
+
+    def __init__(self, problem, handle, R):
+        self.problem = problem
+        self.handle = handle
+        self.R = int(R)
+        self.N = problem.N
+
+    best = None  # filled below from Run
+    state = None
+    _n_state = None
+    close = None
+    __del__ = None
+
+
+def batch_run(problems, specs, force_tile=0, max_steps=0, stream=None):
+    """Run len(problems) instances together (gsb_batch_run). specs: list of
+    dicts with the keyword arguments of Problem.run (variant, M, R, c, dt, A,
+    seed, ...). Returns (runs, info dict)."""
+    n = len(problems)
+    prms = (gsb_params * n)(*[_make_params(**sp) for sp in specs])
+    handles = (_vp * n)(*[p.handle for p in problems])
+    outs = (_vp * n)()
+    info = gsb_batch_info()
+    info.force_tile = int(force_tile)
+    info.max_steps = int(max_steps)
+    _check(lib().gsb_batch_run(n, handles, prms, outs, ctypes.byref(info),
+                               _stream_handle(stream)))
+    runs = [_BatchRun(problems[k], _vp(outs[k]), specs[k]["R"]) for k in range(n)]
+    return runs, {"tile": info.tile, "steps_per_graph": info.steps_per_graph,
+                  "tiles": info.tiles, "ms_step_tile128": info.ms_step_tile128,
+                  "ms_step_tile64": info.ms_step_tile64}
 
 
 def energy_noalloc(J_ptr, N, spins_ptr, R, energies_ptr, stream=None):
@@ -361,3 +428,12 @@ class Run:
             self.close()
         except Exception:
             pass
+
+
+_BatchRun.best = Run.best
+_BatchRun.steps = Run.steps
+_BatchRun.restart = Run.restart
+_BatchRun.state = Run.state
+_BatchRun._n_state = Run._n_state
+_BatchRun.close = Run.close
+_BatchRun.__del__ = Run.__del__
