@@ -282,6 +282,7 @@ def gpu_arm(args, world, rank, local):
                              "ms_per_step": t3[0], "us_per_time_step": 1e3 * km3 / ks3}
         out["fused_vs_plain"] = value / world / out["plain_fp32"]["value"]
         out["e2e"] = e2e_leg(gsb, J, c, A, max(1, min(args.steps, 3)))
+        out["other_configs"] = other_legs(gsb, I, np, torch, stream, Pk, how)
     if rank == 0 and "e2e" not in out:
         out["e2e"] = e2e_leg(gsb, J, c, A, 1)
     if rank == 0:
@@ -321,6 +322,120 @@ def success_report(energies, A, runs, E_target, run_ms):
                     "TTS99_s": tts if math.isfinite(tts) else None})
     rep["per_A"] = per
     return rep
+
+
+def _events(torch, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    return e0, e1
+
+
+def other_legs(gsb, I, np, torch, stream, Pk, how):
+    """The other configurations of the hot path, one run each (after one
+    warm-up), with the dominant kernel's roofline from CUDA events."""
+    import oracle as O
+    out = {}
+    hbm = Pk["hbm_gbs"]
+    # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x the measured SM clock
+    fp32_peak = 152 * 128 * 2 * Pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # --- sparse Max-Cut (CSR), ER mean degree 20, +1 weights, R = 512, M = 5000
+    for N in (2000, 20000):
+        rp, col, val = I.er_graph(N, 20, "+1", 5)
+        lmax, lmin = O.lambda_extremes(O.Coupling(N, rowptr=rp, col=col, val=val), iters=4000,
+                                       tol=1e-10)
+        P = gsb.Problem.csr(N, rp, col, val, stream=stream.cuda_stream)
+        R, M = 512, 5000
+        run = P.run("gbsb", M=M, R=R, c=1 / lmax, dt=O.dt_from_lambda(lmax, lmin), A=0.2, seed=1,
+                    defer=True, profile=True, stream=stream.cuda_stream)
+        run.restart(2)
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        run.restart(3)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, kn, ksteps = run.kernel_time()
+        nnz = len(col)
+        # algorithmic bytes per step: x, y, p read and written (24 B per spin and
+        # replica), x gathered once (4 B), CSR indices and values (8 B per nonzero)
+        bytes_step = 28.0 * N * R + 8.0 * nnz
+        us = 1e3 * kms / ksteps
+        out[f"sparse_N{N}"] = {
+            "workload": f"ER N={N} mean degree 20, +1 weights, R={R}, M={M}, GbSB, CSR",
+            "value": N * R * M / (ms / 1e3), "unit": "spin-updates/s", "ms_per_run": ms,
+            "roofline": {"bound": "hbm", "kernel": "k_csr_step", "achieved": bytes_step / (us * 1e-6) / 1e9,
+                         "peak": hbm, "unit": "GB/s",
+                         "frac": bytes_step / (us * 1e-6) / 1e9 / hbm, "us_per_step": us,
+                         "algorithmic_bytes_per_step": bytes_step, "peak_source": how}}
+        run.close()
+        P.close()
+    # --- 256 batched uneven SK instances, N ~ U{64..1024}, R ~ U{32..256}, M = 1000
+    Ns, Rs = I.batch_sizes(256, seed=0)
+    probs = [gsb.Problem.dense(I.sk_gauss(int(n), 2000 + k), stream=stream.cuda_stream)
+             for k, n in enumerate(Ns)]
+    specs = [dict(variant="gbsb", M=1000, R=int(r), c=0.5, dt=1.25, A=0.2, seed=k)
+             for k, r in enumerate(Rs)]
+    runs, _ = gsb.batch_run(probs, specs, max_steps=20, stream=stream.cuda_stream)  # warm-up
+    for r in runs:
+        r.close()
+    t = time.perf_counter()
+    runs, info = gsb.batch_run(probs, specs, stream=stream.cuda_stream)
+    el = time.perf_counter() - t
+    for r in runs:
+        r.close()
+    su = float(np.sum(Ns * Rs)) * 1000
+    flop = float(np.sum(2.0 * Ns.astype(float) ** 2 * Rs)) * 1000
+    out["batched_256"] = {
+        "workload": "256 SK instances N~U{64..1024}, N(0,1/N) FP32, R~U{32..256}, M=1000, GbSB",
+        "value": su / el, "unit": "spin-updates/s", "ms_per_run": 1e3 * el,
+        "autotune": info, "how": "host wall clock around gsb_batch_run (allocation and probes included)",
+        "roofline": {"bound": "alu", "kernel": f"k_batch_step<{info['tile']}>", "achieved": flop / el / 1e12,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / el / 1e12 / fp32_peak,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}}
+    for P in probs:
+        P.close()
+    # --- Lyapunov exponents: N = 2000 SK, 16 control strengths x 256 replicas
+    J5 = I.sk_gauss(2000, 0)
+    P5 = gsb.Problem.dense(J5, stream=stream.cuda_stream)
+    A16 = [0.025 * k for k in range(16)]
+    steps = 200
+    P5.lyapunov("gbsb", 2000, 256, A16, c=0.5, dt=1.25, renorm_every=10, nsteps=20)
+    t = time.perf_counter()
+    mle = P5.lyapunov("gbsb", 2000, 256, A16, c=0.5, dt=1.25, renorm_every=10, nsteps=steps)
+    el = time.perf_counter() - t
+    flop = 2.0 * 2000 ** 2 * (2 * 16 * 256) * steps
+    out["lyapunov"] = {
+        "workload": "N=2000 SK N(0,1/N), R=256 x 16 A in [0, 0.375], first 200 of M=2000 steps, renorm 10",
+        "value": 16 * 256 * steps / el, "unit": "replica-steps/s (with tangents)",
+        "mean_mle_by_A": [float(np.mean(mle[k][np.isfinite(mle[k])])) if np.isfinite(mle[k]).any()
+                          else None for k in range(16)],
+        "roofline": {"bound": "alu", "kernel": "k_tangent_step", "achieved": flop / el / 1e12,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / el / 1e12 / fp32_peak,
+                     "how": "host wall clock around gsb_lyapunov (allocation included)"}}
+    # --- adjoint gradient: N = 2000 SK, R = 256, 200-step window, checkpoints every 20
+    R5, W = 256, 200
+    x0 = torch.from_numpy(O.init_uniform(R5, 2000, 1).astype(np.float32)).cuda()
+    E = torch.empty(R5, dtype=torch.float64, device="cuda")
+    gx = torch.empty_like(x0)
+    gA = torch.empty(R5, dtype=torch.float64, device="cuda")
+    gdt = torch.empty(R5, dtype=torch.float64, device="cuda")
+    args = (x0.data_ptr(), R5, 0.2, 1.25, 0.5, E.data_ptr(), gx.data_ptr(), gA.data_ptr(),
+            gdt.data_ptr())
+    P5.relaxed_energy_grad("gbsb", 21500, 20, *args, ckpt_every=20, stream=stream.cuda_stream)
+    t = time.perf_counter()
+    P5.relaxed_energy_grad("gbsb", 21500, W, *args, ckpt_every=20, stream=stream.cuda_stream)
+    el = time.perf_counter() - t
+    # forward W + recompute W - K + reverse W SGEMMs of 2 N^2 R flop
+    flop = 2.0 * 2000 ** 2 * R5 * (3 * W - 20)
+    out["adjoint"] = {
+        "workload": "N=2000 SK N(0,1/N), R=256, gradient over a 200-step window, checkpoints every 20",
+        "value": R5 / el, "unit": "gradients/s (one per replica)", "ms_per_call": 1e3 * el,
+        "roofline": {"bound": "alu", "kernel": "k_adj_fwd / k_adj_post (FP32 SGEMM)",
+                     "achieved": flop / el / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": flop / el / 1e12 / fp32_peak,
+                     "how": "host wall clock around gsb_relaxed_energy_grad (allocation included)"}}
+    P5.close()
+    return out
 
 
 def e2e_leg(gsb, J, c, A, K):
