@@ -218,12 +218,13 @@ def gpu_arm(args, world, rank, local):
             kern_steps += nst
             energies.append(run.best()["E"])
         launches = gsb.launch_count() - launches0
+        kernel = run.kernel()
         run.close()
-        return times, (kern_ms, kern_n, kern_steps), np.concatenate(energies), launches
+        return times, (kern_ms, kern_n, kern_steps), np.concatenate(energies), launches, kernel
 
     # headline: GdSB on FP8 tensor cores
     with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0)) as clk:
-        times, (kern_ms, kern_n, kern_steps), energies, launches = timed_runs(
+        times, (kern_ms, kern_n, kern_steps), energies, launches, kernel_name = timed_runs(
             "gdsb", "fp8", args.steps, args.warmup, 1000 * rank)
     clocks = clk.summary()
     total_ms = sum(times)
@@ -244,7 +245,7 @@ def gpu_arm(args, world, rank, local):
     flops_launch = 2.0 * N_SPINS * N_SPINS * R_REPLICAS * steps_per_launch
     achieved = flops_launch / avg_launch_s / 1e12
     roofline = {"bound": "tensor",
-                "kernel": "k_tc_persist<true> (e4m3 J.sgn(x) + Eqs. 3-7, state in TMEM)",
+                "kernel": f"{kernel_name}<true> (e4m3 J.sgn(x) + Eqs. 3-7)",
                 "achieved": round(achieved, 1), "peak": round(fp8_peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / fp8_peak, 4), "traffic": None,
                 "peak_source": f"{how}: 2 x bf16 sustained (e4m3/bf16 nominal ratio)",
@@ -267,7 +268,7 @@ def gpu_arm(args, world, rank, local):
         E = target_energy()
         out["success"] = success_report(energies, A, args.steps, E, ms_per_step)
         # the paper's GbSB (x coupling) on the exact FX32 tensor-core path
-        t2, (km2, kn2, ks2), e2, _ = timed_runs("gbsb", "fx32", 2, 1, 7000)
+        t2, (km2, kn2, ks2), e2, _, _ = timed_runs("gbsb", "fx32", 2, 1, 7000)
         fx_ms = sum(t2) / len(t2)
         us2 = 1e3 * km2 / ks2
         out["gbsb_fx32"] = {"value": N_SPINS * R_REPLICAS * M_STEPS / (fx_ms / 1e3),
@@ -277,7 +278,7 @@ def gpu_arm(args, world, rank, local):
                                                         Pk["bf16_tflops_sustained"],
                             "success": success_report(e2, A, 2, E, fx_ms)}
         # the plain FP32 form, same workload (one run)
-        t3, (km3, kn3, ks3), e3, _ = timed_runs("gdsb", "fp32", 1, 1, 9000)
+        t3, (km3, kn3, ks3), e3, _, _ = timed_runs("gdsb", "fp32", 1, 1, 9000)
         out["plain_fp32"] = {"value": N_SPINS * R_REPLICAS * M_STEPS / (t3[0] / 1e3),
                              "ms_per_step": t3[0], "us_per_time_step": 1e3 * km3 / ks3}
         out["fused_vs_plain"] = value / world / out["plain_fp32"]["value"]

@@ -733,6 +733,13 @@ gsb_status gsb_run_restart(gsb_run_state* run, uint64_t seed, uint32_t flags) {
     return gsb_run_steps(run, run->params.M);
 }
 
+const char* gsb_run_kernel(const gsb_run_state* run) {
+    if (!run) return "";
+    if (run->path == kPathDenseF32) return "k_dense_f32_step";
+    if (run->path == kPathCsr) return "k_csr_step";
+    return tc_kernel_name(run);
+}
+
 gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches, int64_t* steps) {
     if (!run) return set_error(GSB_EINVAL, "run is NULL");
     GSB_CUDA_TRY(cudaStreamSynchronize(run->stream));

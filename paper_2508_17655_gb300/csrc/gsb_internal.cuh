@@ -155,6 +155,7 @@ gsb_status tc_prepare(gsb_run_state* run);
 gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps);
 gsb_status tc_energy(gsb_run_state* run);
 void tc_free(gsb_run_state* run);
+const char* tc_kernel_name(const gsb_run_state* run);
 // GSB_RUN_PROFILE bracketing of a step-kernel launch
 gsb_status prof_begin(gsb_run_state* run);
 gsb_status prof_end(gsb_run_state* run, int steps);

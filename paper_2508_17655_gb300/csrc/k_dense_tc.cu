@@ -266,10 +266,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 // reads TMEM lanes 32 (w % 4).., columns 64 ((w - 2) / 4) .. +63).
 constexpr int kThreadsP = 320;
 constexpr int kEpiThreadsP = 256;
-constexpr int kStagesP = 6;
+// A ring stage holds kAtomsP consecutive 128-byte K slices of J and of V: the
+// MMA issuer's fixed cost per stage (barrier wait, fence, commit -- about as
+// long as four MMAs) is paid once per eight MMAs.
+constexpr int kAtomsP = 2;
+constexpr int kStagesP = 3;
 
 __host__ __device__ constexpr int smem_bytes_persist() {
-    return 1024 + kStagesP * 2 * BM * KB + 256 + BN * 4;
+    return 1024 + kStagesP * kAtomsP * 2 * BM * KB + 256 + BN * 4;
 }
 
 template <bool CONTROL>
@@ -281,7 +285,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                  const float* __restrict__ p_sched, int M, int m0, int nsteps,
                  uint32_t* __restrict__ counters, int* status) {
     constexpr int S = kStagesP;
-    constexpr int SA = BM * KB, SB = BN * KB;
+    constexpr int SA1 = BM * KB, SB1 = BN * KB;  // one K atom of J / of V
+    constexpr int SA = kAtomsP * SA1, SB = kAtomsP * SB1;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
@@ -295,7 +300,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
-    const int nk = Np / KB;
+    const int nk = Np / KB;                       // K atoms per step
+    const int ns = (nk + kAtomsP - 1) / kAtomsP;  // ring stages per step
     const uint32_t nI = gridDim.y;
     uint32_t* ctr = counters + blockIdx.x;
 
@@ -321,18 +327,28 @@ __global__ void __launch_bounds__(kThreadsP, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            uint32_t g = 0;  // ring slot counter across steps
-            const int pre = nk < S ? nk : S;
+            uint32_t g = 0;  // ring stage counter across steps
+            const int pre = ns < S ? ns : S;
             bool ok = true;
+            // K atoms u kAtomsP .. of a step go to stage u
+            auto atoms = [&](int u) { return nk - u * kAtomsP < kAtomsP ? nk - u * kAtomsP : kAtomsP; };
+            auto load_j = [&](int u, uint32_t st) {
+                mbar_arrive_expect_tx(&full[st], (uint32_t)atoms(u) * (SA1 + SB1));
+                for (int a = 0; a < atoms(u); ++a)
+                    tma_load_2d(sA + st * SA + a * SA1, &tmA, &full[st], (u * kAtomsP + a) * KB, i0);
+            };
+            auto load_v = [&](int u, uint32_t st, const CUtensorMap* tv) {
+                for (int a = 0; a < atoms(u); ++a)
+                    tma_load_2d(sB + st * SB + a * SB1, tv, &full[st], (u * kAtomsP + a) * KB, r0);
+            };
             for (int s = 0; s < nsteps && ok; ++s) {
                 const CUtensorMap* tv = ((m0 + s) & 1) ? &tmV1 : &tmV0;
-                // J slices for the first ring slots: independent of the other CTAs
-                for (int kc = 0; kc < pre && ok; ++kc) {
-                    const uint32_t gg = g + kc, st = gg % S, ph = (gg / S) & 1u;
+                // J for the first ring stages: independent of the other CTAs
+                for (int u = 0; u < pre && ok; ++u) {
+                    const uint32_t gg = g + u, st = gg % S, ph = (gg / S) & 1u;
                     if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) ok = false;
                     if (!ok) break;
-                    mbar_arrive_expect_tx(&full[st], SA + SB);
-                    tma_load_2d(sA + st * SA, &tmA, &full[st], kc * KB, i0);
+                    load_j(u, st);
                 }
                 if (!ok) break;
                 // V of this step is complete once every CTA of the replica block published it
@@ -340,19 +356,15 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     if (!wait_counter(ctr, nI * (uint32_t)s, status)) break;
                     fence_proxy_async();
                 }
-                for (int kc = 0; kc < pre; ++kc) {
-                    const uint32_t st = (g + kc) % S;
-                    tma_load_2d(sB + st * SB, tv, &full[st], kc * KB, r0);
-                }
-                for (int kc = pre; kc < nk && ok; ++kc) {
-                    const uint32_t gg = g + kc, st = gg % S, ph = (gg / S) & 1u;
+                for (int u = 0; u < pre; ++u) load_v(u, (g + u) % S, tv);
+                for (int u = pre; u < ns && ok; ++u) {
+                    const uint32_t gg = g + u, st = gg % S, ph = (gg / S) & 1u;
                     if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) ok = false;
                     if (!ok) break;
-                    mbar_arrive_expect_tx(&full[st], SA + SB);
-                    tma_load_2d(sA + st * SA, &tmA, &full[st], kc * KB, i0);
-                    tma_load_2d(sB + st * SB, tv, &full[st], kc * KB, r0);
+                    load_j(u, st);
+                    load_v(u, st, tv);
                 }
-                g += nk;
+                g += ns;
             }
         }
     } else if (warp == 1) {
@@ -363,18 +375,22 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             for (int s = 0; s < nsteps && ok; ++s) {
                 if (s > 0 && !mbar_wait(acce, (uint32_t)(s - 1) & 1u, status)) break;
                 fence_after_sync();
-                for (int kc = 0; kc < nk; ++kc, ++g) {
+                for (int u = 0; u < ns; ++u, ++g) {
                     const uint32_t st = g % S, ph = (g / S) & 1u;
                     if (!mbar_wait(&full[st], ph, status)) {
                         ok = false;
                         break;
                     }
                     fence_after_sync();
-                    const uint32_t a0 = smem_u32(sA + st * SA), b0 = smem_u32(sB + st * SB);
+                    const int na = nk - u * kAtomsP < kAtomsP ? nk - u * kAtomsP : kAtomsP;
+                    for (int a = 0; a < na; ++a) {
+                        const uint32_t a0 = smem_u32(sA + st * SA + a * SA1);
+                        const uint32_t b0 = smem_u32(sB + st * SB + a * SB1);
 #pragma unroll
-                    for (int k = 0; k < KB / 32; ++k)
-                        mma_f8f6f4(tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
-                                   (kc | k) != 0);
+                        for (int k = 0; k < KB / 32; ++k)
+                            mma_f8f6f4(tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32),
+                                       idesc, (u | a | k) != 0);
+                    }
                     mma_commit(&empty[st]);
                 }
                 if (ok) mma_commit(accf);
@@ -423,13 +439,27 @@ __global__ void __launch_bounds__(kThreadsP, 1)
 #pragma unroll 1
             for (int cb = c0; cb < c0 + 64; cb += 16) {
                 float f[16], xs[16], ys[16], ps[16];
-                tmem_ld16(tl + cb, f);
-                tmem_ld16(tl + 128 + cb, xs);
-                tmem_ld16(tl + 256 + cb, ys);
-                if (CONTROL) tmem_ld16(tl + 384 + cb, ps);
+                {
+                    // the four loads in flight together, one wait
+                    uint32_t rf[16], rx[16], ry[16], rp[16];
+                    tmem_ld16_async(tl + cb, rf);
+                    tmem_ld16_async(tl + 128 + cb, rx);
+                    tmem_ld16_async(tl + 256 + cb, ry);
+                    if (CONTROL) tmem_ld16_async(tl + 384 + cb, rp);
+                    tmem_wait_ld(rf);
+                    tmem_wait_ld(rx);
+                    tmem_wait_ld(ry);
+                    if (CONTROL) tmem_wait_ld(rp);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        f[k] = __uint_as_float(rf[k]);
+                        xs[k] = __uint_as_float(rx[k]);
+                        ys[k] = __uint_as_float(ry[k]);
+                        ps[k] = CONTROL ? __uint_as_float(rp[k]) : 0.f;
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
-                    if (!CONTROL) ps[k] = 0.f;
                     sb_update<CONTROL>(xs[k], ys[k], ps[k], f[k], CONTROL ? sAv[cb + k] : 0.f,
                                        c, dt, p_shared, inv_rem);
                 }
@@ -439,9 +469,11 @@ __global__ void __launch_bounds__(kThreadsP, 1)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) vn[(size_t)(r0 + cb + k) * Np + i] = e4m3_sign(xs[k]);
             }
+            // Each thread makes its V bytes visible to the async proxy (the TMA
+            // loads of the other CTAs); the block barrier orders every thread's
+            // writes before the one release add, which is cumulative over them.
             tmem_wait_st();
             fence_before_sync();
-            __threadfence();
             fence_proxy_async();
             named_barrier_sync(1, kEpiThreadsP);
             if (*abort_flag) break;
@@ -565,6 +597,14 @@ gsb_status launch_step(gsb_run_state* run, TcState* T, float p_shared, float inv
 
 bool tc_available() { return true; }
 
+const char* tc_kernel_name(const gsb_run_state* run) {
+    const TcState* T = (const TcState*)run->tc;
+    if (!T) return "none";
+    if (T->kind == 1) return "k_tc_step<fx32>";
+    if (T->persistent) return "k_tc_persist";
+    return "k_tc_step<e4m3>";
+}
+
 gsb_status tc_setup(gsb_run_state* run) {
     const gsb_problem* P = run->prob;
     TcState* T = new TcState();
@@ -603,14 +643,15 @@ gsb_status tc_setup(gsb_run_state* run) {
         GSB_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         T->persistent = coop && per_sm >= 1 && grid <= (long)per_sm * sms &&
                         run->params.steps_per_launch != 1;
-        if (T->persistent) {
+        if (T->persistent)
             GSB_CUDA_TRY(cudaMalloc(&T->counters, sizeof(uint32_t) * (run->Rp / BN)));
-            std::vector<float> ps(run->params.M);
-            for (int m = 0; m < run->params.M; ++m) ps[m] = run_p_shared(run, m + 1);
-            GSB_CUDA_TRY(cudaMalloc(&T->p_sched, sizeof(float) * run->params.M));
-            GSB_CUDA_TRY(cudaMemcpy(T->p_sched, ps.data(), sizeof(float) * run->params.M,
-                                    cudaMemcpyHostToDevice));
-        }
+    }
+    if (T->persistent) {
+        std::vector<float> ps(run->params.M);
+        for (int m = 0; m < run->params.M; ++m) ps[m] = run_p_shared(run, m + 1);
+        GSB_CUDA_TRY(cudaMalloc(&T->p_sched, sizeof(float) * run->params.M));
+        GSB_CUDA_TRY(cudaMemcpy(T->p_sched, ps.data(), sizeof(float) * run->params.M,
+                                cudaMemcpyHostToDevice));
     }
     return tc_prepare(run);
 }

@@ -116,6 +116,8 @@ def _declare(L):
     L.gsb_kernel_time.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.gsb_kernel_time.restype = st
+    L.gsb_run_kernel.argtypes = [_vp]
+    L.gsb_run_kernel.restype = ctypes.c_char_p
     L.gsb_lyapunov.argtypes = [_vp, ctypes.POINTER(gsb_params), ctypes.c_int32,
                                ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.c_int32,
                                ctypes.POINTER(ctypes.c_double), _vp]
@@ -384,6 +386,10 @@ class Run:
 
     def restart(self, seed, defer=False):
         _check(lib().gsb_run_restart(self.handle, int(seed), RUN_DEFER if defer else 0))
+
+    def kernel(self):
+        """Name of the step kernel this run selected."""
+        return lib().gsb_run_kernel(self.handle).decode()
 
     def kernel_time(self):
         """(total ms, launches, steps covered) of the step kernel since the last (re)start."""

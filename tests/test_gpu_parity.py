@@ -336,10 +336,13 @@ def test_lambda_and_auto_parameters_match_oracle():
 
 
 @pytest.mark.parametrize("variant", ["dsb", "gdsb"])
-def test_fp8_persistent_matches_per_step_launches_bit_exact(variant):
-    """The persistent FP8 kernel (state in TMEM, many steps per launch) and the
-    one-step-per-launch FP8 kernel do the same arithmetic: identical bits."""
-    N, R, M = 300, 200, 120
+@pytest.mark.parametrize("N,R", [(100, 130), (300, 200), (2000, 128), (2100, 129)])
+def test_fp8_persistent_matches_per_step_launches_bit_exact(variant, N, R):
+    """The persistent FP8 kernel (state in TMEM, many steps per launch; 1, 3,
+    16 and 17 K atoms per step, so ring stages of two atoms and a last stage of
+    one) and the one-step-per-launch FP8 kernel do the same arithmetic:
+    identical bits."""
+    M = 120
     J = I.sk_pm1(N, 41)
     P = gsb.Problem.dense(J)
     kw = dict(M=M, R=R, c=f32(1 / (2 * math.sqrt(N))), dt=1.25, A=0.3, seed=8, precision="fp8",
@@ -347,6 +350,7 @@ def test_fp8_persistent_matches_per_step_launches_bit_exact(variant):
     outs = []
     for spl in (1, 0, 7):
         run = P.run(variant, steps_per_launch=spl, **kw)
+        assert run.kernel() == ("k_tc_step<e4m3>" if spl == 1 else "k_tc_persist")
         outs.append((run.state(), run.best()))
     for st, b in outs[1:]:
         for k in ("x", "y", "p"):
