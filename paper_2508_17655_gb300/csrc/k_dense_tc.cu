@@ -254,16 +254,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---------------------------------------------------------------------------
 // Persistent form of the FP8 step: one cooperative launch runs many steps.
-// Each CTA keeps its tile's x, y (and p) in TMEM next to the accumulator
-// (columns [0,128) F, [128,256) x, [256,384) y, [384,512) p), so a step moves
-// no state through global memory: only the 16 KB of the next V tile leave the
-// SM. The CTAs that share a replica block (one grid column) then meet at a
+// The tile is transposed against k_tc_step: the MMA forms F^T = V J^T, so a
+// TMEM lane is a replica and a column a spin. Each CTA keeps its tile's x, y
+// (and p) in TMEM next to the accumulator (columns [0,128) F; [128,384) x and
+// y of each 16 spins side by side, 32 columns per chunk, so one 32-column
+// load or store moves both; [384,512) p), so a step moves no state through
+// global memory:
+// only the 16 KB of the next V tile leave the SM, each thread writing 16
+// consecutive bytes of its replica's row of V at a time. The products are
+// +-J_ij and the sums integers, so F is bit-identical to k_tc_step's. The CTAs that share a replica block (one grid column) then meet at a
 // counter in global memory (release add / acquire poll, bounded) before any
 // of them loads that block's next V. J does not change, so the producer issues
 // the first ring slots' J tiles before it waits.
 //
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2-9 epilogue (warp w
-// reads TMEM lanes 32 (w % 4).., columns 64 ((w - 2) / 4) .. +63).
+// reads TMEM lanes 32 (w % 4).. -- its 32 replicas -- and columns 64 ((w - 2)
+// / 4) .. +63 -- 64 spins).
 constexpr int kThreadsP = 320;
 constexpr int kEpiThreadsP = 256;
 // A ring stage holds kAtomsP consecutive 128-byte K slices of J and of V: the
@@ -273,7 +279,7 @@ constexpr int kAtomsP = 2;
 constexpr int kStagesP = 3;
 
 __host__ __device__ constexpr int smem_bytes_persist() {
-    return 1024 + kStagesP * kAtomsP * 2 * BM * KB + 256 + BN * 4;
+    return 1024 + kStagesP * kAtomsP * 2 * BM * KB + 256;
 }
 
 template <bool CONTROL>
@@ -296,7 +302,6 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     uint64_t* accf = empty + S;
     uint64_t* acce = accf + 1;
     uint32_t* tmem_slot = (uint32_t*)(acce + 1);
-    float* sAv = (float*)(smem + S * (SA + SB) + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
@@ -319,7 +324,6 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         tma_prefetch_desc(&tmV1);
     }
     if (warp == 1) tmem_alloc(tmem_slot, 512);
-    if (threadIdx.x >= 64 && threadIdx.x < 64 + BN) sAv[threadIdx.x - 64] = A[r0 + threadIdx.x - 64];
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -388,7 +392,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                         const uint32_t b0 = smem_u32(sB + st * SB + a * SB1);
 #pragma unroll
                         for (int k = 0; k < KB / 32; ++k)
-                            mma_f8f6f4(tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32),
+                            mma_f8f6f4(tmem, sdesc_sw128(b0 + k * 32), sdesc_sw128(a0 + k * 32),
                                        idesc, (u | a | k) != 0);
                     }
                     mma_commit(&empty[st]);
@@ -400,22 +404,24 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         const int ew = warp - 2;
         const int quarter = warp & 3;
         const int c0 = (ew >> 2) * 64;
-        const int i = i0 + quarter * 32 + lane;
+        const int r = r0 + quarter * 32 + lane;  // this thread's replica (TMEM lane)
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-        // state of this thread's spin, columns c0 .. c0+63, into TMEM
+        const float a_r = CONTROL ? A[r] : 0.f;
+        // state of this thread's replica, spins i0 + c0 .. +63, into TMEM
 #pragma unroll 1
         for (int cb = c0; cb < c0 + 64; cb += 16) {
-            const size_t o = (size_t)i * Rp + r0 + cb;
+            const size_t o = (size_t)(i0 + cb) * Rp + r;
             float v[16];
+            float w[16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = x[o + k];
-            tmem_st16(tl + 128 + cb, v);
-#pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = y[o + k];
-            tmem_st16(tl + 256 + cb, v);
+            for (int k = 0; k < 16; ++k) {
+                v[k] = x[o + (size_t)k * Rp];
+                w[k] = y[o + (size_t)k * Rp];
+            }
+            tmem_st32(tl + 128 + 2 * cb, v, w);
             if (CONTROL) {
 #pragma unroll
-                for (int k = 0; k < 16; ++k) v[k] = p[o + k];
+                for (int k = 0; k < 16; ++k) v[k] = p[o + (size_t)k * Rp];
                 tmem_st16(tl + 384 + cb, v);
             }
         }
@@ -435,7 +441,9 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             fence_after_sync();
             const float inv_rem = __frcp_rn((float)(M - m));
             const float p_shared = CONTROL ? 0.f : p_sched[s];
-            uint8_t* vn = (m & 1) ? v0 : v1;  // V(t_{m+1}) goes to buffer (m + 1) & 1
+            // V(t_{m+1}) goes to buffer (m + 1) & 1; this thread's 16 spins of a
+            // chunk are 16 consecutive bytes of its replica's row
+            uint8_t* vrow = ((m & 1) ? v0 : v1) + (size_t)r * Np + i0;
 #pragma unroll 1
             for (int cb = c0; cb < c0 + 64; cb += 16) {
                 float f[16], xs[16], ys[16], ps[16];
@@ -443,8 +451,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     // the four loads in flight together, one wait
                     uint32_t rf[16], rx[16], ry[16], rp[16];
                     tmem_ld16_async(tl + cb, rf);
-                    tmem_ld16_async(tl + 128 + cb, rx);
-                    tmem_ld16_async(tl + 256 + cb, ry);
+                    tmem_ld32_async(tl + 128 + 2 * cb, rx, ry);
                     if (CONTROL) tmem_ld16_async(tl + 384 + cb, rp);
                     tmem_wait_ld(rf);
                     tmem_wait_ld(rx);
@@ -459,22 +466,25 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    sb_update<CONTROL>(xs[k], ys[k], ps[k], f[k], CONTROL ? sAv[cb + k] : 0.f,
-                                       c, dt, p_shared, inv_rem);
-                }
-                tmem_st16(tl + 128 + cb, xs);
-                tmem_st16(tl + 256 + cb, ys);
+                for (int k = 0; k < 16; ++k)
+                    sb_update<CONTROL>(xs[k], ys[k], ps[k], f[k], a_r, c, dt, p_shared, inv_rem);
+                tmem_st32(tl + 128 + 2 * cb, xs, ys);
                 if (CONTROL) tmem_st16(tl + 384 + cb, ps);
+                uint32_t w[4];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) vn[(size_t)(r0 + cb + k) * Np + i] = e4m3_sign(xs[k]);
+                for (int q = 0; q < 4; ++q)
+                    w[q] = (uint32_t)e4m3_sign(xs[4 * q]) | ((uint32_t)e4m3_sign(xs[4 * q + 1]) << 8) |
+                           ((uint32_t)e4m3_sign(xs[4 * q + 2]) << 16) |
+                           ((uint32_t)e4m3_sign(xs[4 * q + 3]) << 24);
+                *reinterpret_cast<uint4*>(vrow + cb) = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            // Each thread makes its V bytes visible to the async proxy (the TMA
-            // loads of the other CTAs); the block barrier orders every thread's
-            // writes before the one release add, which is cumulative over them.
+            // The block barrier orders every thread's V bytes before the one
+            // release add, which is cumulative over them; the readers' TMA loads
+            // (async proxy) are ordered after them by the proxy fence each
+            // producer issues after its acquire -- one proxy fence on the
+            // release/acquire path suffices, none is needed here.
             tmem_wait_st();
             fence_before_sync();
-            fence_proxy_async();
             named_barrier_sync(1, kEpiThreadsP);
             if (*abort_flag) break;
             if (ew == 0 && lane == 0) {
@@ -485,18 +495,18 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         // state back to global memory
 #pragma unroll 1
         for (int cb = c0; cb < c0 + 64; cb += 16) {
-            const size_t o = (size_t)i * Rp + r0 + cb;
+            const size_t o = (size_t)(i0 + cb) * Rp + r;
             float v[16];
-            tmem_ld16(tl + 128 + cb, v);
+            tmem_ld16(tl + 128 + 2 * cb, v);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) x[o + k] = v[k];
-            tmem_ld16(tl + 256 + cb, v);
+            for (int k = 0; k < 16; ++k) x[o + (size_t)k * Rp] = v[k];
+            tmem_ld16(tl + 128 + 2 * cb + 16, v);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) y[o + k] = v[k];
+            for (int k = 0; k < 16; ++k) y[o + (size_t)k * Rp] = v[k];
             if (CONTROL) {
                 tmem_ld16(tl + 384 + cb, v);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) p[o + k] = v[k];
+                for (int k = 0; k < 16; ++k) p[o + (size_t)k * Rp] = v[k];
             }
         }
     }

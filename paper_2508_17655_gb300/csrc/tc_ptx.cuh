@@ -149,6 +149,23 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
                  : "memory");
 }
 
+// 32 consecutive columns: thread t receives lane (base lane + t), columns
+// col .. col+31 (no wait; tmem_wait_ld on both halves before use).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&lo)[16],
+                                                uint32_t (&hi)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(lo[0]), "=r"(lo[1]), "=r"(lo[2]), "=r"(lo[3]), "=r"(lo[4]), "=r"(lo[5]),
+          "=r"(lo[6]), "=r"(lo[7]), "=r"(lo[8]), "=r"(lo[9]), "=r"(lo[10]), "=r"(lo[11]),
+          "=r"(lo[12]), "=r"(lo[13]), "=r"(lo[14]), "=r"(lo[15]), "=r"(hi[0]), "=r"(hi[1]),
+          "=r"(hi[2]), "=r"(hi[3]), "=r"(hi[4]), "=r"(hi[5]), "=r"(hi[6]), "=r"(hi[7]),
+          "=r"(hi[8]), "=r"(hi[9]), "=r"(hi[10]), "=r"(hi[11]), "=r"(hi[12]), "=r"(hi[13]),
+          "=r"(hi[14]), "=r"(hi[15])
+        : "r"(taddr));
+}
+
 // Store 16 consecutive columns of this warp's 32 TMEM lanes (one per thread).
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
     asm volatile(
@@ -160,6 +177,26 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
         "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
         "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
         "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+// Store 32 consecutive columns: lo to col .. col+15, hi to col+16 .. col+31.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&lo)[16],
+                                          const float (&hi)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(__float_as_uint(lo[0])), "r"(__float_as_uint(lo[1])), "r"(__float_as_uint(lo[2])),
+        "r"(__float_as_uint(lo[3])), "r"(__float_as_uint(lo[4])), "r"(__float_as_uint(lo[5])),
+        "r"(__float_as_uint(lo[6])), "r"(__float_as_uint(lo[7])), "r"(__float_as_uint(lo[8])),
+        "r"(__float_as_uint(lo[9])), "r"(__float_as_uint(lo[10])), "r"(__float_as_uint(lo[11])),
+        "r"(__float_as_uint(lo[12])), "r"(__float_as_uint(lo[13])), "r"(__float_as_uint(lo[14])),
+        "r"(__float_as_uint(lo[15])), "r"(__float_as_uint(hi[0])), "r"(__float_as_uint(hi[1])),
+        "r"(__float_as_uint(hi[2])), "r"(__float_as_uint(hi[3])), "r"(__float_as_uint(hi[4])),
+        "r"(__float_as_uint(hi[5])), "r"(__float_as_uint(hi[6])), "r"(__float_as_uint(hi[7])),
+        "r"(__float_as_uint(hi[8])), "r"(__float_as_uint(hi[9])), "r"(__float_as_uint(hi[10])),
+        "r"(__float_as_uint(hi[11])), "r"(__float_as_uint(hi[12])), "r"(__float_as_uint(hi[13])),
+        "r"(__float_as_uint(hi[14])), "r"(__float_as_uint(hi[15]))
         : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() {
