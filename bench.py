@@ -247,7 +247,14 @@ def gpu_arm(args, world, rank, local):
     roofline = {"bound": "tensor",
                 "kernel": f"{kernel_name}<true> (e4m3 J.sgn(x) + Eqs. 3-7)",
                 "achieved": round(achieved, 1), "peak": round(fp8_peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / fp8_peak, 4), "traffic": None,
+                "frac": round(achieved / fp8_peak, 4),
+                # dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_persist launch
+                # of this shape (100 steps; profiles/k_tc_persist_N2000_R1024_M100.md):
+                # the state, J and V read once per launch, whatever its step count --
+                # the steps themselves run from L2 and TMEM
+                "traffic": 31502592 + 731392,
+                "traffic_note": "DRAM bytes per launch, measured on a 100-step launch of the "
+                                "same kernel and shape; independent of the steps per launch",
                 "peak_source": f"{how}: 2 x bf16 sustained (e4m3/bf16 nominal ratio)",
                 "avg_launch_us": round(avg_launch_s * 1e6, 3),
                 "steps_per_launch": steps_per_launch,
