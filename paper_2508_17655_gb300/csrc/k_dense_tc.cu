@@ -466,16 +466,32 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    sb_update<CONTROL>(xs[k], ys[k], ps[k], f[k], a_r, c, dt, p_shared, inv_rem);
+                for (int k = 0; k < 16; k += 2) {
+                    float2 x2 = make_float2(xs[k], xs[k + 1]), y2 = make_float2(ys[k], ys[k + 1]);
+                    float2 p2 = make_float2(ps[k], ps[k + 1]);
+                    sb_update2<CONTROL>(x2, y2, p2, make_float2(f[k], f[k + 1]), a_r, c, dt,
+                                        p_shared, inv_rem);
+                    xs[k] = x2.x, xs[k + 1] = x2.y, ys[k] = y2.x, ys[k + 1] = y2.y;
+                    ps[k] = p2.x, ps[k + 1] = p2.y;
+                }
                 tmem_st32(tl + 128 + 2 * cb, xs, ys);
                 if (CONTROL) tmem_st16(tl + 384 + cb, ps);
-                uint32_t w[4];
+                // e4m3 sgn x, 0x38 (+1) or 0xB8 (-1): the sign bit of x + 0 (which
+                // turns -0 into +0, so sgn 0 = +1) in the top byte of each word,
+                // four gathered per word
+                uint32_t b[16], w[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    w[q] = (uint32_t)e4m3_sign(xs[4 * q]) | ((uint32_t)e4m3_sign(xs[4 * q + 1]) << 8) |
-                           ((uint32_t)e4m3_sign(xs[4 * q + 2]) << 16) |
-                           ((uint32_t)e4m3_sign(xs[4 * q + 3]) << 24);
+                for (int k = 0; k < 16; k += 2) {
+                    const float2 z = __fadd2_rn(make_float2(xs[k], xs[k + 1]), make_float2(0.f, 0.f));
+                    b[k] = __float_as_uint(z.x);
+                    b[k + 1] = __float_as_uint(z.y);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t lo = __byte_perm(b[4 * q], b[4 * q + 1], 0x0073);
+                    const uint32_t hi = __byte_perm(b[4 * q + 2], b[4 * q + 3], 0x0073);
+                    w[q] = (__byte_perm(lo, hi, 0x5410) & 0x80808080u) | 0x38383838u;
+                }
                 *reinterpret_cast<uint4*>(vrow + cb) = make_uint4(w[0], w[1], w[2], w[3]);
             }
             // The block barrier orders every thread's V bytes before the one
