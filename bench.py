@@ -245,7 +245,7 @@ def gpu_arm(args, world, rank, local):
     flops_launch = 2.0 * N_SPINS * N_SPINS * R_REPLICAS * steps_per_launch
     achieved = flops_launch / avg_launch_s / 1e12
     roofline = {"bound": "tensor",
-                "kernel": f"{kernel_name}<true> (e4m3 J.sgn(x) + Eqs. 3-7)",
+                "kernel": f"{kernel_name} (GdSB: e4m3 J.sgn(x) + Eqs. 3-7)",
                 "achieved": round(achieved, 1), "peak": round(fp8_peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / fp8_peak, 4),
                 # dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_persist launch

@@ -160,8 +160,9 @@ gsb_status gsb_run_restart(gsb_run_state* run, uint64_t seed, uint32_t flags);
  * on the run's stream. */
 gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches, int64_t* steps);
 
-/* Name of the step kernel the run selected at gsb_run: "k_tc_persist" (FP8,
- * cooperative, many steps per launch), "k_tc_step<e4m3>"
+/* Name of the step kernel the run selected at gsb_run: "k_tc_persist<cluster>"
+ * (FP8, many steps per launch, one thread-block cluster per 128 replicas),
+ * "k_tc_persist<grid>" (the same, one cooperative launch), "k_tc_step<e4m3>"
  * or "k_tc_step<fx32>" (one step per launch), "k_dense_f32_step" or
  * "k_csr_step". A static string owned by the library; "" for NULL. No GPU
  * work. */

@@ -253,19 +253,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Persistent form of the FP8 step: one cooperative launch runs many steps.
+// Persistent form of the FP8 step: one launch runs many steps.
 // The tile is transposed against k_tc_step: the MMA forms F^T = V J^T, so a
 // TMEM lane is a replica and a column a spin. Each CTA keeps its tile's x, y
 // (and p) in TMEM next to the accumulator (columns [0,128) F; [128,384) x and
 // y of each 16 spins side by side, 32 columns per chunk, so one 32-column
 // load or store moves both; [384,512) p), so a step moves no state through
-// global memory:
-// only the 16 KB of the next V tile leave the SM, each thread writing 16
-// consecutive bytes of its replica's row of V at a time. The products are
-// +-J_ij and the sums integers, so F is bit-identical to k_tc_step's. The CTAs that share a replica block (one grid column) then meet at a
-// counter in global memory (release add / acquire poll, bounded) before any
-// of them loads that block's next V. J does not change, so the producer issues
-// the first ring slots' J tiles before it waits.
+// global memory: only the 16 KB of the next V tile leave the SM, each thread
+// writing 16 consecutive bytes of its replica's row of V at a time. The
+// products are +-J_ij and the sums integers, so F is bit-identical to
+// k_tc_step's whatever the order of the K slices.
+//
+// The CTAs that share a replica block (a column) exchange those V tiles
+// between steps in one of two ways:
+//   CLUSTER = true (Np <= 16 x 128): the column is one thread-block cluster.
+//     After its epilogue each CTA arrives (release, cluster scope) on the
+//     step's barrier (count: the CTAs of the column) in every CTA of the
+//     cluster, and a producer waits on its own copy before it loads the step's
+//     V, the K slices in rotated order from its own. Columns are independent
+//     clusters, so no grid-wide co-residency is needed. Two barriers,
+//     alternating with the step's parity: a writer can run at most one step
+//     ahead of a reader, so a reader's parity wait is never two phases behind.
+//   CLUSTER = false (any Np): a cooperative launch; the column meets at a
+//     counter in global memory (release add / acquire poll, bounded) before
+//     any of its CTAs loads the column's next V.
+// J does not change, so the producer issues the first ring stages' J tiles
+// before it waits.
 //
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2-9 epilogue (warp w
 // reads TMEM lanes 32 (w % 4).. -- its 32 replicas -- and columns 64 ((w - 2)
@@ -277,12 +290,13 @@ constexpr int kEpiThreadsP = 256;
 // long as four MMAs) is paid once per eight MMAs.
 constexpr int kAtomsP = 2;
 constexpr int kStagesP = 3;
+constexpr int kMaxClusterP = 16;  // the largest (non-portable) cluster
 
 __host__ __device__ constexpr int smem_bytes_persist() {
-    return 1024 + kStagesP * kAtomsP * 2 * BM * KB + 256;
+    return 1024 + kStagesP * kAtomsP * 2 * BM * KB + 512;
 }
 
-template <bool CONTROL>
+template <bool CONTROL, bool CLUSTER>
 __global__ void __launch_bounds__(kThreadsP, 1)
     k_tc_persist(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmV0,
                  const __grid_constant__ CUtensorMap tmV1, int Np, int Rp, float* __restrict__ x,
@@ -301,14 +315,19 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     uint64_t* empty = full + S;
     uint64_t* accf = empty + S;
     uint64_t* acce = accf + 1;
-    uint32_t* tmem_slot = (uint32_t*)(acce + 1);
+    uint64_t* vready = acce + 1;  // [2]: the column's V of a step, one arrival per writer
+    uint32_t* tmem_slot = (uint32_t*)(vready + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
-    const int nk = Np / KB;                       // K atoms per step
+    const int nk = Np / KB;                       // K atoms per step == spin blocks
     const int ns = (nk + kAtomsP - 1) / kAtomsP;  // ring stages per step
-    const uint32_t nI = gridDim.y;
-    uint32_t* ctr = counters + blockIdx.x;
+    // spin block (the CTA's own K slice) and replica block
+    const int own = CLUSTER ? (int)blockIdx.x : (int)blockIdx.y;
+    const int rb = CLUSTER ? (int)blockIdx.y : (int)blockIdx.x;
+    const int i0 = own * BM, r0 = rb * BN;
+    uint32_t* ctr = counters + rb;
+    // the k-th K atom of a step: rotated from the CTA's own slice in the cluster form
+    auto atom = [&](int k) { return CLUSTER ? (own + k) % nk : k; };
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < S; ++st) {
@@ -317,6 +336,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         }
         mbar_init(accf, 1);
         mbar_init(acce, 1);
+        mbar_init(&vready[0], (uint32_t)nk);
+        mbar_init(&vready[1], (uint32_t)nk);
         tmem_slot[1] = 0u;  // epilogue abort flag
         fence_barrier_init();
         tma_prefetch_desc(&tmA);
@@ -327,6 +348,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
+    // every CTA's barriers exist before any CTA arrives on them
+    if (CLUSTER) cluster_sync();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
@@ -339,11 +362,13 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             auto load_j = [&](int u, uint32_t st) {
                 mbar_arrive_expect_tx(&full[st], (uint32_t)atoms(u) * (SA1 + SB1));
                 for (int a = 0; a < atoms(u); ++a)
-                    tma_load_2d(sA + st * SA + a * SA1, &tmA, &full[st], (u * kAtomsP + a) * KB, i0);
+                    tma_load_2d(sA + st * SA + a * SA1, &tmA, &full[st], atom(u * kAtomsP + a) * KB,
+                                i0);
             };
             auto load_v = [&](int u, uint32_t st, const CUtensorMap* tv) {
                 for (int a = 0; a < atoms(u); ++a)
-                    tma_load_2d(sB + st * SB + a * SB1, tv, &full[st], (u * kAtomsP + a) * KB, r0);
+                    tma_load_2d(sB + st * SB + a * SB1, tv, &full[st], atom(u * kAtomsP + a) * KB,
+                                r0);
             };
             for (int s = 0; s < nsteps && ok; ++s) {
                 const CUtensorMap* tv = ((m0 + s) & 1) ? &tmV1 : &tmV0;
@@ -355,9 +380,14 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     load_j(u, st);
                 }
                 if (!ok) break;
-                // V of this step is complete once every CTA of the replica block published it
+                // V of this step is complete once every CTA of the replica block
+                // published it: all nk arrivals on this step's barrier (cluster
+                // form), or the counter at nk per step (grid form)
                 if (s > 0) {
-                    if (!wait_counter(ctr, nI * (uint32_t)s, status)) break;
+                    if (CLUSTER ? !mbar_wait_cluster(&vready[(s - 1) & 1],
+                                                     (uint32_t)((s - 1) >> 1) & 1u, status)
+                                : !wait_counter(ctr, (uint32_t)nk * (uint32_t)s, status))
+                        break;
                     fence_proxy_async();
                 }
                 for (int u = 0; u < pre; ++u) load_v(u, (g + u) % S, tv);
@@ -495,17 +525,24 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                 *reinterpret_cast<uint4*>(vrow + cb) = make_uint4(w[0], w[1], w[2], w[3]);
             }
             // The block barrier orders every thread's V bytes before the one
-            // release add, which is cumulative over them; the readers' TMA loads
-            // (async proxy) are ordered after them by the proxy fence each
-            // producer issues after its acquire -- one proxy fence on the
-            // release/acquire path suffices, none is needed here.
+            // release (add or remote arrivals), which is cumulative over them;
+            // the readers' TMA loads (async proxy) are ordered after them by the
+            // proxy fence each producer issues after its acquire -- one proxy
+            // fence on the release/acquire path suffices, none is needed here.
             tmem_wait_st();
             fence_before_sync();
             named_barrier_sync(1, kEpiThreadsP);
             if (*abort_flag) break;
-            if (ew == 0 && lane == 0) {
-                mbar_arrive(acce);
-                red_release_add(ctr, 1u);
+            if (ew == 0) {
+                if (lane == 0) mbar_arrive(acce);
+                if (!CLUSTER) {
+                    if (lane == 0) red_release_add(ctr, 1u);
+                } else if (s + 1 < nsteps && lane < nk) {
+                    // this CTA's slice of V(t_{m+1}) is out: lane q tells reader q
+                    // (one warp instruction; each lane passed the block barrier,
+                    // so each release covers every thread's V bytes)
+                    mbar_arrive_remote(&vready[s & 1], (uint32_t)lane);
+                }
             }
         }
         // state back to global memory
@@ -532,6 +569,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         fence_after_sync();
         tmem_dealloc(tmem, 512);
     }
+    // no CTA leaves while another may still arrive on its barriers
+    if (CLUSTER) cluster_sync();
 }
 
 // V(t_0) from x(t_0): spin-major x [Np][Rp] -> replica-major operand planes.
@@ -564,7 +603,8 @@ struct TcState {
     CUtensorMap tmB[2];
     int vcur = 0;
     int kind = 0;
-    bool persistent = false;     // the cooperative multi-step kernel fits the grid
+    bool persistent = false;     // a multi-step kernel runs this shape
+    bool cluster = false;        // ... in its cluster form (else the cooperative grid form)
     uint32_t* counters = nullptr;  // one per replica block
     float* p_sched = nullptr;      // p(t_{m+1}) for m = 0..M-1 (shared schedule)
 };
@@ -619,6 +659,21 @@ gsb_status launch_step(gsb_run_state* run, TcState* T, float p_shared, float inv
     return GSB_OK;
 }
 
+// Cluster form: grid (spin blocks, replica blocks), one cluster per replica block.
+void cluster_config(const gsb_run_state* run, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at) {
+    const int nk = run->Np / BM;
+    cfg->gridDim = dim3(nk, run->Rp / BN);
+    cfg->blockDim = dim3(kThreadsP);
+    cfg->dynamicSmemBytes = smem_bytes_persist();
+    cfg->stream = run->stream;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = nk;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg->attrs = at;
+    cfg->numAttrs = 1;
+}
+
 }  // namespace
 
 bool tc_available() { return true; }
@@ -627,7 +682,7 @@ const char* tc_kernel_name(const gsb_run_state* run) {
     const TcState* T = (const TcState*)run->tc;
     if (!T) return "none";
     if (T->kind == 1) return "k_tc_step<fx32>";
-    if (T->persistent) return "k_tc_persist";
+    if (T->persistent) return T->cluster ? "k_tc_persist<cluster>" : "k_tc_persist<grid>";
     return "k_tc_step<e4m3>";
 }
 
@@ -654,23 +709,49 @@ gsb_status tc_setup(gsb_run_state* run) {
                                run->Np, 4 * (uint64_t)run->Rp)))
                 return st;
     }
-    if (T->kind == 0) {
-        // co-residency of the whole grid (one CTA per SM) decides the persistent form
-        int dev = 0, sms = 0, per_sm = 0;
-        GSB_CUDA_TRY(cudaGetDevice(&dev));
-        GSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        auto kern = run->control ? (const void*)k_tc_persist<true> : (const void*)k_tc_persist<false>;
-        GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem_bytes_persist()));
-        GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsP,
-                                                                   smem_bytes_persist()));
-        const long grid = (long)(run->Rp / BN) * (run->Np / BM);
-        int coop = 0;
-        GSB_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-        T->persistent = coop && per_sm >= 1 && grid <= (long)per_sm * sms &&
-                        run->params.steps_per_launch != 1;
-        if (T->persistent)
-            GSB_CUDA_TRY(cudaMalloc(&T->counters, sizeof(uint32_t) * (run->Rp / BN)));
+    if (T->kind == 0 && run->params.steps_per_launch != 1) {
+        // Two multi-step forms. The cluster form (one cluster of Np/128 CTAs per
+        // replica block, Np <= 16 x 128) runs in waves when not every cluster
+        // fits at once; the grid form needs the whole grid co-resident. Take the
+        // cluster form if all its clusters fit (its exchange is cheaper), else
+        // the grid form if it fits, else the cluster form in waves.
+        const int nrb = run->Rp / BN;
+        int nclusters = 0;
+        if (run->Np / BM <= kMaxClusterP) {
+            auto kern = run->control ? k_tc_persist<true, true> : k_tc_persist<false, true>;
+            GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              smem_bytes_persist()));
+            if (run->Np / BM > 8)
+                GSB_CUDA_TRY(
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            cluster_config(run, &cfg, at);
+            if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                nclusters = 0;
+            }
+        }
+        bool grid_fits = false;
+        {
+            int dev = 0, sms = 0, per_sm = 0, coop = 0;
+            GSB_CUDA_TRY(cudaGetDevice(&dev));
+            GSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            GSB_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+            auto kern = run->control ? (const void*)k_tc_persist<true, false>
+                                     : (const void*)k_tc_persist<false, false>;
+            GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              smem_bytes_persist()));
+            GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsP,
+                                                                       smem_bytes_persist()));
+            grid_fits = coop && per_sm >= 1 && (long)nrb * (run->Np / BM) <= (long)per_sm * sms;
+        }
+        if (nclusters >= nrb || (nclusters >= 1 && !grid_fits)) {
+            T->persistent = T->cluster = true;
+        } else if (grid_fits) {
+            T->persistent = true;
+            GSB_CUDA_TRY(cudaMalloc(&T->counters, sizeof(uint32_t) * nrb));
+        }
     }
     if (T->persistent) {
         std::vector<float> ps(run->params.M);
@@ -695,22 +776,33 @@ gsb_status tc_prepare(gsb_run_state* run) {
     return GSB_OK;
 }
 
-// Persistent launch over steps [m0, m0 + n): cooperative, one CTA per tile.
+// Persistent launch over steps [m0, m0 + n), one CTA per tile: in clusters
+// (one per replica block) or cooperative.
 template <bool CONTROL>
 gsb_status launch_persist(gsb_run_state* run, TcState* T, int m0, int n) {
-    const int nrb = run->Rp / BN;
-    GSB_CUDA_TRY(cudaMemsetAsync(T->counters, 0, sizeof(uint32_t) * nrb, run->stream));
-    dim3 grid(nrb, run->Np / BM);
     int Np = run->Np, Rp = run->Rp, M = run->params.M;
     float c = run->c, dt = run->dt;
     const float* ps = T->p_sched + m0;
-    void* args[] = {(void*)&T->tmA, (void*)&T->tmB[0], (void*)&T->tmB[1], &Np, &Rp,
-                    (void*)&run->x[0], (void*)&run->y, (void*)&run->p, (void*)&run->A,
-                    (void*)&run->v8[0], (void*)&run->v8[1], &c, &dt, (void*)&ps, &M, &m0, &n,
-                    (void*)&T->counters, (void*)&run->status};
-    GSB_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_tc_persist<CONTROL>, grid,
-                                             dim3(kThreadsP), args, smem_bytes_persist(),
-                                             run->stream));
+    if (T->cluster) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        cluster_config(run, &cfg, at);
+        GSB_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_persist<CONTROL, true>, T->tmA, T->tmB[0],
+                                        T->tmB[1], Np, Rp, run->x[0], run->y, run->p,
+                                        (const float*)run->A, run->v8[0], run->v8[1], c, dt, ps, M,
+                                        m0, n, (uint32_t*)nullptr, run->status));
+    } else {
+        const int nrb = run->Rp / BN;
+        GSB_CUDA_TRY(cudaMemsetAsync(T->counters, 0, sizeof(uint32_t) * nrb, run->stream));
+        dim3 grid(nrb, run->Np / BM);
+        void* args[] = {(void*)&T->tmA, (void*)&T->tmB[0], (void*)&T->tmB[1], &Np, &Rp,
+                        (void*)&run->x[0], (void*)&run->y, (void*)&run->p, (void*)&run->A,
+                        (void*)&run->v8[0], (void*)&run->v8[1], &c, &dt, (void*)&ps, &M, &m0, &n,
+                        (void*)&T->counters, (void*)&run->status};
+        GSB_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_tc_persist<CONTROL, false>, grid,
+                                                 dim3(kThreadsP), args, smem_bytes_persist(),
+                                                 run->stream));
+    }
     count_launch();
     T->vcur = (m0 + n) & 1;
     return GSB_OK;

@@ -336,12 +336,14 @@ def test_lambda_and_auto_parameters_match_oracle():
 
 
 @pytest.mark.parametrize("variant", ["dsb", "gdsb"])
-@pytest.mark.parametrize("N,R", [(100, 130), (300, 200), (2000, 128), (2100, 129)])
-def test_fp8_persistent_matches_per_step_launches_bit_exact(variant, N, R):
+@pytest.mark.parametrize("N,R,form", [(100, 130, "cluster"), (300, 200, "cluster"),
+                                      (2000, 128, "cluster"), (2100, 129, "grid")])
+def test_fp8_persistent_matches_per_step_launches_bit_exact(variant, N, R, form):
     """The persistent FP8 kernel (state in TMEM, many steps per launch; 1, 3,
     16 and 17 K atoms per step, so ring stages of two atoms and a last stage of
-    one) and the one-step-per-launch FP8 kernel do the same arithmetic:
-    identical bits."""
+    one; clusters of 1, 3 and 16 CTAs per replica block, and the cooperative
+    grid form above 16 spin blocks) and the one-step-per-launch FP8 kernel do
+    the same arithmetic: identical bits."""
     M = 120
     J = I.sk_pm1(N, 41)
     P = gsb.Problem.dense(J)
@@ -350,7 +352,29 @@ def test_fp8_persistent_matches_per_step_launches_bit_exact(variant, N, R):
     outs = []
     for spl in (1, 0, 7):
         run = P.run(variant, steps_per_launch=spl, **kw)
-        assert run.kernel() == ("k_tc_step<e4m3>" if spl == 1 else "k_tc_persist")
+        assert run.kernel() == ("k_tc_step<e4m3>" if spl == 1 else f"k_tc_persist<{form}>")
+        outs.append((run.state(), run.best()))
+    for st, b in outs[1:]:
+        for k in ("x", "y", "p"):
+            assert np.array_equal(st[k], outs[0][0][k]), k
+        assert np.array_equal(b["E"], outs[0][1]["E"])
+        assert np.array_equal(b["s"], outs[0][1]["s"])
+        assert np.array_equal(b["step"], outs[0][1]["step"])
+
+
+def test_fp8_cluster_form_in_waves_matches_per_step_launches_bit_exact():
+    """R = 2304 at N = 2000 needs 18 replica blocks x 16 spin blocks = 288
+    CTAs, more than fit at once: the grid form cannot run and the cluster form
+    runs its clusters in waves (clusters never wait on one another). Bit-exact
+    against one launch per step."""
+    N, R, M = 2000, 2304, 40
+    P = gsb.Problem.dense(I.sk_pm1(N, 43))
+    kw = dict(M=M, R=R, c=f32(1 / (2 * math.sqrt(N))), dt=1.25, A=0.3, seed=9, precision="fp8",
+              eval_every=20)
+    outs = []
+    for spl in (1, 0):
+        run = P.run("gdsb", steps_per_launch=spl, **kw)
+        assert run.kernel() == ("k_tc_step<e4m3>" if spl == 1 else "k_tc_persist<cluster>")
         outs.append((run.state(), run.best()))
     for st, b in outs[1:]:
         for k in ("x", "y", "p"):
