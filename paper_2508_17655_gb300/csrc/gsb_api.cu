@@ -83,49 +83,107 @@ void free_problem(gsb_problem* P) {
     delete P;
 }
 
-gsb_status create_dense(gsb_problem* P, const float* Jh, const float* hh, bool validate,
-                        cudaStream_t s) {
+// Dense J on the device: padding to Np, the auxiliary spin of h, and per-row
+// statistics in one pass, one block per row. Row sums of |J| and of J are
+// FP64 in a fixed reduction order; flags[0] collects the largest |J| (as its
+// bits), flags[1] bit 0 "not an integer", bit 1 "not finite", bit 2 "nonzero
+// diagonal", bit 3 "not symmetric" (bits 1-3 only when validating).
+template <typename T>
+__global__ void __launch_bounds__(256) k_prepare_J(const T* __restrict__ Jr,
+                                                   const float* __restrict__ h, int Nu, int N,
+                                                   int Np, int validate, float* __restrict__ J32,
+                                                   double* __restrict__ row_abs,
+                                                   double* __restrict__ row_sum,
+                                                   unsigned* __restrict__ flags) {
+    const int i = blockIdx.x;
+    auto value = [&](int a, int b) -> float {
+        if (a < Nu && b < Nu) return (float)Jr[(size_t)a * Nu + b];
+        if (a < Nu) return b == Nu ? h[a] : 0.f;  // column of the auxiliary spin
+        return b < Nu ? h[b] : 0.f;               // its row
+    };
+    double sa = 0.0, ss = 0.0;
+    float mx = 0.f;
+    unsigned fl = 0u;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const float v = value(i, j);
+        J32[(size_t)i * Np + j] = v;
+        sa += fabs((double)v);
+        ss += (double)v;
+        mx = fmaxf(mx, fabsf(v));
+        if (v != nearbyintf(v)) fl |= 1u;
+        if (validate) {
+            if (!isfinite(v)) fl |= 2u;
+            if (i == j && v != 0.f) fl |= 4u;
+            if (j > i && v != value(j, i)) fl |= 8u;
+        }
+    }
+    __shared__ double ra[256], rs[256];
+    ra[threadIdx.x] = sa;
+    rs[threadIdx.x] = ss;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            ra[threadIdx.x] += ra[threadIdx.x + w];
+            rs[threadIdx.x] += rs[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        row_abs[i] = ra[0];
+        row_sum[i] = rs[0];
+    }
+    const unsigned mfl = __reduce_or_sync(0xffffffffu, fl);
+    const unsigned mmx = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));  // mx >= 0
+    if ((threadIdx.x & 31) == 0) {
+        if (mfl) atomicOr(&flags[1], mfl);
+        atomicMax(&flags[0], mmx);
+    }
+}
+
+// Jr: N_user x N_user row-major (int8 or FP32), on the device; h: N_user
+// floats on the device or NULL.
+template <typename T>
+gsb_status create_dense(gsb_problem* P, const T* Jr, const float* h, bool validate, cudaStream_t s) {
     const int Nu = P->N_user;
     const int N = P->N;
     const int Np = P->Np;
-    std::vector<float> Jp((size_t)Np * Np, 0.f);
-    for (int i = 0; i < Nu; ++i)
-        for (int j = 0; j < Nu; ++j) Jp[(size_t)i * Np + j] = Jh[(size_t)i * Nu + j];
-    if (hh) {
-        for (int i = 0; i < Nu; ++i) {
-            Jp[(size_t)i * Np + Nu] = hh[i];
-            Jp[(size_t)Nu * Np + i] = hh[i];
-        }
+    const size_t n = (size_t)Np * Np;
+    gsb_status st;
+    if ((st = dev_alloc(&P->J32, n)) != GSB_OK) return st;
+    double* stats = nullptr;  // row_abs [N], row_sum [N], then 2 flag words
+    if ((st = dev_alloc(&stats, 2 * (size_t)N + 1)) != GSB_OK) return st;
+    unsigned* flags = reinterpret_cast<unsigned*>(stats + 2 * (size_t)N);
+    std::vector<double> hs(2 * (size_t)N + 1);
+    cudaError_t e = cudaMemsetAsync(P->J32, 0, n * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        k_prepare_J<T><<<N, 256, 0, s>>>(Jr, h, Nu, N, Np, validate ? 1 : 0, P->J32, stats,
+                                         stats + N, flags);
+        e = cudaGetLastError();
     }
-    bool integer = true;
-    float mx = 0.f;
-    double sum = 0.0, max_row = 0.0;
+    if (e == cudaSuccess) count_launch();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs.data(), stats, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(stats);
+    if (e != cudaSuccess) return set_error(GSB_ECUDA, std::string("preparing J: ") + cudaGetErrorString(e));
+    unsigned fw[2];
+    memcpy(fw, &hs[2 * (size_t)N], sizeof(fw));
+    if (fw[1] & 2u) return set_error(GSB_EINVAL, "J has a non-finite entry");
+    if (fw[1] & 4u) return set_error(GSB_EINVAL, "J has a nonzero diagonal entry (Eq. 1 needs J_ii = 0)");
+    if (fw[1] & 8u) return set_error(GSB_EINVAL, "J is not symmetric (Eq. 1 needs J_ij = J_ji)");
+    double max_row = 0.0, sum = 0.0;
     for (int i = 0; i < N; ++i) {
-        double row = 0.0;
-        for (int j = 0; j < N; ++j) row += fabs((double)Jp[(size_t)i * Np + j]);
-        max_row = std::max(max_row, row);
-        for (int j = 0; j < N; ++j) {
-            const float v = Jp[(size_t)i * Np + j];
-            if (validate) {
-                if (!isfinite(v)) return set_error(GSB_EINVAL, "J has a non-finite entry");
-                if (i == j && v != 0.f)
-                    return set_error(GSB_EINVAL, "J has a nonzero diagonal entry (Eq. 1 needs J_ii = 0)");
-                if (j > i && v != Jp[(size_t)j * Np + i])
-                    return set_error(GSB_EINVAL, "J is not symmetric (Eq. 1 needs J_ij = J_ji)");
-            }
-            integer = integer && is_integer(v);
-            mx = std::max(mx, fabsf(v));
-            sum += v;
-        }
+        max_row = std::max(max_row, hs[i]);
+        sum += hs[N + i];
     }
+    float mx;
+    memcpy(&mx, &fw[0], sizeof(mx));
+    const bool integer = !(fw[1] & 1u);
     P->integer_J = integer;
     P->max_abs_J = mx;
     P->max_row_abs = max_row;
     P->W_tot = -0.5 * sum;
-    const size_t n = (size_t)Np * Np;
-    gsb_status st;
-    if ((st = dev_alloc(&P->J32, n)) != GSB_OK) return st;
-    GSB_CUDA_TRY(cudaMemcpyAsync(P->J32, Jp.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
     if (integer && mx <= 16.f)
         if ((st = dev_alloc(&P->J8, n)) != GSB_OK) return st;
     // FX32 digit planes: every partial sum |sum_j J_ij d_j| <= 128 max row sum stays
@@ -136,7 +194,6 @@ gsb_status create_dense(gsb_problem* P, const float* Jh, const float* hh, bool v
         k_convert_J<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P->J32, P->J8, P->J16, n);
         GSB_LAUNCH_CHECK("k_convert_J");
     }
-    GSB_CUDA_TRY(cudaStreamSynchronize(s));  // Jp goes out of scope
     return GSB_OK;
 }
 
@@ -364,14 +421,35 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
             free_problem(P);
             return set_error(GSB_EINVAL, "dense J too large; use CSR");
         }
-        std::vector<float> Jf((size_t)N * N);
-        if (format == GSB_J_DENSE_I8) {
-            auto J8 = fetch((const int8_t*)J, (size_t)N * N, device_in);
-            for (size_t k = 0; k < Jf.size(); ++k) Jf[k] = (float)J8[k];
-        } else {
-            Jf = fetch((const float*)J, (size_t)N * N, device_in);
+        // the raw J (and h) on the device, then padding and checks there
+        const size_t eb = format == GSB_J_DENSE_I8 ? 1 : sizeof(float);
+        const size_t nb = (size_t)N * N * eb;
+        void* Jd = nullptr;
+        float* hd = nullptr;
+        cudaError_t e = cudaSuccess;
+        if (!device_in) {
+            e = cudaMalloc(&Jd, nb);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(Jd, J, nb, cudaMemcpyHostToDevice, s);
         }
-        st = create_dense(P, Jf.data(), h ? hv.data() : nullptr, validate, s);
+        if (e == cudaSuccess && h) {
+            e = cudaMalloc(&hd, sizeof(float) * N);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hd, hv.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s);
+        }
+        if (e != cudaSuccess) {
+            cudaFree(Jd);
+            cudaFree(hd);
+            free_problem(P);
+            return set_error(GSB_ECUDA, std::string("uploading J: ") + cudaGetErrorString(e));
+        }
+        const void* Jsrc = device_in ? J : Jd;
+        if (format == GSB_J_DENSE_I8)
+            st = create_dense(P, (const int8_t*)Jsrc, hd, validate, s);
+        else
+            st = create_dense(P, (const float*)Jsrc, hd, validate, s);
+        cudaStreamSynchronize(s);  // the temporaries may be in use by the conversion
+        cudaFree(Jd);
+        cudaFree(hd);
     } else if (format == GSB_J_CSR_F32) {
         if (J || !rowptr || (nnz > 0 && (!col || !val)) || nnz < 0) {
             free_problem(P);

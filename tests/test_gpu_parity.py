@@ -316,6 +316,15 @@ def test_invalid_inputs_are_rejected():
     with pytest.raises(gsb.GsbError) as e:
         gsb.Problem.dense(np.array([[1, 1], [1, 0]], np.float32))
     assert e.value.status == gsb.EINVAL
+    with pytest.raises(gsb.GsbError) as e:
+        gsb.Problem.dense(np.array([[0, np.nan], [np.nan, 0]], np.float32))
+    assert e.value.status == gsb.EINVAL
+    # a symmetry violation far from the diagonal of a larger matrix
+    Jbad = I.sk_pm1(300, 3).astype(np.float32)
+    Jbad[17, 250] = -Jbad[17, 250]
+    with pytest.raises(gsb.GsbError) as e:
+        gsb.Problem.dense(Jbad)
+    assert e.value.status == gsb.EINVAL
     P = gsb.Problem.dense(I.sk_gauss(8, 1))
     with pytest.raises(gsb.GsbError) as e:
         P.run("dsb", M=10, R=4, c=1, dt=1, precision="fp8")
