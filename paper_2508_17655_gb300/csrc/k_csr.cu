@@ -63,9 +63,10 @@ __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowpt
         }
     }
     if (!SIGN && EXACT) {
-        const double s = 9.313225746154785e-10;  // 2^-30
-        acc = make_float4((float)((double)qa[0] * s), (float)((double)qa[1] * s),
-                          (float)((double)qa[2] * s), (float)((double)qa[3] * s));
+        // one correctly rounded int64 -> FP32 conversion, then the exact 2^-30
+        const float s = 9.313225746154785e-10f;
+        acc = make_float4(__ll2float_rn(qa[0]) * s, __ll2float_rn(qa[1]) * s,
+                          __ll2float_rn(qa[2]) * s, __ll2float_rn(qa[3]) * s);
     }
     return acc;
 }

@@ -1,30 +1,26 @@
 // k_dense_tc.cu -- dense time step on the sm_103a tensor cores.
 //
-// One CTA owns a tile of 128 spins (rows of J, TMEM lanes) x 128 replicas
-// (TMEM columns). The many-body term F = J V over the full K = Np is a chain
-// of tcgen05.mma into one FP32 TMEM accumulator, fed by a TMA ring of
-// 128-byte-swizzled K slices of J and V. The epilogue warps read F back with
-// tcgen05.ld and apply Eqs. 7, 3, 4, 5 to their spin (one TMEM lane per
-// thread), then write the next step's V operand.
+// The many-body term F = J V over the full K = Np is a chain of tcgen05.mma
+// into FP32 TMEM accumulators, fed by a TMA ring of 128-byte-swizzled K
+// slices of J and V; epilogue warps read F back with tcgen05.ld, apply
+// Eqs. 7, 3, 4, 5 and write the next step's V operand. Two exact forms:
 //
-//   KIND 0 (GSB_PREC_FP8):    J and V = sgn x in e4m3, kind::f8f6f4. Exact:
-//                             products are +-J_ij, partial sums are integers
-//                             far below 2^24 (|J| <= 16, N < 2^20).
-//   KIND 1 (GSB_PREC_FX32):   J in bf16 (integer) and x as the 32-bit fixed
-//                             point integer q = rint(x 2^30), written as four
-//                             signed base-256 digits d_0..d_3 (bf16, exact).
-//                             Digit plane k accumulates D_k = J d_k in its own
-//                             128-column TMEM accumulator; every partial sum
-//                             is an integer below 2^24 (128 sum_j |J_ij| <
-//                             2^24), so D_k is exact whatever order the tensor
-//                             core adds in. The epilogue forms
-//                             sum_k 256^k D_k exactly in int64 and rounds
-//                             2^-30 times it once to FP32: f is the correctly
-//                             rounded J x_q, and x_q = x for |x| >= 2^-7.
-//
-// Warp roles (192 threads): warp 0 lane 0 issues TMA, warp 1 owns TMEM and
-// its lane 0 issues MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes
-// 32 (w % 4) .. +31, as tcgen05.ld requires).
+//   FP8  (GSB_PREC_FP8):  J and V = sgn x in e4m3, kind::f8f6f4. Products are
+//                         +-J_ij and partial sums integers far below 2^24
+//                         (|J| <= 16, N < 2^20): exact in any order.
+//                         k_tc_step (one step per launch, the reference form)
+//                         and k_tc_persist (many steps per launch).
+//   FX32 (GSB_PREC_FX32): J in bf16 (integer) and x as the 32-bit fixed
+//                         point integer q = rint(x 2^30), written as four
+//                         signed base-256 digits d_0..d_3 (bf16, exact).
+//                         Digit plane k accumulates D_k = J d_k in its own
+//                         128-column TMEM accumulator; every partial sum is an
+//                         integer below 2^24 (128 sum_j |J_ij| < 2^24), so D_k
+//                         is exact whatever order the tensor core adds in. The
+//                         epilogue forms sum_k 256^k D_k exactly in int64 and
+//                         rounds 2^-30 times it once to FP32: f is the
+//                         correctly rounded J x_q, and x_q = x for
+//                         |x| >= 2^-7. k_fx32_step.
 #include <cudaTypedefs.h>
 
 #include "gsb_update.cuh"
@@ -39,28 +35,14 @@ using namespace tc;
 constexpr int BM = 128;   // spins per tile
 constexpr int BN = 128;   // replicas per tile
 constexpr int KB = 128;   // bytes of K per pipeline stage (one swizzle row)
+// k_tc_step: warp 0 lane 0 issues TMA, warp 1 owns TMEM and its lane 0 issues
+// MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes 32 (w % 4) ..
+// +31, as tcgen05.ld requires).
 constexpr int kThreads = 192;
+constexpr int kStagesS = 6;
 
-template <int KIND>
-struct Cfg;
-template <>
-struct Cfg<0> {
-    static constexpr int kElem = 1, kPlanes = 1, kStages = 6;
-    static constexpr uint32_t kTmemCols = 128;
-};
-template <>
-struct Cfg<1> {
-    static constexpr int kElem = 2, kPlanes = 4, kStages = 2;
-    static constexpr uint32_t kTmemCols = 512;  // one 128-column accumulator per digit plane
-};
-
-template <int KIND>
-__host__ __device__ constexpr int stage_a_bytes() { return BM * KB; }
-template <int KIND>
-__host__ __device__ constexpr int stage_b_bytes() { return Cfg<KIND>::kPlanes * BN * KB; }
-template <int KIND>
-__host__ __device__ constexpr int smem_bytes() {
-    return 1024 /*alignment slack*/ + Cfg<KIND>::kStages * (stage_a_bytes<KIND>() + stage_b_bytes<KIND>()) + 256;
+__host__ __device__ constexpr int smem_bytes_step() {
+    return 1024 /*alignment slack*/ + kStagesS * (BM * KB + BN * KB) + 256;
 }
 
 __device__ __forceinline__ uint8_t e4m3_sign(float x) { return x >= 0.f ? 0x38 : 0xB8; }  // +-1.0
@@ -80,23 +62,29 @@ __device__ __forceinline__ void fx32_digits(float x, __nv_bfloat16 (&d)[4]) {
     d[3] = __int2bfloat16_rn(q);
 }
 
-// f = 2^-30 sum_k 256^k D_k, from exact integer accumulators, rounded once.
+// f = 2^-30 sum_k 256^k D_k, from exact integer accumulators (|D_k| < 2^24,
+// so each converts to int32 exactly), rounded once: the int64 sum is rounded
+// to FP32 by one conversion and the power-of-two scale is exact. No FP64 (a
+// slow pipe on this part).
 __device__ __forceinline__ float fx32_combine(float d0, float d1, float d2, float d3) {
-    const long long v = (long long)d0 + ((long long)d1 << 8) + ((long long)d2 << 16) +
-                        ((long long)d3 << 24);
-    return (float)((double)v * 9.313225746154785e-10);  // 2^-30
+    const long long v = (long long)__float2int_rn(d0) + ((long long)__float2int_rn(d1) << 8) +
+                        ((long long)__float2int_rn(d2) << 16) +
+                        ((long long)__float2int_rn(d3) << 24);
+    return __ll2float_rn(v) * 9.313225746154785e-10f;  // 2^-30
 }
 
-template <int KIND, bool CONTROL>
+// One FP8 step per launch. One CTA owns 128 spins (rows of J, TMEM lanes) x
+// 128 replicas (TMEM columns); the epilogue thread of a spin updates its 128
+// oscillators.
+template <bool CONTROL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_step(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int Np, int Rp, float* __restrict__ x, float* __restrict__ y,
-              float* __restrict__ p, const float* __restrict__ A, void* __restrict__ vnext,
+              float* __restrict__ p, const float* __restrict__ A, uint8_t* __restrict__ vnext,
               float c, float dt, float p_shared, float inv_rem, int* status) {
-    constexpr int S = Cfg<KIND>::kStages;
-    constexpr int PL = Cfg<KIND>::kPlanes;
-    constexpr int SA = stage_a_bytes<KIND>();
-    constexpr int SB = stage_b_bytes<KIND>();
+    constexpr int S = kStagesS;
+    constexpr int SA = BM * KB;
+    constexpr int SB = BN * KB;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
@@ -108,8 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
-    const int nk = Np * Cfg<KIND>::kElem / KB;
-    constexpr int kElemsPerSlice = KB / Cfg<KIND>::kElem;
+    const int nk = Np / KB;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -121,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
     }
-    constexpr uint32_t kTmemCols = Cfg<KIND>::kTmemCols;
+    constexpr uint32_t kTmemCols = 128;
     if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
     fence_before_sync();
     __syncthreads();
@@ -135,16 +122,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t ph = (uint32_t)(kc / S) & 1u;
                 if (kc >= S && !mbar_wait(&empty[s], ph ^ 1u, status)) break;
                 mbar_arrive_expect_tx(&full[s], SA + SB);
-                tma_load_2d(sA + s * SA, &tmA, &full[s], kc * kElemsPerSlice, i0);
-#pragma unroll
-                for (int q = 0; q < PL; ++q)
-                    tma_load_2d(sB + s * SB + q * BN * KB, &tmB, &full[s], kc * kElemsPerSlice,
-                                q * Rp + r0);
+                tma_load_2d(sA + s * SA, &tmA, &full[s], kc * KB, i0);
+                tma_load_2d(sB + s * SB, &tmB, &full[s], kc * KB, r0);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_make(KIND == 0 ? 0u : 1u, BM, BN);
+            constexpr uint32_t idesc = idesc_make(0u, BM, BN);
             bool ok = true;
             for (int kc = 0; kc < nk && ok; ++kc) {
                 const int s = kc % S;
@@ -157,18 +141,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t a0 = smem_u32(sA + s * SA);
                 const uint32_t b0 = smem_u32(sB + s * SB);
 #pragma unroll
-                for (int k = 0; k < KB / 32; ++k) {  // 32 bytes of K per MMA
-                    const uint64_t ad = sdesc_sw128(a0 + k * 32);
-#pragma unroll
-                    for (int q = 0; q < PL; ++q) {
-                        const uint64_t bd = sdesc_sw128(b0 + q * BN * KB + k * 32);
-                        const uint32_t acc = (kc | k) != 0;
-                        if (KIND == 0)
-                            mma_f8f6f4(tmem, ad, bd, idesc, acc);
-                        else  // digit plane q into accumulator columns [128 q, 128 q + 128)
-                            mma_f16(tmem + q * BN, ad, bd, idesc, acc);
-                    }
-                }
+                for (int k = 0; k < KB / 32; ++k)  // 32 bytes of K per MMA
+                    mma_f8f6f4(tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
+                               (kc | k) != 0);
                 mma_commit(&empty[s]);
             }
             if (ok) mma_commit(accf);
@@ -187,14 +162,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int cb = 0; cb < BN; cb += 16) {
                 float f[16];
                 tmem_ld16(taddr + cb, f);
-                if (KIND == 1) {
-                    float d1[16], d2[16], d3[16];
-                    tmem_ld16(taddr + BN + cb, d1);
-                    tmem_ld16(taddr + 2 * BN + cb, d2);
-                    tmem_ld16(taddr + 3 * BN + cb, d3);
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) f[k] = fx32_combine(f[k], d1[k], d2[k], d3[k]);
-                }
                 const size_t o = (size_t)i * Rp + r0 + cb;
                 float xs[16], ys[16], ps[16], as[16];
 #pragma unroll
@@ -226,21 +193,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         *reinterpret_cast<float4*>(p + o + 4 * q) =
                             make_float4(ps[4 * q], ps[4 * q + 1], ps[4 * q + 2], ps[4 * q + 3]);
                 }
-                // next step's operand, replica-major [plane][Rp][Np]
+                // next step's operand, replica-major [Rp][Np]
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const size_t vo = (size_t)(r0 + cb + k) * Np + i;
-                    if (KIND == 0) {
-                        reinterpret_cast<uint8_t*>(vnext)[vo] = e4m3_sign(xs[k]);
-                    } else {
-                        __nv_bfloat16 d[4];
-                        fx32_digits(xs[k], d);
-                        __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(vnext);
-                        const size_t plane = (size_t)Rp * Np;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) v[q * plane + vo] = d[q];
-                    }
-                }
+                for (int k = 0; k < 16; ++k) vnext[(size_t)(r0 + cb + k) * Np + i] = e4m3_sign(xs[k]);
             }
         }
     }
@@ -640,21 +595,211 @@ gsb_status make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dtyp
     return GSB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// FX32 step (one step per launch), with the tile transposed as in k_tc_persist:
+// digit plane q of V (x as rint(x 2^30) in four base-256 digits) is the A
+// operand, so D_q = V_q J^T lands with a replica per TMEM lane and a spin per
+// column, in columns [128 q, 128 q + 128). Each epilogue thread then owns a
+// replica: it reads and writes x, y, p coalesced across the warp, holds its
+// control strength in a register, and writes the next step's four digit
+// planes 32 contiguous bytes at a time. The digit sums are exact integers, so
+// f is the same as k_tc_step<1>'s in any order.
+// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2-9 epilogue (warp w: TMEM
+// lanes 32 (w % 4).., spins 64 ((w - 2) / 4) .. +63 of the tile).
+constexpr int kThreadsF = 320;
+constexpr int kStagesF = 2;
+__host__ __device__ constexpr int smem_bytes_fx32() {
+    return 1024 + kStagesF * (4 * BN * KB + BM * KB) + 256;
+}
+
+template <bool CONTROL>
+__global__ void __launch_bounds__(kThreadsF, 1)
+    k_fx32_step(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmV,
+                int Np, int Rp, float* __restrict__ x, float* __restrict__ y,
+                float* __restrict__ p, const float* __restrict__ A,
+                __nv_bfloat16* __restrict__ vnext, float c, float dt, float p_shared,
+                float inv_rem, int* status) {
+    constexpr int S = kStagesF;
+    constexpr int SV1 = BN * KB, SV = 4 * SV1, SJ = BM * KB;  // bytes per stage
+    constexpr int kElems = KB / 2;                          // bf16 elements of K per stage
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sV = smem;
+    uint8_t* sJ = smem + S * SV;
+    uint64_t* full = (uint64_t*)(sJ + S * SJ);
+    uint64_t* empty = full + S;
+    uint64_t* accf = empty + S;
+    uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * BN, i0 = blockIdx.y * BM;
+    const int nk = Np / kElems;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(accf, 1);
+        fence_barrier_init();
+        tma_prefetch_desc(&tmJ);
+        tma_prefetch_desc(&tmV);
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kc = 0; kc < nk; ++kc) {
+                const int st = kc % S;
+                const uint32_t ph = (uint32_t)(kc / S) & 1u;
+                if (kc >= S && !mbar_wait(&empty[st], ph ^ 1u, status)) break;
+                mbar_arrive_expect_tx(&full[st], SV + SJ);
+                tma_load_2d(sJ + st * SJ, &tmJ, &full[st], kc * kElems, i0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    tma_load_2d(sV + st * SV + q * SV1, &tmV, &full[st], kc * kElems, q * Rp + r0);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_make(1u, BN, BM);
+            bool ok = true;
+            for (int kc = 0; kc < nk && ok; ++kc) {
+                const int st = kc % S;
+                const uint32_t ph = (uint32_t)(kc / S) & 1u;
+                if (!mbar_wait(&full[st], ph, status)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t j0 = smem_u32(sJ + st * SJ);
+                const uint32_t v0 = smem_u32(sV + st * SV);
+#pragma unroll
+                for (int k = 0; k < KB / 32; ++k) {  // 16 bf16 of K per MMA
+                    const uint64_t jd = sdesc_sw128(j0 + k * 32);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        mma_f16(tmem + q * BN, sdesc_sw128(v0 + q * SV1 + k * 32), jd, idesc,
+                                (kc | k) != 0);
+                }
+                mma_commit(&empty[st]);
+            }
+            if (ok) mma_commit(accf);
+        }
+    } else {
+        const int ew = warp - 2;
+        const int quarter = warp & 3;
+        const int c0 = (ew >> 2) * 64;
+        const int r = r0 + quarter * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+        const float a_r = CONTROL ? A[r] : 0.f;
+        const size_t plane = (size_t)Rp * Np;
+        __nv_bfloat16* vrow = vnext + (size_t)r * Np + i0;
+        // tcgen05.ld is warp-collective: proceed only if every lane saw the accumulator
+        const bool ready = __all_sync(0xffffffffu, mbar_wait(accf, 0, status));
+        if (ready) {
+            fence_after_sync();
+#pragma unroll 1
+            for (int cb = c0; cb < c0 + 64; cb += 16) {
+                float f[16];
+                {
+                    uint32_t d0[16], d1[16], d2[16], d3[16];
+                    tmem_ld16_async(tl + cb, d0);
+                    tmem_ld16_async(tl + BN + cb, d1);
+                    tmem_ld16_async(tl + 2 * BN + cb, d2);
+                    tmem_ld16_async(tl + 3 * BN + cb, d3);
+                    tmem_wait_ld(d0);
+                    tmem_wait_ld(d1);
+                    tmem_wait_ld(d2);
+                    tmem_wait_ld(d3);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        f[k] = fx32_combine(__uint_as_float(d0[k]), __uint_as_float(d1[k]),
+                                            __uint_as_float(d2[k]), __uint_as_float(d3[k]));
+                }
+                const size_t o = (size_t)(i0 + cb) * Rp + r;
+                float xs[16], ys[16], ps[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    xs[k] = x[o + (size_t)k * Rp];
+                    ys[k] = y[o + (size_t)k * Rp];
+                    ps[k] = CONTROL ? p[o + (size_t)k * Rp] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    float2 x2 = make_float2(xs[k], xs[k + 1]), y2 = make_float2(ys[k], ys[k + 1]);
+                    float2 p2 = make_float2(ps[k], ps[k + 1]);
+                    sb_update2<CONTROL>(x2, y2, p2, make_float2(f[k], f[k + 1]), a_r, c, dt,
+                                        p_shared, inv_rem);
+                    xs[k] = x2.x, xs[k + 1] = x2.y, ys[k] = y2.x, ys[k + 1] = y2.y;
+                    ps[k] = p2.x, ps[k + 1] = p2.y;
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    x[o + (size_t)k * Rp] = xs[k];
+                    y[o + (size_t)k * Rp] = ys[k];
+                    if (CONTROL) p[o + (size_t)k * Rp] = ps[k];
+                }
+                // next step's digit planes: 16 bf16 (32 bytes) of this replica's row each
+                uint32_t w[4][8];
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    __nv_bfloat16 da[4], db[4];
+                    fx32_digits(xs[k], da);
+                    fx32_digits(xs[k + 1], db);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        w[q][k / 2] = (uint32_t)__bfloat16_as_ushort(da[q]) |
+                                      ((uint32_t)__bfloat16_as_ushort(db[q]) << 16);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4* dst = reinterpret_cast<uint4*>(vrow + q * plane + cb);
+                    dst[0] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+                    dst[1] = make_uint4(w[q][4], w[q][5], w[q][6], w[q][7]);
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 template <int KIND, bool CONTROL>
 gsb_status launch_step(gsb_run_state* run, TcState* T, float p_shared, float inv_rem) {
-    auto kern = k_tc_step<KIND, CONTROL>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem_bytes<KIND>()));
-        attr_set = true;
-    }
     dim3 grid(run->Rp / BN, run->Np / BM);
-    void* vnext = KIND == 0 ? (void*)run->v8[T->vcur ^ 1] : (void*)run->v16[T->vcur ^ 1];
-    kern<<<grid, kThreads, smem_bytes<KIND>(), run->stream>>>(
-        T->tmA, T->tmB[T->vcur], run->Np, run->Rp, run->x[0], run->y, run->p, run->A, vnext,
-        run->c, run->dt, p_shared, inv_rem, run->status);
-    GSB_LAUNCH_CHECK("k_tc_step");
+    static bool attr_set = false;
+    if constexpr (KIND == 1) {
+        if (!attr_set) {
+            GSB_CUDA_TRY(cudaFuncSetAttribute(k_fx32_step<CONTROL>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              smem_bytes_fx32()));
+            attr_set = true;
+        }
+        k_fx32_step<CONTROL><<<grid, kThreadsF, smem_bytes_fx32(), run->stream>>>(
+            T->tmA, T->tmB[T->vcur], run->Np, run->Rp, run->x[0], run->y, run->p, run->A,
+            run->v16[T->vcur ^ 1], run->c, run->dt, p_shared, inv_rem, run->status);
+        GSB_LAUNCH_CHECK("k_fx32_step");
+    } else {
+        if (!attr_set) {
+            GSB_CUDA_TRY(cudaFuncSetAttribute(k_tc_step<CONTROL>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              smem_bytes_step()));
+            attr_set = true;
+        }
+        k_tc_step<CONTROL><<<grid, kThreads, smem_bytes_step(), run->stream>>>(
+            T->tmA, T->tmB[T->vcur], run->Np, run->Rp, run->x[0], run->y, run->p, run->A,
+            run->v8[T->vcur ^ 1], run->c, run->dt, p_shared, inv_rem, run->status);
+        GSB_LAUNCH_CHECK("k_tc_step");
+    }
     T->vcur ^= 1;
     return GSB_OK;
 }
