@@ -59,6 +59,25 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(rank):
+    """Seed of a rank's replica set: ranks draw disjoint replicas (Philox
+    counters are keyed by the seed), so N ranks do N independent sets --
+    replicas only, no data-path exchange."""
+    return 1000 * rank
+
+
+def job_time_and_value(total_ms, units_per_rank, world, device=None):
+    """Whole-job figures from one rank's timed total: the slowest rank's time
+    (max over ranks, the only collective) and all ranks' units over it."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, units_per_rank * world / (total_ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -225,16 +244,10 @@ def gpu_arm(args, world, rank, local):
     # headline: GdSB on FP8 tensor cores
     with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0)) as clk:
         times, (kern_ms, kern_n, kern_steps), energies, launches, kernel_name = timed_runs(
-            "gdsb", "fp8", args.steps, args.warmup, 1000 * rank)
+            "gdsb", "fp8", args.steps, args.warmup, rank_seed(rank))
     clocks = clk.summary()
-    total_ms = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = N_SPINS * R_REPLICAS * M_STEPS * args.steps * world
-    value = units / (total_ms / 1e3)
+    total_ms, value = job_time_and_value(sum(times), N_SPINS * R_REPLICAS * M_STEPS * args.steps,
+                                         world, dev)
     ms_per_step = total_ms / args.steps
 
     Pk, how = peaks()
