@@ -62,6 +62,17 @@ __device__ __forceinline__ void fx32_digits(float x, __nv_bfloat16 (&d)[4]) {
     d[3] = __int2bfloat16_rn(q);
 }
 
+// The same digits from the bytes of u = q + 0x808080: d_k = byte_k(u) - 128
+// for k < 3 and d_3 = u >> 24 (arithmetic), since u = q + 128 (1 + 256 +
+// 65536); returned as bf16 bit patterns.
+__device__ __forceinline__ void fx32_digit_bits(float x, uint16_t (&d)[4]) {
+    const int u = __float2int_rn(x * 1073741824.0f) + 0x808080;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        d[k] = __bfloat16_as_ushort(__int2bfloat16_rn((int)((u >> (8 * k)) & 255) - 128));
+    d[3] = __bfloat16_as_ushort(__int2bfloat16_rn(u >> 24));
+}
+
 // f = 2^-30 sum_k 256^k D_k, from exact integer accumulators (|D_k| < 2^24,
 // so each converts to int32 exactly), rounded once: the int64 sum is rounded
 // to FP32 by one conversion and the power-of-two scale is exact. No FP64 (a
@@ -699,38 +710,47 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const float a_r = CONTROL ? A[r] : 0.f;
         const size_t plane = (size_t)Rp * Np;
         __nv_bfloat16* vrow = vnext + (size_t)r * Np + i0;
+        // Chunks of 8 spins; the state of the next chunk is loaded while this one
+        // is processed (the first before the accumulator is ready), so the L2
+        // latency of the loads overlaps work.
+        constexpr int CW = 8;
+        float xn[CW], yn[CW], pn[CW];
+        auto load_state = [&](int cb) {
+            const size_t o = (size_t)(i0 + cb) * Rp + r;
+#pragma unroll
+            for (int k = 0; k < CW; ++k) {
+                xn[k] = x[o + (size_t)k * Rp];
+                yn[k] = y[o + (size_t)k * Rp];
+                pn[k] = CONTROL ? p[o + (size_t)k * Rp] : 0.f;
+            }
+        };
+        load_state(c0);
         // tcgen05.ld is warp-collective: proceed only if every lane saw the accumulator
         const bool ready = __all_sync(0xffffffffu, mbar_wait(accf, 0, status));
         if (ready) {
             fence_after_sync();
 #pragma unroll 1
-            for (int cb = c0; cb < c0 + 64; cb += 16) {
-                float f[16];
-                {
-                    uint32_t d0[16], d1[16], d2[16], d3[16];
-                    tmem_ld16_async(tl + cb, d0);
-                    tmem_ld16_async(tl + BN + cb, d1);
-                    tmem_ld16_async(tl + 2 * BN + cb, d2);
-                    tmem_ld16_async(tl + 3 * BN + cb, d3);
-                    tmem_wait_ld(d0);
-                    tmem_wait_ld(d1);
-                    tmem_wait_ld(d2);
-                    tmem_wait_ld(d3);
+            for (int cb = c0; cb < c0 + 64; cb += CW) {
+                uint32_t d0[CW], d1[CW], d2[CW], d3[CW];
+                tmem_ld8_async(tl + cb, d0);
+                tmem_ld8_async(tl + BN + cb, d1);
+                tmem_ld8_async(tl + 2 * BN + cb, d2);
+                tmem_ld8_async(tl + 3 * BN + cb, d3);
+                float xs[CW], ys[CW], ps[CW];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        f[k] = fx32_combine(__uint_as_float(d0[k]), __uint_as_float(d1[k]),
-                                            __uint_as_float(d2[k]), __uint_as_float(d3[k]));
-                }
-                const size_t o = (size_t)(i0 + cb) * Rp + r;
-                float xs[16], ys[16], ps[16];
+                for (int k = 0; k < CW; ++k) xs[k] = xn[k], ys[k] = yn[k], ps[k] = pn[k];
+                if (cb + CW < c0 + 64) load_state(cb + CW);
+                tmem_wait_ld8(d0);
+                tmem_wait_ld8(d1);
+                tmem_wait_ld8(d2);
+                tmem_wait_ld8(d3);
+                float f[CW];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    xs[k] = x[o + (size_t)k * Rp];
-                    ys[k] = y[o + (size_t)k * Rp];
-                    ps[k] = CONTROL ? p[o + (size_t)k * Rp] : 0.f;
-                }
+                for (int k = 0; k < CW; ++k)
+                    f[k] = fx32_combine(__uint_as_float(d0[k]), __uint_as_float(d1[k]),
+                                        __uint_as_float(d2[k]), __uint_as_float(d3[k]));
 #pragma unroll
-                for (int k = 0; k < 16; k += 2) {
+                for (int k = 0; k < CW; k += 2) {
                     float2 x2 = make_float2(xs[k], xs[k + 1]), y2 = make_float2(ys[k], ys[k + 1]);
                     float2 p2 = make_float2(ps[k], ps[k + 1]);
                     sb_update2<CONTROL>(x2, y2, p2, make_float2(f[k], f[k + 1]), a_r, c, dt,
@@ -738,30 +758,27 @@ __global__ void __launch_bounds__(kThreadsF, 1)
                     xs[k] = x2.x, xs[k + 1] = x2.y, ys[k] = y2.x, ys[k + 1] = y2.y;
                     ps[k] = p2.x, ps[k + 1] = p2.y;
                 }
+                const size_t o = (size_t)(i0 + cb) * Rp + r;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
+                for (int k = 0; k < CW; ++k) {
                     x[o + (size_t)k * Rp] = xs[k];
                     y[o + (size_t)k * Rp] = ys[k];
                     if (CONTROL) p[o + (size_t)k * Rp] = ps[k];
                 }
-                // next step's digit planes: 16 bf16 (32 bytes) of this replica's row each
-                uint32_t w[4][8];
+                // next step's digit planes: 8 bf16 (16 bytes) of this replica's row each
+                uint32_t w[4][CW / 2];
 #pragma unroll
-                for (int k = 0; k < 16; k += 2) {
-                    __nv_bfloat16 da[4], db[4];
-                    fx32_digits(xs[k], da);
-                    fx32_digits(xs[k + 1], db);
+                for (int k = 0; k < CW; k += 2) {
+                    uint16_t da[4], db[4];
+                    fx32_digit_bits(xs[k], da);
+                    fx32_digit_bits(xs[k + 1], db);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        w[q][k / 2] = (uint32_t)__bfloat16_as_ushort(da[q]) |
-                                      ((uint32_t)__bfloat16_as_ushort(db[q]) << 16);
+                    for (int q = 0; q < 4; ++q) w[q][k / 2] = (uint32_t)da[q] | ((uint32_t)db[q] << 16);
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint4* dst = reinterpret_cast<uint4*>(vrow + q * plane + cb);
-                    dst[0] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
-                    dst[1] = make_uint4(w[q][4], w[q][5], w[q][6], w[q][7]);
-                }
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4*>(vrow + q * plane + cb) =
+                        make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
             }
         }
     }
