@@ -30,7 +30,7 @@ namespace {
 using namespace f32;
 
 // One forward step that also records y~ (the momentum before the wall test).
-template <bool SIGN, bool CONTROL>
+template <bool SIGN, bool CONTROL, int T>
 __global__ void __launch_bounds__(256) k_adj_fwd(const float* __restrict__ J, int Np, int Rp,
                                                  const float* __restrict__ x, const float* __restrict__ y,
                                                  const float* __restrict__ p, float* __restrict__ xn,
@@ -38,57 +38,57 @@ __global__ void __launch_bounds__(256) k_adj_fwd(const float* __restrict__ J, in
                                                  float* __restrict__ yt_out,
                                                  const float* __restrict__ A, float c, float dt,
                                                  float p_shared, float inv_rem) {
-    __shared__ __align__(16) F32Smem sm;
-    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
-    float acc[8][8];
-    sgemm_tile<SIGN>(J, x, Np, Rp, i0, r0, acc, sm);
+    using TT = Tile<T>;
+    __shared__ __align__(16) typename TT::Smem sm;
+    const int i0 = blockIdx.y * T, r0 = blockIdx.x * T;
+    float acc[TT::NA][TT::NB];
+    TT::template gemm<SIGN>(J, x, Np, Rp, i0, r0, acc, sm);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int cols[2] = {r0 + tx * 4, r0 + 64 + tx * 4};
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const size_t rowoff = (size_t)(i0 + row_of(a, ty)) * Rp;
+    for (int a = 0; a < TT::NA; ++a) {
+        const size_t rowoff = (size_t)(i0 + TT::row(a, ty)) * Rp;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const size_t o = rowoff + cols[h] + q;
-                const float xo = x[o];
-                float pv = CONTROL ? p[o] : 0.f;
-                const float g = 1.f - (CONTROL ? A[cols[h] + q] : 0.f) * xo * xo;
-                const float pnv = CONTROL ? pv - g * pv * inv_rem : p_shared;
-                const float ytv = y[o] - (pnv * xo - c * acc[a][h * 4 + q]) * dt;
-                float xt = xo + ytv * dt, yv = ytv;
-                if (fabsf(xt) > 1.f) {
-                    xt = sgnf(xt);
-                    yv = 0.f;
-                }
-                xn[o] = xt;
-                yn[o] = yv;
-                if (CONTROL) pn[o] = pnv;
-                yt_out[o] = ytv;
+        for (int b = 0; b < TT::NB; ++b) {
+            const int col = r0 + TT::col(b, tx);
+            const size_t o = rowoff + col;
+            const float xo = x[o];
+            float pv = CONTROL ? p[o] : 0.f;
+            const float g = 1.f - (CONTROL ? A[col] : 0.f) * xo * xo;
+            const float pnv = CONTROL ? pv - g * pv * inv_rem : p_shared;
+            const float ytv = y[o] - (pnv * xo - c * acc[a][b]) * dt;
+            float xt = xo + ytv * dt, yv = ytv;
+            if (fabsf(xt) > 1.f) {
+                xt = sgnf(xt);
+                yv = 0.f;
             }
+            xn[o] = xt;
+            yn[o] = yv;
+            if (CONTROL) pn[o] = pnv;
+            yt_out[o] = ytv;
         }
     }
 }
 
 // Seed: G = J x(t_W); lx = -G, ly = lp = 0, e_acc[r] += sum_i x_i G_i.
+template <int T>
 __global__ void __launch_bounds__(256) k_adj_seed(const float* __restrict__ J, int Np, int Rp,
                                                   const float* __restrict__ x, float* __restrict__ lx,
                                                   float* __restrict__ ly, float* __restrict__ lp,
                                                   double* __restrict__ e_acc) {
-    __shared__ __align__(16) F32Smem sm;
-    __shared__ float red[16][BN + 1];
-    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
-    float acc[8][8];
-    sgemm_tile<false>(J, x, Np, Rp, i0, r0, acc, sm);
+    using TT = Tile<T>;
+    __shared__ __align__(16) typename TT::Smem sm;
+    __shared__ float red[16][T + 1];
+    const int i0 = blockIdx.y * T, r0 = blockIdx.x * T;
+    float acc[TT::NA][TT::NB];
+    TT::template gemm<false>(J, x, Np, Rp, i0, r0, acc, sm);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const int col = b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4);
+    for (int b = 0; b < TT::NB; ++b) {
+        const int col = TT::col(b, tx);
         float part = 0.f;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const size_t o = (size_t)(i0 + row_of(a, ty)) * Rp + r0 + col;
+        for (int a = 0; a < TT::NA; ++a) {
+            const size_t o = (size_t)(i0 + TT::row(a, ty)) * Rp + r0 + col;
             part = fmaf(x[o], acc[a][b], part);
             lx[o] = -acc[a][b];
             ly[o] = 0.f;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_adj_seed(const float* __restrict__ J, i
         red[ty][col] = part;
     }
     __syncthreads();
-    if (threadIdx.x < BN) {
+    if (threadIdx.x < T) {
         double s = 0.0;
         for (int t = 0; t < 16; ++t) s += (double)red[t][threadIdx.x];
         atomicAdd(&e_acc[r0 + threadIdx.x], s);
@@ -119,7 +119,7 @@ __global__ void k_adj_pre(const float* __restrict__ x, const float* __restrict__
 
 // Second half: G = J lf (skipped for the sgn coupling), then every adjoint of
 // the step's inputs and the per-replica gA, gdt sums.
-template <bool SIGN, bool CONTROL>
+template <bool SIGN, bool CONTROL, int T>
 __global__ void __launch_bounds__(256) k_adj_post(const float* __restrict__ J, int Np, int Rp,
                                                   const float* __restrict__ lf,
                                                   const float* __restrict__ x,
@@ -133,27 +133,28 @@ __global__ void __launch_bounds__(256) k_adj_post(const float* __restrict__ J, i
                                                   float p_shared, float inv_rem,
                                                   double* __restrict__ gA,
                                                   double* __restrict__ gdt) {
-    __shared__ __align__(16) F32Smem sm;
-    __shared__ float redA[16][BN + 1], redT[16][BN + 1];
-    const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
-    float acc[8][8];
+    using TT = Tile<T>;
+    __shared__ __align__(16) typename TT::Smem sm;
+    __shared__ float redA[16][T + 1], redT[16][T + 1];
+    const int i0 = blockIdx.y * T, r0 = blockIdx.x * T;
+    float acc[TT::NA][TT::NB];
     if (!SIGN) {
-        sgemm_tile<false>(J, lf, Np, Rp, i0, r0, acc, sm);
+        TT::template gemm<false>(J, lf, Np, Rp, i0, r0, acc, sm);
     } else {
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < TT::NA; ++a)
 #pragma unroll
-            for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+            for (int b = 0; b < TT::NB; ++b) acc[a][b] = 0.f;
     }
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const int col = b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4);
+    for (int b = 0; b < TT::NB; ++b) {
+        const int col = TT::col(b, tx);
         const float a_r = CONTROL ? A[r0 + col] : 0.f;
         float sA = 0.f, sT = 0.f;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const size_t o = (size_t)(i0 + row_of(a, ty)) * Rp + r0 + col;
+        for (int a = 0; a < TT::NA; ++a) {
+            const size_t o = (size_t)(i0 + TT::row(a, ty)) * Rp + r0 + col;
             const float xo = x[o], ytv = yt[o];
             const bool clamped = fabsf(xo + ytv * dt) > 1.f;
             const float lxt = clamped ? 0.f : lx[o];
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256) k_adj_post(const float* __restrict__ J, i
         redT[ty][col] = sT;
     }
     __syncthreads();
-    if (threadIdx.x < BN) {
+    if (threadIdx.x < T) {
         double a = 0.0, t = 0.0;
         for (int k = 0; k < 16; ++k) {
             a += (double)redA[k][threadIdx.x];
@@ -288,19 +289,28 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
     GSB_CUDA_TRY(cudaMemsetAsync(sy, 0, sizeof(float) * nst, s));
     k_fill<<<(unsigned)((nst + 255) / 256), 256, 0, s>>>(sp, 1.f, nst);
     GSB_LAUNCH_CHECK("k_fill");
-    const dim3 grid(Rp / BN, Np / BM);
+    // 64 x 64 tiles when 128 x 128 ones would leave SMs idle (few replicas)
+    int sms = 0, dev = 0;
+    GSB_CUDA_TRY(cudaGetDevice(&dev));
+    GSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const bool t64 = (long)(Rp / 128) * (Np / 128) < sms;
+    const int T = t64 ? 64 : 128;
+    const dim3 grid(Rp / T, Np / T);
     auto fwd = [&](int m, int slot) -> gsb_status {
         const size_t a = (size_t)slot * nst, b = (size_t)(slot + 1) * nst;
         const float p_shared = (float)(1.0 - (double)(m + 1) / (double)Q.M);
         const float inv_rem = 1.0f / (float)(Q.M - m);
-#define GSB_ADJ_FWD(S, C)                                                                        \
-    k_adj_fwd<S, C><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + a, sy + a, sp + a, sx + b, sy + b, \
-                                         sp + b, syt + a, Ad, c, dt, p_shared, inv_rem)
+#define GSB_ADJ_FWD(S, C, TS)                                                                     \
+    k_adj_fwd<S, C, TS><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + a, sy + a, sp + a, sx + b,     \
+                                             sy + b, sp + b, syt + a, Ad, c, dt, p_shared, inv_rem)
+#define GSB_ADJ_FWD_T(S, C) \
+    if (t64) GSB_ADJ_FWD(S, C, 64); else GSB_ADJ_FWD(S, C, 128)
         if (sign) {
-            if (control) GSB_ADJ_FWD(true, true); else GSB_ADJ_FWD(true, false);
+            if (control) { GSB_ADJ_FWD_T(true, true); } else { GSB_ADJ_FWD_T(true, false); }
         } else {
-            if (control) GSB_ADJ_FWD(false, true); else GSB_ADJ_FWD(false, false);
+            if (control) { GSB_ADJ_FWD_T(false, true); } else { GSB_ADJ_FWD_T(false, false); }
         }
+#undef GSB_ADJ_FWD_T
 #undef GSB_ADJ_FWD
         GSB_LAUNCH_CHECK("k_adj_fwd");
         return GSB_OK;
@@ -339,8 +349,12 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
     }
     // seed from x(t_W) (slot of the last segment's end)
     const int Llast = seg_len(nseg - 1);
-    k_adj_seed<<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + (size_t)Llast * nst, lx, ly,
-                                    control ? lp : nullptr, e_acc);
+    if (t64)
+        k_adj_seed<64><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + (size_t)Llast * nst, lx, ly,
+                                            control ? lp : nullptr, e_acc);
+    else
+        k_adj_seed<128><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + (size_t)Llast * nst, lx, ly,
+                                             control ? lp : nullptr, e_acc);
     GSB_LAUNCH_CHECK("k_adj_seed");
     // reverse sweep, segment by segment; the last segment is still in the slots
     for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -360,15 +374,18 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
                                                                          nst, c, dt);
                 GSB_LAUNCH_CHECK("k_adj_pre");
             }
-#define GSB_ADJ_POST(S, C)                                                                      \
-    k_adj_post<S, C><<<grid, 256, 0, s>>>(P->J32, Np, Rp, lf, sx + a, sy + a, sp + a, sp + b,   \
-                                          syt + a, lx, ly, lp, Ad, c, dt, p_shared, inv_rem, gA, \
-                                          gdt)
+#define GSB_ADJ_POST(S, C, TS)                                                                  \
+    k_adj_post<S, C, TS><<<grid, 256, 0, s>>>(P->J32, Np, Rp, lf, sx + a, sy + a, sp + a, sp + b, \
+                                              syt + a, lx, ly, lp, Ad, c, dt, p_shared, inv_rem,  \
+                                              gA, gdt)
+#define GSB_ADJ_POST_T(S, C) \
+    if (t64) GSB_ADJ_POST(S, C, 64); else GSB_ADJ_POST(S, C, 128)
             if (sign) {
-                if (control) GSB_ADJ_POST(true, true); else GSB_ADJ_POST(true, false);
+                if (control) { GSB_ADJ_POST_T(true, true); } else { GSB_ADJ_POST_T(true, false); }
             } else {
-                if (control) GSB_ADJ_POST(false, true); else GSB_ADJ_POST(false, false);
+                if (control) { GSB_ADJ_POST_T(false, true); } else { GSB_ADJ_POST_T(false, false); }
             }
+#undef GSB_ADJ_POST_T
 #undef GSB_ADJ_POST
             GSB_LAUNCH_CHECK("k_adj_post");
         }

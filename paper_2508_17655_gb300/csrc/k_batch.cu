@@ -40,64 +40,6 @@ struct BatchTile {
     int inst, i0, r0, work;
 };
 
-// 64 x 64 tile: 256 threads, 4 x 4 accumulators each (rows 4ty.., columns 4tx..).
-struct Smem64 {
-    float A[2][BK][64 + 4];
-    float B[2][BK][64];
-};
-
-template <bool SIGN>
-__device__ __forceinline__ void sgemm_tile64(const float* __restrict__ J, const float* __restrict__ X,
-                                             int Np, int Rp, int i0, int r0, float (&acc)[4][4],
-                                             Smem64& sm) {
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int a_row = tid >> 2, a_k = (tid & 3) * 2;
-    const int b_k = tid >> 5, b_c = (tid & 31) * 2;
-    const float* Ap = J + (size_t)(i0 + a_row) * Np + a_k;
-    const float* Bp = X + (size_t)b_k * Rp + r0 + b_c;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    auto ldb = [&](const float* q) {
-        float2 v = *reinterpret_cast<const float2*>(q);
-        if (SIGN) {
-            v.x = sgnf(v.x);
-            v.y = sgnf(v.y);
-        }
-        return v;
-    };
-    float2 ra = *reinterpret_cast<const float2*>(Ap);
-    float2 rb = ldb(Bp);
-    auto stash = [&](int buf) {
-        sm.A[buf][a_k + 0][a_row] = ra.x;
-        sm.A[buf][a_k + 1][a_row] = ra.y;
-        *reinterpret_cast<float2*>(&sm.B[buf][b_k][b_c]) = rb;
-    };
-    stash(0);
-    __syncthreads();
-    const int nk = Np / BK;
-    for (int kt = 0; kt < nk; ++kt) {
-        const int buf = kt & 1;
-        if (kt + 1 < nk) {
-            ra = *reinterpret_cast<const float2*>(Ap + (size_t)(kt + 1) * BK);
-            rb = ldb(Bp + (size_t)(kt + 1) * BK * Rp);
-        }
-#pragma unroll
-        for (int k = 0; k < BK; ++k) {
-            const float4 a = *reinterpret_cast<const float4*>(&sm.A[buf][k][ty * 4]);
-            const float4 b = *reinterpret_cast<const float4*>(&sm.B[buf][k][tx * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w};
-            const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-        }
-        if (kt + 1 < nk) stash(buf ^ 1);
-        __syncthreads();
-    }
-}
 
 __device__ __forceinline__ void batch_update4(const BatchInst& I, const float* xc, float* xn,
                                               size_t o, int r, const float* f, bool control,
