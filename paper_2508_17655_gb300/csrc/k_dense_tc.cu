@@ -50,21 +50,9 @@ __device__ __forceinline__ uint8_t e4m3_sign(float x) { return x >= 0.f ? 0x38 :
 // x as four signed base-256 digits of q = rint(x 2^30), |x| <= 1:
 // q = d0 + 256 d1 + 65536 d2 + 16777216 d3, d0..d2 in [-128, 127], |d3| <= 64.
 // x 2^30 is exact in FP32 (a power-of-two scaling), so q = x 2^30 exactly
-// whenever |x| >= 2^-7.
-__device__ __forceinline__ void fx32_digits(float x, __nv_bfloat16 (&d)[4]) {
-    int q = __float2int_rn(x * 1073741824.0f);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int dk = ((q + 128) & 255) - 128;
-        d[k] = __int2bfloat16_rn(dk);
-        q = (q - dk) >> 8;  // exact: q - dk is a multiple of 256
-    }
-    d[3] = __int2bfloat16_rn(q);
-}
-
-// The same digits from the bytes of u = q + 0x808080: d_k = byte_k(u) - 128
-// for k < 3 and d_3 = u >> 24 (arithmetic), since u = q + 128 (1 + 256 +
-// 65536); returned as bf16 bit patterns.
+// whenever |x| >= 2^-7. With u = q + 0x808080 = q + 128 (1 + 256 + 65536):
+// d_k = byte_k(u) - 128 for k < 3 and d_3 = u >> 24 (arithmetic); returned as
+// bf16 bit patterns (each digit is exact in bf16).
 __device__ __forceinline__ void fx32_digit_bits(float x, uint16_t (&d)[4]) {
     const int u = __float2int_rn(x * 1073741824.0f) + 0x808080;
 #pragma unroll
@@ -554,9 +542,9 @@ __global__ void k_tc_prep(const float* __restrict__ x, void* __restrict__ v, int
         if (KIND == 0) {
             reinterpret_cast<uint8_t*>(v)[vo] = e4m3_sign(xv);
         } else {
-            __nv_bfloat16 d[4];
-            fx32_digits(xv, d);
-            __nv_bfloat16* vb = reinterpret_cast<__nv_bfloat16*>(v);
+            uint16_t d[4];
+            fx32_digit_bits(xv, d);
+            uint16_t* vb = reinterpret_cast<uint16_t*>(v);
             const size_t plane = (size_t)Rp * Np;
 #pragma unroll
             for (int q = 0; q < 4; ++q) vb[q * plane + vo] = d[q];
