@@ -47,6 +47,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gsb", "reference"], default="gsb")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain-FP32 / GbSB / TTS legs")
+    ap.add_argument("--leg", choices=LEGS, default=None,
+                    help="run one extra configuration alone and print its line (profiling)")
+    ap.add_argument("--leg-M", type=int, default=0,
+                    help="step count for the sparse / fx32 leg (default: the configuration's)")
     ap.add_argument("--M", type=int, default=M_STEPS,
                     help="time steps per run (the workload has 2000; smaller only for profiling)")
     return ap.parse_args()
@@ -351,21 +355,33 @@ def _events(torch, stream):
     return e0, e1
 
 
-def other_legs(gsb, I, np, torch, stream, Pk, how):
+LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "adjoint", "fx32")
+
+
+def fp32_alu_peak(Pk):
+    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x the max SM clock."""
+    return 152 * 128 * 2 * Pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
     """The other configurations of the hot path, one run each (after one
-    warm-up), with the dominant kernel's roofline from CUDA events."""
+    warm-up), with the dominant kernel's roofline from CUDA events. only:
+    the name of a single leg to run; leg_M: a shorter step count for the
+    sparse and FX32 legs (profiling)."""
     import oracle as O
     out = {}
     hbm = Pk["hbm_gbs"]
-    # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x the measured SM clock
-    fp32_peak = 152 * 128 * 2 * Pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak = fp32_alu_peak(Pk)
+    want = lambda name: only is None or only == name
     # --- sparse Max-Cut (CSR), ER mean degree 20, +1 weights, R = 512, M = 5000
     for N in (2000, 20000):
+        if not want(f"sparse_N{N}"):
+            continue
         rp, col, val = I.er_graph(N, 20, "+1", 5)
         lmax, lmin = O.lambda_extremes(O.Coupling(N, rowptr=rp, col=col, val=val), iters=4000,
                                        tol=1e-10)
         P = gsb.Problem.csr(N, rp, col, val, stream=stream.cuda_stream)
-        R, M = 512, 5000
+        R, M = 512, leg_M or 5000
         run = P.run("gbsb", M=M, R=R, c=1 / lmax, dt=O.dt_from_lambda(lmax, lmin), A=0.2, seed=1,
                     defer=True, profile=True, stream=stream.cuda_stream)
         run.restart(2)
@@ -390,34 +406,66 @@ def other_legs(gsb, I, np, torch, stream, Pk, how):
                          "algorithmic_bytes_per_step": bytes_step, "peak_source": how}}
         run.close()
         P.close()
+    # --- FX32 (GbSB, J.x exact on bf16 digit planes), the headline shape, one run
+    if only == "fx32":
+        J = I.sk_pm1(N_SPINS, 0)
+        A = np.repeat(np.array(A_VALUES, np.float32), R_REPLICAS // len(A_VALUES))
+        P = gsb.Problem.dense(J, stream=stream.cuda_stream)
+        M = leg_M or M_STEPS
+        run = P.run("gbsb", M=M, R=R_REPLICAS, c=1.0 / (2.0 * math.sqrt(N_SPINS)), dt=DT, A=A,
+                    seed=1, precision="fx32", defer=True, profile=True,
+                    stream=stream.cuda_stream)
+        run.restart(2)
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        run.restart(3)
+        e1.record(stream)
+        e1.synchronize()
+        kms, kn, ksteps = run.kernel_time()
+        us = 1e3 * kms / ksteps
+        out["fx32"] = {"workload": f"{WORKLOAD}, GbSB on FX32, M={M}",
+                       "value": N_SPINS * R_REPLICAS * M / (e0.elapsed_time(e1) / 1e3),
+                       "unit": "spin-updates/s", "kernel": run.kernel(), "us_per_step": us,
+                       "tensor_frac_bf16_4planes": (4 * 2.0 * N_SPINS ** 2 * R_REPLICAS / (us * 1e-6)
+                                                    / 1e12) / Pk["bf16_tflops_sustained"]}
+        run.close()
+        P.close()
+    if only is not None and only not in ("batched_256", "lyapunov", "adjoint"):
+        return out
     # --- 256 batched uneven SK instances, N ~ U{64..1024}, R ~ U{32..256}, M = 1000
     Ns, Rs = I.batch_sizes(256, seed=0)
     probs = [gsb.Problem.dense(I.sk_gauss(int(n), 2000 + k), stream=stream.cuda_stream)
-             for k, n in enumerate(Ns)]
+             for k, n in enumerate(Ns)] if want("batched_256") else []
     specs = [dict(variant="gbsb", M=1000, R=int(r), c=0.5, dt=1.25, A=0.2, seed=k)
              for k, r in enumerate(Rs)]
-    runs, _ = gsb.batch_run(probs, specs, max_steps=20, stream=stream.cuda_stream)  # warm-up
-    for r in runs:
-        r.close()
-    t = time.perf_counter()
-    runs, info = gsb.batch_run(probs, specs, stream=stream.cuda_stream)
-    el = time.perf_counter() - t
-    for r in runs:
-        r.close()
-    su = float(np.sum(Ns * Rs)) * 1000
-    flop = float(np.sum(2.0 * Ns.astype(float) ** 2 * Rs)) * 1000
-    out["batched_256"] = {
-        "workload": "256 SK instances N~U{64..1024}, N(0,1/N) FP32, R~U{32..256}, M=1000, GbSB",
-        "value": su / el, "unit": "spin-updates/s", "ms_per_run": 1e3 * el,
-        "autotune": info, "how": "host wall clock around gsb_batch_run (allocation and probes included)",
-        "roofline": {"bound": "alu", "kernel": f"k_batch_step<{info['tile']}>", "achieved": flop / el / 1e12,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / el / 1e12 / fp32_peak,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}}
+    if probs:
+        runs, _ = gsb.batch_run(probs, specs, max_steps=20, stream=stream.cuda_stream)  # warm-up
+        for r in runs:
+            r.close()
+        t = time.perf_counter()
+        runs, info = gsb.batch_run(probs, specs, stream=stream.cuda_stream)
+        el = time.perf_counter() - t
+        for r in runs:
+            r.close()
+        su = float(np.sum(Ns * Rs)) * 1000
+        flop = float(np.sum(2.0 * Ns.astype(float) ** 2 * Rs)) * 1000
+    if probs:
+        out["batched_256"] = {
+            "workload": "256 SK instances N~U{64..1024}, N(0,1/N) FP32, R~U{32..256}, M=1000, GbSB",
+            "value": su / el, "unit": "spin-updates/s", "ms_per_run": 1e3 * el,
+            "autotune": info, "how": "host wall clock around gsb_batch_run (allocation and probes included)",
+            "roofline": {"bound": "alu", "kernel": f"k_batch_step<{info['tile']}>", "achieved": flop / el / 1e12,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / el / 1e12 / fp32_peak,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}}
     for P in probs:
         P.close()
+    if only is not None and only not in ("lyapunov", "adjoint"):
+        return out
     # --- Lyapunov exponents: N = 2000 SK, 16 control strengths x 256 replicas
     J5 = I.sk_gauss(2000, 0)
     P5 = gsb.Problem.dense(J5, stream=stream.cuda_stream)
+    if not want("lyapunov"):
+        return adjoint_leg(gsb, O, np, torch, stream, P5, out, fp32_peak)
     A16 = [0.025 * k for k in range(16)]
     steps = 200
     P5.lyapunov("gbsb", 2000, 256, A16, c=0.5, dt=1.25, renorm_every=10, nsteps=20)
@@ -433,7 +481,15 @@ def other_legs(gsb, I, np, torch, stream, Pk, how):
         "roofline": {"bound": "alu", "kernel": "k_tangent_step", "achieved": flop / el / 1e12,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / el / 1e12 / fp32_peak,
                      "how": "host wall clock around gsb_lyapunov (allocation included)"}}
-    # --- adjoint gradient: N = 2000 SK, R = 256, 200-step window, checkpoints every 20
+    if only == "lyapunov":
+        P5.close()
+        return out
+    return adjoint_leg(gsb, O, np, torch, stream, P5, out, fp32_peak)
+
+
+def adjoint_leg(gsb, O, np, torch, stream, P5, out, fp32_peak):
+    """Adjoint gradient: N = 2000 SK (the problem P5), R = 256, 200-step
+    window, checkpoints every 20; closes P5."""
     R5, W = 256, 200
     x0 = torch.from_numpy(O.init_uniform(R5, 2000, 1).astype(np.float32)).cuda()
     E = torch.empty(R5, dtype=torch.float64, device="cuda")
@@ -516,8 +572,22 @@ def main():
         os.environ["CUDA_VISIBLE_DEVICES"] = ids[local % len(ids)]
     if args.impl == "reference":
         reference_arm(args, world, rank)
+    elif args.leg:
+        leg_arm(args)
     else:
         gpu_arm(args, world, rank, local)
+
+
+def leg_arm(args):
+    """One extra configuration alone (one GPU), for profiling its kernel."""
+    import numpy as np
+    import torch
+    from paper_2508_17655_gb300 import build, gsb, inputs as I
+    build.build()
+    stream = torch.cuda.Stream(device=torch.device("cuda", 0))
+    Pk, how = peaks()
+    out = other_legs(gsb, I, np, torch, stream, Pk, how, only=args.leg, leg_M=args.leg_M)
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
 
 
 if __name__ == "__main__":

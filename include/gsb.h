@@ -163,9 +163,9 @@ gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches, in
 /* Name of the step kernel the run selected at gsb_run: "k_tc_persist<cluster>"
  * (FP8, many steps per launch, one thread-block cluster per 128 replicas),
  * "k_tc_persist<grid>" (the same, one cooperative launch), "k_tc_step<e4m3>"
- * or "k_tc_step<fx32>" (one step per launch), "k_dense_f32_step" or
- * "k_csr_step". A static string owned by the library; "" for NULL. No GPU
- * work. */
+ * (FP8, one step per launch), "k_fx32_step" (FX32 digit planes, one step per
+ * launch), "k_dense_f32_step" or "k_csr_step". A static string owned by the
+ * library; "" for NULL. No GPU work. */
 const char* gsb_run_kernel(const gsb_run_state* run);
 
 /* Best state per replica (host outputs, each nullable): spins R x N int8,

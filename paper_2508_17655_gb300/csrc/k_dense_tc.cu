@@ -831,7 +831,7 @@ bool tc_available() { return true; }
 const char* tc_kernel_name(const gsb_run_state* run) {
     const TcState* T = (const TcState*)run->tc;
     if (!T) return "none";
-    if (T->kind == 1) return "k_tc_step<fx32>";
+    if (T->kind == 1) return "k_fx32_step";
     if (T->persistent) return T->cluster ? "k_tc_persist<cluster>" : "k_tc_persist<grid>";
     return "k_tc_step<e4m3>";
 }
