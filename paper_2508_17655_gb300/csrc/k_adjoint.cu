@@ -29,20 +29,78 @@ namespace {
 
 using namespace f32;
 
+// MODE selects how a kernel gets its SGEMM: 128 or 64 -- a fused T x T tile;
+// kSplitK -- 64 x 64 tiles whose K is split kSplitK ways by k_adj_gemm_part
+// (more CTAs when few replicas leave SMs idle), the kernel adding the partial
+// sums in a fixed order (deterministic: a recomputed step is bit-identical).
+constexpr int kSplitK = 4;
+template <int MODE>
+struct Mode {
+    static constexpr int T = MODE == 128 ? 128 : 64;
+    static constexpr bool split = MODE == kSplitK;
+};
+
+// F_s = J[:, K_s] X[K_s, :] for the K slice s = blockIdx.z of kSplitK, 64 x 64
+// tiles, into Fp[s] ([Np][Rp] each).
+template <bool SIGN>
+__global__ void __launch_bounds__(256) k_adj_gemm_part(const float* __restrict__ J,
+                                                       const float* __restrict__ X, int Np, int Rp,
+                                                       float* __restrict__ Fp) {
+    __shared__ __align__(16) Smem64 sm;
+    const int i0 = blockIdx.y * 64, r0 = blockIdx.x * 64, sl = blockIdx.z;
+    const int klen = Np / kSplitK;
+    float acc[4][4];
+    sgemm_tile64<SIGN>(J, X, Np, Rp, i0, r0, acc, sm, sl * klen, klen);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float* F = Fp + (size_t)sl * Np * Rp;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        *reinterpret_cast<float4*>(F + (size_t)(i0 + ty * 4 + a) * Rp + r0 + tx * 4) =
+            make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+}
+
+// acc = the tile's SGEMM, fused or from the split-K partials.
+template <int MODE, bool SIGN>
+__device__ __forceinline__ void adj_gemm(const float* J, const float* X, int Np, int Rp, int i0,
+                                         int r0, const float* Fp,
+                                         float (&acc)[Tile<Mode<MODE>::T>::NA][Tile<Mode<MODE>::T>::NB],
+                                         typename Tile<Mode<MODE>::T>::Smem& sm) {
+    using TT = Tile<Mode<MODE>::T>;
+    if constexpr (!Mode<MODE>::split) {
+        TT::template gemm<SIGN>(J, X, Np, Rp, i0, r0, acc, sm);
+    } else {
+        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+        const size_t nst = (size_t)Np * Rp;
+#pragma unroll
+        for (int a = 0; a < TT::NA; ++a) {
+            const size_t o = (size_t)(i0 + TT::row(a, ty)) * Rp + r0 + TT::col(0, tx);
+            float4 v = *reinterpret_cast<const float4*>(Fp + o);
+#pragma unroll
+            for (int sl = 1; sl < kSplitK; ++sl) {
+                const float4 w = *reinterpret_cast<const float4*>(Fp + sl * nst + o);
+                v.x += w.x, v.y += w.y, v.z += w.z, v.w += w.w;
+            }
+            acc[a][0] = v.x, acc[a][1] = v.y, acc[a][2] = v.z, acc[a][3] = v.w;
+        }
+    }
+}
+
 // One forward step that also records y~ (the momentum before the wall test).
-template <bool SIGN, bool CONTROL, int T>
+template <bool SIGN, bool CONTROL, int MODE>
 __global__ void __launch_bounds__(256) k_adj_fwd(const float* __restrict__ J, int Np, int Rp,
                                                  const float* __restrict__ x, const float* __restrict__ y,
                                                  const float* __restrict__ p, float* __restrict__ xn,
                                                  float* __restrict__ yn, float* __restrict__ pn,
                                                  float* __restrict__ yt_out,
                                                  const float* __restrict__ A, float c, float dt,
-                                                 float p_shared, float inv_rem) {
+                                                 float p_shared, float inv_rem,
+                                                 const float* __restrict__ Fp) {
+    constexpr int T = Mode<MODE>::T;
     using TT = Tile<T>;
     __shared__ __align__(16) typename TT::Smem sm;
     const int i0 = blockIdx.y * T, r0 = blockIdx.x * T;
     float acc[TT::NA][TT::NB];
-    TT::template gemm<SIGN>(J, x, Np, Rp, i0, r0, acc, sm);
+    adj_gemm<MODE, SIGN>(J, x, Np, Rp, i0, r0, Fp, acc, sm);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int a = 0; a < TT::NA; ++a) {
@@ -70,17 +128,19 @@ __global__ void __launch_bounds__(256) k_adj_fwd(const float* __restrict__ J, in
 }
 
 // Seed: G = J x(t_W); lx = -G, ly = lp = 0, e_acc[r] += sum_i x_i G_i.
-template <int T>
+template <int MODE>
 __global__ void __launch_bounds__(256) k_adj_seed(const float* __restrict__ J, int Np, int Rp,
                                                   const float* __restrict__ x, float* __restrict__ lx,
                                                   float* __restrict__ ly, float* __restrict__ lp,
-                                                  double* __restrict__ e_acc) {
+                                                  double* __restrict__ e_acc,
+                                                  const float* __restrict__ Fp) {
+    constexpr int T = Mode<MODE>::T;
     using TT = Tile<T>;
     __shared__ __align__(16) typename TT::Smem sm;
     __shared__ float red[16][T + 1];
     const int i0 = blockIdx.y * T, r0 = blockIdx.x * T;
     float acc[TT::NA][TT::NB];
-    TT::template gemm<false>(J, x, Np, Rp, i0, r0, acc, sm);
+    adj_gemm<MODE, false>(J, x, Np, Rp, i0, r0, Fp, acc, sm);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int b = 0; b < TT::NB; ++b) {
@@ -119,7 +179,7 @@ __global__ void k_adj_pre(const float* __restrict__ x, const float* __restrict__
 
 // Second half: G = J lf (skipped for the sgn coupling), then every adjoint of
 // the step's inputs and the per-replica gA, gdt sums.
-template <bool SIGN, bool CONTROL, int T>
+template <bool SIGN, bool CONTROL, int MODE>
 __global__ void __launch_bounds__(256) k_adj_post(const float* __restrict__ J, int Np, int Rp,
                                                   const float* __restrict__ lf,
                                                   const float* __restrict__ x,
@@ -132,14 +192,16 @@ __global__ void __launch_bounds__(256) k_adj_post(const float* __restrict__ J, i
                                                   const float* __restrict__ A, float c, float dt,
                                                   float p_shared, float inv_rem,
                                                   double* __restrict__ gA,
-                                                  double* __restrict__ gdt) {
+                                                  double* __restrict__ gdt,
+                                                  const float* __restrict__ Fp) {
+    constexpr int T = Mode<MODE>::T;
     using TT = Tile<T>;
     __shared__ __align__(16) typename TT::Smem sm;
     __shared__ float redA[16][T + 1], redT[16][T + 1];
     const int i0 = blockIdx.y * T, r0 = blockIdx.x * T;
     float acc[TT::NA][TT::NB];
     if (!SIGN) {
-        TT::template gemm<false>(J, lf, Np, Rp, i0, r0, acc, sm);
+        adj_gemm<MODE, false>(J, lf, Np, Rp, i0, r0, Fp, acc, sm);
     } else {
 #pragma unroll
         for (int a = 0; a < TT::NA; ++a)
@@ -289,22 +351,43 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
     GSB_CUDA_TRY(cudaMemsetAsync(sy, 0, sizeof(float) * nst, s));
     k_fill<<<(unsigned)((nst + 255) / 256), 256, 0, s>>>(sp, 1.f, nst);
     GSB_LAUNCH_CHECK("k_fill");
-    // 64 x 64 tiles when 128 x 128 ones would leave SMs idle (few replicas)
+    // 64 x 64 tiles when 128 x 128 ones would leave SMs idle (few replicas),
+    // and K split kSplitK ways when even those give fewer than two CTAs per SM
     int sms = 0, dev = 0;
     GSB_CUDA_TRY(cudaGetDevice(&dev));
     GSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const bool t64 = (long)(Rp / 128) * (Np / 128) < sms;
-    const int T = t64 ? 64 : 128;
+    const long tiles64 = (long)(Rp / 64) * (Np / 64);
+    const int mode = (long)(Rp / 128) * (Np / 128) >= sms ? 128 : (tiles64 >= 2L * sms ? 64 : kSplitK);
+    const int T = mode == 128 ? 128 : 64;
     const dim3 grid(Rp / T, Np / T);
+    float* Fp = nullptr;  // split-K partial sums
+    if (mode == kSplitK && (st = B.alloc(&Fp, kSplitK * nst))) return st;
+    // the partial sums of J X for a kernel in the split mode
+    auto gemm_part = [&](const float* X, bool sgn) -> gsb_status {
+        const dim3 g(Rp / 64, Np / 64, kSplitK);
+        if (sgn)
+            k_adj_gemm_part<true><<<g, 256, 0, s>>>(P->J32, X, Np, Rp, Fp);
+        else
+            k_adj_gemm_part<false><<<g, 256, 0, s>>>(P->J32, X, Np, Rp, Fp);
+        GSB_LAUNCH_CHECK("k_adj_gemm_part");
+        return GSB_OK;
+    };
     auto fwd = [&](int m, int slot) -> gsb_status {
         const size_t a = (size_t)slot * nst, b = (size_t)(slot + 1) * nst;
         const float p_shared = (float)(1.0 - (double)(m + 1) / (double)Q.M);
         const float inv_rem = 1.0f / (float)(Q.M - m);
-#define GSB_ADJ_FWD(S, C, TS)                                                                     \
-    k_adj_fwd<S, C, TS><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + a, sy + a, sp + a, sx + b,     \
-                                             sy + b, sp + b, syt + a, Ad, c, dt, p_shared, inv_rem)
-#define GSB_ADJ_FWD_T(S, C) \
-    if (t64) GSB_ADJ_FWD(S, C, 64); else GSB_ADJ_FWD(S, C, 128)
+        if (mode == kSplitK) {
+            gsb_status g = gemm_part(sx + a, sign);
+            if (g != GSB_OK) return g;
+        }
+#define GSB_ADJ_FWD(S, C, MD)                                                                     \
+    k_adj_fwd<S, C, MD><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + a, sy + a, sp + a, sx + b,     \
+                                             sy + b, sp + b, syt + a, Ad, c, dt, p_shared, inv_rem, \
+                                             Fp)
+#define GSB_ADJ_FWD_T(S, C)                                               \
+    if (mode == 128) GSB_ADJ_FWD(S, C, 128);                              \
+    else if (mode == 64) GSB_ADJ_FWD(S, C, 64);                           \
+    else GSB_ADJ_FWD(S, C, kSplitK)
         if (sign) {
             if (control) { GSB_ADJ_FWD_T(true, true); } else { GSB_ADJ_FWD_T(true, false); }
         } else {
@@ -349,12 +432,19 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
     }
     // seed from x(t_W) (slot of the last segment's end)
     const int Llast = seg_len(nseg - 1);
-    if (t64)
-        k_adj_seed<64><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + (size_t)Llast * nst, lx, ly,
-                                            control ? lp : nullptr, e_acc);
-    else
-        k_adj_seed<128><<<grid, 256, 0, s>>>(P->J32, Np, Rp, sx + (size_t)Llast * nst, lx, ly,
-                                             control ? lp : nullptr, e_acc);
+    {
+        const float* xW = sx + (size_t)Llast * nst;
+        if (mode == kSplitK && (st = gemm_part(xW, false))) return st;
+        if (mode == 128)
+            k_adj_seed<128><<<grid, 256, 0, s>>>(P->J32, Np, Rp, xW, lx, ly, control ? lp : nullptr,
+                                                 e_acc, Fp);
+        else if (mode == 64)
+            k_adj_seed<64><<<grid, 256, 0, s>>>(P->J32, Np, Rp, xW, lx, ly, control ? lp : nullptr,
+                                                e_acc, Fp);
+        else
+            k_adj_seed<kSplitK><<<grid, 256, 0, s>>>(P->J32, Np, Rp, xW, lx, ly,
+                                                     control ? lp : nullptr, e_acc, Fp);
+    }
     GSB_LAUNCH_CHECK("k_adj_seed");
     // reverse sweep, segment by segment; the last segment is still in the slots
     for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -374,12 +464,15 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
                                                                          nst, c, dt);
                 GSB_LAUNCH_CHECK("k_adj_pre");
             }
-#define GSB_ADJ_POST(S, C, TS)                                                                  \
-    k_adj_post<S, C, TS><<<grid, 256, 0, s>>>(P->J32, Np, Rp, lf, sx + a, sy + a, sp + a, sp + b, \
+            if (mode == kSplitK && !sign && (st = gemm_part(lf, false))) return st;
+#define GSB_ADJ_POST(S, C, MD)                                                                  \
+    k_adj_post<S, C, MD><<<grid, 256, 0, s>>>(P->J32, Np, Rp, lf, sx + a, sy + a, sp + a, sp + b, \
                                               syt + a, lx, ly, lp, Ad, c, dt, p_shared, inv_rem,  \
-                                              gA, gdt)
-#define GSB_ADJ_POST_T(S, C) \
-    if (t64) GSB_ADJ_POST(S, C, 64); else GSB_ADJ_POST(S, C, 128)
+                                              gA, gdt, Fp)
+#define GSB_ADJ_POST_T(S, C)                                              \
+    if (mode == 128) GSB_ADJ_POST(S, C, 128);                             \
+    else if (mode == 64) GSB_ADJ_POST(S, C, 64);                          \
+    else GSB_ADJ_POST(S, C, kSplitK)
             if (sign) {
                 if (control) { GSB_ADJ_POST_T(true, true); } else { GSB_ADJ_POST_T(true, false); }
             } else {

@@ -86,14 +86,19 @@ struct Smem64 {
     float B[2][BK][64];
 };
 
+// K = Np, J rows Np apart; or, with ldj and k0/klen, the K range [k0, k0 + klen).
 template <bool SIGN>
 __device__ __forceinline__ void sgemm_tile64(const float* __restrict__ J, const float* __restrict__ X,
                                              int Np, int Rp, int i0, int r0, float (&acc)[4][4],
-                                             Smem64& sm) {
+                                             Smem64& sm, int k0 = 0, int klen = -1) {
+    const int ldj = Np;
+    if (klen < 0) klen = Np;
+    J += k0;
+    X += (size_t)k0 * Rp;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int a_row = tid >> 2, a_k = (tid & 3) * 2;
     const int b_k = tid >> 5, b_c = (tid & 31) * 2;
-    const float* Ap = J + (size_t)(i0 + a_row) * Np + a_k;
+    const float* Ap = J + (size_t)(i0 + a_row) * ldj + a_k;
     const float* Bp = X + (size_t)b_k * Rp + r0 + b_c;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -116,7 +121,7 @@ __device__ __forceinline__ void sgemm_tile64(const float* __restrict__ J, const 
     };
     stash(0);
     __syncthreads();
-    const int nk = Np / BK;
+    const int nk = klen / BK;
     for (int kt = 0; kt < nk; ++kt) {
         const int buf = kt & 1;
         if (kt + 1 < nk) {
