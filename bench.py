@@ -355,7 +355,8 @@ def _events(torch, stream):
     return e0, e1
 
 
-LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "adjoint", "fx32")
+LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "adjoint", "fx32",
+        "twin_delta")
 
 
 def fp32_alu_peak(Pk):
@@ -429,6 +430,42 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
                        "tensor_frac_bf16_4planes": (4 * 2.0 * N_SPINS ** 2 * R_REPLICAS / (us * 1e-6)
                                                     / 1e12) / Pk["bf16_tflops_sustained"]}
         run.close()
+        P.close()
+    # --- twin trajectories (Sec. IV, Eq. 8): delta(t_M) over A on the K2000 shape
+    # at the step count of Fig. 1(d) (M = 21,500), 100 pairs per A, GbSB
+    if want("twin_delta"):
+        J = I.sk_pm1(N_SPINS, 0)
+        P = gsb.Problem.dense(J, stream=stream.cuda_stream)
+        M, pairs = leg_M or 21500, 100
+        c = 1.0 / (2.0 * math.sqrt(N_SPINS))
+        tw = P.twin_run("gbsb", M=M, R=pairs, A_values=A_VALUES, c=c, dt=DT, seed=1,
+                        profile=True, stream=stream.cuda_stream)
+        tw.steps(20)  # warm-up
+        tw.restart(2, defer=True)
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        tw.steps(M)
+        delta = tw.delta()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, kn, ksteps = tw.kernel_time()
+        us = 1e3 * kms / ksteps
+        reps = 2 * pairs * len(A_VALUES)
+        # FX32: four bf16 digit planes, 2 N^2 flops per plane and replica
+        tflops = 4 * 2.0 * N_SPINS ** 2 * reps / (us * 1e-6) / 1e12
+        d = delta.reshape(len(A_VALUES), pairs)
+        out["twin_delta"] = {
+            "workload": f"N={N_SPINS} +-1 complete graph, {len(A_VALUES)} A x {pairs} twin pairs "
+                        f"({reps} replicas), M={M}, dt={DT}, GbSB (Fig. 1(d))",
+            "value": N_SPINS * reps * M / (ms / 1e3), "unit": "spin-updates/s", "ms_per_run": ms,
+            "kernel": tw.kernel(), "us_per_step": us,
+            "A": A_VALUES, "mean_delta_tM": [float(v) for v in d.mean(axis=1)],
+            "roofline": {"bound": "tensor", "kernel": tw.kernel(), "achieved": tflops,
+                         "peak": Pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                         "frac": tflops / Pk["bf16_tflops_sustained"],
+                         "peak_source": how + " (bf16 sustained)"}}
+        tw.close()
         P.close()
     if only is not None and only not in ("batched_256", "lyapunov", "adjoint"):
         return out

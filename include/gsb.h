@@ -203,6 +203,27 @@ gsb_status gsb_lyapunov(gsb_problem* problem, const gsb_params* params, int32_t 
                         const float* A_values, int32_t renorm_every, int32_t nsteps,
                         double* mle_out, void* stream);
 
+/* Twin trajectories, the chaos measure of Sec. IV. Starts a run (as gsb_run)
+ * of 2 nA R replicas in nA x R pairs: replica a R + r is trajectory (1) of pair
+ * (a, r) and replica nA R + a R + r its trajectory (2); both use the control
+ * strength A_values[a] (host, length nA; unused by bSB / dSB). Initial state:
+ * x^(1)_i = +-0.1 and x^(2)_i = x^(1)_i +- 2e-6 with independent random signs
+ * (Philox4x32-10 keyed by params->seed, counter (i, pair index, 2, 0) for the
+ * first sign and (i, pair index, 3, 0) for the second, a draw >= 0 meaning +),
+ * the FP64 value rounded once to FP32; y = 0, p = 1. params->R is the number of
+ * pairs per control strength; x0, y0 and A_per_replica must be NULL; x0_range
+ * and y0_uniform are ignored; everything else as in gsb_run (GSB_RUN_DEFER
+ * included). gsb_run_restart on the handle redraws twin initial states. Dense or
+ * CSR problems without h (GSB_EUNSUPPORTED otherwise). */
+gsb_status gsb_twin_run(gsb_problem* problem, const gsb_params* params, int32_t nA,
+                        const float* A_values, gsb_run_state** out, void* stream);
+
+/* Normalised distance of Eq. 8 between the twins of every pair at the run's
+ * current step: delta = sqrt(sum_i (x^(1)_i - x^(2)_i)^2 / (4N)), summed in FP64
+ * in a fixed order. delta_out: host, nA R doubles in pair order. GSB_EINVAL for
+ * a run not made by gsb_twin_run. Blocks on the run's stream. */
+gsb_status gsb_twin_delta(gsb_run_state* run, double* delta_out);
+
 /* Gradient of the relaxed energy E = -1/2 x(t_W)^T J x(t_W) (Eq. 1 with the
  * continuous positions; not in the paper) after the first `window` steps of an
  * M-step run started from x(0) = x0, y(0) = 0, p(0) = 1, with respect to x0,

@@ -299,6 +299,7 @@ void free_run(gsb_run_state* r) {
     cudaFree(r->y);
     cudaFree(r->p);
     cudaFree(r->A);
+    cudaFree(r->twin_part);
     cudaFree(r->sched);
     cudaFree(r->e_acc);
     cudaFree(r->best_e);

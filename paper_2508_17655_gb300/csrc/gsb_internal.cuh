@@ -87,6 +87,9 @@ struct gsb_run_state {
     float* p = nullptr;       // individual parameters (GbSB / GdSB)
     int8_t* s8[2] = {nullptr, nullptr};  // sgn x for the CSR sgn coupling
     float* A = nullptr;       // [Rp]
+    // twin runs (Sec. IV): pair q runs as replicas q and twin_pairs + q
+    int twin_pairs = 0;
+    double* twin_part = nullptr;  // partial sums of Eq. 8, [chunks][twin_pairs] + [twin_pairs]
     float* sched = nullptr;   // [M+1] or null
     // tcgen05 operands, replica-major [Rp][Np] (K-major B operand)
     uint8_t* v8[2] = {nullptr, nullptr};

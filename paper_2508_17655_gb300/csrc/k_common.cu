@@ -53,6 +53,32 @@ __global__ void k_init_state(float* __restrict__ x, float* __restrict__ y, float
     if (p) p[o] = 1.f;
 }
 
+// Twin initial conditions of the chaos measure (Sec. IV): pair q = 0..Q-1 runs as
+// replicas q and Q + q. x^(1)_i = +-0.1 and x^(2)_i = x^(1)_i +- 2e-6, each sign
+// drawn independently (Philox streams 2 and 3 at counter (i, q, stream, 0); a
+// draw >= 0 gives +); x^(2) is the FP64 sum rounded once to FP32. y = 0, p = 1.
+__global__ void k_twin_init(float* __restrict__ x, float* __restrict__ y, float* __restrict__ p,
+                            int N, int Q, int Np, int Rp, uint2 key) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (r >= Rp || i >= Np) return;
+    const size_t o = (size_t)i * Rp + r;
+    float xv = 0.f;
+    if (i < N && r < 2 * Q) {
+        const int q = r < Q ? r : r - Q;
+        const double x1 = uniform_draw(i, q, 2u, key, 1.f) >= 0.f ? 0.1 : -0.1;
+        if (r < Q) {
+            xv = __double2float_rn(x1);
+        } else {
+            const double e = uniform_draw(i, q, 3u, key, 1.f) >= 0.f ? 2e-6 : -2e-6;
+            xv = __double2float_rn(x1 + e);
+        }
+    }
+    x[o] = xv;
+    y[o] = 0.f;
+    if (p) p[o] = 1.f;
+}
+
 __global__ void k_sign_extract(const float* __restrict__ x, int8_t* __restrict__ s, size_t n) {
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) s[k] = x[k] >= 0.f ? (int8_t)1 : (int8_t)-1;
@@ -97,10 +123,16 @@ gsb_status launch_init_state(gsb_run_state* run, const float* x0_rm, const float
     const float scale = range * 1.1920928955078125e-07f;  // times 2^-23, exact
     const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     dim3 grid((run->Rp + 127) / 128, run->Np);
-    k_init_state<<<grid, 128, 0, run->stream>>>(run->x[0], run->y, run->p, run->N, run->R,
-                                                run->Np, run->Rp, key, scale, P.y0_uniform,
-                                                x0_rm, y0_rm);
-    GSB_LAUNCH_CHECK("k_init_state");
+    if (run->twin_pairs > 0) {
+        k_twin_init<<<grid, 128, 0, run->stream>>>(run->x[0], run->y, run->p, run->N,
+                                                   run->twin_pairs, run->Np, run->Rp, key);
+        GSB_LAUNCH_CHECK("k_twin_init");
+    } else {
+        k_init_state<<<grid, 128, 0, run->stream>>>(run->x[0], run->y, run->p, run->N, run->R,
+                                                    run->Np, run->Rp, key, scale, P.y0_uniform,
+                                                    x0_rm, y0_rm);
+        GSB_LAUNCH_CHECK("k_init_state");
+    }
     run->cur = 0;
     if (run->s8[0]) return launch_sign_extract(run);
     return GSB_OK;

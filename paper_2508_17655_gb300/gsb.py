@@ -122,6 +122,11 @@ def _declare(L):
                                ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.c_int32,
                                ctypes.POINTER(ctypes.c_double), _vp]
     L.gsb_lyapunov.restype = st
+    L.gsb_twin_run.argtypes = [_vp, ctypes.POINTER(gsb_params), ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp), _vp]
+    L.gsb_twin_run.restype = st
+    L.gsb_twin_delta.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    L.gsb_twin_delta.restype = st
     L.gsb_relaxed_energy_grad.argtypes = [_vp, ctypes.POINTER(gsb_params), ctypes.c_int32,
                                           ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gsb_relaxed_energy_grad.restype = st
@@ -301,6 +306,36 @@ class Problem:
                                   _stream_handle(stream)))
         return out.reshape(len(A), int(R))
 
+    def twin_run(self, variant, M, R, A_values, *, c=0.0, dt=0.0, seed=0, precision="auto",
+                 eval_every=0, schedule=None, steps_per_launch=0, defer=True, profile=False,
+                 stream=None):
+        """Twin trajectories of Sec. IV (gsb_twin_run): len(A_values) x R pairs,
+        deferred by default; advance with .steps(n), read Eq. 8 with .delta()."""
+        return TwinRun(self, variant, M, R, A_values, c=c, dt=dt, seed=seed,
+                       precision=precision, eval_every=eval_every, schedule=schedule,
+                       steps_per_launch=steps_per_launch, defer=defer, profile=profile,
+                       stream=stream)
+
+    def twin_delta(self, variant, M, R, A_values, *, record_every=0, stream=None, **kw):
+        """delta(t_m) of Eq. 8 for len(A_values) x R twin pairs at m =
+        record_every, 2 record_every, ..., M (record_every = 0: t_M only).
+        Returns (steps, array n_records x len(A_values) x R)."""
+        M = int(M)
+        k = M if record_every <= 0 else int(record_every)
+        marks = list(range(k, M, k)) + [M]
+        tw = self.twin_run(variant, M, R, A_values, stream=stream, **kw)
+        try:
+            out = []
+            done = 0
+            for m in marks:
+                tw.steps(m - done)
+                done = m
+                out.append(tw.delta())
+        finally:
+            tw.close()
+        nA = len(np.atleast_1d(A_values))
+        return np.asarray(marks), np.stack(out).reshape(len(marks), nA, int(R))
+
     def relaxed_energy_grad(self, variant, M, window, x0_ptr, R, A, dt, c, energy_ptr,
                             grad_x0_ptr=None, grad_A_ptr=None, grad_dt_ptr=None,
                             ckpt_every=20, stream=None):
@@ -434,6 +469,39 @@ class Run:
             self.close()
         except Exception:
             pass
+
+
+class TwinRun(Run):
+    """Twin trajectories of Sec. IV (gsb_twin_run): len(A_values) x R pairs;
+    replica a R + r is trajectory (1) of pair (a, r), replica
+    len(A_values) R + a R + r its trajectory (2)."""
+
+    def __init__(self, problem, variant, M, R, A_values, *, c, dt, seed, precision, eval_every,
+                 schedule, steps_per_launch, defer, profile, stream):
+        self.problem = problem
+        A = np.ascontiguousarray(np.atleast_1d(A_values), dtype=np.float32)
+        self.pairs = len(A) * int(R)
+        self.R = 2 * self.pairs
+        self.N = problem.N
+        prm = _make_params(variant, M, R, c=c, dt=dt, seed=seed, precision=precision,
+                           eval_every=eval_every)
+        keep = None
+        if schedule is not None:
+            keep = np.ascontiguousarray(schedule, dtype=np.float32)
+            prm.schedule = _p(keep, ctypes.c_float)
+        prm.steps_per_launch = int(steps_per_launch)
+        prm.flags = (RUN_DEFER if defer else 0) | (RUN_PROFILE if profile else 0)
+        out = _vp()
+        _check(lib().gsb_twin_run(problem.handle, ctypes.byref(prm), len(A),
+                                  _p(A, ctypes.c_float), ctypes.byref(out),
+                                  _stream_handle(stream)))
+        self.handle = out
+
+    def delta(self):
+        """Eq. 8 for every pair at the current step (host, FP64)."""
+        out = np.zeros(self.pairs, dtype=np.float64)
+        _check(lib().gsb_twin_delta(self.handle, _p(out, ctypes.c_double)))
+        return out
 
 
 _BatchRun.best = Run.best

@@ -401,6 +401,27 @@ def test_twin_distance_values():
     assert abs(O.twin_delta(a, b)[0] - vals["twin_delta_chaos"]) < 5e-3
 
 
+def test_twin_regular_without_control_chaotic_with_it():
+    """Sec. IV: without the control of Eq. 7 (A = 0) the twins end together,
+    delta(t_M) ~ 0 (regular dynamics); a strong control (A = 1) drives them
+    apart, delta(t_M) of order 1/sqrt 2 (chaos). N = 200 SK, c = 1/lambda_max,
+    dt = 1.25, M = 1000, 40 pairs each. A dropped control term, a wrong sign in
+    Eq. 7 or twins that share one trajectory each break one of the two."""
+    N, R, M = 200, 40, 1000
+    J = I.sk_pm1(N, 0).astype(np.float64)
+    lmax, _ = O.lambda_extremes(O.as_coupling(J))
+    x1, x2 = O.twin_initial(R, N, seed=12)
+    x = np.vstack([x1, x2])
+    means = []
+    for A in (0.0, 1.0):
+        r = O.run(J, "gbsb", x, 0 * x, c=1 / lmax, dt=1.25, M=M, A=A)
+        d = O.twin_delta(r["x"][:R], r["x"][R:])
+        assert np.all(d <= 1.0)
+        means.append(float(d.mean()))
+    assert means[0] < 1e-3
+    assert means[1] > 0.3
+
+
 # ---------------------------------------------------------------- tangent-linear
 
 @pytest.mark.parametrize("variant", ["gbsb", "bsb", "gdsb", "dsb"])
