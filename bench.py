@@ -327,7 +327,7 @@ def success_report(energies, A, runs, E_target, run_ms):
     that strength: P_batch = 1 - (1 - P_S)^128, TTS = T log(0.01)/log(1 - P_batch)
     (Sec. VI), T = run time (all 8 strengths share one run)."""
     import numpy as np
-    import oracle as O
+    from paper_2508_17655_gb300 import stats
     rep = {"target_E": E_target, "runs": runs}
     if E_target is None:
         rep["note"] = "no target file"
@@ -339,9 +339,9 @@ def success_report(energies, A, runs, E_target, run_ms):
         k = int(np.sum(e <= E_target + 1e-9))
         n = len(e)
         ps = k / n
-        lo, hi = O.clopper_pearson(k, n, 0.99)
-        pb = 1.0 - (1.0 - ps) ** (R_REPLICAS // len(A_VALUES))
-        tts = O.tts(pb, run_ms / 1e3)
+        lo, hi = stats.binomial_interval(k, n, 0.99)
+        pb = stats.batch_success(ps, R_REPLICAS // len(A_VALUES))
+        tts = stats.time_to_solution(pb, run_ms / 1e3)
         per.append({"A": a, "P_S": ps, "P_S_ci99": [lo, hi], "n": n,
                     "mean_E": float(np.mean(e)), "min_E": float(np.min(e)),
                     "TTS99_s": tts if math.isfinite(tts) else None})
@@ -369,7 +369,6 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
     warm-up), with the dominant kernel's roofline from CUDA events. only:
     the name of a single leg to run; leg_M: a shorter step count for the
     sparse and FX32 legs (profiling)."""
-    import oracle as O
     out = {}
     hbm = Pk["hbm_gbs"]
     fp32_peak = fp32_alu_peak(Pk)
@@ -379,11 +378,11 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         if not want(f"sparse_N{N}"):
             continue
         rp, col, val = I.er_graph(N, 20, "+1", 5)
-        lmax, lmin = O.lambda_extremes(O.Coupling(N, rowptr=rp, col=col, val=val), iters=4000,
-                                       tol=1e-10)
         P = gsb.Problem.csr(N, rp, col, val, stream=stream.cuda_stream)
         R, M = 512, leg_M or 5000
-        run = P.run("gbsb", M=M, R=R, c=1 / lmax, dt=O.dt_from_lambda(lmax, lmin), A=0.2, seed=1,
+        # c = 1/lambda_max and dt from Eq. 13, with the extreme eigenvalues found
+        # by the library's power iteration on the GPU (App. A)
+        run = P.run("gbsb", M=M, R=R, c=0.0, dt=0.0, A=0.2, seed=1,
                     defer=True, profile=True, stream=stream.cuda_stream)
         run.restart(2)
         e0, e1 = _events(torch, stream)
@@ -502,7 +501,7 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
     J5 = I.sk_gauss(2000, 0)
     P5 = gsb.Problem.dense(J5, stream=stream.cuda_stream)
     if not want("lyapunov"):
-        return adjoint_leg(gsb, O, np, torch, stream, P5, out, fp32_peak)
+        return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak)
     A16 = [0.025 * k for k in range(16)]
     steps = 200
     P5.lyapunov("gbsb", 2000, 256, A16, c=0.5, dt=1.25, renorm_every=10, nsteps=20)
@@ -521,14 +520,14 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
     if only == "lyapunov":
         P5.close()
         return out
-    return adjoint_leg(gsb, O, np, torch, stream, P5, out, fp32_peak)
+    return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak)
 
 
-def adjoint_leg(gsb, O, np, torch, stream, P5, out, fp32_peak):
+def adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak):
     """Adjoint gradient: N = 2000 SK (the problem P5), R = 256, 200-step
     window, checkpoints every 20; closes P5."""
     R5, W = 256, 200
-    x0 = torch.from_numpy(O.init_uniform(R5, 2000, 1).astype(np.float32)).cuda()
+    x0 = torch.from_numpy(I.uniform_state(R5, 2000, 1)).cuda()
     E = torch.empty(R5, dtype=torch.float64, device="cuda")
     gx = torch.empty_like(x0)
     gA = torch.empty(R5, dtype=torch.float64, device="cuda")

@@ -10,6 +10,8 @@ the tests, the benchmark and the oracle all take their couplings from here.
   +-1 edge weights W, stored as J = -W in CSR (G-set-like sparse Max-Cut,
   Sec. III: J in {0, -1} or {0, +-1}).
 * ``ring`` / ``complete``: graphs whose maximum cut is known in closed form.
+* ``batch_sizes``: sizes of a batch of uneven instances.
+* ``uniform_state``: an explicit initial state, uniform in [-0.1, 0.1).
 """
 from __future__ import annotations
 
@@ -119,3 +121,10 @@ def batch_sizes(n: int, seed: int = 0, nmin: int = 64, nmax: int = 1024,
     Ns = rng.integers(nmin, nmax + 1, size=n)
     Rs = rng.integers(rmin, rmax + 1, size=n)
     return Ns.astype(np.int64), Rs.astype(np.int64)
+
+
+def uniform_state(R: int, N: int, seed: int = 0, rng: float = 0.1) -> np.ndarray:
+    """R x N float32 positions drawn i.i.d. uniform in [-rng, rng) (the range of
+    x(0), App. A), for callers that hand the library an explicit initial state."""
+    g = np.random.default_rng(seed)
+    return g.uniform(-rng, rng, size=(R, N)).astype(np.float32)
