@@ -239,6 +239,25 @@ def test_best_state_bookkeeping_is_exact(path):
     assert np.all((b["step"] % 7 == 0) | (b["step"] == M))
 
 
+@pytest.mark.parametrize("variant,kernel", [("gdsb", "k_tc_persist"), ("gbsb", "k_fx32_step")])
+def test_best_state_bookkeeping_full_size(variant, kernel):
+    """The timed configuration itself (N = 2000 +-1 complete graph, R = 1024 in
+    8 control strengths x 128, M = 2000, dt = 1.25, c = 1/(2 sqrt N)) on the
+    tensor-core path the bench runs: every reported energy is the exact energy
+    of the reported spins, every cut (W_tot - E)/2, found at t_M."""
+    N, R, M = 2000, 1024, 2000
+    J = I.sk_pm1(N, 0)
+    Jo = J.astype(np.float64)
+    A = np.repeat(np.float32([0.0, 0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35]), 128)
+    run = gsb.Problem.dense(J).run(variant, M=M, R=R, c=f32(1 / (2 * math.sqrt(N))), dt=1.25,
+                                   A=A, seed=1)
+    assert run.kernel().startswith(kernel)
+    b = run.best()
+    np.testing.assert_array_equal(b["E"], O.energy(Jo, b["s"]))
+    np.testing.assert_array_equal(b["cut"], (O.total_weight(Jo) - b["E"]) / 2)
+    assert np.all(b["step"] == M)
+
+
 def test_short_run_best_matches_oracle_where_spins_agree():
     N, R, M = 300, 96, 40
     J = I.sk_pm1(N, 12)

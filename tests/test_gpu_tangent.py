@@ -61,6 +61,33 @@ def test_lyapunov_short_window_matches_oracle(variant):
     assert err.size == 0 or np.all(err <= 1e-4), f"max |mle gpu - oracle| {err.max():.2e}"
 
 
+def test_lyapunov_config5_shape_sampled():
+    """The chaos configuration as the bench runs it (N = 2000 SK Gaussian,
+    16 control strengths x 256 replicas in one call, c = 0.5, dt = 1.25,
+    M = 2000, renormalised every 10 steps), first 50 steps: 16 sampled replicas
+    (one per control strength) within 1e-4 of the oracle's exponent."""
+    N, R, M, n, renorm = 2000, 256, 2000, 50, 10
+    A16 = [0.025 * k for k in range(16)]
+    J = I.sk_gauss(N, 0)
+    c, dt = 0.5, f32(1.25)
+    got = gsb.Problem.dense(J).lyapunov("gbsb", M, R, A16, c=c, dt=dt, seed=3,
+                                        renorm_every=renorm, nsteps=n).ravel()
+    pick = np.array([k * R + (37 * k) % R for k in range(16)])
+    x0 = O.init_uniform(16 * R, N, 3)[pick]
+    dx0 = O.init_uniform(16 * R, N, 3, stream=4, rng=1.0)[pick]
+    dx0 /= np.linalg.norm(dx0, axis=1, keepdims=True)
+    A_rep = np.repeat(A16, R)[pick]
+    Jo = J.astype(np.float64)
+    t = O.tangent_run(Jo, "gbsb", x0, 0 * x0, dx0, c=c, dt=dt, M=M, A=A_rep, nsteps=n,
+                      renorm_every=renorm)
+    want = t["log_sum"] / (n * dt)
+    margin = O.run(Jo, "gbsb", x0, 0 * x0, c=c, dt=dt, M=M, A=A_rep, nsteps=n)["margin"]
+    ok = margin >= 2e-6
+    assert ok.sum() >= 12
+    err = np.abs(got[pick] - want)[ok]
+    assert np.all(err <= 1e-4), f"max |mle gpu - oracle| {err.max():.2e}"
+
+
 def test_lyapunov_unstable_equilibrium_growth_rate():
     """Near the x = 0 equilibrium of a ferromagnet (J = 1 - I) with p ~ 1, the
     uniform mode grows by mu per step, mu^2 - (2 - k dt^2) mu + 1 = 0,
