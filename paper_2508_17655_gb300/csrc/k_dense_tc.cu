@@ -555,7 +555,6 @@ __global__ void k_tc_prep(const float* __restrict__ x, void* __restrict__ v, int
 struct TcState {
     CUtensorMap tmA;
     CUtensorMap tmB[2];
-    CUtensorMap tmS[3];  // FX32: the x, y, p state as 128 x 128 FP32 boxes
     int vcur = 0;
     int kind = 0;
     bool persistent = false;     // a multi-step kernel runs this shape
@@ -595,24 +594,6 @@ gsb_status make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dtyp
     return GSB_OK;
 }
 
-// 2D map of a spin-major FP32 state array [Np][Rp]: inner dimension replicas,
-// box of 128 replicas (512 bytes) by 128 spins, no swizzle.
-gsb_status make_state_map(CUtensorMap* map, const float* base, int Np, int Rp) {
-    auto encode = get_encode();
-    if (!encode) return set_error(GSB_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    cuuint64_t dims[2] = {(cuuint64_t)Rp, (cuuint64_t)Np};
-    cuuint64_t strides[1] = {(cuuint64_t)Rp * 4u};
-    cuuint32_t box[2] = {(cuuint32_t)BN, (cuuint32_t)BM};
-    cuuint32_t estr[2] = {1u, 1u};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-        return set_error(GSB_ECUDA, "cuTensorMapEncodeTiled (state) failed: " + std::to_string((int)r));
-    return GSB_OK;
-}
-
 // ---------------------------------------------------------------------------
 // FX32 step (one step per launch), with the tile transposed as in k_tc_persist:
 // digit plane q of V (x as rint(x 2^30) in four base-256 digits) is the A
@@ -622,26 +603,17 @@ gsb_status make_state_map(CUtensorMap* map, const float* base, int Np, int Rp) {
 // control strength in a register, and writes the next step's four digit
 // planes 32 contiguous bytes at a time. The digit sums are exact integers, so
 // f is the same as k_tc_step<1>'s in any order.
-// The tile's state arrives by TMA, as 128 spins x 128 replicas FP32 boxes: y
-// into its own buffer while the K loop runs, x (and p) into the ring once the
-// last MMA is done; the epilogue reads it from shared memory, so no thread
-// waits on an L2 round trip per element.
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2-9 epilogue (warp w: TMEM
 // lanes 32 (w % 4).., spins 64 ((w - 2) / 4) .. +63 of the tile).
 constexpr int kThreadsF = 320;
 constexpr int kStagesF = 2;
-constexpr int kRingF = kStagesF * (4 * BN * KB + BM * KB);
-constexpr int kStateTileF = BM * BN * 4;  // one FP32 state box
 __host__ __device__ constexpr int smem_bytes_fx32() {
-    return 1024 + kRingF + kStateTileF + 256;
+    return 1024 + kStagesF * (4 * BN * KB + BM * KB) + 256;
 }
-static_assert(kRingF >= 2 * kStateTileF, "x and p reuse the ring");
 
 template <bool CONTROL>
 __global__ void __launch_bounds__(kThreadsF, 1)
     k_fx32_step(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmV,
-                const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-                const __grid_constant__ CUtensorMap tmP,
                 int Np, int Rp, float* __restrict__ x, float* __restrict__ y,
                 float* __restrict__ p, const float* __restrict__ A,
                 __nv_bfloat16* __restrict__ vnext, float c, float dt, float p_shared,
@@ -653,15 +625,10 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sV = smem;
     uint8_t* sJ = smem + S * SV;
-    // state boxes [spin][replica]: x and p over the ring after the K loop, y apart
-    const float* sX = reinterpret_cast<const float*>(smem);
-    const float* sP = reinterpret_cast<const float*>(smem + kStateTileF);
-    float* sY = reinterpret_cast<float*>(smem + kRingF);
-    uint64_t* full = (uint64_t*)(smem + kRingF + kStateTileF);
+    uint64_t* full = (uint64_t*)(sJ + S * SJ);
     uint64_t* empty = full + S;
     uint64_t* accf = empty + S;
-    uint64_t* sbar = accf + 1;  // [2]: y landed; x (and p) landed
-    uint32_t* tmem_slot = (uint32_t*)(sbar + 2);
+    uint32_t* tmem_slot = (uint32_t*)(accf + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = blockIdx.x * BN, i0 = blockIdx.y * BM;
@@ -673,8 +640,6 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             mbar_init(&empty[st], 1);
         }
         mbar_init(accf, 1);
-        mbar_init(&sbar[0], 1);
-        mbar_init(&sbar[1], 1);
         fence_barrier_init();
         tma_prefetch_desc(&tmJ);
         tma_prefetch_desc(&tmV);
@@ -733,28 +698,24 @@ __global__ void __launch_bounds__(kThreadsF, 1)
         const float a_r = CONTROL ? A[r] : 0.f;
         const size_t plane = (size_t)Rp * Np;
         __nv_bfloat16* vrow = vnext + (size_t)r * Np + i0;
-        const int rl = quarter * 32 + lane;  // this thread's replica in the tile
-        const bool leader = ew == 0 && lane == 0;
-        // y does not wait for the MMAs: its buffer is not part of the ring
-        if (leader) {
-            mbar_arrive_expect_tx(&sbar[0], kStateTileF);
-            tma_load_2d(sY, &tmY, &sbar[0], r0, i0);
-        }
+        // Chunks of 8 spins; the state of the next chunk is loaded while this one
+        // is processed (the first before the accumulator is ready), so the L2
+        // latency of the loads overlaps work.
+        constexpr int CW = 8;
+        float xn[CW], yn[CW], pn[CW];
+        auto load_state = [&](int cb) {
+            const size_t o = (size_t)(i0 + cb) * Rp + r;
+#pragma unroll
+            for (int k = 0; k < CW; ++k) {
+                xn[k] = x[o + (size_t)k * Rp];
+                yn[k] = y[o + (size_t)k * Rp];
+                pn[k] = CONTROL ? p[o + (size_t)k * Rp] : 0.f;
+            }
+        };
+        load_state(c0);
         // tcgen05.ld is warp-collective: proceed only if every lane saw the accumulator
         const bool ready = __all_sync(0xffffffffu, mbar_wait(accf, 0, status));
-        // the last MMA has read the ring: x and p may overwrite it
-        if (ready && leader) {
-            mbar_arrive_expect_tx(&sbar[1], CONTROL ? 2 * kStateTileF : kStateTileF);
-            tma_load_2d(smem, &tmX, &sbar[1], r0, i0);
-            if (CONTROL) tma_load_2d(smem + kStateTileF, &tmP, &sbar[1], r0, i0);
-        }
-        // every started copy lands before the CTA may exit (bounded waits)
-        bool landed = __all_sync(0xffffffffu, mbar_wait(&sbar[0], 0, status));
-        if (ready) landed = __all_sync(0xffffffffu, mbar_wait(&sbar[1], 0, status)) && landed;
-        // Chunks of 8 spins, the state read from the boxes in shared memory
-        // (row = spin, a warp's 32 replicas contiguous: one wavefront a row).
-        constexpr int CW = 8;
-        if (ready && landed) {
+        if (ready) {
             fence_after_sync();
 #pragma unroll 1
             for (int cb = c0; cb < c0 + 64; cb += CW) {
@@ -765,11 +726,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
                 tmem_ld8_async(tl + 3 * BN + cb, d3);
                 float xs[CW], ys[CW], ps[CW];
 #pragma unroll
-                for (int k = 0; k < CW; ++k) {
-                    xs[k] = sX[(cb + k) * BN + rl];
-                    ys[k] = sY[(cb + k) * BN + rl];
-                    ps[k] = CONTROL ? sP[(cb + k) * BN + rl] : 0.f;
-                }
+                for (int k = 0; k < CW; ++k) xs[k] = xn[k], ys[k] = yn[k], ps[k] = pn[k];
+                if (cb + CW < c0 + 64) load_state(cb + CW);
                 tmem_wait_ld8(d0);
                 tmem_wait_ld8(d1);
                 tmem_wait_ld8(d2);
@@ -832,8 +790,7 @@ gsb_status launch_step(gsb_run_state* run, TcState* T, float p_shared, float inv
             attr_set = true;
         }
         k_fx32_step<CONTROL><<<grid, kThreadsF, smem_bytes_fx32(), run->stream>>>(
-            T->tmA, T->tmB[T->vcur], T->tmS[0], T->tmS[1], T->tmS[CONTROL ? 2 : 0], run->Np,
-            run->Rp, run->x[0], run->y, run->p, run->A,
+            T->tmA, T->tmB[T->vcur], run->Np, run->Rp, run->x[0], run->y, run->p, run->A,
             run->v16[T->vcur ^ 1], run->c, run->dt, p_shared, inv_rem, run->status);
         GSB_LAUNCH_CHECK("k_fx32_step");
     } else {
@@ -901,9 +858,6 @@ gsb_status tc_setup(gsb_run_state* run) {
             if ((st = make_map(&T->tmB[b], run->v16[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                                run->Np, 4 * (uint64_t)run->Rp)))
                 return st;
-        const float* state[3] = {run->x[0], run->y, run->p};
-        for (int k = 0; k < 3; ++k)
-            if (state[k] && (st = make_state_map(&T->tmS[k], state[k], run->Np, run->Rp))) return st;
     }
     if (T->kind == 0 && run->params.steps_per_launch != 1) {
         // Two multi-step forms. The cluster form (one cluster of Np/128 CTAs per
