@@ -47,6 +47,15 @@ __host__ __device__ constexpr int smem_bytes_step() {
 
 __device__ __forceinline__ uint8_t e4m3_sign(float x) { return x >= 0.f ? 0x38 : 0xB8; }  // +-1.0
 
+// bf16 bits of the integer n - 128 for 0 <= n <= 255, without a conversion
+// instruction: the float with exponent 2^23 and n in its mantissa is 2^23 + n;
+// subtracting 2^23 + 128 leaves n - 128 exactly, whose at most 8 significant
+// bits make its top 16 bits its bf16 encoding.
+__device__ __forceinline__ uint16_t small_int_bf16(int n) {
+    const float f = __int_as_float(0x4B000000 | n) - 8388736.0f;  // 2^23 + 128
+    return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
 // x as four signed base-256 digits of q = rint(x 2^30), |x| <= 1:
 // q = d0 + 256 d1 + 65536 d2 + 16777216 d3, d0..d2 in [-128, 127], |d3| <= 64.
 // x 2^30 is exact in FP32 (a power-of-two scaling), so q = x 2^30 exactly
@@ -56,9 +65,8 @@ __device__ __forceinline__ uint8_t e4m3_sign(float x) { return x >= 0.f ? 0x38 :
 __device__ __forceinline__ void fx32_digit_bits(float x, uint16_t (&d)[4]) {
     const int u = __float2int_rn(x * 1073741824.0f) + 0x808080;
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-        d[k] = __bfloat16_as_ushort(__int2bfloat16_rn((int)((u >> (8 * k)) & 255) - 128));
-    d[3] = __bfloat16_as_ushort(__int2bfloat16_rn(u >> 24));
+    for (int k = 0; k < 3; ++k) d[k] = small_int_bf16((u >> (8 * k)) & 255);
+    d[3] = small_int_bf16((u >> 24) + 128);  // the top digit, in [-64, 64]
 }
 
 // f = 2^-30 sum_k 256^k D_k, from exact integer accumulators (|D_k| < 2^24,
