@@ -15,7 +15,7 @@
  * order). Replicas are independent, so an OpenMP loop over replicas is the only
  * parallelism.
  *
- * Readings of points the paper leaves open (each is also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - Eq. 5 writes t_{k+1}; it is read as t_{m+1}.
  *   - The wall test is strict: |x| > 1. |x| == 1 keeps y.
  *   - sgn(0) = +1, for spins and for the dSB coupling.
@@ -30,7 +30,7 @@
  *     eval_every, and always at m+1 == M; strict improvement, so the earliest
  *     step wins a tie.
  *
- * Parity status per function:
+ * Parity status per function (what pins each one):
  *   orc_philox4x32_10 .... pinned (published known-answer vectors)
  *   orc_init_uniform ..... pinned (range, symmetry of the integer map)
  *   orc_energy_* / cut ... pinned (cut identity, closed-form graphs, brute force)
