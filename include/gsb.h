@@ -279,6 +279,18 @@ gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems, const gsb_para
 gsb_status gsb_energy_noalloc(const float* J, int32_t N, const int8_t* spins, int32_t R,
                               double* energies, void* stream);
 
+/* Check of the device-side failure detection (not in the paper). Every wait of
+ * the library's kernels (on an mbarrier, a counter another CTA advances, a
+ * barrier of a thread-block cluster) gives up after a time limit, sets a
+ * status word and lets the kernel return, so a lost arrival ends the call with
+ * GSB_ETIMEOUT instead of hanging the GPU. This entry runs one such wait, with
+ * limit_ns (1 us .. 10 s) of device time, in a one-warp kernel on `stream`:
+ * kind 0 waits on an mbarrier nobody arrives on, kind 1 on a counter in global
+ * memory nobody advances -- both return GSB_ETIMEOUT after about limit_ns --
+ * and kind 2 on a counter that already holds (GSB_OK at once). The CUDA
+ * context stays usable afterwards. Blocks on `stream`. */
+gsb_status gsb_wait_check(int32_t kind, int64_t limit_ns, void* stream);
+
 /* Message for the last non-OK status returned on the calling thread. */
 const char* gsb_last_error(void);
 

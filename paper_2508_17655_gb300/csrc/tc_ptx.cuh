@@ -7,8 +7,32 @@
 namespace gsb {
 namespace tc {
 
-// Every spin-wait gives up after this many polls and reports a timeout.
-constexpr uint32_t kSpinLimit = 1u << 26;
+// Every device-side wait gives up after this much %globaltimer time (ns) and
+// reports a timeout in the status word; no wait of a correct run comes near it.
+constexpr uint64_t kWaitLimitNs = 4000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Poll until poll() holds or limit_ns have passed; on expiry set the timeout
+// bit (1) in *status and return false. The first poll is free of timer reads.
+template <typename Poll>
+__device__ __forceinline__ bool bounded_wait(Poll poll, int* status, uint64_t limit_ns) {
+    if (poll()) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (poll()) return true;
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(status, 1);
+            return false;
+        }
+    }
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -43,12 +67,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait for the phase with the given parity; false (and the timeout
-// bit in *status) if it did not complete within kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    atomicOr(status, 1);
-    return false;
+// bit in *status) if it did not complete within limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status,
+                                          uint64_t limit_ns = kWaitLimitNs) {
+    return bounded_wait([&] { return mbar_try_wait(bar, parity); }, status, limit_ns);
 }
 
 // Wait on a barrier that other CTAs of the cluster arrive on: acquire at
@@ -64,11 +86,9 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* status) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait_cluster(bar, parity)) return true;
-    atomicOr(status, 1);
-    return false;
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* status,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
+    return bounded_wait([&] { return mbar_try_wait_cluster(bar, parity); }, status, limit_ns);
 }
 // Arrive (release at cluster scope) on the barrier at the offset of bar in the
 // shared memory of the cluster's CTA with rank cta.
@@ -268,11 +288,9 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async;" ::: "memory");
 }
 // Bounded wait until *addr >= target; false (timeout bit in *status) on expiry.
-__device__ __forceinline__ bool wait_counter(const uint32_t* addr, uint32_t target, int* status) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
-        if (ld_acquire(addr) >= target) return true;
-    atomicOr(status, 1);
-    return false;
+__device__ __forceinline__ bool wait_counter(const uint32_t* addr, uint32_t target, int* status,
+                                             uint64_t limit_ns = kWaitLimitNs) {
+    return bounded_wait([&] { return ld_acquire(addr) >= target; }, status, limit_ns);
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA

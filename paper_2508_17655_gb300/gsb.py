@@ -137,6 +137,8 @@ def _declare(L):
     L.gsb_energy_noalloc.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
     L.gsb_run_destroy.restype = st
+    L.gsb_wait_check.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp]
+    L.gsb_wait_check.restype = st
     L.gsb_last_error.argtypes = []
     L.gsb_last_error.restype = ctypes.c_char_p
     L.gsb_version.restype = ctypes.c_int32
@@ -160,6 +162,13 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def wait_check(kind, limit_ns, stream=None):
+    """gsb_wait_check: one bounded device-side wait (0: mbarrier, 1: counter,
+    both never satisfied; 2: a counter already at its target). Raises GsbError
+    with status ETIMEOUT when the wait gives up."""
+    _check(lib().gsb_wait_check(int(kind), int(limit_ns), _stream_handle(stream)))
 
 
 def launch_count():
