@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* full = (uint64_t*)(sB + S * SB);
     uint64_t* empty = full + S;
     uint64_t* accf = empty + S;
-    uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+    uint64_t* drain = accf + 1;  // the MMA issuer's last commit (all its MMAs done)
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(accf, 1);
+        mbar_init(drain, 1);
         fence_barrier_init();
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
@@ -124,6 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
+            int armed = 0;
             for (int kc = 0; kc < nk; ++kc) {
                 const int s = kc % S;
                 const uint32_t ph = (uint32_t)(kc / S) & 1u;
@@ -131,7 +134,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_arrive_expect_tx(&full[s], SA + SB);
                 tma_load_2d(sA + s * SA, &tmA, &full[s], kc * KB, i0);
                 tma_load_2d(sB + s * SB, &tmB, &full[s], kc * KB, r0);
+                armed = kc + 1;
             }
+            // no copy in flight when the CTA leaves
+            for (int kc = armed > S ? armed - S : 0; kc < armed; ++kc)
+                mbar_wait(&full[kc % S], (uint32_t)(kc / S) & 1u, status, kDrainLimitNs);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -154,6 +161,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mma_commit(&empty[s]);
             }
             if (ok) mma_commit(accf);
+            // every MMA issued has finished before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0, status, kDrainLimitNs);
         }
     } else {
         // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31
@@ -278,7 +288,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     uint64_t* accf = empty + S;
     uint64_t* acce = accf + 1;
     uint64_t* vready = acce + 1;  // [2]: the column's V of a step, one arrival per writer
-    uint32_t* tmem_slot = (uint32_t*)(vready + 2);
+    uint64_t* drain = vready + 2;  // the MMA issuer's last commit (all its MMAs done)
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = Np / KB;                       // K atoms per step == spin blocks
@@ -300,6 +311,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         mbar_init(acce, 1);
         mbar_init(&vready[0], (uint32_t)nk);
         mbar_init(&vready[1], (uint32_t)nk);
+        mbar_init(drain, 1);
         tmem_slot[1] = 0u;  // epilogue abort flag
         fence_barrier_init();
         tma_prefetch_desc(&tmA);
@@ -332,36 +344,51 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     tma_load_2d(sB + st * SB + a * SB1, tv, &full[st], atom(u * kAtomsP + a) * KB,
                                 r0);
             };
+            uint32_t armed = 0;  // ring positions whose full barrier has been armed
             for (int s = 0; s < nsteps && ok; ++s) {
                 const CUtensorMap* tv = ((m0 + s) & 1) ? &tmV1 : &tmV0;
                 // J for the first ring stages: independent of the other CTAs
-                for (int u = 0; u < pre && ok; ++u) {
+                int nj = 0;
+                for (int u = 0; u < pre; ++u) {
                     const uint32_t gg = g + u, st = gg % S, ph = (gg / S) & 1u;
-                    if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) ok = false;
-                    if (!ok) break;
+                    if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) {
+                        ok = false;
+                        break;
+                    }
                     load_j(u, st);
+                    armed = gg + 1;
+                    ++nj;
                 }
-                if (!ok) break;
                 // V of this step is complete once every CTA of the replica block
                 // published it: all nk arrivals on this step's barrier (cluster
                 // form), or the counter at nk per step (grid form)
-                if (s > 0) {
-                    if (CLUSTER ? !mbar_wait_cluster(&vready[(s - 1) & 1],
+                if (ok && s > 0) {
+                    ok = CLUSTER ? mbar_wait_cluster(&vready[(s - 1) & 1],
                                                      (uint32_t)((s - 1) >> 1) & 1u, status)
-                                : !wait_counter(ctr, (uint32_t)nk * (uint32_t)s, status))
-                        break;
-                    fence_proxy_async();
+                                 : wait_counter(ctr, (uint32_t)nk * (uint32_t)s, status);
+                    if (ok) fence_proxy_async();
                 }
-                for (int u = 0; u < pre; ++u) load_v(u, (g + u) % S, tv);
-                for (int u = pre; u < ns && ok; ++u) {
+                // V of the stages whose J is out -- after a failed wait too, so that
+                // every armed barrier completes its phase (the step's results are
+                // void then; the status word says so)
+                for (int u = 0; u < nj; ++u) load_v(u, (g + u) % S, tv);
+                if (!ok) break;
+                for (int u = pre; u < ns; ++u) {
                     const uint32_t gg = g + u, st = gg % S, ph = (gg / S) & 1u;
-                    if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) ok = false;
-                    if (!ok) break;
+                    if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) {
+                        ok = false;
+                        break;
+                    }
                     load_j(u, st);
                     load_v(u, st, tv);
+                    armed = gg + 1;
                 }
                 g += ns;
             }
+            // no copy is in flight when the CTA leaves: the last phase armed on
+            // every stage has landed
+            for (uint32_t gg = armed > (uint32_t)S ? armed - S : 0u; gg < armed; ++gg)
+                mbar_wait(&full[gg % S], (gg / S) & 1u, status, kDrainLimitNs);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -391,6 +418,9 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                 }
                 if (ok) mma_commit(accf);
             }
+            // every MMA issued has finished before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0, status, kDrainLimitNs);
         }
     } else {
         const int ew = warp - 2;
@@ -636,7 +666,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     uint64_t* full = (uint64_t*)(sJ + S * SJ);
     uint64_t* empty = full + S;
     uint64_t* accf = empty + S;
-    uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+    uint64_t* drain = accf + 1;  // the MMA issuer's last commit (all its MMAs done)
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = blockIdx.x * BN, i0 = blockIdx.y * BM;
@@ -648,6 +679,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             mbar_init(&empty[st], 1);
         }
         mbar_init(accf, 1);
+        mbar_init(drain, 1);
         fence_barrier_init();
         tma_prefetch_desc(&tmJ);
         tma_prefetch_desc(&tmV);
@@ -660,6 +692,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 
     if (warp == 0) {
         if (lane == 0) {
+            int armed = 0;
             for (int kc = 0; kc < nk; ++kc) {
                 const int st = kc % S;
                 const uint32_t ph = (uint32_t)(kc / S) & 1u;
@@ -669,7 +702,11 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     tma_load_2d(sV + st * SV + q * SV1, &tmV, &full[st], kc * kElems, q * Rp + r0);
+                armed = kc + 1;
             }
+            // no copy in flight when the CTA leaves
+            for (int kc = armed > S ? armed - S : 0; kc < armed; ++kc)
+                mbar_wait(&full[kc % S], (uint32_t)(kc / S) & 1u, status, kDrainLimitNs);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -696,6 +733,9 @@ __global__ void __launch_bounds__(kThreadsF, 1)
                 mma_commit(&empty[st]);
             }
             if (ok) mma_commit(accf);
+            // every MMA issued has finished before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0, status, kDrainLimitNs);
         }
     } else {
         const int ew = warp - 2;

@@ -10,6 +10,9 @@ namespace tc {
 // Every device-side wait gives up after this much %globaltimer time (ns) and
 // reports a timeout in the status word; no wait of a correct run comes near it.
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
+// Limit of the waits a CTA makes before it leaves, for its own copies and MMAs
+// to finish (they complete in microseconds once issued).
+constexpr uint64_t kDrainLimitNs = 200000000ull;
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
