@@ -553,15 +553,23 @@ def adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak):
 
 def e2e_leg(gsb, J, c, A, K):
     """Same metric through the public C ABI with host buffers: create the
-    problem from host J (int8), run, read best spins / energies / cuts back."""
+    problem from host J (int8, in pinned memory), run, read best spins /
+    energies / cuts back into pinned host arrays."""
     import numpy as np
+    import torch
+    Jh = torch.empty(J.shape, dtype=torch.int8, pin_memory=True).numpy()
+    Jh[...] = J
+    out = {"s": torch.empty((R_REPLICAS, N_SPINS), dtype=torch.int8, pin_memory=True).numpy(),
+           "E": torch.empty(R_REPLICAS, dtype=torch.float64, pin_memory=True).numpy(),
+           "cut": torch.empty(R_REPLICAS, dtype=torch.float64, pin_memory=True).numpy(),
+           "step": torch.empty(R_REPLICAS, dtype=torch.int32, pin_memory=True).numpy()}
     times = []
     for k in range(K):
         t = time.perf_counter()
-        P = gsb.Problem.dense(J)
+        P = gsb.Problem.dense(Jh)
         run = P.run("gdsb", M=M_STEPS, R=R_REPLICAS, c=c, dt=DT, A=A, seed=5000 + k,
                     precision="fp8")
-        b = run.best()
+        b = run.best(out=out)
         run.close()
         P.close()
         times.append(time.perf_counter() - t)

@@ -171,7 +171,9 @@ const char* gsb_run_kernel(const gsb_run_state* run);
 /* Best state per replica (host outputs, each nullable): spins R x N int8,
  * energies (Eq. 1), cut values (W_tot - E)/2 with W = -J (Sec. III), and the
  * step m at which it was found. Blocks on the run's stream. Replicas that have
- * not been evaluated yet report energy +inf and step -1. */
+ * not been evaluated yet report energy +inf and step -1. Without h the spins are
+ * copied from the device straight into `spins` (page-locked host memory makes
+ * that copy fastest). */
 gsb_status gsb_best(gsb_run_state* run, int8_t* spins, double* energies, double* cuts,
                     int32_t* step_found);
 

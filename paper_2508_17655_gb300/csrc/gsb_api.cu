@@ -305,6 +305,7 @@ void free_run(gsb_run_state* r) {
     cudaFree(r->best_e);
     cudaFree(r->best_step);
     cudaFree(r->best_s);
+    cudaFree(r->best_out);
     cudaFree(r->flag);
     cudaFree(r->status);
     for (cudaEvent_t e : r->prof_events) cudaEventDestroy(e);
@@ -687,28 +688,29 @@ gsb_status gsb_best(gsb_run_state* run, int8_t* spins, double* energies, double*
                                  run->stream));
     GSB_CUDA_TRY(cudaMemcpyAsync(stp.data(), run->best_step, sizeof(int32_t) * R,
                                  cudaMemcpyDeviceToHost, run->stream));
+    // spins: transposed on the device into the host layout, then copied straight
+    // into the caller's array (no auxiliary spin), or staged for the gauge fix
     std::vector<int8_t> s;
+    const bool direct = !run->prob->has_h;
     if (spins) {
-        int8_t* tmp = nullptr;
-        if ((st = dev_alloc(&tmp, (size_t)R * N))) return st;
-        st = launch_transpose_i8_to_host_layout(run->best_s, tmp, run->Np, run->Rp, N, R,
-                                                run->stream);
-        if (st == GSB_OK) {
+        if (!run->best_out && (st = dev_alloc(&run->best_out, (size_t)R * N))) return st;
+        if ((st = launch_transpose_i8_to_host_layout(run->best_s, run->best_out, run->Np,
+                                                     run->Rp, N, R, run->stream)))
+            return st;
+        int8_t* dst = spins;
+        if (!direct) {
             s.resize((size_t)R * N);
-            if (cudaMemcpyAsync(s.data(), tmp, (size_t)R * N, cudaMemcpyDeviceToHost,
-                                run->stream) != cudaSuccess)
-                st = cuda_error(cudaGetLastError(), "copy best spins");
+            dst = s.data();
         }
-        cudaStreamSynchronize(run->stream);
-        cudaFree(tmp);
-        if (st != GSB_OK) return st;
+        GSB_CUDA_TRY(cudaMemcpyAsync(dst, run->best_out, (size_t)R * N, cudaMemcpyDeviceToHost,
+                                     run->stream));
     }
     GSB_CUDA_TRY(cudaStreamSynchronize(run->stream));
     for (int r = 0; r < R; ++r) {
         if (energies) energies[r] = e[r];
         if (cuts) cuts[r] = isfinite(e[r]) ? 0.5 * (run->prob->W_tot - e[r]) : -INFINITY;
         if (step_found) step_found[r] = stp[r];
-        if (spins) {
+        if (spins && !direct) {
             const int8_t* src = &s[(size_t)r * N];
             // gauge-fix the auxiliary spin of the h augmentation to +1
             const int8_t g = (run->prob->has_h && src[Nu] < 0) ? -1 : 1;

@@ -99,6 +99,7 @@ struct gsb_run_state {
     double* best_e = nullptr;   // [Rp]
     int32_t* best_step = nullptr;
     int8_t* best_s = nullptr;   // [Np][Rp]
+    int8_t* best_out = nullptr; // [R][N]: best spins in the host layout (gsb_best, lazily)
     int32_t* flag = nullptr;    // [Rp]
     int* status = nullptr;      // device status word
     void* tc = nullptr;         // tcgen05 path state (tensor maps, barriers)

@@ -444,11 +444,20 @@ class Run:
                                      ctypes.byref(k)))
         return ms.value, n.value, k.value
 
-    def best(self):
-        spins = np.zeros((self.R, self.N), dtype=np.int8)
-        e = np.zeros(self.R, dtype=np.float64)
-        cut = np.zeros(self.R, dtype=np.float64)
-        step = np.zeros(self.R, dtype=np.int32)
+    def best(self, out=None):
+        """Best state per replica: dict of spins s (R x N int8), energies E, cuts
+        and the step found. out: optional dict of preallocated host arrays with
+        those keys (e.g. views of pinned memory) to fill instead."""
+        if out is None:
+            out = {"s": np.zeros((self.R, self.N), dtype=np.int8),
+                   "E": np.zeros(self.R, dtype=np.float64),
+                   "cut": np.zeros(self.R, dtype=np.float64),
+                   "step": np.zeros(self.R, dtype=np.int32)}
+        spins, e, cut, step = out["s"], out["E"], out["cut"], out["step"]
+        for a, dt, shape in ((spins, np.int8, (self.R, self.N)), (e, np.float64, (self.R,)),
+                             (cut, np.float64, (self.R,)), (step, np.int32, (self.R,))):
+            if a.dtype != dt or a.shape != shape or not a.flags.c_contiguous:
+                raise ValueError("best(out=...): wrong dtype, shape or layout")
         _check(lib().gsb_best(self.handle, _p(spins, ctypes.c_int8), _p(e, ctypes.c_double),
                               _p(cut, ctypes.c_double), _p(step, ctypes.c_int32)))
         return {"s": spins, "E": e, "cut": cut, "step": step}
