@@ -386,6 +386,25 @@ def test_tts_formula():
     assert O.ps_error(0.5, 100) == pytest.approx(0.05)
 
 
+def test_clopper_pearson_closed_forms_and_tails():
+    """The exact binomial interval behind the P_S error bars: at k = 0 and
+    k = n it has the closed forms 1 - (a/2)^(1/n) and (a/2)^(1/n); inside, its
+    bounds make the binomial tails exactly a/2 (summed term by term here)."""
+    from math import comb
+    a = 0.01
+    for n in (1, 7, 50, 1000):
+        lo, hi = O.clopper_pearson(0, n, 0.99)
+        assert lo == 0.0 and hi == pytest.approx(1 - (a / 2) ** (1 / n), rel=1e-10)
+        lo, hi = O.clopper_pearson(n, n, 0.99)
+        assert hi == 1.0 and lo == pytest.approx((a / 2) ** (1 / n), rel=1e-10)
+    for n, k in ((10, 3), (40, 17), (100, 1), (1000, 12)):
+        lo, hi = O.clopper_pearson(k, n, 0.99)
+        upper_tail = sum(comb(n, j) * lo ** j * (1 - lo) ** (n - j) for j in range(k, n + 1))
+        lower_tail = sum(comb(n, j) * hi ** j * (1 - hi) ** (n - j) for j in range(0, k + 1))
+        assert upper_tail == pytest.approx(a / 2, rel=1e-7)
+        assert lower_tail == pytest.approx(a / 2, rel=1e-7)
+
+
 def test_twin_distance_values():
     vals = _paper_values()
     x1, x2 = O.twin_initial(8, 500, seed=4)
