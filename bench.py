@@ -356,7 +356,7 @@ def _events(torch, stream):
 
 
 LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "adjoint", "fx32",
-        "twin_delta")
+        "twin_delta", "grid")
 
 
 def fp32_alu_peak(Pk):
@@ -379,6 +379,9 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
             continue
         rp, col, val = I.er_graph(N, 20, "+1", 5)
         P = gsb.Problem.csr(N, rp, col, val, stream=stream.cuda_stream)
+        t_l = time.perf_counter()
+        _, lmax, lmin = P.info(stream=stream.cuda_stream)  # power iteration on the GPU (App. A)
+        setup_ms = 1e3 * (time.perf_counter() - t_l)
         R, M = 512, leg_M or 5000
         # c = 1/lambda_max and dt from Eq. 13, with the extreme eigenvalues found
         # by the library's power iteration on the GPU (App. A)
@@ -400,6 +403,8 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         out[f"sparse_N{N}"] = {
             "workload": f"ER N={N} mean degree 20, +1 weights, R={R}, M={M}, GbSB, CSR",
             "value": N * R * M / (ms / 1e3), "unit": "spin-updates/s", "ms_per_run": ms,
+            "lambda_setup": {"ms": setup_ms, "lambda_max": lmax, "lambda_min": lmin,
+                             "how": "host wall clock around gsb_problem_info (power iteration)"},
             "roofline": {"bound": "hbm", "kernel": "k_csr_step", "achieved": bytes_step / (us * 1e-6) / 1e9,
                          "peak": hbm, "unit": "GB/s",
                          "frac": bytes_step / (us * 1e-6) / 1e9 / hbm, "us_per_step": us,
@@ -465,6 +470,37 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
                          "frac": tflops / Pk["bf16_tflops_sustained"],
                          "peak_source": how + " (bf16 sustained)"}}
         tw.close()
+        P.close()
+    # --- (M, A) grid of Fig. 1(a): P_S, C_ave / C_best and TTS99 per cell through the
+    # sweep harness, GdSB on FP8 at the headline shape, 128 replicas per A and M
+    if want("grid"):
+        from paper_2508_17655_gb300 import sweep
+        J = I.sk_pm1(N_SPINS, 0)
+        P = gsb.Problem.dense(J, stream=stream.cuda_stream)
+        Ms = [500, 1000, 2000, 4000] if not leg_M else [leg_M]
+        reps = R_REPLICAS // len(A_VALUES)
+        c = 1.0 / (2.0 * math.sqrt(N_SPINS))
+        E_t = target_energy()
+        sweep.success_grid(P, "gdsb", [100], A_VALUES, reps, E_t if E_t is not None else -1e300,
+                           c=c, dt=DT, seed=3, stream=stream.cuda_stream)  # warm-up
+        g = sweep.success_grid(P, "gdsb", Ms, A_VALUES, reps,
+                               E_t if E_t is not None else -1e300, c=c, dt=DT, seed=4,
+                               stream=stream.cuda_stream)
+        su = float(sum(N_SPINS * R_REPLICAS * M for M in Ms))
+        wall = float(np.sum(g["run_s"]))
+        tf = 2.0 * N_SPINS ** 2 * R_REPLICAS * sum(Ms) / wall / 1e12
+        out["grid"] = {
+            "workload": f"N={N_SPINS} +-1 complete graph, GdSB on FP8, M in {Ms} x A in "
+                        f"{A_VALUES}, {reps} replicas per cell, target E={E_t}",
+            "value": su / wall, "unit": "spin-updates/s",
+            "how": "host wall clock around each run of the grid (creation to best states)",
+            "M": Ms, "A": A_VALUES,
+            "P_S": g["P_S"].tolist(), "C_ave_over_C_best": g["C_ave_over_C_best"].tolist(),
+            "C_best": g["C_best"], "run_s": g["run_s"].tolist(),
+            "roofline": {"bound": "tensor", "kernel": "k_tc_persist", "achieved": tf,
+                         "peak": 2.0 * Pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                         "frac": tf / (2.0 * Pk["bf16_tflops_sustained"]),
+                         "peak_source": how + " (2 x bf16 sustained, e4m3)"}}
         P.close()
     if only is not None and only not in ("batched_256", "lyapunov", "adjoint"):
         return out
