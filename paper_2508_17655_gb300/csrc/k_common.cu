@@ -213,11 +213,19 @@ gsb_status launch_best_keep(gsb_run_state* run, int step) {
     return GSB_OK;
 }
 
-// ---------------------------------------------------------------- power iteration
-// Extreme eigenvalues of J (App. A): spectral radius rho from J^2, then the
-// dominant eigenvalues of J + sigma I and sigma I - J with sigma = 1.01 rho.
+// ---------------------------------------------------------------- extreme eigenvalues
+// lambda_max and lambda_min of J (App. A) by the Lanczos method: from a random
+// unit v_0, w = J v_j - beta_j v_{j-1}, alpha_j = v_j . w, w -= alpha_j v_j
+// (and once more against v_j, the local correction), beta_{j+1} = |w|,
+// v_{j+1} = w / beta_{j+1}, all on the GPU in FP64. The extreme eigenvalues of
+// the tridiagonal matrix T (alpha on the diagonal, beta beside it) converge to
+// those of J from inside; the loss of orthogonality of the plain recurrence
+// only adds copies of converged Ritz values, not wrong extremes. The host
+// bisects T's Sturm sequence for them every kCheck steps and stops once both
+// stand still (or the Krylov space is invariant). Every sum is a block
+// reduction added in a fixed order: the result does not vary run to run.
 
-// w = J v, one warp per row (dense FP32 or CSR).
+// w = J v, one warp per row (dense FP32 or CSR), FP64 accumulation.
 __global__ void k_gemv_dense(const float* __restrict__ J, const double* __restrict__ v,
                              double* __restrict__ w, int N, int Np) {
     const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -241,147 +249,191 @@ __global__ void k_gemv_csr(const int32_t* __restrict__ rowptr, const int32_t* __
     if (!lane) w[row] = acc;
 }
 
-// acc[0] += v.w', acc[1] += w'.w' with w' = sigma v + sgn w.
-__global__ void k_pi_dots(const double* __restrict__ v, double* __restrict__ w, int N,
-                          double sigma, double sgn, double* acc) {
-    __shared__ double s0[8], s1[8];
-    double a = 0.0, b = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const double wi = sigma * v[i] + sgn * w[i];
-        w[i] = wi;
-        a += v[i] * wi;
-        b += wi * wi;
-    }
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (threadIdx.x % 32 == 0) {
-        s0[threadIdx.x / 32] = a;
-        s1[threadIdx.x / 32] = b;
-    }
+constexpr int kLzThreads = 256;
+
+// part[block] = sum over the block's grid-stride slice of a_i b_i, added in a
+// fixed order (warp shuffles, then the warps in order).
+__global__ void __launch_bounds__(kLzThreads) k_lz_dot(const double* __restrict__ a,
+                                                       const double* __restrict__ b, int N,
+                                                       double* __restrict__ part) {
+    __shared__ double ws[kLzThreads / 32];
+    double t = 0.0;
+    for (int i = blockIdx.x * kLzThreads + threadIdx.x; i < N; i += gridDim.x * kLzThreads)
+        t += a[i] * b[i];
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x % 32 == 0) ws[threadIdx.x / 32] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x / 32); ++k) {
-            a += s0[k];
-            b += s1[k];
-        }
-        atomicAdd(&acc[0], a);
-        atomicAdd(&acc[1], b);
+        double u = 0.0;
+        for (int k = 0; k < kLzThreads / 32; ++k) u += ws[k];
+        part[blockIdx.x] = u;
     }
 }
 
-// v = w / |w|, records the Rayleigh quotient v.w' (v unit) in rq[it].
-__global__ void k_pi_normalize(double* __restrict__ v, const double* __restrict__ w, int N,
-                               double* acc, double* rq, int it) {
-    const double nrm = sqrt(acc[1]);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        v[i] = nrm > 0.0 ? w[i] / nrm : 0.0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) rq[it] = acc[0];
+// The sum of the parts, in block order (every block computes the same value).
+__device__ __forceinline__ double parts_sum(const double* __restrict__ part, int nparts) {
+    __shared__ double t;
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < nparts; ++k) u += part[k];
+        t = u;
+    }
+    __syncthreads();
+    return t;
 }
 
-__global__ void k_pi_init(double* v, int N) {
+// w -= coef v with coef = the dot product in part; alpha[j] = coef (set) or
+// += coef (accumulate), written by block 0.
+__global__ void k_lz_remove(const double* __restrict__ part, int nparts,
+                            const double* __restrict__ v, int N, double* __restrict__ w,
+                            double* __restrict__ alpha, int j, int accumulate) {
+    const double coef = parts_sum(part, nparts);
+    if (blockIdx.x == 0 && threadIdx.x == 0) alpha[j] = accumulate ? alpha[j] + coef : coef;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        w[i] -= coef * v[i];
+}
+
+// w -= beta[j] vprev
+__global__ void k_lz_axpy(const double* __restrict__ beta, int j, const double* __restrict__ vprev,
+                          int N, double* __restrict__ w) {
+    const double bj = beta[j];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        w[i] -= bj * vprev[i];
+}
+
+// nrm = sqrt(<w, w>) from part; beta[j] = nrm; dst = w / nrm (0 if nrm is 0)
+__global__ void k_lz_normalize(const double* __restrict__ part, int nparts,
+                               const double* __restrict__ w, int N, double* __restrict__ dst,
+                               double* __restrict__ beta, int j) {
+    const double nrm = sqrt(parts_sum(part, nparts));
+    if (blockIdx.x == 0 && threadIdx.x == 0) beta[j] = nrm;
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        dst[i] = w[i] * inv;
+}
+
+__global__ void k_lz_start(double* v, int N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)i, 0u, 77u, 0u), make_uint2(2718u, 0u));
     v[i] = ((double)(w.x >> 8) + 0.5) / 16777216.0 - 0.5;
 }
 
-__global__ void k_pi_zero(double* acc) {
-    acc[0] = 0.0;
-    acc[1] = 0.0;
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal a[0..n-1] and off-diagonal b[1..n-1] (signs of the LDL^T pivots).
+int sturm_below(const std::vector<double>& a, const std::vector<double>& b, int n, double x) {
+    int c = 0;
+    double q = 1.0;
+    for (int k = 0; k < n; ++k) {
+        q = a[k] - x - (k ? b[k] * b[k] / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++c;
+    }
+    return c;
 }
 
-__global__ void k_pi_unit(double* v, int N, double* acc) {
-    // normalise the start vector: acc[1] must hold |v|^2
-    const double nrm = sqrt(acc[1]);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        v[i] /= nrm;
+// Smallest and largest eigenvalue of that matrix: bisection on the count
+// inside the Gershgorin interval.
+void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b, int n,
+                      double* lmin, double* lmax) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int k = 0; k < n; ++k) {
+        const double r = (k ? fabs(b[k]) : 0.0) + (k + 1 < n ? fabs(b[k + 1]) : 0.0);
+        lo = fmin(lo, a[k] - r);
+        hi = fmax(hi, a[k] + r);
+    }
+    auto bisect = [&](int target) {  // the x where the count reaches target
+        double l = lo - (fabs(lo) + 1.0) * 1e-12, h = hi + (fabs(hi) + 1.0) * 1e-12;
+        for (int it = 0; it < 300; ++it) {
+            const double mid = 0.5 * (l + h);
+            if (mid <= l || mid >= h) break;
+            if (sturm_below(a, b, n, mid) >= target) h = mid; else l = mid;
+        }
+        return 0.5 * (l + h);
+    };
+    *lmin = bisect(1);
+    *lmax = bisect(n);
 }
 
-__global__ void k_pi_sqnorm(const double* v, int N, double* acc) {
-    double b = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        b += v[i] * v[i];
-    for (int o = 16; o; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-    if (threadIdx.x % 32 == 0) atomicAdd(&acc[1], b);
-}
-
-// One power iteration phase on the GPU. mode 0: J^2 (returns rho^2);
-// mode 1: J + sigma I; mode 2: sigma I - J. Returns the converged Rayleigh
-// quotient of the iterated operator.
-static gsb_status power_phase(gsb_problem* P, cudaStream_t s, int mode, double sigma,
-                              double* result) {
+gsb_status compute_lambda(gsb_problem* P, cudaStream_t s) {
+    if (P->have_lambda) return GSB_OK;
     const int N = P->N;
-    double *v = nullptr, *w = nullptr, *w2 = nullptr, *acc = nullptr, *rq = nullptr;
-    const int kChunk = 64, kMaxIt = 20000;
-    GSB_CUDA_TRY(cudaMalloc(&v, sizeof(double) * N));
-    GSB_CUDA_TRY(cudaMalloc(&w, sizeof(double) * N));
-    GSB_CUDA_TRY(cudaMalloc(&w2, sizeof(double) * N));
-    GSB_CUDA_TRY(cudaMalloc(&acc, sizeof(double) * 2));
-    GSB_CUDA_TRY(cudaMalloc(&rq, sizeof(double) * kChunk));
-    gsb_status st = GSB_OK;
-    const int gb = (N + 255) / 256 < 256 ? (N + 255) / 256 : 256;
+    const int mmax = N < 2000 ? N : 2000;  // steps at most
+    constexpr int kCheck = 16;
+    const int eb = (N + kLzThreads - 1) / kLzThreads;
+    const int nparts = eb < 256 ? eb : 256;
+    double *v[3] = {nullptr, nullptr, nullptr}, *w = nullptr, *part = nullptr, *alpha = nullptr,
+           *beta = nullptr;
+    auto release = [&]() {
+        for (double* q : v) cudaFree(q);
+        cudaFree(w);
+        cudaFree(part);
+        cudaFree(alpha);
+        cudaFree(beta);
+    };
+    bool ok = true;
+    for (double*& q : v) ok = ok && cudaMalloc(&q, sizeof(double) * N) == cudaSuccess;
+    ok = ok && cudaMalloc(&w, sizeof(double) * N) == cudaSuccess &&
+         cudaMalloc(&part, sizeof(double) * nparts) == cudaSuccess &&
+         cudaMalloc(&alpha, sizeof(double) * (mmax + 1)) == cudaSuccess &&
+         cudaMalloc(&beta, sizeof(double) * (mmax + 2)) == cudaSuccess;
+    if (!ok) {
+        release();
+        return set_error(GSB_ENOMEM, "eigenvalue workspace");
+    }
     auto gemv = [&](const double* in, double* out) {
         const int blocks = (N + 7) / 8;
         if (P->csr)
             k_gemv_csr<<<blocks, 256, 0, s>>>(P->rowptr, P->col, P->val, in, out, N);
         else
             k_gemv_dense<<<blocks, 256, 0, s>>>(P->J32, in, out, N, P->Np);
-        count_launch();
     };
-    k_pi_init<<<(N + 255) / 256, 256, 0, s>>>(v, N);
-    k_pi_zero<<<1, 1, 0, s>>>(acc);
-    k_pi_sqnorm<<<gb, 256, 0, s>>>(v, N, acc);
-    k_pi_unit<<<gb, 256, 0, s>>>(v, N, acc);
-    count_launch(4);
-    double prev = 0.0, cur = 0.0;
-    double host_rq[kChunk];
-    for (int it0 = 0; it0 < kMaxIt; it0 += kChunk) {
-        for (int it = 0; it < kChunk; ++it) {
-            gemv(v, w);
-            double sg = -1.0;
-            if (mode == 0) {
-                gemv(w, w2);
-                std::swap(w, w2);
-                sg = 1.0;
-            } else if (mode == 1) {
-                sg = 1.0;
-            }
-            k_pi_zero<<<1, 1, 0, s>>>(acc);
-            k_pi_dots<<<gb, 256, 0, s>>>(v, w, N, mode == 0 ? 0.0 : sigma, sg, acc);
-            k_pi_normalize<<<gb, 256, 0, s>>>(v, w, N, acc, rq, it);
-            count_launch(3);
-        }
-        cudaError_t e = cudaMemcpyAsync(host_rq, rq, sizeof(host_rq), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            st = cuda_error(e, "power iteration");
+    // v_0: random, unit (beta[0] holds its norm before scaling; unused after)
+    k_lz_start<<<eb, kLzThreads, 0, s>>>(w, N);
+    k_lz_dot<<<nparts, kLzThreads, 0, s>>>(w, w, N, part);
+    k_lz_normalize<<<nparts, kLzThreads, 0, s>>>(part, nparts, w, N, v[0], beta, 0);
+    count_launch(3);
+    std::vector<double> a(mmax + 1), b(mmax + 2);
+    double pmin = 0.0, pmax = 0.0, lmin = 0.0, lmax = 0.0;
+    gsb_status st = GSB_OK;
+    int prev = 2, cur = 0, next = 1;  // v[prev] = v_{j-1}, v[cur] = v_j
+    for (int j = 0; j < mmax; ++j) {
+        gemv(v[cur], w);
+        if (j > 0) k_lz_axpy<<<nparts, kLzThreads, 0, s>>>(beta, j, v[prev], N, w);
+        k_lz_dot<<<nparts, kLzThreads, 0, s>>>(v[cur], w, N, part);
+        k_lz_remove<<<nparts, kLzThreads, 0, s>>>(part, nparts, v[cur], N, w, alpha, j, 0);
+        k_lz_dot<<<nparts, kLzThreads, 0, s>>>(v[cur], w, N, part);
+        k_lz_remove<<<nparts, kLzThreads, 0, s>>>(part, nparts, v[cur], N, w, alpha, j, 1);
+        k_lz_dot<<<nparts, kLzThreads, 0, s>>>(w, w, N, part);
+        k_lz_normalize<<<nparts, kLzThreads, 0, s>>>(part, nparts, w, N, v[next], beta, j + 1);
+        count_launch(j > 0 ? 8 : 7);
+        const int t = prev;
+        prev = cur;
+        cur = next;
+        next = t;
+        const int n = j + 1;
+        if (n % kCheck != 0 && n != mmax) continue;
+        if (cudaMemcpyAsync(a.data(), alpha, sizeof(double) * n, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(b.data(), beta, sizeof(double) * (n + 1), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "eigenvalue iteration");
             break;
         }
-        cur = host_rq[kChunk - 1];
-        prev = host_rq[kChunk - 2];
-        if (it0 > 0 && fabs(cur - prev) <= 1e-12 * fabs(cur)) break;
+        tridiag_extremes(a, b, n, &lmin, &lmax);
+        const double scale = fmax(fabs(lmin), fabs(lmax)) + 1e-300;
+        // the Krylov space is invariant (b[n] = 0), or both Ritz values stand still
+        if (b[n] <= 1e-12 * scale ||
+            (n > kCheck && fabs(lmax - pmax) <= 1e-14 * scale && fabs(lmin - pmin) <= 1e-14 * scale))
+            break;
+        pmin = lmin;
+        pmax = lmax;
     }
-    *result = cur;
-    cudaFree(v);
-    cudaFree(w);
-    cudaFree(w2);
-    cudaFree(acc);
-    cudaFree(rq);
-    return st;
-}
-
-gsb_status compute_lambda(gsb_problem* P, cudaStream_t s) {
-    if (P->have_lambda) return GSB_OK;
-    double rho2 = 0.0, top = 0.0, bot = 0.0;
-    gsb_status st = power_phase(P, s, 0, 0.0, &rho2);
+    release();
     if (st != GSB_OK) return st;
-    const double sigma = 1.01 * sqrt(rho2 > 0.0 ? rho2 : 0.0) + 1e-300;
-    if ((st = power_phase(P, s, 1, sigma, &top)) != GSB_OK) return st;
-    if ((st = power_phase(P, s, 2, sigma, &bot)) != GSB_OK) return st;
-    P->lambda_max = top - sigma;
-    P->lambda_min = sigma - bot;
+    P->lambda_max = lmax;
+    P->lambda_min = lmin;
     P->have_lambda = true;
     return GSB_OK;
 }

@@ -363,6 +363,41 @@ def test_lambda_and_auto_parameters_match_oracle():
     assert abs(gl - lmax) <= 1e-6 * abs(lmax) and abs(gm - lmin) <= 1e-6 * abs(lmin)
 
 
+@pytest.mark.parametrize("case", ["sk_pm1_2000", "gauss_300_h", "er_2000", "ring_64", "pair"])
+def test_lambda_extremes_match_dense_eigensolver(case):
+    """The GPU eigenvalue setup (App. A) against LAPACK on the dense matrix:
+    the K2000-shaped instance, a Gaussian SK matrix with a local field (the
+    augmented N + 1 matrix), a sparse +-1 ER graph, a ring (eigenvalues +-2 in
+    closed form) and a single coupled pair (+-1)."""
+    if case == "sk_pm1_2000":
+        J = I.sk_pm1(2000, 0)
+        P, Jd = gsb.Problem.dense(J), J.astype(np.float64)
+    elif case == "gauss_300_h":
+        J = I.sk_gauss(300, 3)
+        h = np.random.default_rng(5).standard_normal(300).astype(np.float32) * 0.1
+        P = gsb.Problem.dense(J, h=h)
+        Jd = np.zeros((301, 301))
+        Jd[:300, :300] = J
+        Jd[:300, 300] = Jd[300, :300] = h
+    elif case == "er_2000":
+        rp, col, val = I.er_graph(2000, 20, "pm1", 7)
+        P, Jd = gsb.Problem.csr(2000, rp, col, val), I.csr_to_dense(2000, rp, col, val)
+    elif case == "ring_64":
+        J = I.ring(64)
+        P, Jd = gsb.Problem.dense(J.astype(np.float32)), J
+    else:
+        J = np.array([[0.0, 1.0], [1.0, 0.0]])
+        P, Jd = gsb.Problem.dense(J.astype(np.float32)), J
+    ev = np.linalg.eigvalsh(Jd)
+    n, lmax, lmin = P.info()
+    assert n == Jd.shape[0]
+    scale = float(np.max(np.abs(ev)))
+    assert abs(lmax - ev[-1]) <= 1e-9 * scale, (lmax, ev[-1])
+    assert abs(lmin - ev[0]) <= 1e-9 * scale, (lmin, ev[0])
+    if case == "ring_64":
+        assert abs(lmax - 2.0) <= 1e-12 and abs(lmin + 2.0) <= 1e-12
+
+
 @pytest.mark.parametrize("variant", ["dsb", "gdsb"])
 @pytest.mark.parametrize("N,R,form", [(100, 130, "cluster"), (300, 200, "cluster"),
                                       (2000, 128, "cluster"), (2100, 129, "grid"),
