@@ -380,11 +380,11 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         rp, col, val = I.er_graph(N, 20, "+1", 5)
         P = gsb.Problem.csr(N, rp, col, val, stream=stream.cuda_stream)
         t_l = time.perf_counter()
-        _, lmax, lmin = P.info(stream=stream.cuda_stream)  # power iteration on the GPU (App. A)
+        _, lmax, lmin = P.info(stream=stream.cuda_stream)  # Lanczos on the GPU (App. A)
         setup_ms = 1e3 * (time.perf_counter() - t_l)
         R, M = 512, leg_M or 5000
         # c = 1/lambda_max and dt from Eq. 13, with the extreme eigenvalues found
-        # by the library's power iteration on the GPU (App. A)
+        # by the library's Lanczos iteration on the GPU (App. A)
         run = P.run("gbsb", M=M, R=R, c=0.0, dt=0.0, A=0.2, seed=1,
                     defer=True, profile=True, stream=stream.cuda_stream)
         run.restart(2)
@@ -404,7 +404,7 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
             "workload": f"ER N={N} mean degree 20, +1 weights, R={R}, M={M}, GbSB, CSR",
             "value": N * R * M / (ms / 1e3), "unit": "spin-updates/s", "ms_per_run": ms,
             "lambda_setup": {"ms": setup_ms, "lambda_max": lmax, "lambda_min": lmin,
-                             "how": "host wall clock around gsb_problem_info (power iteration)"},
+                             "how": "host wall clock around gsb_problem_info (Lanczos)"},
             "roofline": {"bound": "hbm", "kernel": "k_csr_step", "achieved": bytes_step / (us * 1e-6) / 1e9,
                          "peak": hbm, "unit": "GB/s",
                          "frac": bytes_step / (us * 1e-6) / 1e9 / hbm, "us_per_step": us,

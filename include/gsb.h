@@ -134,8 +134,9 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
 gsb_status gsb_destroy(gsb_problem* problem);
 
 /* Number of spins (including the auxiliary one when h was given) and the
- * extreme eigenvalues of J used for c and dt (computed on the GPU by power
- * iteration on first use; App. A). */
+ * extreme eigenvalues of J used for c and dt (computed on the GPU on first use
+ * by the Lanczos method in FP64, to 1e-14 relative stationarity of the Ritz
+ * values; App. A). Blocks on `stream` the first time. */
 gsb_status gsb_problem_info(gsb_problem* problem, int32_t* n_spins, double* lambda_max,
                             double* lambda_min, void* stream);
 

@@ -150,7 +150,7 @@ gsb_status launch_csr_energy(const gsb_problem* prob, const float* x_sm, int Rp,
                              cudaStream_t s);
 // best keeping
 gsb_status launch_best_keep(gsb_run_state* run, int step);
-// power iteration (App. A)
+// Lanczos iteration (App. A)
 gsb_status compute_lambda(gsb_problem* prob, cudaStream_t s);
 // tcgen05 path
 bool tc_available();

@@ -1,5 +1,5 @@
 // k_common.cu -- state initialisation (App. A), layout transposes, energy
-// best-keeping, and the power iteration that sets c and dt (App. A, Eq. 13).
+// best-keeping, and the Lanczos iteration that sets c and dt (App. A, Eq. 13).
 #include "gsb_internal.cuh"
 
 namespace gsb {
