@@ -123,6 +123,34 @@ void count_launch(int n = 1);
         if (e_ != cudaSuccess) return ::gsb::cuda_error(e_, #call); \
     } while (0)
 
+// Programmatic dependent launch: a step kernel launched with launch_pdl may
+// start (its prologue, its loads of data no earlier kernel writes) while the
+// kernel before it in the stream finishes. It calls griddep_trigger() once its
+// own CTAs are all resident, so the next step may be scheduled, and
+// griddep_wait() before its first access to anything the earlier kernel
+// writes or reads; the wait returns once that kernel has completed and its
+// memory operations are visible.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 #define GSB_LAUNCH_CHECK(what)                                 \
     do {                                                       \
         ::gsb::count_launch();                                 \

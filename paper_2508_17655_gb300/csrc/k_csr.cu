@@ -78,6 +78,11 @@ __global__ void __launch_bounds__(256) k_csr_step(
     const int8_t* __restrict__ sc, float* __restrict__ xn, int8_t* __restrict__ sn,
     float* __restrict__ y, float* __restrict__ p, const float* __restrict__ A, float c, float dt,
     float p_shared, float inv_rem) {
+    // launched with programmatic dependent launch: the next step may be
+    // scheduled once every block of this one has started; everything below
+    // reads or writes state the previous step touched, so it waits for it
+    griddep_trigger();
+    griddep_wait();
     const int i = blockIdx.y * kWarpsPerBlock + (threadIdx.x >> 5);
     if (i >= N) return;
     const int rlane = blockIdx.x * kReplicasPerWarp + (threadIdx.x & 31) * 4;
@@ -169,10 +174,11 @@ gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc) {
     const int cur = run->cur;
     const float inv_rem = 1.0f / (float)(sc.M - sc.m);
 #define GSB_CSR_LAUNCH(S, C, E)                                                              \
-    k_csr_step<S, C, E><<<grid, 256, 0, run->stream>>>(                                      \
-        P->rowptr, P->col, P->val, run->N, run->Rp, run->x[cur], run->s8[cur],               \
-        run->x[cur ^ 1], run->s8[cur ^ 1], run->y, run->p, run->A, sc.c, sc.dt, sc.p_next,   \
-        inv_rem)
+    GSB_CUDA_TRY(launch_pdl(k_csr_step<S, C, E>, grid, dim3(256), 0, run->stream, P->rowptr,   \
+                            P->col, P->val, run->N, run->Rp, (const float*)run->x[cur],      \
+                            (const int8_t*)run->s8[cur], run->x[cur ^ 1], run->s8[cur ^ 1],  \
+                            run->y, run->p, (const float*)run->A, sc.c, sc.dt, sc.p_next,    \
+                            inv_rem))
     // exact fixed-point x coupling when J is integer and 2^30 sum_k |J_ik| fits in int64
     const bool exact = P->integer_J && P->max_row_abs < 4294967296.0;
     if (run->sign_coupling) {

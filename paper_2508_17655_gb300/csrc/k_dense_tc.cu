@@ -688,12 +688,27 @@ __global__ void __launch_bounds__(kThreadsF, 1)
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
+    griddep_trigger();  // every CTA of this step is resident: the next may be scheduled
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
         if (lane == 0) {
             int armed = 0;
-            for (int kc = 0; kc < nk; ++kc) {
+            // J of the first stages does not depend on the previous step: it is
+            // requested before the wait for that step, V after it
+            const int pre = nk < S ? nk : S;
+            for (int kc = 0; kc < pre; ++kc) {
+                mbar_arrive_expect_tx(&full[kc], SV + SJ);
+                tma_load_2d(sJ + kc * SJ, &tmJ, &full[kc], kc * kElems, i0);
+            }
+            griddep_wait();
+            for (int kc = 0; kc < pre; ++kc) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    tma_load_2d(sV + kc * SV + q * SV1, &tmV, &full[kc], kc * kElems, q * Rp + r0);
+                armed = kc + 1;
+            }
+            for (int kc = pre; kc < nk; ++kc) {
                 const int st = kc % S;
                 const uint32_t ph = (uint32_t)(kc / S) & 1u;
                 if (kc >= S && !mbar_wait(&empty[st], ph ^ 1u, status)) break;
@@ -760,6 +775,8 @@ __global__ void __launch_bounds__(kThreadsF, 1)
                 pn[k] = CONTROL ? p[o + (size_t)k * Rp] : 0.f;
             }
         };
+        // x, y, p and the V buffer written below are the previous step's
+        griddep_wait();
         load_state(c0);
         // tcgen05.ld is warp-collective: proceed only if every lane saw the accumulator
         const bool ready = __all_sync(0xffffffffu, mbar_wait(accf, 0, status));
@@ -837,9 +854,10 @@ gsb_status launch_step(gsb_run_state* run, TcState* T, float p_shared, float inv
                                               smem_bytes_fx32()));
             attr_set = true;
         }
-        k_fx32_step<CONTROL><<<grid, kThreadsF, smem_bytes_fx32(), run->stream>>>(
-            T->tmA, T->tmB[T->vcur], run->Np, run->Rp, run->x[0], run->y, run->p, run->A,
-            run->v16[T->vcur ^ 1], run->c, run->dt, p_shared, inv_rem, run->status);
+        GSB_CUDA_TRY(launch_pdl(k_fx32_step<CONTROL>, grid, dim3(kThreadsF), smem_bytes_fx32(),
+                                run->stream, T->tmA, T->tmB[T->vcur], run->Np, run->Rp,
+                                run->x[0], run->y, run->p, run->A, run->v16[T->vcur ^ 1], run->c,
+                                run->dt, p_shared, inv_rem, run->status));
         GSB_LAUNCH_CHECK("k_fx32_step");
     } else {
         if (!attr_set) {
