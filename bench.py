@@ -217,9 +217,13 @@ def gpu_arm(args, world, rank, local):
 
     P = gsb.Problem.dense(J, stream=stream.cuda_stream)
 
-    def timed_runs(variant, precision, K, W, seed0):
+    def timed_runs(variant, precision, K, W, seed0, profile=True):
+        # profile: events around every step-kernel launch (the per-launch time of
+        # the roofline); they also keep consecutive launches from overlapping, so
+        # one-step-per-launch paths are timed without them and their kernel time
+        # comes from a separate profiled run
         run = P.run(variant, M=M_STEPS, R=R_REPLICAS, c=c, dt=DT, A=A, seed=seed0,
-                    precision=precision, defer=True, profile=True, stream=stream.cuda_stream)
+                    precision=precision, defer=True, profile=profile, stream=stream.cuda_stream)
         for w in range(W):
             run.restart(seed0 + 1 + w)
         times, kern_ms, kern_n, kern_steps, energies = [], 0.0, 0, 0, []
@@ -235,10 +239,11 @@ def gpu_arm(args, world, rank, local):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-            ms, n, nst = run.kernel_time()
-            kern_ms += ms
-            kern_n += n
-            kern_steps += nst
+            if profile:
+                ms, n, nst = run.kernel_time()
+                kern_ms += ms
+                kern_n += n
+                kern_steps += nst
             energies.append(run.best()["E"])
         launches = gsb.launch_count() - launches0
         kernel = run.kernel()
@@ -292,9 +297,11 @@ def gpu_arm(args, world, rank, local):
         E = target_energy()
         out["success"] = success_report(energies, A, args.steps, E, ms_per_step)
         # the paper's GbSB (x coupling) on the exact FX32 tensor-core path
-        t2, (km2, kn2, ks2), e2, _, _ = timed_runs("gbsb", "fx32", 2, 1, 7000)
+        t2, _, e2, _, _ = timed_runs("gbsb", "fx32", 2, 1, 7000, profile=False)
         fx_ms = sum(t2) / len(t2)
-        us2 = 1e3 * km2 / ks2
+        us2 = kernel_us(lambda m, prof: P.run("gbsb", M=m, R=R_REPLICAS, c=c, dt=DT, A=A, seed=1,
+                                               precision="fx32", defer=True, profile=prof,
+                                               stream=stream.cuda_stream), 500)
         out["gbsb_fx32"] = {"value": N_SPINS * R_REPLICAS * M_STEPS / (fx_ms / 1e3),
                             "ms_per_step": fx_ms, "us_per_time_step": us2,
                             "tensor_frac_bf16_4planes": (4 * 2.0 * N_SPINS ** 2 * R_REPLICAS /
@@ -302,9 +309,12 @@ def gpu_arm(args, world, rank, local):
                                                         Pk["bf16_tflops_sustained"],
                             "success": success_report(e2, A, 2, E, fx_ms)}
         # the plain FP32 form, same workload (one run)
-        t3, (km3, kn3, ks3), e3, _, _ = timed_runs("gdsb", "fp32", 1, 1, 9000)
+        t3, _, e3, _, _ = timed_runs("gdsb", "fp32", 1, 1, 9000, profile=False)
+        us3 = kernel_us(lambda m, prof: P.run("gdsb", M=m, R=R_REPLICAS, c=c, dt=DT, A=A, seed=1,
+                                               precision="fp32", defer=True, profile=prof,
+                                               stream=stream.cuda_stream), 200)
         out["plain_fp32"] = {"value": N_SPINS * R_REPLICAS * M_STEPS / (t3[0] / 1e3),
-                             "ms_per_step": t3[0], "us_per_time_step": 1e3 * km3 / ks3}
+                             "ms_per_step": t3[0], "us_per_time_step": us3}
         out["fused_vs_plain"] = value / world / out["plain_fp32"]["value"]
         out["e2e"] = e2e_leg(gsb, J, c, A, max(1, min(args.steps, 3)))
         out["other_configs"] = other_legs(gsb, I, np, torch, stream, Pk, how)
@@ -364,6 +374,18 @@ def fp32_alu_peak(Pk):
     return 152 * 128 * 2 * Pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
+def kernel_us(make_run, steps):
+    """Average duration of one step-kernel launch: a run of `steps` steps made by
+    make_run(steps, profile=True), timed by the events the library records
+    around each launch (which also keeps consecutive launches from overlapping,
+    so this is the kernel's own time)."""
+    r = make_run(steps, True)
+    r.restart(2)
+    kms, _, ksteps = r.kernel_time()
+    r.close()
+    return 1e3 * kms / ksteps
+
+
 def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
     """The other configurations of the hot path, one run each (after one
     warm-up), with the dominant kernel's roofline from CUDA events. only:
@@ -385,8 +407,9 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         R, M = 512, leg_M or 5000
         # c = 1/lambda_max and dt from Eq. 13, with the extreme eigenvalues found
         # by the library's Lanczos iteration on the GPU (App. A)
-        run = P.run("gbsb", M=M, R=R, c=0.0, dt=0.0, A=0.2, seed=1,
-                    defer=True, profile=True, stream=stream.cuda_stream)
+        mk = lambda m, prof: P.run("gbsb", M=m, R=R, c=0.0, dt=0.0, A=0.2, seed=1, defer=True,
+                                   profile=prof, stream=stream.cuda_stream)
+        run = mk(M, False)
         run.restart(2)
         e0, e1 = _events(torch, stream)
         e0.record(stream)
@@ -394,12 +417,11 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
-        kms, kn, ksteps = run.kernel_time()
+        us = kernel_us(mk, min(M, 1000))
         nnz = len(col)
         # algorithmic bytes per step: x, y, p read and written (24 B per spin and
         # replica), x gathered once (4 B), CSR indices and values (8 B per nonzero)
         bytes_step = 28.0 * N * R + 8.0 * nnz
-        us = 1e3 * kms / ksteps
         out[f"sparse_N{N}"] = {
             "workload": f"ER N={N} mean degree 20, +1 weights, R={R}, M={M}, GbSB, CSR",
             "value": N * R * M / (ms / 1e3), "unit": "spin-updates/s", "ms_per_run": ms,
@@ -417,17 +439,17 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         A = np.repeat(np.array(A_VALUES, np.float32), R_REPLICAS // len(A_VALUES))
         P = gsb.Problem.dense(J, stream=stream.cuda_stream)
         M = leg_M or M_STEPS
-        run = P.run("gbsb", M=M, R=R_REPLICAS, c=1.0 / (2.0 * math.sqrt(N_SPINS)), dt=DT, A=A,
-                    seed=1, precision="fx32", defer=True, profile=True,
-                    stream=stream.cuda_stream)
+        mk = lambda m, prof: P.run("gbsb", M=m, R=R_REPLICAS, c=1.0 / (2.0 * math.sqrt(N_SPINS)),
+                                   dt=DT, A=A, seed=1, precision="fx32", defer=True,
+                                   profile=prof, stream=stream.cuda_stream)
+        run = mk(M, False)
         run.restart(2)
         e0, e1 = _events(torch, stream)
         e0.record(stream)
         run.restart(3)
         e1.record(stream)
         e1.synchronize()
-        kms, kn, ksteps = run.kernel_time()
-        us = 1e3 * kms / ksteps
+        us = kernel_us(mk, min(M, 500))
         out["fx32"] = {"workload": f"{WORKLOAD}, GbSB on FX32, M={M}",
                        "value": N_SPINS * R_REPLICAS * M / (e0.elapsed_time(e1) / 1e3),
                        "unit": "spin-updates/s", "kernel": run.kernel(), "us_per_step": us,
@@ -442,8 +464,9 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         P = gsb.Problem.dense(J, stream=stream.cuda_stream)
         M, pairs = leg_M or 21500, 100
         c = 1.0 / (2.0 * math.sqrt(N_SPINS))
-        tw = P.twin_run("gbsb", M=M, R=pairs, A_values=A_VALUES, c=c, dt=DT, seed=1,
-                        profile=True, stream=stream.cuda_stream)
+        mk = lambda m, prof: P.twin_run("gbsb", M=m, R=pairs, A_values=A_VALUES, c=c, dt=DT,
+                                        seed=1, profile=prof, stream=stream.cuda_stream)
+        tw = mk(M, False)
         tw.steps(20)  # warm-up
         tw.restart(2, defer=True)
         e0, e1 = _events(torch, stream)
@@ -453,8 +476,7 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
-        kms, kn, ksteps = tw.kernel_time()
-        us = 1e3 * kms / ksteps
+        us = kernel_us(mk, 500)
         reps = 2 * pairs * len(A_VALUES)
         # FX32: four bf16 digit planes, 2 N^2 flops per plane and replica
         tflops = 4 * 2.0 * N_SPINS ** 2 * reps / (us * 1e-6) / 1e12
