@@ -21,11 +21,14 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Poll until poll() holds or limit_ns have passed; on expiry set the timeout
-// bit (1) in *status and return false. The first poll is free of timer reads.
-// A cap on the polls bounds the loop even if the timer were not to advance.
+// bit (1) in *status and return false. The first 64 polls read no timer (a
+// wait on the hot path is over by then). A cap on the polls bounds the loop
+// even if the timer were not to advance.
 template <typename Poll>
 __device__ __forceinline__ bool bounded_wait(Poll poll, int* status, uint64_t limit_ns) {
-    if (poll()) return true;
+#pragma unroll 1
+    for (int i = 0; i < 64; ++i)
+        if (poll()) return true;
     const uint64_t t0 = global_ns();
 #pragma unroll 1
     for (uint32_t round = 0; round < (1u << 22); ++round) {
