@@ -286,8 +286,10 @@ gsb_status gsb_energy_noalloc(const float* J, int32_t N, const int8_t* spins, in
  * the library's kernels (on an mbarrier, a counter another CTA advances, a
  * barrier of a thread-block cluster) gives up after a time limit, sets a
  * status word and lets the kernel return, so a lost arrival ends the call with
- * GSB_ETIMEOUT instead of hanging the GPU. This entry runs one such wait, with
- * limit_ns (1 us .. 10 s) of device time, in a one-warp kernel on `stream`:
+ * GSB_ETIMEOUT instead of hanging the GPU (the kernels' limit is 8e9 SM clock
+ * cycles, about 4 s). This entry runs one such wait, limited to limit_ns
+ * (1 us .. 10 s) worth of cycles at the device's rated SM clock, in a one-warp
+ * kernel on `stream`:
  * kind 0 waits on an mbarrier nobody arrives on, kind 1 on a counter in global
  * memory nobody advances -- both return GSB_ETIMEOUT after about limit_ns --
  * and kind 2 on a counter that already holds (GSB_OK at once). The CUDA

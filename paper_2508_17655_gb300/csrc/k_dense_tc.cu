@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // no copy in flight when the CTA leaves
             for (int kc = armed > S ? armed - S : 0; kc < armed; ++kc)
-                mbar_wait(&full[kc % S], (uint32_t)(kc / S) & 1u, status, kDrainLimitNs);
+                mbar_wait(&full[kc % S], (uint32_t)(kc / S) & 1u, status, kDrainLimitCycles);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (ok) mma_commit(accf);
             // every MMA issued has finished before TMEM is released
             mma_commit(drain);
-            mbar_wait(drain, 0, status, kDrainLimitNs);
+            mbar_wait(drain, 0, status, kDrainLimitCycles);
         }
     } else {
         // epilogue: warp w owns TMEM lanes 32 (w % 4) .. +31
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             // no copy is in flight when the CTA leaves: the last phase armed on
             // every stage has landed
             for (uint32_t gg = armed > (uint32_t)S ? armed - S : 0u; gg < armed; ++gg)
-                mbar_wait(&full[gg % S], (gg / S) & 1u, status, kDrainLimitNs);
+                mbar_wait(&full[gg % S], (gg / S) & 1u, status, kDrainLimitCycles);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             }
             // every MMA issued has finished before TMEM is released
             mma_commit(drain);
-            mbar_wait(drain, 0, status, kDrainLimitNs);
+            mbar_wait(drain, 0, status, kDrainLimitCycles);
         }
     } else {
         const int ew = warp - 2;
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             }
             // no copy in flight when the CTA leaves
             for (int kc = armed > S ? armed - S : 0; kc < armed; ++kc)
-                mbar_wait(&full[kc % S], (uint32_t)(kc / S) & 1u, status, kDrainLimitNs);
+                mbar_wait(&full[kc % S], (uint32_t)(kc / S) & 1u, status, kDrainLimitCycles);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(kThreadsF, 1)
             if (ok) mma_commit(accf);
             // every MMA issued has finished before TMEM is released
             mma_commit(drain);
-            mbar_wait(drain, 0, status, kDrainLimitNs);
+            mbar_wait(drain, 0, status, kDrainLimitCycles);
         }
     } else {
         const int ew = warp - 2;

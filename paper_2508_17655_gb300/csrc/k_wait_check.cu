@@ -15,15 +15,15 @@ using namespace tc;
 // kind 0: an mbarrier of count 1 that nobody arrives on; kind 1: a counter in
 // global memory waited on for a value nobody adds; kind 2: the counter already
 // at its target (completes at once).
-__global__ void k_wait_check(int kind, uint64_t limit_ns, const uint32_t* ctr, int* status) {
+__global__ void k_wait_check(int kind, uint64_t limit_cycles, const uint32_t* ctr, int* status) {
     __shared__ uint64_t bar;
     if (threadIdx.x != 0) return;
     if (kind == 0) {
         mbar_init(&bar, 1);
         fence_barrier_init();
-        mbar_wait(&bar, 0, status, limit_ns);
+        mbar_wait(&bar, 0, status, limit_cycles);
     } else {
-        wait_counter(ctr, kind == 1 ? 1u : 0u, status, limit_ns);
+        wait_counter(ctr, kind == 1 ? 1u : 0u, status, limit_cycles);
     }
 }
 
@@ -38,6 +38,11 @@ extern "C" gsb_status gsb_wait_check(int32_t kind, int64_t limit_ns, void* strea
     if (limit_ns < 1000 || limit_ns > 10000000000ll)
         return set_error(GSB_EINVAL, "limit_ns must be in [1 us, 10 s]");
     cudaStream_t s = (cudaStream_t)stream;
+    // the waits count SM clock cycles: the limit at the device's rated clock
+    int dev = 0, khz = 0;
+    GSB_CUDA_TRY(cudaGetDevice(&dev));
+    GSB_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const uint64_t limit_cycles = (uint64_t)((double)limit_ns * (double)khz * 1e-6) + 1;
     uint32_t* ctr = nullptr;
     int* status = nullptr;
     GSB_CUDA_TRY(cudaMalloc(&ctr, sizeof(uint32_t)));
@@ -53,7 +58,7 @@ extern "C" gsb_status gsb_wait_check(int32_t kind, int64_t limit_ns, void* strea
             st = cuda_error(cudaGetLastError(), "memset");
             break;
         }
-        k_wait_check<<<1, 32, 0, s>>>(kind, (uint64_t)limit_ns, ctr, status);
+        k_wait_check<<<1, 32, 0, s>>>(kind, limit_cycles, ctr, status);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess)

@@ -7,35 +7,25 @@
 namespace gsb {
 namespace tc {
 
-// Every device-side wait gives up after this much %globaltimer time (ns) and
+// Every device-side wait gives up after this many SM clock cycles (about 4 s
+// at the 2 GHz clock; clock64 is a register read, unlike the global timer, so
+// a waiting thread can check it often without slowing its response) and
 // reports a timeout in the status word; no wait of a correct run comes near it.
-constexpr uint64_t kWaitLimitNs = 4000000000ull;
+constexpr uint64_t kWaitLimitCycles = 8000000000ull;
 // Limit of the waits a CTA makes before it leaves, for its own copies and MMAs
-// to finish (they complete in microseconds once issued).
-constexpr uint64_t kDrainLimitNs = 200000000ull;
+// to finish (they complete in microseconds once issued): about 0.2 s.
+constexpr uint64_t kDrainLimitCycles = 400000000ull;
 
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Poll until poll() holds or limit_ns have passed; on expiry set the timeout
-// bit (1) in *status and return false. The first 64 polls read no timer (a
-// wait on the hot path is over by then). A cap on the polls bounds the loop
-// even if the timer were not to advance.
+// Poll until poll() holds or limit_cycles have passed; on expiry set the
+// timeout bit (1) in *status and return false.
 template <typename Poll>
-__device__ __forceinline__ bool bounded_wait(Poll poll, int* status, uint64_t limit_ns) {
+__device__ __forceinline__ bool bounded_wait(Poll poll, int* status, uint64_t limit_cycles) {
+    const long long t0 = clock64();
+    for (;;) {
 #pragma unroll 1
-    for (int i = 0; i < 64; ++i)
-        if (poll()) return true;
-    const uint64_t t0 = global_ns();
-#pragma unroll 1
-    for (uint32_t round = 0; round < (1u << 22); ++round) {
-#pragma unroll 1
-        for (int i = 0; i < 32; ++i)
+        for (int i = 0; i < 16; ++i)
             if (poll()) return true;
-        if (global_ns() - t0 > limit_ns) break;
+        if ((uint64_t)(clock64() - t0) > limit_cycles) break;
     }
     atomicOr(status, 1);
     return false;
@@ -74,10 +64,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait for the phase with the given parity; false (and the timeout
-// bit in *status) if it did not complete within limit_ns.
+// bit in *status) if it did not complete within limit_cycles.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status,
-                                          uint64_t limit_ns = kWaitLimitNs) {
-    return bounded_wait([&] { return mbar_try_wait(bar, parity); }, status, limit_ns);
+                                          uint64_t limit_cycles = kWaitLimitCycles) {
+    return bounded_wait([&] { return mbar_try_wait(bar, parity); }, status, limit_cycles);
 }
 
 // Wait on a barrier that other CTAs of the cluster arrive on: acquire at
@@ -94,8 +84,8 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
     return ok != 0;
 }
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* status,
-                                                  uint64_t limit_ns = kWaitLimitNs) {
-    return bounded_wait([&] { return mbar_try_wait_cluster(bar, parity); }, status, limit_ns);
+                                                  uint64_t limit_cycles = kWaitLimitCycles) {
+    return bounded_wait([&] { return mbar_try_wait_cluster(bar, parity); }, status, limit_cycles);
 }
 // Arrive (release at cluster scope) on the barrier at the offset of bar in the
 // shared memory of the cluster's CTA with rank cta.
@@ -296,8 +286,8 @@ __device__ __forceinline__ void fence_proxy_async() {
 }
 // Bounded wait until *addr >= target; false (timeout bit in *status) on expiry.
 __device__ __forceinline__ bool wait_counter(const uint32_t* addr, uint32_t target, int* status,
-                                             uint64_t limit_ns = kWaitLimitNs) {
-    return bounded_wait([&] { return ld_acquire(addr) >= target; }, status, limit_ns);
+                                             uint64_t limit_cycles = kWaitLimitCycles) {
+    return bounded_wait([&] { return ld_acquire(addr) >= target; }, status, limit_cycles);
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA
