@@ -22,7 +22,8 @@ template <typename Poll>
 __device__ __forceinline__ bool bounded_wait(Poll poll, int* status, uint64_t limit_cycles) {
     const long long t0 = clock64();
     for (;;) {
-#pragma unroll 1
+        // unrolled by the compiler: several polls in flight at once, which
+        // measurably shortens the time from the condition to its detection
         for (int i = 0; i < 16; ++i)
             if (poll()) return true;
         if ((uint64_t)(clock64() - t0) > limit_cycles) break;
