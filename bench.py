@@ -274,7 +274,7 @@ def gpu_arm(args, world, rank, local):
                 # of this shape (100 steps; profiles/k_tc_persist_N2000_R1024_M100.md):
                 # the state, J and V read once per launch, whatever its step count --
                 # the steps themselves run from L2 and TMEM
-                "traffic": 31490560 + 741632,
+                "traffic": 31493376 + 890112,
                 "traffic_note": "DRAM bytes per launch, measured on a 100-step launch of the "
                                 "same kernel and shape; independent of the steps per launch",
                 "peak_source": f"{how}: 2 x bf16 sustained (e4m3/bf16 nominal ratio)",
