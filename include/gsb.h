@@ -133,6 +133,16 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
                       const float* h, uint32_t flags, void* stream);
 gsb_status gsb_destroy(gsb_problem* problem);
 
+/* Device memory: the blocks of destroyed problems and runs are kept (up to
+ * 1 GiB in all) and handed to the next problem or run that needs a block of the
+ * same size on the same device, so creating one of the same shape again costs
+ * no cudaMalloc / cudaFree. gsb_destroy waits for the device to be idle, and
+ * gsb_run_destroy for the run's stream, before their blocks are kept. This call
+ * returns every kept block to CUDA (for an application that needs the memory).
+ * Host side only; not to be called while another thread creates or destroys
+ * handles. */
+gsb_status gsb_release_cached_memory(void);
+
 /* Number of spins (including the auxiliary one when h was given) and the
  * extreme eigenvalues of J used for c and dt (computed on the GPU on first use
  * by the Lanczos method in FP64, to 1e-14 relative stationarity of the Ritz

@@ -8,6 +8,9 @@
 #include <limits>
 #include <string>
 #include <vector>
+#include <map>
+#include <mutex>
+#include <unordered_map>
 
 #include "gsb_internal.cuh"
 
@@ -30,6 +33,86 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
+// ---- device block cache (see cache_alloc in gsb_internal.cuh)
+struct BlockCache {
+    std::mutex mu;
+    std::map<std::pair<int, size_t>, std::vector<void*>> free;  // (device, bytes) -> blocks
+    std::unordered_map<void*, std::pair<int, size_t>> live;      // blocks handed out
+    size_t cached = 0;
+};
+BlockCache& block_cache() {
+    static BlockCache* c = new BlockCache();  // never destroyed: outlives every handle
+    return *c;
+}
+constexpr size_t kCacheCap = (size_t)1 << 30;
+
+}  // namespace
+
+void* cache_alloc(size_t bytes) {
+    if (bytes == 0) return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    const size_t b = (bytes + 511) & ~(size_t)511;
+    BlockCache& c = block_cache();
+    {
+        std::lock_guard<std::mutex> g(c.mu);
+        auto it = c.free.find({dev, b});
+        if (it != c.free.end() && !it->second.empty()) {
+            void* p = it->second.back();
+            it->second.pop_back();
+            c.cached -= b;
+            c.live[p] = {dev, b};
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, b) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(c.mu);
+    c.live[p] = {dev, b};
+    return p;
+}
+
+void cache_free(void* p) {
+    if (!p) return;
+    BlockCache& c = block_cache();
+    std::lock_guard<std::mutex> g(c.mu);
+    auto it = c.live.find(p);
+    if (it == c.live.end()) {
+        cudaFree(p);
+        return;
+    }
+    const std::pair<int, size_t> key = it->second;
+    c.live.erase(it);
+    if (c.cached + key.second <= kCacheCap) {
+        c.free[key].push_back(p);
+        c.cached += key.second;
+    } else {
+        cudaFree(p);
+    }
+}
+
+gsb_status cache_release() {
+    BlockCache& c = block_cache();
+    std::lock_guard<std::mutex> g(c.mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaError_t err = cudaSuccess;
+    for (auto& kv : c.free) {
+        if (kv.second.empty()) continue;
+        cudaSetDevice(kv.first.first);
+        for (void* q : kv.second) {
+            const cudaError_t e = cudaFree(q);
+            if (e != cudaSuccess) err = e;
+        }
+    }
+    if (!c.free.empty()) cudaSetDevice(cur);
+    c.free.clear();
+    c.cached = 0;
+    return err == cudaSuccess ? GSB_OK : cuda_error(err, "cudaFree");
+}
+
+namespace {
+
 gsb_status check_device(int* dev_out) {
     int dev = 0;
     GSB_CUDA_TRY(cudaGetDevice(&dev));
@@ -40,14 +123,6 @@ gsb_status check_device(int* dev_out) {
                                          std::string(prop.name) + " is sm_" +
                                          std::to_string(prop.major) + std::to_string(prop.minor));
     *dev_out = dev;
-    return GSB_OK;
-}
-
-template <typename T>
-gsb_status dev_alloc(T** p, size_t count) {
-    *p = nullptr;
-    if (count == 0) return GSB_OK;
-    GSB_CUDA_TRY(cudaMalloc((void**)p, sizeof(T) * count));
     return GSB_OK;
 }
 
@@ -74,12 +149,15 @@ bool is_integer(float v) { return v == nearbyintf(v); }
 
 void free_problem(gsb_problem* P) {
     if (!P) return;
-    cudaFree(P->J32);
-    cudaFree(P->J8);
-    cudaFree(P->J16);
-    cudaFree(P->rowptr);
-    cudaFree(P->col);
-    cudaFree(P->val);
+    // runs on any stream may still read J: the blocks are reused only once the
+    // device is idle (as a cudaFree would have waited)
+    cudaDeviceSynchronize();
+    dev_free(P->J32);
+    dev_free(P->J8);
+    dev_free(P->J16);
+    dev_free(P->rowptr);
+    dev_free(P->col);
+    dev_free(P->val);
     delete P;
 }
 
@@ -165,7 +243,8 @@ gsb_status create_dense(gsb_problem* P, const T* Jr, const float* h, bool valida
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hs.data(), stats, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(stats);
+    cudaStreamSynchronize(s);
+    dev_free(stats);
     if (e != cudaSuccess) return set_error(GSB_ECUDA, std::string("preparing J: ") + cudaGetErrorString(e));
     unsigned fw[2];
     memcpy(fw, &hs[2 * (size_t)N], sizeof(fw));
@@ -289,25 +368,26 @@ std::vector<T> fetch(const T* p, size_t n, bool device) {
 
 void free_run(gsb_run_state* r) {
     if (!r) return;
+    cudaStreamSynchronize(r->stream);  // nothing of the run is in flight
     if (r->tc) tc_free(r);
     for (int b = 0; b < 2; ++b) {
-        cudaFree(r->x[b]);
-        cudaFree(r->s8[b]);
-        cudaFree(r->v8[b]);
-        cudaFree(r->v16[b]);
+        dev_free(r->x[b]);
+        dev_free(r->s8[b]);
+        dev_free(r->v8[b]);
+        dev_free(r->v16[b]);
     }
-    cudaFree(r->y);
-    cudaFree(r->p);
-    cudaFree(r->A);
-    cudaFree(r->twin_part);
-    cudaFree(r->sched);
-    cudaFree(r->e_acc);
-    cudaFree(r->best_e);
-    cudaFree(r->best_step);
-    cudaFree(r->best_s);
-    cudaFree(r->best_out);
-    cudaFree(r->flag);
-    cudaFree(r->status);
+    dev_free(r->y);
+    dev_free(r->p);
+    dev_free(r->A);
+    dev_free(r->twin_part);
+    dev_free(r->sched);
+    dev_free(r->e_acc);
+    dev_free(r->best_e);
+    dev_free(r->best_step);
+    dev_free(r->best_s);
+    dev_free(r->best_out);
+    dev_free(r->flag);
+    dev_free(r->status);
     for (cudaEvent_t e : r->prof_events) cudaEventDestroy(e);
     delete r;
 }
@@ -430,17 +510,18 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
         float* hd = nullptr;
         cudaError_t e = cudaSuccess;
         if (!device_in) {
-            e = cudaMalloc(&Jd, nb);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(Jd, J, nb, cudaMemcpyHostToDevice, s);
+            Jd = cache_alloc(nb);
+            e = Jd ? cudaMemcpyAsync(Jd, J, nb, cudaMemcpyHostToDevice, s) : cudaErrorMemoryAllocation;
         }
         if (e == cudaSuccess && h) {
-            e = cudaMalloc(&hd, sizeof(float) * N);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(hd, hv.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s);
+            hd = (float*)cache_alloc(sizeof(float) * N);
+            e = hd ? cudaMemcpyAsync(hd, hv.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s)
+                   : cudaErrorMemoryAllocation;
         }
         if (e != cudaSuccess) {
-            cudaFree(Jd);
-            cudaFree(hd);
+            cudaStreamSynchronize(s);
+            dev_free(Jd);
+            dev_free(hd);
             free_problem(P);
             return set_error(GSB_ECUDA, std::string("uploading J: ") + cudaGetErrorString(e));
         }
@@ -450,8 +531,8 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
         else
             st = create_dense(P, (const float*)Jsrc, hd, validate, s);
         cudaStreamSynchronize(s);  // the temporaries may be in use by the conversion
-        cudaFree(Jd);
-        cudaFree(hd);
+        dev_free(Jd);
+        dev_free(hd);
     } else if (format == GSB_J_CSR_F32) {
         if (J || !rowptr || (nnz > 0 && (!col || !val)) || nnz < 0) {
             free_problem(P);
@@ -479,6 +560,8 @@ gsb_status gsb_destroy(gsb_problem* problem) {
     free_problem(problem);
     return GSB_OK;
 }
+
+gsb_status gsb_release_cached_memory(void) { return cache_release(); }
 
 gsb_status gsb_problem_info(gsb_problem* P, int32_t* n_spins, double* lmax, double* lmin,
                             void* stream) {
@@ -615,8 +698,8 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
     st = launch_init_state(run, x0d, y0d);
     if (x0d || y0d) {
         cudaStreamSynchronize(s);
-        cudaFree(x0d);
-        cudaFree(y0d);
+        dev_free(x0d);
+        dev_free(y0d);
     }
     if (st != GSB_OK) return fail(st);
     if (path == kPathTcFp8 || path == kPathTcFx32) {
@@ -749,7 +832,8 @@ gsb_status gsb_get_state(gsb_run_state* run, float* x, float* y, float* p, int32
             for (size_t k = 0; k < (size_t)R * N; ++k) it.dst[k] = pv;
         }
     }
-    cudaFree(tmp);
+    cudaStreamSynchronize(run->stream);
+    dev_free(tmp);
     if (st != GSB_OK) return st;
     if (steps_done) *steps_done = run->steps_done;
     return check_status_word(run);
@@ -768,9 +852,9 @@ gsb_status gsb_energy(gsb_problem* P, int32_t R, const int8_t* spins, double* en
     gsb_status st = GSB_OK;
     if ((st = dev_alloc(&sd, (size_t)R * P->N)) || (st = dev_alloc(&xd, nst)) ||
         (st = dev_alloc(&acc, Rp))) {
-        cudaFree(sd);
-        cudaFree(xd);
-        cudaFree(acc);
+        dev_free(sd);
+        dev_free(xd);
+        dev_free(acc);
         return st;
     }
     std::vector<double> h(R);
@@ -796,9 +880,9 @@ gsb_status gsb_energy(gsb_problem* P, int32_t R, const int8_t* spins, double* en
         for (int r = 0; r < R; ++r) energies[r] = -0.5 * h[r];
     } while (0);
     cudaStreamSynchronize(s);
-    cudaFree(sd);
-    cudaFree(xd);
-    cudaFree(acc);
+    dev_free(sd);
+    dev_free(xd);
+    dev_free(acc);
     return st;
 }
 

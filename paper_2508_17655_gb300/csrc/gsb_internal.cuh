@@ -151,6 +151,26 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
 }
 
+// Device memory of problems and runs. Blocks freed by a destroyed problem or
+// run (after the GPU is done with them) are kept, up to 1 GiB, for the next
+// allocation of the same size on the same device, so creating a problem and a
+// run of the same shape again allocates nothing. cache_free returns a block
+// that did not come from cache_alloc straight to CUDA.
+void* cache_alloc(size_t bytes);
+void cache_free(void* p);
+gsb_status cache_release();
+
+template <typename T>
+gsb_status dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return GSB_OK;
+    *p = (T*)cache_alloc(sizeof(T) * count);
+    if (!*p) return set_error(GSB_ENOMEM, "device allocation of " +
+                                              std::to_string(sizeof(T) * count) + " bytes");
+    return GSB_OK;
+}
+inline void dev_free(void* p) { cache_free(p); }
+
 #define GSB_LAUNCH_CHECK(what)                                 \
     do {                                                       \
         ::gsb::count_launch();                                 \

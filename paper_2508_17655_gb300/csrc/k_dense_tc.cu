@@ -910,14 +910,16 @@ gsb_status tc_setup(gsb_run_state* run) {
     const size_t n = (size_t)run->Np * run->Rp;
     gsb_status st;
     if (T->kind == 0) {
-        for (int b = 0; b < 2; ++b) GSB_CUDA_TRY(cudaMalloc(&run->v8[b], n));
+        for (int b = 0; b < 2; ++b)
+            if ((st = dev_alloc(&run->v8[b], n))) return st;
         if ((st = make_map(&T->tmA, P->J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P->Np, P->Np))) return st;
         for (int b = 0; b < 2; ++b)
             if ((st = make_map(&T->tmB[b], run->v8[b], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, run->Np,
                                run->Rp)))
                 return st;
     } else {
-        for (int b = 0; b < 2; ++b) GSB_CUDA_TRY(cudaMalloc(&run->v16[b], 4 * n * sizeof(__nv_bfloat16)));
+        for (int b = 0; b < 2; ++b)
+            if ((st = dev_alloc(&run->v16[b], 4 * n))) return st;
         if ((st = make_map(&T->tmA, P->J16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, P->Np, P->Np)))
             return st;
         for (int b = 0; b < 2; ++b)
@@ -966,13 +968,13 @@ gsb_status tc_setup(gsb_run_state* run) {
             T->persistent = T->cluster = true;
         } else if (grid_fits) {
             T->persistent = true;
-            GSB_CUDA_TRY(cudaMalloc(&T->counters, sizeof(uint32_t) * nrb));
+            if ((st = dev_alloc(&T->counters, (size_t)nrb))) return st;
         }
     }
     if (T->persistent) {
         std::vector<float> ps(run->params.M);
         for (int m = 0; m < run->params.M; ++m) ps[m] = run_p_shared(run, m + 1);
-        GSB_CUDA_TRY(cudaMalloc(&T->p_sched, sizeof(float) * run->params.M));
+        if ((st = dev_alloc(&T->p_sched, (size_t)run->params.M))) return st;
         GSB_CUDA_TRY(cudaMemcpy(T->p_sched, ps.data(), sizeof(float) * run->params.M,
                                 cudaMemcpyHostToDevice));
     }
@@ -1078,8 +1080,8 @@ gsb_status tc_energy(gsb_run_state* run) {
 void tc_free(gsb_run_state* run) {
     TcState* T = (TcState*)run->tc;
     if (T) {
-        cudaFree(T->counters);
-        cudaFree(T->p_sched);
+        dev_free(T->counters);
+        dev_free(T->p_sched);
     }
     delete T;
     run->tc = nullptr;

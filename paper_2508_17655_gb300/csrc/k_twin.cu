@@ -79,9 +79,9 @@ extern "C" gsb_status gsb_twin_run(gsb_problem* P, const gsb_params* prm, int32_
     run->params.A_per_replica = nullptr;
     run->twin_pairs = npairs;
     const size_t nbuf = ((size_t)twin_chunks(run->N) + 1) * npairs;
-    if (cudaMalloc(&run->twin_part, nbuf * sizeof(double)) != cudaSuccess) {
+    if ((st = dev_alloc(&run->twin_part, nbuf)) != GSB_OK) {
         gsb_run_destroy(run);
-        return set_error(GSB_ENOMEM, "twin distance buffer");
+        return st;
     }
     st = launch_init_state(run, nullptr, nullptr);
     if (st == GSB_OK && (run->path == kPathTcFp8 || run->path == kPathTcFx32)) st = tc_prepare(run);

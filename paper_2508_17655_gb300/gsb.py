@@ -137,6 +137,8 @@ def _declare(L):
     L.gsb_energy_noalloc.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
     L.gsb_run_destroy.restype = st
+    L.gsb_release_cached_memory.argtypes = []
+    L.gsb_release_cached_memory.restype = st
     L.gsb_wait_check.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp]
     L.gsb_wait_check.restype = st
     L.gsb_last_error.argtypes = []
@@ -162,6 +164,11 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def release_cached_memory():
+    """Return the device blocks the library keeps for reuse to CUDA."""
+    _check(lib().gsb_release_cached_memory())
 
 
 def wait_check(kind, limit_ns, stream=None):

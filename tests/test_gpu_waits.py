@@ -51,3 +51,36 @@ def test_wait_check_rejects_bad_arguments():
     with pytest.raises(gsb.GsbError) as e:
         gsb.wait_check(0, 10)
     assert e.value.status == gsb.EINVAL
+
+
+def test_reused_device_blocks_give_identical_runs():
+    """Problems and runs created again with the same shape take the blocks the
+    destroyed ones left (no cudaMalloc); whatever those blocks held, the new run
+    follows the same trajectory (every buffer the step kernels read is written
+    first), on the FP8, FX32, FP32 and CSR paths, and after the cache is
+    returned to CUDA."""
+    def once(kind):
+        if kind == "csr":
+            rp, col, val = I.er_graph(300, 12, "pm1", 2)
+            P = gsb.Problem.csr(300, rp, col, val)
+            run = P.run("gdsb", M=120, R=200, c=0.05, dt=0.8, A=0.3, seed=6, eval_every=40)
+        else:
+            variant, prec = {"fp8": ("gdsb", "fp8"), "fx32": ("gbsb", "fx32"),
+                             "fp32": ("gbsb", "fp32")}[kind]
+            P = gsb.Problem.dense(I.sk_pm1(300, 2))
+            run = P.run(variant, M=120, R=200, c=0.03, dt=1.0, A=0.3, seed=6, precision=prec,
+                        eval_every=40)
+        b, st = run.best(), run.state()
+        run.close()
+        P.close()
+        return b, st
+    for kind in ("fp8", "fx32", "fp32", "csr"):
+        first = once(kind)
+        again = once(kind)
+        for k in ("E", "s", "step"):
+            np.testing.assert_array_equal(first[0][k], again[0][k])
+        for k in ("x", "y", "p"):
+            np.testing.assert_array_equal(first[1][k], again[1][k])
+    gsb.release_cached_memory()
+    after = once("fp8")
+    np.testing.assert_array_equal(after[0]["E"], once("fp8")[0]["E"])
