@@ -366,7 +366,7 @@ def _events(torch, stream):
 
 
 LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "adjoint", "fx32",
-        "twin_delta", "grid")
+        "twin_delta", "grid", "twin_valley")
 
 
 def fp32_alu_peak(Pk):
@@ -524,6 +524,28 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
                          "frac": tf / (2.0 * Pk["bf16_tflops_sustained"]),
                          "peak_source": how + " (2 x bf16 sustained, e4m3)"}}
         P.close()
+    # --- delta(t_M) over (Delta_t, t_M) at A = 0.2 (Fig. 1(j), the "valley of chaos"), the
+    # K2000 shape, 100 twin pairs per cell; only on request (--leg twin_valley)
+    if only == "twin_valley":
+        from paper_2508_17655_gb300 import sweep
+        J = I.sk_pm1(N_SPINS, 0)
+        P = gsb.Problem.dense(J, stream=stream.cuda_stream)
+        dts = [0.5, 0.75, 1.0, 1.25]
+        tMs = [1250.0, 2500.0, 5000.0, 10000.0, 26875.0]
+        t = time.perf_counter()
+        g = sweep.delta_grid_dt(P, "gbsb", dts, tMs, 0.2, 100, c=1.0 / (2.0 * math.sqrt(N_SPINS)),
+                                seed=5, stream=stream.cuda_stream)
+        el = time.perf_counter() - t
+        su = float(N_SPINS * 200 * np.sum(g["M"]))
+        out["twin_valley"] = {
+            "workload": f"N={N_SPINS} +-1 complete graph, GbSB, A=0.2, 100 twin pairs per cell, "
+                        f"dt in {dts} x t_M in {tMs}",
+            "value": su / el, "unit": "spin-updates/s",
+            "how": "host wall clock around the whole grid (run creation to distances)",
+            "dt": dts, "t_M": tMs, "M": g["M"].tolist(),
+            "mean_delta_tM": g["delta_mean"].tolist()}
+        P.close()
+        return out
     if only is not None and only not in ("batched_256", "lyapunov", "adjoint"):
         return out
     # --- 256 batched uneven SK instances, N ~ U{64..1024}, R ~ U{32..256}, M = 1000
