@@ -76,6 +76,7 @@ int main(void) {
     if (gsb_twin_delta(NULL, NULL) != GSB_EINVAL) return 8;
     if (gsb_wait_check(7, 1000000, NULL) != GSB_EINVAL) return 9;
     if (strcmp(gsb_run_kernel(NULL), "") != 0) return 10;
+    if (gsb_release_cached_memory() != GSB_OK) return 11;  /* nothing kept yet */
     printf("ok\n");
     return 0;
 }
