@@ -43,3 +43,34 @@ def test_delta_grid_equals_twin_runs():
         _, d = P.twin_delta("gbsb", M, pairs, As, c=0.05, dt=0.5, seed=4)
         np.testing.assert_array_equal(g["delta"][i], d[-1])
         np.testing.assert_array_equal(g["delta_mean"][i], d[-1].mean(axis=1))
+
+
+def test_delta_grid_dt_equals_twin_runs():
+    """The (dt, t_M) grid of Fig. 1(j): each cell is a twin run with
+    M = round(t_M / dt) steps, its mean distance that run's."""
+    N, pairs = 120, 24
+    J = I.sk_pm1(N, 2)
+    P = gsb.Problem.dense(J)
+    dts, tMs = [0.5, 1.25], [25.0, 60.0]
+    g = sweep.delta_grid_dt(P, "gbsb", dts, tMs, 0.3, pairs, c=0.05, seed=8)
+    assert g["M"].tolist() == [[50, 120], [20, 48]]
+    for a, dt in enumerate(dts):
+        for b, tM in enumerate(tMs):
+            M = int(round(tM / dt))
+            _, d = P.twin_delta("gbsb", M, pairs, [0.3], c=0.05, dt=dt, seed=8)
+            assert g["delta_mean"][a, b] == float(d[-1][0].mean())
+
+
+def test_success_grid_dt_cells_are_runs():
+    N, reps = 100, 64
+    J = I.sk_pm1(N, 0)
+    P = gsb.Problem.dense(J)
+    dts, tMs = [0.5, 1.0], [100.0]
+    g = sweep.success_grid_dt(P, "gdsb", dts, tMs, 0.2, reps, -600.0, c=0.05, seed=3)
+    for a, dt in enumerate(dts):
+        M = int(round(100.0 / dt))
+        run = P.run("gdsb", M=M, R=reps, c=0.05, dt=dt, A=0.2, seed=3)
+        E = run.best()["E"]
+        run.close()
+        assert g["mean_E"][a, 0] == pytest.approx(float(E.mean()), rel=1e-14)
+        assert g["P_S"][a, 0] == float(np.mean(E <= -600.0 + 1e-9))
