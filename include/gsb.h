@@ -192,6 +192,19 @@ gsb_status gsb_best(gsb_run_state* run, int8_t* spins, double* energies, double*
  * done so far. For bSB/dSB, p holds the shared parameter in every entry. */
 gsb_status gsb_get_state(gsb_run_state* run, float* x, float* y, float* p, int32_t* steps_done);
 
+/* Checkpoint / resume (not in the paper): put a run at step steps_done
+ * (0..M) with the state x, y (and p for GbSB / GdSB; ignored otherwise), host
+ * R x n_spins each in the layout gsb_get_state returns, and optionally the best
+ * records as gsb_best returns them (spins R x N, energies R, step found R; all
+ * three or none: none clears them). gsb_run_steps then continues exactly as the
+ * run the state was taken from would have: a run stopped after k steps, saved
+ * with gsb_get_state and gsb_best, and restored into a fresh deferred run of the
+ * same problem and parameters ends bit-identical to one never interrupted.
+ * Blocks on the run's stream. */
+gsb_status gsb_run_set_state(gsb_run_state* run, const float* x, const float* y, const float* p,
+                             int32_t steps_done, const int8_t* best_spins,
+                             const double* best_energies, const int32_t* best_step);
+
 /* Ising energies (Eq. 1) of R caller spin vectors (host, R x N int8 +-1) into
  * energies (host, length R). Evaluated on the GPU. */
 gsb_status gsb_energy(gsb_problem* problem, int32_t R, const int8_t* spins, double* energies,

@@ -839,6 +839,69 @@ gsb_status gsb_get_state(gsb_run_state* run, float* x, float* y, float* p, int32
     return check_status_word(run);
 }
 
+gsb_status gsb_run_set_state(gsb_run_state* run, const float* x, const float* y, const float* p,
+                             int32_t steps_done, const int8_t* best_spins,
+                             const double* best_energies, const int32_t* best_step) {
+    if (!run || !x || !y) return set_error(GSB_EINVAL, "run, x and y are required");
+    if (steps_done < 0 || steps_done > run->params.M)
+        return set_error(GSB_EINVAL, "steps_done must be in 0..M");
+    if (run->control && !p) return set_error(GSB_EINVAL, "p is required for GbSB / GdSB");
+    const bool best = best_spins && best_energies && best_step;
+    if (!best && (best_spins || best_energies || best_step))
+        return set_error(GSB_EINVAL, "best records: all three or none");
+    const int R = run->R, N = run->N, Nu = run->prob->N_user;
+    cudaStream_t s = run->stream;
+    gsb_status st;
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = reset_bookkeeping(run))) return st;
+    float* tmp = nullptr;
+    int8_t* tmp8 = nullptr;
+    if ((st = dev_alloc(&tmp, (size_t)R * N))) return st;
+    struct Item {
+        const float* src;
+        float* dst;
+    } items[3] = {{x, run->x[0]}, {y, run->y}, {run->control ? p : nullptr, run->p}};
+    do {
+        for (const Item& it : items) {
+            if (!it.src) continue;
+            if (cudaMemcpyAsync(tmp, it.src, sizeof(float) * (size_t)R * N,
+                                cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                st = cuda_error(cudaGetLastError(), "copy state");
+                break;
+            }
+            if ((st = launch_rm_to_sm(tmp, it.dst, N, N, R, run->Np, run->Rp, s))) break;
+            // the stage is reused by the next array only after this transpose
+            if (cudaStreamSynchronize(s) != cudaSuccess) {
+                st = cuda_error(cudaGetLastError(), "copy state");
+                break;
+            }
+        }
+        if (st != GSB_OK || !best) break;
+        // best records: spins in the user layout (the auxiliary spin of h is +1)
+        if ((st = dev_alloc(&tmp8, (size_t)R * Nu))) break;
+        if (cudaMemcpyAsync(tmp8, best_spins, (size_t)R * Nu, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(run->best_e, best_energies, sizeof(double) * R,
+                            cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(run->best_step, best_step, sizeof(int32_t) * R,
+                            cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "copy best records");
+            break;
+        }
+        st = launch_rm_to_sm_i8(tmp8, run->best_s, Nu, N, R, run->Np, run->Rp, (int8_t)1, s);
+    } while (0);
+    cudaStreamSynchronize(s);
+    dev_free(tmp);
+    dev_free(tmp8);
+    if (st != GSB_OK) return st;
+    run->cur = 0;
+    run->steps_done = steps_done;
+    // operands derived from x: sgn x for the CSR sign coupling, V for the tensor cores
+    if (run->s8[0] && (st = launch_sign_extract(run))) return st;
+    if ((run->path == kPathTcFp8 || run->path == kPathTcFx32) && (st = tc_prepare(run))) return st;
+    return GSB_OK;
+}
+
 gsb_status gsb_energy(gsb_problem* P, int32_t R, const int8_t* spins, double* energies,
                       void* stream) {
     if (!P || !spins || !energies || R < 1) return set_error(GSB_EINVAL, "bad argument");

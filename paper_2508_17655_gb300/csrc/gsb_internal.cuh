@@ -182,6 +182,10 @@ inline void dev_free(void* p) { cache_free(p); }
 // init / util
 gsb_status launch_init_state(gsb_run_state* run, const float* x0_dev_rm, const float* y0_dev_rm);
 gsb_status launch_sign_extract(gsb_run_state* run);
+gsb_status launch_rm_to_sm(const float* src_rm, float* dst_sm, int ncols, int N, int R, int Np,
+                           int Rp, cudaStream_t s);
+gsb_status launch_rm_to_sm_i8(const int8_t* src_rm, int8_t* dst_sm, int ncols, int N, int R,
+                              int Np, int Rp, int8_t aux, cudaStream_t s);
 gsb_status launch_transpose_to_host_layout(const float* src_sm, float* dst_rm, int Np, int Rp,
                                            int N, int R, cudaStream_t s);
 gsb_status launch_transpose_i8_to_host_layout(const int8_t* src_sm, int8_t* dst_rm, int Np,

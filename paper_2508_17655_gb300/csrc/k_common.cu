@@ -117,6 +117,44 @@ __global__ void k_spins_in(const int8_t* __restrict__ s, float* __restrict__ x, 
     }
 }
 
+// Host-layout [R][ncols] (replica-major) to the spin-major state layout
+// [Np][Rp]: rows ncols .. N-1 (the auxiliary spin of the h augmentation) get
+// `aux`, padded spins and replicas get 0.
+template <typename T>
+__global__ void k_rm_to_sm(const T* __restrict__ src, T* __restrict__ dst, int ncols, int N, int R,
+                           int Rp, T aux) {
+    __shared__ T tile[32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, i = i0 + threadIdx.x;
+        T v = T(0);
+        if (r < R && i < ncols) v = src[(size_t)r * ncols + i];
+        else if (r < R && i < N) v = aux;
+        tile[k][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int i = i0 + k, r = r0 + threadIdx.x;
+        dst[(size_t)i * Rp + r] = tile[threadIdx.x][k];
+    }
+}
+
+gsb_status launch_rm_to_sm(const float* src, float* dst, int ncols, int N, int R, int Np, int Rp,
+                           cudaStream_t s) {
+    dim3 grid(Np / 32, Rp / 32), block(32, 8);
+    k_rm_to_sm<float><<<grid, block, 0, s>>>(src, dst, ncols, N, R, Rp, 0.f);
+    GSB_LAUNCH_CHECK("k_rm_to_sm");
+    return GSB_OK;
+}
+
+gsb_status launch_rm_to_sm_i8(const int8_t* src, int8_t* dst, int ncols, int N, int R, int Np,
+                              int Rp, int8_t aux, cudaStream_t s) {
+    dim3 grid(Np / 32, Rp / 32), block(32, 8);
+    k_rm_to_sm<int8_t><<<grid, block, 0, s>>>(src, dst, ncols, N, R, Rp, aux);
+    GSB_LAUNCH_CHECK("k_rm_to_sm");
+    return GSB_OK;
+}
+
 gsb_status launch_init_state(gsb_run_state* run, const float* x0_rm, const float* y0_rm) {
     const gsb_params& P = run->params;
     const float range = P.x0_range > 0.f ? P.x0_range : 0.1f;

@@ -137,6 +137,11 @@ def _declare(L):
     L.gsb_energy_noalloc.restype = st
     L.gsb_run_destroy.argtypes = [_vp]
     L.gsb_run_destroy.restype = st
+    L.gsb_run_set_state.argtypes = [_vp, ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                    ctypes.c_int32, ctypes.POINTER(ctypes.c_int8),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
+    L.gsb_run_set_state.restype = st
     L.gsb_release_cached_memory.argtypes = []
     L.gsb_release_cached_memory.restype = st
     L.gsb_wait_check.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp]
@@ -478,6 +483,22 @@ class Run:
         _check(lib().gsb_get_state(self.handle, _p(x, ctypes.c_float), _p(y, ctypes.c_float),
                                    _p(p, ctypes.c_float), ctypes.byref(done)))
         return {"x": x, "y": y, "p": p, "steps": done.value}
+
+    def set_state(self, state, best=None):
+        """Checkpoint / resume (gsb_run_set_state): state as returned by state()
+        (x, y, p, steps), best as returned by best() or None."""
+        x = np.ascontiguousarray(state["x"], dtype=np.float32)
+        y = np.ascontiguousarray(state["y"], dtype=np.float32)
+        p = None if state.get("p") is None else np.ascontiguousarray(state["p"], dtype=np.float32)
+        s = e = k = None
+        if best is not None:
+            s = np.ascontiguousarray(best["s"], dtype=np.int8)
+            e = np.ascontiguousarray(best["E"], dtype=np.float64)
+            k = np.ascontiguousarray(best["step"], dtype=np.int32)
+        _check(lib().gsb_run_set_state(self.handle, _p(x, ctypes.c_float), _p(y, ctypes.c_float),
+                                       _p(p, ctypes.c_float), int(state["steps"]),
+                                       _p(s, ctypes.c_int8), _p(e, ctypes.c_double),
+                                       _p(k, ctypes.c_int32)))
 
     def _n_state(self):
         n = ctypes.c_int32()

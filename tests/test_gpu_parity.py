@@ -447,3 +447,40 @@ def test_fp8_cluster_form_in_waves_matches_per_step_launches_bit_exact():
         assert np.array_equal(b["E"], outs[0][1]["E"])
         assert np.array_equal(b["s"], outs[0][1]["s"])
         assert np.array_equal(b["step"], outs[0][1]["step"])
+
+
+@pytest.mark.parametrize("kind", ["fp8", "fx32", "fp32", "csr", "h"])
+def test_checkpoint_resume_is_bit_identical(kind):
+    """A run stopped after 50 of 120 steps, saved (state and best records),
+    destroyed, and restored into a fresh deferred run of the same problem and
+    parameters ends bit-identical to the run never interrupted; energies are
+    evaluated every 20 steps, so the restored best records take part."""
+    M, R, k = 120, 200, 50
+    if kind == "csr":
+        rp, col, val = I.er_graph(300, 12, "pm1", 4)
+        P = gsb.Problem.csr(300, rp, col, val)
+        kw = dict(variant="gdsb", c=0.05, dt=0.8)
+    elif kind == "h":
+        N = 150
+        P = gsb.Problem.dense(I.sk_gauss(N, 4), h=np.random.default_rng(2).standard_normal(N).astype(np.float32) * 0.2)
+        kw = dict(variant="gbsb", c=0.5, dt=1.0)
+    else:
+        variant, prec = {"fp8": ("gdsb", "fp8"), "fx32": ("gbsb", "fx32"),
+                         "fp32": ("gbsb", "fp32")}[kind]
+        P = gsb.Problem.dense(I.sk_pm1(300, 4))
+        kw = dict(variant=variant, c=0.03, dt=1.0, precision=prec)
+    variant = kw.pop("variant")
+    whole = P.run(variant, M=M, R=R, A=0.3, seed=12, eval_every=20, **kw)
+    want_b, want_s = whole.best(), whole.state()
+    part = P.run(variant, M=M, R=R, A=0.3, seed=12, eval_every=20, defer=True, **kw)
+    part.steps(k)
+    saved_s, saved_b = part.state(), part.best()
+    part.close()
+    resumed = P.run(variant, M=M, R=R, A=0.3, seed=99, eval_every=20, defer=True, **kw)
+    resumed.set_state(saved_s, saved_b)
+    resumed.steps(M - k)
+    got_b, got_s = resumed.best(), resumed.state()
+    for key in ("x", "y", "p"):
+        np.testing.assert_array_equal(got_s[key], want_s[key], err_msg=key)
+    for key in ("E", "s", "step", "cut"):
+        np.testing.assert_array_equal(got_b[key], want_b[key], err_msg=key)
