@@ -276,35 +276,58 @@ gsb_status create_dense(gsb_problem* P, const T* Jr, const float* h, bool valida
     return GSB_OK;
 }
 
-gsb_status create_csr(gsb_problem* P, const int32_t* rp, const int32_t* ci, const float* vv,
-                      int64_t nnz, const float* hh, bool validate, cudaStream_t s) {
-    const int Nu = P->N_user;
-    const int N = P->N;
+// Host-side checks of a CSR matrix (Eq. 1 form): rowptr from 0 to nnz and
+// monotone (checked in full before any row is read), column indices in range
+// and strictly increasing within each row; with validate also finite values,
+// a zero diagonal and the symmetric partner (j, i) of every entry with the same
+// value. Needs no GPU.
+gsb_status check_csr(int Nu, const int32_t* rp, const int32_t* ci, const float* vv, int64_t nnz,
+                     bool validate) {
+    if (nnz < 0) return set_error(GSB_EINVAL, "nnz must be >= 0");
     if (rp[0] != 0 || rp[Nu] != nnz) return set_error(GSB_EINVAL, "rowptr must run from 0 to nnz");
-    std::vector<int32_t> rowptr(N + 1, 0), col;
-    std::vector<float> val;
-    col.reserve(nnz + (hh ? 2 * Nu : 0));
-    val.reserve(col.capacity());
-    for (int i = 0; i < Nu; ++i) {
+    for (int i = 0; i < Nu; ++i)
         if (rp[i + 1] < rp[i]) return set_error(GSB_EINVAL, "rowptr is not monotone");
+    for (int i = 0; i < Nu; ++i) {
         int prev = -1;
         for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
             const int j = ci[k];
             if (j < 0 || j >= Nu) return set_error(GSB_EINVAL, "column index out of range");
             if (j <= prev) return set_error(GSB_EINVAL, "column indices must increase within a row");
             prev = j;
-            if (validate) {
-                if (!isfinite(vv[k])) return set_error(GSB_EINVAL, "J has a non-finite entry");
-                if (j == i && vv[k] != 0.f)
-                    return set_error(GSB_EINVAL, "J has a nonzero diagonal entry (Eq. 1 needs J_ii = 0)");
-                // symmetric partner (j, i) with the same value
-                const int32_t* b = ci + rp[j];
-                const int32_t* e = ci + rp[j + 1];
-                const int32_t* f = std::lower_bound(b, e, i);
-                if (f == e || *f != i || vv[rp[j] + (f - b)] != vv[k])
-                    return set_error(GSB_EINVAL, "J is not symmetric (Eq. 1 needs J_ij = J_ji)");
-            }
-            col.push_back(j);
+        }
+    }
+    if (!validate) return GSB_OK;
+    for (int i = 0; i < Nu; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            if (!isfinite(vv[k])) return set_error(GSB_EINVAL, "J has a non-finite entry");
+            if (j == i && vv[k] != 0.f)
+                return set_error(GSB_EINVAL, "J has a nonzero diagonal entry (Eq. 1 needs J_ii = 0)");
+            const int32_t* b = ci + rp[j];
+            const int32_t* e = ci + rp[j + 1];
+            const int32_t* f = std::lower_bound(b, e, i);
+            if (f == e || *f != i || vv[rp[j] + (f - b)] != vv[k])
+                return set_error(GSB_EINVAL, "J is not symmetric (Eq. 1 needs J_ij = J_ji)");
+        }
+    return GSB_OK;
+}
+
+// checked: check_csr already ran on these arrays (host input, in gsb_create)
+gsb_status create_csr(gsb_problem* P, const int32_t* rp, const int32_t* ci, const float* vv,
+                      int64_t nnz, const float* hh, bool validate, bool checked, cudaStream_t s) {
+    const int Nu = P->N_user;
+    const int N = P->N;
+    if (!checked) {
+        gsb_status cst = check_csr(Nu, rp, ci, vv, nnz, validate);
+        if (cst != GSB_OK) return cst;
+    }
+    std::vector<int32_t> rowptr(N + 1, 0), col;
+    std::vector<float> val;
+    col.reserve(nnz + (hh ? 2 * Nu : 0));
+    val.reserve(col.capacity());
+    for (int i = 0; i < Nu; ++i) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            col.push_back(ci[k]);
             val.push_back(vv[k]);
         }
         if (hh && hh[i] != 0.f) {
@@ -480,6 +503,13 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
     *out = nullptr;
     if (N < 1) return set_error(GSB_EINVAL, "N must be >= 1");
     if (N > (1 << 20)) return set_error(GSB_EINVAL, "N too large");
+    // a host CSR matrix is checked before anything touches the device
+    if (format == GSB_J_CSR_F32 && !(flags & GSB_CREATE_DEVICE_INPUT)) {
+        if (J || !rowptr || (nnz > 0 && (!col || !val)) || nnz < 0)
+            return set_error(GSB_EINVAL, "CSR format takes rowptr, col, val");
+        gsb_status cst = check_csr(N, rowptr, col, val, nnz, !(flags & GSB_CREATE_NO_VALIDATE));
+        if (cst != GSB_OK) return cst;
+    }
     int dev = 0;
     gsb_status st = check_device(&dev);
     if (st != GSB_OK) return st;
@@ -543,7 +573,7 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
         auto vv = fetch(val, (size_t)nnz, device_in);
         P->csr = true;
         st = create_csr(P, rp.data(), ci.data(), vv.data(), nnz, h ? hv.data() : nullptr,
-                        validate, s);
+                        validate, !device_in, s);
     } else {
         free_problem(P);
         return set_error(GSB_EINVAL, "unknown J format");
