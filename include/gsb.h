@@ -143,6 +143,14 @@ gsb_status gsb_destroy(gsb_problem* problem);
  * handles. */
 gsb_status gsb_release_cached_memory(void);
 
+/* Cap on the device memory the library's problems and runs hold at once
+ * (bytes; 0 = no cap). An allocation that would pass it fails with GSB_ENOMEM,
+ * and the call that needed it leaves nothing allocated. gsb_memory_usage
+ * reports the bytes held by live handles and the bytes kept for reuse (each
+ * output nullable). Host side only. */
+gsb_status gsb_set_memory_limit(int64_t bytes);
+gsb_status gsb_memory_usage(int64_t* in_use, int64_t* kept);
+
 /* Number of spins (including the auxiliary one when h was given) and the
  * extreme eigenvalues of J used for c and dt (computed on the GPU on first use
  * by the Lanczos method in FP64, to 1e-14 relative stationarity of the Ritz

@@ -39,6 +39,8 @@ struct BlockCache {
     std::map<std::pair<int, size_t>, std::vector<void*>> free;  // (device, bytes) -> blocks
     std::unordered_map<void*, std::pair<int, size_t>> live;      // blocks handed out
     size_t cached = 0;
+    size_t in_use = 0;  // bytes handed out
+    size_t limit = 0;   // cap on in_use (0: none)
 };
 BlockCache& block_cache() {
     static BlockCache* c = new BlockCache();  // never destroyed: outlives every handle
@@ -56,19 +58,25 @@ void* cache_alloc(size_t bytes) {
     BlockCache& c = block_cache();
     {
         std::lock_guard<std::mutex> g(c.mu);
+        if (c.limit && c.in_use + b > c.limit) return nullptr;
         auto it = c.free.find({dev, b});
         if (it != c.free.end() && !it->second.empty()) {
             void* p = it->second.back();
             it->second.pop_back();
             c.cached -= b;
             c.live[p] = {dev, b};
+            c.in_use += b;
             return p;
         }
     }
     void* p = nullptr;
-    if (cudaMalloc(&p, b) != cudaSuccess) return nullptr;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+        cudaGetLastError();  // the caller reports GSB_ENOMEM; no sticky error remains
+        return nullptr;
+    }
     std::lock_guard<std::mutex> g(c.mu);
     c.live[p] = {dev, b};
+    c.in_use += b;
     return p;
 }
 
@@ -83,6 +91,7 @@ void cache_free(void* p) {
     }
     const std::pair<int, size_t> key = it->second;
     c.live.erase(it);
+    c.in_use -= key.second;
     if (c.cached + key.second <= kCacheCap) {
         c.free[key].push_back(p);
         c.cached += key.second;
@@ -592,6 +601,22 @@ gsb_status gsb_destroy(gsb_problem* problem) {
 }
 
 gsb_status gsb_release_cached_memory(void) { return cache_release(); }
+
+gsb_status gsb_set_memory_limit(int64_t bytes) {
+    if (bytes < 0) return set_error(GSB_EINVAL, "bytes must be >= 0");
+    BlockCache& c = block_cache();
+    std::lock_guard<std::mutex> g(c.mu);
+    c.limit = (size_t)bytes;
+    return GSB_OK;
+}
+
+gsb_status gsb_memory_usage(int64_t* in_use, int64_t* kept) {
+    BlockCache& c = block_cache();
+    std::lock_guard<std::mutex> g(c.mu);
+    if (in_use) *in_use = (int64_t)c.in_use;
+    if (kept) *kept = (int64_t)c.cached;
+    return GSB_OK;
+}
 
 gsb_status gsb_problem_info(gsb_problem* P, int32_t* n_spins, double* lmax, double* lmin,
                             void* stream) {

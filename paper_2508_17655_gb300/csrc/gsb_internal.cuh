@@ -165,8 +165,9 @@ gsb_status dev_alloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) return GSB_OK;
     *p = (T*)cache_alloc(sizeof(T) * count);
-    if (!*p) return set_error(GSB_ENOMEM, "device allocation of " +
-                                              std::to_string(sizeof(T) * count) + " bytes");
+    if (!*p)
+        return set_error(GSB_ENOMEM, "device allocation of " + std::to_string(sizeof(T) * count) +
+                                         " bytes failed (device memory, or the library's limit)");
     return GSB_OK;
 }
 inline void dev_free(void* p) { cache_free(p); }

@@ -142,6 +142,10 @@ def _declare(L):
                                     ctypes.c_int32, ctypes.POINTER(ctypes.c_int8),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
     L.gsb_run_set_state.restype = st
+    L.gsb_set_memory_limit.argtypes = [ctypes.c_int64]
+    L.gsb_set_memory_limit.restype = st
+    L.gsb_memory_usage.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.gsb_memory_usage.restype = st
     L.gsb_release_cached_memory.argtypes = []
     L.gsb_release_cached_memory.restype = st
     L.gsb_wait_check.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp]
@@ -174,6 +178,19 @@ def _stream_handle(stream):
 def release_cached_memory():
     """Return the device blocks the library keeps for reuse to CUDA."""
     _check(lib().gsb_release_cached_memory())
+
+
+def set_memory_limit(nbytes):
+    """Cap on the device bytes the library's problems and runs hold (0: none)."""
+    _check(lib().gsb_set_memory_limit(int(nbytes)))
+
+
+def memory_usage():
+    """(bytes held by live problems and runs, bytes kept for reuse)."""
+    a = ctypes.c_int64()
+    b = ctypes.c_int64()
+    _check(lib().gsb_memory_usage(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def wait_check(kind, limit_ns, stream=None):

@@ -77,6 +77,12 @@ int main(void) {
     if (gsb_wait_check(7, 1000000, NULL) != GSB_EINVAL) return 9;
     if (strcmp(gsb_run_kernel(NULL), "") != 0) return 10;
     if (gsb_release_cached_memory() != GSB_OK) return 11;  /* nothing kept yet */
+    if (gsb_set_memory_limit(-1) != GSB_EINVAL) return 12;
+    if (gsb_set_memory_limit(0) != GSB_OK) return 13;
+    {
+        int64_t used = -1, kept = -1;
+        if (gsb_memory_usage(&used, &kept) != GSB_OK || used != 0 || kept != 0) return 14;
+    }
     printf("ok\n");
     return 0;
 }

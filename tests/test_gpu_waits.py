@@ -84,3 +84,30 @@ def test_reused_device_blocks_give_identical_runs():
     gsb.release_cached_memory()
     after = once("fp8")
     np.testing.assert_array_equal(after[0]["E"], once("fp8")[0]["E"])
+
+
+def test_memory_limit_gives_enomem_and_leaves_nothing_behind():
+    """Failure detection on the host: a cap on the library's device memory makes
+    an allocation fail; the call returns GSB_ENOMEM with a message and releases
+    what it had taken; with the cap lifted the same call succeeds."""
+    gsb.release_cached_memory()
+    used0, _ = gsb.memory_usage()
+    try:
+        gsb.set_memory_limit(used0 + (1 << 20))  # 1 MiB of headroom
+        with pytest.raises(gsb.GsbError) as e:
+            gsb.Problem.dense(I.sk_pm1(2000, 0))  # 16 MB of FP32 J alone
+        assert e.value.status == gsb.ENOMEM
+        assert gsb.memory_usage()[0] == used0
+        P = gsb.Problem.dense(I.sk_pm1(64, 0))  # well inside the cap
+        used1, _ = gsb.memory_usage()
+        with pytest.raises(gsb.GsbError) as e:
+            P.run("gdsb", M=10, R=65536, c=0.1, dt=1.0)
+        assert e.value.status == gsb.ENOMEM
+        assert gsb.memory_usage()[0] == used1
+    finally:
+        gsb.set_memory_limit(0)
+    run = P.run("gdsb", M=10, R=65536, c=0.1, dt=1.0)
+    assert np.all(np.isfinite(run.best()["E"]))
+    run.close()
+    P.close()
+    assert gsb.memory_usage()[0] == used0
