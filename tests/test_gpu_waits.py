@@ -90,6 +90,8 @@ def test_memory_limit_gives_enomem_and_leaves_nothing_behind():
     """Failure detection on the host: a cap on the library's device memory makes
     an allocation fail; the call returns GSB_ENOMEM with a message and releases
     what it had taken; with the cap lifted the same call succeeds."""
+    import gc
+    gc.collect()  # handles of earlier tests freed now, not during this one
     gsb.release_cached_memory()
     used0, _ = gsb.memory_usage()
     try:
