@@ -562,7 +562,8 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
             dev_free(Jd);
             dev_free(hd);
             free_problem(P);
-            return set_error(GSB_ECUDA, std::string("uploading J: ") + cudaGetErrorString(e));
+            return set_error(e == cudaErrorMemoryAllocation ? GSB_ENOMEM : GSB_ECUDA,
+                             std::string("uploading J: ") + cudaGetErrorString(e));
         }
         const void* Jsrc = device_in ? J : Jd;
         if (format == GSB_J_DENSE_I8)
