@@ -133,6 +133,33 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
                       const float* h, uint32_t flags, void* stream);
 gsb_status gsb_destroy(gsb_problem* problem);
 
+/* QUBO input (not in the paper, which notes only that other problems map to
+ * the Ising form of Eq. 1): minimise f(b) = sum_ij Q_ij b_i b_j over
+ * b in {0,1}^N, with Q (N x N row-major float, any square matrix: asymmetric
+ * entries and the diagonal, which acts as a linear term since b_i^2 = b_i,
+ * are allowed). With s = 2b - 1 and Qs = (Q + Q^T)/2 this is the Ising problem
+ * J_ij = -(Q_ij + Q_ji) for i != j, J_ii = 0, local field
+ * h_i = -sum_j (Q_ij + Q_ji), scaled by 4 so that integer Q keeps integer J
+ * and h (and the exact tensor-core paths): f(b) = scale * E(s) + offset with
+ * scale = 1/4 and offset = (sum_ij Q_ij + sum_i Q_ii)/4, E as gsb_best
+ * reports it. The scale does not change the dynamics when c is left to its
+ * default 1/lambda_max (App. A) and dt to Eq. 13.
+ *
+ * gsb_qubo_to_ising: that map on the host, no GPU needed: Q (host, N x N) ->
+ * J (host, N x N, written), h (host, length N, written), scale and offset
+ * (host, nullable). GSB_EINVAL for N outside 1..65536, a NULL array or a
+ * non-finite entry of Q.
+ *
+ * gsb_create_qubo: gsb_create of that Ising problem (dense FP32 J with the
+ * local field h, so one auxiliary spin is added and gauge-fixed to +1 on
+ * output: b_i = (1 + s_i)/2 for the spins gsb_best returns). Q is host memory,
+ * or device memory with flags = GSB_CREATE_DEVICE_INPUT (no other flag is
+ * accepted). scale and offset as above (nullable). */
+gsb_status gsb_qubo_to_ising(int32_t N, const float* Q, float* J, float* h, double* scale,
+                             double* offset);
+gsb_status gsb_create_qubo(gsb_problem** out, int32_t N, const float* Q, uint32_t flags,
+                           double* scale, double* offset, void* stream);
+
 /* Device memory: the blocks of destroyed problems and runs are kept (up to
  * 1 GiB in all) and handed to the next problem or run that needs a block of the
  * same size on the same device, so creating one of the same shape again costs
@@ -306,10 +333,14 @@ gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems, const gsb_para
  * interface variant of gsb_energy. J (device, N x N row-major float), spins
  * (device, R x N int8 +-1) and energies (device, length R, written) belong to
  * the caller; the kernels run on `stream`. The per-replica accumulators are a
- * fixed array inside the library (1 <= R <= 65536; larger R gives GSB_EINVAL),
- * one per device, shared by all calls: each call clears it first, and calls
- * whose work overlaps on the GPU race on it. N <= 29,000. The first call on a
- * device looks up that array's device address (once per device). */
+ * fixed array inside the library (1 <= R <= 65536 and 1 <= N <= 29,000; other
+ * sizes give GSB_EINVAL), one per device, held by every device that loads the
+ * library until the process exits, and shared by all calls: each call clears it
+ * first, and calls whose work overlaps on the GPU race on it. Each call looks
+ * up that array's device address with the caller's device current (a host-side
+ * lookup, so it stays right after a device reset); the first call on a device
+ * may load the library's module there and should come before any stream
+ * capture. */
 gsb_status gsb_energy_noalloc(const float* J, int32_t N, const int8_t* spins, int32_t R,
                               double* energies, void* stream);
 
@@ -326,6 +357,19 @@ gsb_status gsb_energy_noalloc(const float* J, int32_t N, const int8_t* spins, in
  * and kind 2 on a counter that already holds (GSB_OK at once). The CUDA
  * context stays usable afterwards. Blocks on `stream`. */
 gsb_status gsb_wait_check(int32_t kind, int64_t limit_ns, void* stream);
+
+/* Device-time profile of the library's own multi-launch calls (not in the
+ * paper). After gsb_set_call_profiling(1) on a thread, each later
+ * gsb_batch_run, gsb_lyapunov and gsb_relaxed_energy_grad on that thread
+ * records CUDA events on its stream around every launch of its step kernels
+ * (graph launches of captured steps included; the events also keep launches
+ * from overlapping), and gsb_last_call_profile then gives the summed device
+ * time of those launches in ms, their number, and the time steps they covered
+ * (each output nullable). Allocation, set-up and copies are outside the
+ * bracketed launches. gsb_set_call_profiling(0) turns it off. Host side; no
+ * GPU work of its own. */
+gsb_status gsb_set_call_profiling(int32_t on);
+gsb_status gsb_last_call_profile(double* kernel_ms, int64_t* launches, int64_t* steps);
 
 /* Message for the last non-OK status returned on the calling thread. */
 const char* gsb_last_error(void);

@@ -52,7 +52,8 @@ def _declare(L):
     L.orc_run.argtypes = [ctypes.c_int32, _dp, _i32p, _i32p, _dp, ctypes.c_int32,
                           ctypes.c_int32, _dp, _dp, ctypes.c_double, ctypes.c_double,
                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                          _dp, _dp, _dp, ctypes.c_int32, _dp, _i8p, _i32p, ctypes.c_int32, _dp]
+                          _dp, _dp, _dp, ctypes.c_int32, _dp, _i8p, _i32p, ctypes.c_int32, _dp,
+                          _dp]
     L.orc_run.restype = ctypes.c_int
     L.orc_tangent_run.argtypes = [ctypes.c_int32, _dp, _i32p, _i32p, _dp, ctypes.c_int32,
                                   ctypes.c_int32, _dp, _dp, ctypes.c_double, ctypes.c_double,
@@ -194,7 +195,8 @@ def run(J, variant, x, y, *, c, dt, M, A=0.0, p=None, sched=None, m0=0, nsteps=N
     x, y: R x N arrays (copied). p: R x N (default: ones = p(0), App. A).
     A: scalar or per-replica control strength. Returns a dict with x, y, p, the
     best-state record (E, s, step) and per-replica decision margins (the
-    smallest distance of a wall test or a sign from its threshold)."""
+    smallest distance of a wall test or a sign from its threshold; wall_margin:
+    of a wall test alone)."""
     C = as_coupling(J)
     coupling, control = VARIANTS[variant]
     x = np.array(x, dtype=np.float64, copy=True, order="C")
@@ -212,14 +214,16 @@ def run(J, variant, x, y, *, c, dt, M, A=0.0, p=None, sched=None, m0=0, nsteps=N
     else:
         best = {k: np.array(v, copy=True) for k, v in best.items()}
     margin = np.full(R, np.inf)
+    wall_margin = np.full(R, np.inf)
     rc = lib().orc_run(*C.args(), coupling, control, _ptr(Aarr, _dp), _ptr(sch, _dp),
                        float(c), float(dt), int(M), int(m0), int(nsteps), int(R),
                        _ptr(x, _dp), _ptr(y, _dp), _ptr(p, _dp), int(eval_every),
                        _ptr(best["E"], _dp), _ptr(best["s"], _i8p),
-                       _ptr(best["step"], _i32p), int(nthreads), _ptr(margin, _dp))
+                       _ptr(best["step"], _i32p), int(nthreads), _ptr(margin, _dp),
+                       _ptr(wall_margin, _dp))
     if rc != 0:
         raise ValueError("orc_run rejected its arguments")
-    return {"x": x, "y": y, "p": p, "best": best, "margin": margin}
+    return {"x": x, "y": y, "p": p, "best": best, "margin": margin, "wall_margin": wall_margin}
 
 
 def tangent_run(J, variant, x, y, dx, *, c, dt, M, A=0.0, p=None, dy=None, dp=None, sched=None,

@@ -228,13 +228,15 @@ double orc_bruteforce(int32_t N, const double* J, int8_t* s_best) {
  * any floating-point decision from its threshold over this segment: | |x| - 1 |
  * before the wall test of Eq. 5, and |x| where sgn x enters the coupling. It
  * only observes the iteration; a decision closer than rounding error to its
- * threshold may go either way in another precision.
+ * threshold may go either way in another precision. wall_margin (nullable,
+ * length R) receives the wall tests' part of it alone.
  * Returns 0, or -1 on bad arguments. */
 int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* col,
             const double* val, int32_t coupling, int32_t control, const double* A,
             const double* sched, double c, double dt, int32_t M, int32_t m0, int32_t nsteps,
             int32_t R, double* x, double* y, double* p, int32_t eval_every, double* best_E,
-            int8_t* best_s, int32_t* best_step, int32_t nthreads, double* margin) {
+            int8_t* best_s, int32_t* best_step, int32_t nthreads, double* margin,
+            double* wall_margin) {
     if (N <= 0 || R <= 0 || M <= 0 || m0 < 0 || nsteps < 0 || m0 + nsteps > M) return -1;
     if (!J && !(rowptr && col && val)) return -1;
     if (control == 1 && !A) return -1;
@@ -251,7 +253,7 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
         double* v = (double*)malloc(sizeof(double) * (size_t)N);
         double* f = (double*)malloc(sizeof(double) * (size_t)N);
         int8_t* s = (int8_t*)malloc((size_t)N);
-        double mrg = INFINITY;
+        double mrg = INFINITY, wmrg = INFINITY;
         for (int32_t m = m0; m < m0 + nsteps; ++m) {
             /* FP: bifurcation parameter(s) at t_{m+1}, from x(t_m) */
             if (control == 1) {
@@ -275,7 +277,8 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
             /* Eq. 5: perfectly inelastic walls at |x| = 1 */
             for (int32_t i = 0; i < N; ++i) {
                 /* a wall test is a near-tie unless x was not moved (y == 0) */
-                if (yr[i] != 0.0 && fabs(fabs(xr[i]) - 1.0) < mrg) mrg = fabs(fabs(xr[i]) - 1.0);
+                if (yr[i] != 0.0 && fabs(fabs(xr[i]) - 1.0) < wmrg) wmrg = fabs(fabs(xr[i]) - 1.0);
+                if (wmrg < mrg) mrg = wmrg;
                 if (fabs(xr[i]) > 1.0) {
                     xr[i] = orc_sgn(xr[i]);
                     yr[i] = 0.0;
@@ -295,6 +298,7 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
             }
         }
         if (margin) margin[r] = mrg;
+        if (wall_margin) wall_margin[r] = wmrg;
         free(v);
         free(f);
         free(s);

@@ -59,24 +59,27 @@ void* cache_alloc(size_t bytes) {
     {
         std::lock_guard<std::mutex> g(c.mu);
         if (c.limit && c.in_use + b > c.limit) return nullptr;
+        // counted before the lock is released, so that two threads allocating
+        // at once cannot both pass the cap
+        c.in_use += b;
         auto it = c.free.find({dev, b});
         if (it != c.free.end() && !it->second.empty()) {
             void* p = it->second.back();
             it->second.pop_back();
             c.cached -= b;
             c.live[p] = {dev, b};
-            c.in_use += b;
             return p;
         }
     }
     void* p = nullptr;
-    if (cudaMalloc(&p, b) != cudaSuccess) {
-        cudaGetLastError();  // the caller reports GSB_ENOMEM; no sticky error remains
+    const bool ok = cudaMalloc(&p, b) == cudaSuccess;
+    if (!ok) cudaGetLastError();  // the caller reports GSB_ENOMEM; no sticky error remains
+    std::lock_guard<std::mutex> g(c.mu);
+    if (!ok) {
+        c.in_use -= b;
         return nullptr;
     }
-    std::lock_guard<std::mutex> g(c.mu);
     c.live[p] = {dev, b};
-    c.in_use += b;
     return p;
 }
 
@@ -158,8 +161,12 @@ bool is_integer(float v) { return v == nearbyintf(v); }
 
 void free_problem(gsb_problem* P) {
     if (!P) return;
-    // runs on any stream may still read J: the blocks are reused only once the
-    // device is idle (as a cudaFree would have waited)
+    // runs on any stream of the problem's device may still read J: the blocks
+    // are reused only once that device is idle (as a cudaFree would have
+    // waited), whichever device the caller has made current
+    int cur = -1;
+    const bool switched = cudaGetDevice(&cur) == cudaSuccess && cur != P->device &&
+                          cudaSetDevice(P->device) == cudaSuccess;
     cudaDeviceSynchronize();
     dev_free(P->J32);
     dev_free(P->J8);
@@ -167,6 +174,7 @@ void free_problem(gsb_problem* P) {
     dev_free(P->rowptr);
     dev_free(P->col);
     dev_free(P->val);
+    if (switched) cudaSetDevice(cur);
     delete P;
 }
 
@@ -491,6 +499,62 @@ gsb_status prof_end(gsb_run_state* run, int steps) {
     return GSB_OK;
 }
 
+namespace {
+struct CallProfile {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    double ms = 0.0;
+    int64_t launches = 0;
+    int64_t steps = 0;
+};
+thread_local CallProfile g_call_prof;
+}  // namespace
+
+void call_prof_reset() {
+    g_call_prof.used = 0;
+    g_call_prof.ms = 0.0;
+    g_call_prof.launches = 0;
+    g_call_prof.steps = 0;
+}
+
+gsb_status call_prof_begin(cudaStream_t s) {
+    CallProfile& c = g_call_prof;
+    if (!c.on) return GSB_OK;
+    while (c.used + 2 > c.ev.size()) {
+        cudaEvent_t e;
+        GSB_CUDA_TRY(cudaEventCreate(&e));
+        c.ev.push_back(e);
+    }
+    GSB_CUDA_TRY(cudaEventRecord(c.ev[c.used], s));
+    return GSB_OK;
+}
+
+gsb_status call_prof_end(cudaStream_t s, int steps) {
+    CallProfile& c = g_call_prof;
+    if (!c.on) return GSB_OK;
+    GSB_CUDA_TRY(cudaEventRecord(c.ev[c.used + 1], s));
+    c.used += 2;
+    c.launches += 1;
+    c.steps += steps;
+    return GSB_OK;
+}
+
+gsb_status call_prof_collect() {
+    CallProfile& c = g_call_prof;
+    if (!c.on) return GSB_OK;
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < c.used; k += 2) {
+        GSB_CUDA_TRY(cudaEventSynchronize(c.ev[k + 1]));
+        float t = 0.f;
+        GSB_CUDA_TRY(cudaEventElapsedTime(&t, c.ev[k], c.ev[k + 1]));
+        total += t;
+    }
+    c.ms = total;
+    c.used = 0;
+    return GSB_OK;
+}
+
 bool run_is_eval_step(const gsb_run_state* run, int step) { return is_eval_step(run, step); }
 float run_p_shared(const gsb_run_state* run, int step) { return p_shared_at(run, step); }
 gsb_status run_evaluate(gsb_run_state* run, int step) { return evaluate(run, step); }
@@ -502,6 +566,19 @@ using namespace gsb;
 extern "C" {
 
 const char* gsb_last_error(void) { return g_last_error.c_str(); }
+
+gsb_status gsb_set_call_profiling(int32_t on) {
+    g_call_prof.on = on != 0;
+    call_prof_reset();
+    return GSB_OK;
+}
+
+gsb_status gsb_last_call_profile(double* kernel_ms, int64_t* launches, int64_t* steps) {
+    if (kernel_ms) *kernel_ms = g_call_prof.ms;
+    if (launches) *launches = g_call_prof.launches;
+    if (steps) *steps = g_call_prof.steps;
+    return GSB_OK;
+}
 int32_t gsb_version(void) { return 100; }
 int64_t gsb_launch_count(void) { return g_launches.load(); }
 
@@ -594,6 +671,54 @@ gsb_status gsb_create(gsb_problem** out, int32_t N, int32_t format, const void* 
     }
     *out = P;
     return GSB_OK;
+}
+
+// QUBO f(b) = sum_ij Q_ij b_i b_j, b in {0,1}^N, as an Ising problem (Eq. 1
+// with a local field) under s = 2b - 1. With Qs = (Q + Q^T)/2,
+//   f = 1/4 sum_{i!=j} Qs_ij s_i s_j + 1/2 sum_i s_i sum_j Qs_ij
+//       + 1/4 sum_ij Q_ij + 1/4 sum_i Q_ii,
+// so J_ij = -Qs_ij / 2 (i != j), h_i = -sum_j Qs_ij / 2 give f = E(s) + const.
+// Everything is scaled by 4 so that integer Q gives integer J and h:
+// J'_ij = -(Q_ij + Q_ji), h'_i = -sum_j (Q_ij + Q_ji), f = E'/4 + offset.
+gsb_status gsb_qubo_to_ising(int32_t N, const float* Q, float* J, float* h, double* scale,
+                             double* offset) {
+    if (N < 1 || N > (1 << 16)) return set_error(GSB_EINVAL, "N must be in 1..65536");
+    if (!Q || !J || !h) return set_error(GSB_EINVAL, "Q, J and h are required");
+    const size_t n = (size_t)N;
+    double total = 0.0, diag = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        double hs = 0.0;
+        for (size_t j = 0; j < n; ++j) {
+            const double a = Q[i * n + j], b = Q[j * n + i];
+            if (!isfinite(a)) return set_error(GSB_EINVAL, "Q has a non-finite entry");
+            total += a;
+            hs += a + b;
+            J[i * n + j] = i == j ? 0.f : (float)(-(a + b));
+        }
+        diag += Q[i * n + i];
+        h[i] = (float)(-hs);
+    }
+    if (scale) *scale = 0.25;
+    if (offset) *offset = 0.25 * (total + diag);
+    return GSB_OK;
+}
+
+gsb_status gsb_create_qubo(gsb_problem** out, int32_t N, const float* Q, uint32_t flags,
+                           double* scale, double* offset, void* stream) {
+    if (!out) return set_error(GSB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > (1 << 16)) return set_error(GSB_EINVAL, "N must be in 1..65536");
+    if (!Q) return set_error(GSB_EINVAL, "Q is NULL");
+    if (flags & ~(uint32_t)GSB_CREATE_DEVICE_INPUT)
+        return set_error(GSB_EINVAL, "gsb_create_qubo takes GSB_CREATE_DEVICE_INPUT only");
+    const size_t n = (size_t)N * N;
+    std::vector<float> q = fetch(Q, n, (flags & GSB_CREATE_DEVICE_INPUT) != 0);
+    std::vector<float> J(n), h((size_t)N);
+    gsb_status st = gsb_qubo_to_ising(N, q.data(), J.data(), h.data(), scale, offset);
+    if (st != GSB_OK) return st;
+    // J is symmetric with a zero diagonal by construction
+    return gsb_create(out, N, GSB_J_DENSE_F32, J.data(), nullptr, nullptr, nullptr, 0, h.data(),
+                      0u, stream);
 }
 
 gsb_status gsb_destroy(gsb_problem* problem) {

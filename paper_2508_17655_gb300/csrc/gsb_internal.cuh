@@ -216,6 +216,14 @@ const char* tc_kernel_name(const gsb_run_state* run);
 // GSB_RUN_PROFILE bracketing of a step-kernel launch
 gsb_status prof_begin(gsb_run_state* run);
 gsb_status prof_end(gsb_run_state* run, int steps);
+// gsb_set_call_profiling: CUDA events around the step-kernel launches of the
+// calling thread's next gsb_batch_run / gsb_lyapunov / gsb_relaxed_energy_grad.
+// call_prof_reset at the call's start, begin/end around each launch (no-ops
+// while profiling is off), call_prof_collect once the stream is synchronised.
+void call_prof_reset();
+gsb_status call_prof_begin(cudaStream_t s);
+gsb_status call_prof_end(cudaStream_t s, int steps);
+gsb_status call_prof_collect();
 // host loop helpers shared with the tcgen05 path
 bool run_is_eval_step(const gsb_run_state* run, int step);
 float run_p_shared(const gsb_run_state* run, int step);

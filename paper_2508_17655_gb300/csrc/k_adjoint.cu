@@ -342,6 +342,7 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
         GSB_CUDA_TRY(cudaMemcpyAsync(Ad, Ah.data(), sizeof(float) * Rp, cudaMemcpyHostToDevice, s));
         GSB_CUDA_TRY(cudaStreamSynchronize(s));
     }
+    call_prof_reset();
     GSB_CUDA_TRY(cudaMemsetAsync(e_acc, 0, sizeof(double) * Rp, s));
     GSB_CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * Rp, s));
     GSB_CUDA_TRY(cudaMemsetAsync(gdt, 0, sizeof(double) * Rp, s));
@@ -376,6 +377,8 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
         const size_t a = (size_t)slot * nst, b = (size_t)(slot + 1) * nst;
         const float p_shared = (float)(1.0 - (double)(m + 1) / (double)Q.M);
         const float inv_rem = 1.0f / (float)(Q.M - m);
+        gsb_status pst = call_prof_begin(s);
+        if (pst != GSB_OK) return pst;
         if (mode == kSplitK) {
             gsb_status g = gemm_part(sx + a, sign);
             if (g != GSB_OK) return g;
@@ -396,7 +399,7 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
 #undef GSB_ADJ_FWD_T
 #undef GSB_ADJ_FWD
         GSB_LAUNCH_CHECK("k_adj_fwd");
-        return GSB_OK;
+        return call_prof_end(s, 1);
     };
     auto save_ckpt = [&](int seg) -> gsb_status {
         for (int q = 0; q < 3; ++q) {
@@ -432,6 +435,7 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
     }
     // seed from x(t_W) (slot of the last segment's end)
     const int Llast = seg_len(nseg - 1);
+    if ((st = call_prof_begin(s))) return st;
     {
         const float* xW = sx + (size_t)Llast * nst;
         if (mode == kSplitK && (st = gemm_part(xW, false))) return st;
@@ -446,6 +450,7 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
                                                      control ? lp : nullptr, e_acc, Fp);
     }
     GSB_LAUNCH_CHECK("k_adj_seed");
+    if ((st = call_prof_end(s, 1))) return st;
     // reverse sweep, segment by segment; the last segment is still in the slots
     for (int seg = nseg - 1; seg >= 0; --seg) {
         const int L = seg_len(seg);
@@ -459,6 +464,7 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
             const size_t a = (size_t)k * nst, b = (size_t)(k + 1) * nst;
             const float p_shared = (float)(1.0 - (double)(m + 1) / (double)Q.M);
             const float inv_rem = 1.0f / (float)(Q.M - m);
+            if ((st = call_prof_begin(s))) return st;
             if (!sign) {
                 k_adj_pre<<<(unsigned)((nst + 255) / 256), 256, 0, s>>>(sx + a, syt + a, lx, ly, lf,
                                                                          nst, c, dt);
@@ -481,6 +487,7 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
 #undef GSB_ADJ_POST_T
 #undef GSB_ADJ_POST
             GSB_LAUNCH_CHECK("k_adj_post");
+            if ((st = call_prof_end(s, 1))) return st;
         }
     }
     k_finish<<<(R + 255) / 256, 256, 0, s>>>(e_acc, energy, gA, grad_A, gdt, grad_dt, R);
@@ -490,5 +497,5 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
         if (st != GSB_OK) return st;
     }
     GSB_CUDA_TRY(cudaStreamSynchronize(s));  // buffers are freed on return
-    return GSB_OK;
+    return call_prof_collect();
 }

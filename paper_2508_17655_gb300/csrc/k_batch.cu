@@ -130,7 +130,8 @@ struct BatchState {
     }
 };
 
-gsb_status launch_batch_step(BatchState& B, int which, cudaStream_t s) {
+// One batched time step: every tile of every instance, then the step counter.
+gsb_status launch_batch_step_raw(BatchState& B, int which, cudaStream_t s) {
     if (B.ntiles[which] == 0) return GSB_OK;
     if (which == 0)
         k_batch_step<128><<<B.ntiles[0], 256, 0, s>>>(B.d_inst, B.d_tiles[0], B.d_m);
@@ -140,6 +141,14 @@ gsb_status launch_batch_step(BatchState& B, int which, cudaStream_t s) {
     k_batch_advance<<<1, 1, 0, s>>>(B.d_m);
     GSB_LAUNCH_CHECK("k_batch_advance");
     return GSB_OK;
+}
+
+// The same, with the call-profile events around it (outside graph capture).
+gsb_status launch_batch_step(BatchState& B, int which, cudaStream_t s) {
+    gsb_status st = call_prof_begin(s);
+    if (st == GSB_OK) st = launch_batch_step_raw(B, which, s);
+    if (st == GSB_OK) st = call_prof_end(s, 1);
+    return st;
 }
 
 }  // namespace
@@ -237,6 +246,7 @@ extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
     GSB_CUDA_TRY(cudaStreamSynchronize(s));
     cudaStream_t caller = s;
     s = own.s;
+    call_prof_reset();
 
     // autotune the tile on the first steps (both sizes give the same bits)
     const int force = info ? info->force_tile : 0;
@@ -271,7 +281,7 @@ extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
         cudaGraph_t g;
         GSB_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         for (int k = 0; k < G; ++k)
-            if ((st = launch_batch_step(B, which, s))) {
+            if ((st = launch_batch_step_raw(B, which, s))) {
                 cudaStreamEndCapture(s, &g);
                 return cleanup(st);
             }
@@ -279,9 +289,11 @@ extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
         cudaGraphExec_t ex;
         GSB_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
         cudaGraphDestroy(g);
+        if ((st = call_prof_begin(s))) return cleanup(st);
         GSB_CUDA_TRY(cudaEventRecord(e0, s));
         GSB_CUDA_TRY(cudaGraphLaunch(ex, s));
         GSB_CUDA_TRY(cudaEventRecord(e1, s));
+        if ((st = call_prof_end(s, G))) return cleanup(st);
         GSB_CUDA_TRY(cudaEventSynchronize(e1));
         float t = 0.f;
         GSB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
@@ -298,7 +310,9 @@ extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
     }
     // the remaining steps: full chunks by graph replay, the tail step by step
     while (exec && m + chunk <= M_max) {
+        if ((st = call_prof_begin(s))) return cleanup(st);
         GSB_CUDA_TRY(cudaGraphLaunch(exec, s));
+        if ((st = call_prof_end(s, chunk))) return cleanup(st);
         m += chunk;
     }
     if (exec) cudaGraphExecDestroy(exec);
@@ -309,6 +323,7 @@ extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = call_prof_collect())) return cleanup(st);
     s = caller;
     // record how far each run got; evaluate the ones that reached t_M
     for (int k = 0; k < n; ++k) {

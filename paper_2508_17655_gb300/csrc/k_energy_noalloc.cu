@@ -9,12 +9,11 @@
 // back. They pass device buffers for J, the spins and the energies; this
 // entry point only launches kernels on their stream.
 //
-// Limits and sharing: at most kMaxReplicas spin vectors per call. The scratch
-// array is one per device and is shared by every call on that device; it keeps
-// the last call's partial sums, so each call clears it first, and two calls
-// whose work overlaps on the GPU (different streams, no ordering) race on it.
-#include <mutex>
-
+// Limits and sharing: at most kMaxReplicas spin vectors of at most kMaxN
+// spins per call. The scratch array is one per device and is shared by every
+// call on that device; it keeps the last call's partial sums, so each call
+// clears it first, and two calls whose work overlaps on the GPU (different
+// streams, no ordering) race on it.
 #include "gsb_internal.cuh"
 
 namespace gsb {
@@ -22,8 +21,11 @@ namespace gsb {
 namespace {
 
 constexpr int kMaxReplicas = 65536;  // 512 KiB of doubles, held by every device that loads the library
-constexpr int kMaxDevices = 64;
 constexpr int kReplicasPerBlock = 8;
+// The spins of kReplicasPerBlock replicas are staged in shared memory, one byte
+// each: 8 x 29,000 = 232,000 bytes, within the 227 KiB (232,448 bytes) a block
+// may opt in to on this GPU.
+constexpr int kMaxN = 29000;
 constexpr int kRowsPerBlock = 64;
 
 __device__ __align__(256) double g_energy_scratch[kMaxReplicas];
@@ -79,23 +81,19 @@ __global__ void k_energy_finish(const double* __restrict__ acc, double* __restri
     if (r < R) e[r] = -0.5 * acc[r];
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the symbol's name is only a host-side handle).
-std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
+// Device address of the scratch array on the current device. In host code the
+// symbol's name is only a host-side handle, not a device address. The lookup
+// is a host-side table query that allocates nothing; doing it on every call
+// (rather than caching one address per device number) keeps the address right
+// when the caller resets a device, after which the module is loaded again and
+// the array may sit elsewhere. The first call on a device may load the
+// library's module there, which is why it should come before any stream
+// capture.
 gsb_status scratch_for_current_device(double** out) {
-    int dev = 0;
-    GSB_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return set_error(GSB_ENODEV, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_energy_scratch);
-        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_energy_scratch)");
-        g_scratch_ptr[dev] = (double*)p;
-    }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_energy_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_energy_scratch)");
+    *out = (double*)p;
     return GSB_OK;
 }
 
@@ -108,12 +106,13 @@ using namespace gsb;
 extern "C" gsb_status gsb_energy_noalloc(const float* J, int32_t N, const int8_t* spins,
                                          int32_t R, double* energies, void* stream) {
     if (!J || !spins || !energies) return set_error(GSB_EINVAL, "NULL device pointer");
-    if (N < 1) return set_error(GSB_EINVAL, "N must be >= 1");
+    if (N < 1 || N > kMaxN)
+        return set_error(GSB_EINVAL, "gsb_energy_noalloc takes 1 to " + std::to_string(kMaxN) +
+                                         " spins");
     if (R < 1 || R > kMaxReplicas)
         return set_error(GSB_EINVAL, "gsb_energy_noalloc takes 1 to " +
                                          std::to_string(kMaxReplicas) + " spin vectors per call");
     const size_t smem = (size_t)kReplicasPerBlock * N;
-    if (smem > 227 * 1024) return set_error(GSB_EINVAL, "N too large for gsb_energy_noalloc");
     double* acc = nullptr;
     gsb_status st = scratch_for_current_device(&acc);
     if (st != GSB_OK) return st;

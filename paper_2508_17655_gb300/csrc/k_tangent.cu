@@ -268,12 +268,14 @@ extern "C" gsb_status gsb_lyapunov(gsb_problem* P, const gsb_params* prm, int32_
     if (st != GSB_OK) return st;
     int cur = 0;
     const dim3 grid(C / BN, Np / BM);
+    call_prof_reset();
     for (int m = 0; m < nsteps; ++m) {
         const float p_shared = (float)(1.0 - (double)(m + 1) / (double)Q.M);
         const float inv_rem = 1.0f / (float)(Q.M - m);
 #define GSB_TAN_LAUNCH(S, CT)                                                                  \
     k_tangent_step<S, CT><<<grid, 256, 0, s>>>(P->J32, Np, C, B.x[cur], B.x[cur ^ 1], B.y, B.p, \
                                                B.A, (float)c, (float)dt, p_shared, inv_rem)
+        if ((st = call_prof_begin(s)) != GSB_OK) return st;
         if (sign) {
             if (control) GSB_TAN_LAUNCH(true, true); else GSB_TAN_LAUNCH(true, false);
         } else {
@@ -281,6 +283,7 @@ extern "C" gsb_status gsb_lyapunov(gsb_problem* P, const gsb_params* prm, int32_
         }
 #undef GSB_TAN_LAUNCH
         GSB_LAUNCH_CHECK("k_tangent_step");
+        if ((st = call_prof_end(s, 1)) != GSB_OK) return st;
         cur ^= 1;
         if ((m + 1) % renorm_every == 0 || m + 1 == nsteps)
             if ((st = renorm(cur, 1)) != GSB_OK) return st;
@@ -288,6 +291,7 @@ extern "C" gsb_status gsb_lyapunov(gsb_problem* P, const gsb_params* prm, int32_
     std::vector<double> ls(R);
     GSB_CUDA_TRY(cudaMemcpyAsync(ls.data(), B.log_sum, R * sizeof(double), cudaMemcpyDeviceToHost, s));
     GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = call_prof_collect()) != GSB_OK) return st;
     const double T = (double)nsteps * (double)(float)dt;
     for (int r = 0; r < R; ++r) mle_out[r] = ls[r] / T;
     return GSB_OK;

@@ -93,6 +93,13 @@ def _declare(L):
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), fp,
                              ctypes.c_int64, fp, ctypes.c_uint32, _vp]
     L.gsb_create.restype = st
+    L.gsb_qubo_to_ising.argtypes = [ctypes.c_int32, fp, fp, fp, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
+    L.gsb_qubo_to_ising.restype = st
+    L.gsb_create_qubo.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, _vp, ctypes.c_uint32,
+                                  ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), _vp]
+    L.gsb_create_qubo.restype = st
     L.gsb_destroy.argtypes = [_vp]
     L.gsb_destroy.restype = st
     L.gsb_problem_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32),
@@ -150,6 +157,12 @@ def _declare(L):
     L.gsb_release_cached_memory.restype = st
     L.gsb_wait_check.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp]
     L.gsb_wait_check.restype = st
+    L.gsb_set_call_profiling.argtypes = [ctypes.c_int32]
+    L.gsb_set_call_profiling.restype = st
+    L.gsb_last_call_profile.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64)]
+    L.gsb_last_call_profile.restype = st
     L.gsb_last_error.argtypes = []
     L.gsb_last_error.restype = ctypes.c_char_p
     L.gsb_version.restype = ctypes.c_int32
@@ -198,6 +211,22 @@ def wait_check(kind, limit_ns, stream=None):
     both never satisfied; 2: a counter already at its target). Raises GsbError
     with status ETIMEOUT when the wait gives up."""
     _check(lib().gsb_wait_check(int(kind), int(limit_ns), _stream_handle(stream)))
+
+
+def set_call_profiling(on):
+    """gsb_set_call_profiling: CUDA events around the step-kernel launches of
+    this thread's later batch / Lyapunov / gradient calls."""
+    _check(lib().gsb_set_call_profiling(int(bool(on))))
+
+
+def last_call_profile():
+    """(device ms of the step-kernel launches, launches, time steps covered) of
+    this thread's last profiled batch / Lyapunov / gradient call."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    k = ctypes.c_int64()
+    _check(lib().gsb_last_call_profile(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)))
+    return ms.value, n.value, k.value
 
 
 def launch_count():
@@ -256,6 +285,21 @@ def batch_run(problems, specs, force_tile=0, max_steps=0, stream=None):
                   "ms_step_tile64": info.ms_step_tile64}
 
 
+def qubo_to_ising(Q):
+    """gsb_qubo_to_ising (host only, no GPU): the Ising form of the QUBO
+    f(b) = b^T Q b under s = 2b - 1. Returns (J, h, scale, offset) with
+    f(b) = scale * E(s) + offset."""
+    Qc = np.ascontiguousarray(Q, dtype=np.float32)
+    N = Qc.shape[0]
+    J = np.zeros((N, N), dtype=np.float32)
+    h = np.zeros(N, dtype=np.float32)
+    sc = ctypes.c_double()
+    off = ctypes.c_double()
+    _check(lib().gsb_qubo_to_ising(N, _p(Qc, ctypes.c_float), _p(J, ctypes.c_float),
+                                   _p(h, ctypes.c_float), ctypes.byref(sc), ctypes.byref(off)))
+    return J, h, sc.value, off.value
+
+
 def energy_noalloc(J_ptr, N, spins_ptr, R, energies_ptr, stream=None):
     """gsb_energy_noalloc on caller device buffers (raw pointers, e.g. from
     torch tensors' data_ptr()): J N x N float32, spins R x N int8, energies R
@@ -285,6 +329,24 @@ class Problem:
                                 None, 0, _p(hc, ctypes.c_float),
                                 0 if validate else CREATE_NO_VALIDATE, _stream_handle(stream)))
         return cls(out, N)
+
+    @classmethod
+    def qubo(cls, Q, stream=None):
+        """gsb_create_qubo: the QUBO f(b) = b^T Q b as an Ising problem (with one
+        auxiliary spin). Returns the problem; its .scale and .offset give
+        f(b) = scale * E + offset for the energies E that runs report, and
+        b = (1 + s) / 2 for their spins."""
+        Qc = np.ascontiguousarray(Q, dtype=np.float32)
+        N = Qc.shape[0]
+        out = _vp()
+        sc = ctypes.c_double()
+        off = ctypes.c_double()
+        _check(lib().gsb_create_qubo(ctypes.byref(out), N, Qc.ctypes.data_as(_vp), 0,
+                                     ctypes.byref(sc), ctypes.byref(off),
+                                     _stream_handle(stream)))
+        P = cls(out, N)
+        P.scale, P.offset = sc.value, off.value
+        return P
 
     @classmethod
     def csr(cls, N, rowptr, col, val, h=None, stream=None, validate=True):

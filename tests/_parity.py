@@ -1,6 +1,15 @@
 """Shared helpers for the GPU-vs-oracle parity tests."""
 import numpy as np
 
+# Per test: how many replicas were judged under a widened bar or excused as
+# decision near-ties, out of how many compared. Printed in the terminal
+# summary of the run (tests/conftest.py).
+WIDENED = []
+
+
+def note_widened(what, n_widened, n_total, how):
+    WIDENED.append((str(what), int(n_widened), int(n_total), str(how)))
+
 # FP32 trajectories over the first 50 steps, before chaos decorrelates them:
 # max |gpu - oracle| <= RTOL * max |oracle| for each of x, y, p.
 RTOL_TRAJ = 1e-5
@@ -43,6 +52,7 @@ def assert_replicas_close(gpu, ref, margin, rtol=RTOL_TRAJ, rtol_max=None, what=
     norm_err = np.linalg.norm(diff, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-30)
     max_err = np.max(np.abs(diff), axis=1)
     checked = np.asarray(margin) >= TIE_MARGIN
+    note_widened(what, int((~checked).sum()), len(checked), "excused: near-tie decision")
     assert checked.mean() >= 1.0 - max_excused, (
         f"{what}: {int((~checked).sum())} of {len(checked)} replicas are near-ties")
     if checked.any():
@@ -76,6 +86,7 @@ def assert_one_step_close(state0, gpu1, ref1, J, variant, c, dt, margin, eps=1e-
     mag_y = np.abs(y0) + dt * np.abs(p1 * x0) + c * dt * coup
     mag_x = np.abs(x0) + dt * mag_y
     checked = np.asarray(margin) >= TIE_MARGIN
+    note_widened(what, int((~checked).sum()), len(checked), "excused: near-tie decision")
     assert checked.mean() >= 1.0 - max_excused, f"{what}: too many near-tie replicas"
     # Eq. 7 subtracts (1 - A x^2) p / (M - m) from p: its operands bound the error
     p0 = np.asarray(state0["p"], np.float64)
@@ -110,6 +121,30 @@ def assert_within_fp32_drift(gpu_x, ref, drift, base, factor=3.0, margin_min=2e-
     g = np.asarray(gpu_x, np.float64)
     err = np.linalg.norm(g - ref["x"], axis=1) / np.linalg.norm(ref["x"], axis=1)
     tol = np.maximum(base, factor * drift)
+    note_widened("fp32-drift bar", int(np.sum(tol > base)), len(tol),
+                 f"bar widened to {factor:g} x FP32-storage drift")
     ok = (err <= tol) | (ref["margin"] < margin_min)
     assert ok.all(), f"errors {err[~ok]} vs tolerances {tol[~ok]}"
     return err
+
+
+def sign_tie_replicas(step_oracle, x0, nsteps, factor=10.0):
+    """Which replicas' FP64 trajectories pass a decision (a sign entering the
+    coupling, or a wall test) within factor x the deviation that FP32 storage
+    of the state has caused by that step: there FP32 arithmetic may take the
+    other branch, and a sign flip changes the coupling by 2 c dt |J_ij|, so the
+    trajectories part at O(1e-2) for any FP32 implementation. Runs the FP64
+    oracle one step at a time beside the same oracle restarted every step from
+    its state rounded to FP32 (both oracle-only). step_oracle(x, y, p, m0,
+    nsteps) runs the oracle. Returns (FP64 state after nsteps, tie mask)."""
+    xa, ya, pa = x0, 0 * x0, None
+    xb, yb, pb = x0, 0 * x0, None
+    tie = np.zeros(x0.shape[0], bool)
+    for m in range(nsteps):
+        a = step_oracle(xa, ya, pa, m, 1)
+        xa, ya, pa = a["x"], a["y"], a["p"]
+        b = step_oracle(xb, yb, pb, m, 1)
+        xb, yb, pb = (b[k].astype(np.float32).astype(np.float64) for k in ("x", "y", "p"))
+        dev = np.max(np.abs(xa - xb), axis=1)
+        tie |= a["margin"] < factor * dev
+    return {"x": xa, "y": ya, "p": pa}, tie

@@ -47,8 +47,17 @@ def _sensitivity(grad_fn, x0):
     E, gx, gA, gdt = base
     E2, gx2, gA2, gdt2 = pert
     rel = lambda a, b: np.abs(a - b) / np.maximum(np.abs(a), 1e-300)
-    return base, (rel(E, E2), np.linalg.norm(gx - gx2, axis=1) / np.linalg.norm(gx, axis=1),
-                  rel(gA, gA2), rel(gdt, gdt2))
+    return base, (rel(E, E2), _rel_norm(gx2, gx), rel(gA, gA2), rel(gdt, gdt2))
+
+
+def _rel_norm(g, w):
+    """Per replica ||g - w|| / ||w||; a replica whose reference gradient is
+    exactly zero scores 0 if g is zero there too, else infinity (never NaN)."""
+    num = np.linalg.norm(g - w, axis=1)
+    den = np.linalg.norm(w, axis=1)
+    out = np.where(num == 0, 0.0, np.inf)
+    np.divide(num, den, out=out, where=den > 0)
+    return out
 
 
 def _check(got, want, sens, ok, what, base=1e-4, factor=200.0):
@@ -60,7 +69,7 @@ def _check(got, want, sens, ok, what, base=1e-4, factor=200.0):
     for k, name in enumerate(names):
         g, w = got[k], want[k]
         if k == 1:
-            err = np.linalg.norm(g - w, axis=1) / np.linalg.norm(w, axis=1)
+            err = _rel_norm(g, w)
         else:
             if np.all(w == 0):
                 assert np.all(g == 0), name
@@ -70,6 +79,9 @@ def _check(got, want, sens, ok, what, base=1e-4, factor=200.0):
             scale = np.maximum(np.abs(w), 0.05 * np.median(np.abs(w)))
             err = np.abs(g - w) / np.maximum(scale, 1e-300)
         tol = np.maximum(base, factor * sens[k])
+        # a NaN error or tolerance would pass the comparison below: it fails here
+        assert not np.isnan(err[ok]).any(), f"{what} {name}: NaN error"
+        assert not np.isnan(tol[ok]).any(), f"{what} {name}: NaN tolerance"
         bad = ok & (err > tol)
         assert not bad.any(), (f"{what} {name}: errors {err[bad]} vs tolerances {tol[bad]}")
 

@@ -12,7 +12,7 @@ import oracle as O
 from paper_2508_17655_gb300 import gsb, inputs as I
 from tests._parity import (RTOL_TRAJ, assert_one_step_close, assert_replicas_close,
                            assert_traj_close, assert_within_fp32_drift,
-                           fp32_storage_drift, spins)
+                           fp32_storage_drift, note_widened, sign_tie_replicas, spins)
 
 pytestmark = pytest.mark.gpu
 
@@ -85,17 +85,69 @@ def test_dense_50_steps_k2000_setting(variant, precision):
     """The 1e-5 bar on the first 50 steps, at config-2 shape (N = 2000 +-1
     complete graph, R = 1024, dt = 1.25, c = 1/(2 sqrt N)) with the paper's
     K2000 step count M = 21,500 (Fig. 1(d)). "auto" is the tensor-core path
-    (FP8 for sgn x, BF16x3 for x). Sampled replicas vs the oracle."""
+    (FP8 for sgn x, FX32 digit planes for x). Sampled replicas vs the oracle.
+    For the sgn couplings a replica is excused only if its FP64 trajectory
+    passes a sign (or wall) decision within 10x the deviation FP32 storage of
+    the state has caused by that step (measured on the oracle alone): there any
+    FP32 implementation may take the other branch. Every other sampled replica
+    is held to the bar; the full-size one-step test below checks every element
+    of every replica with no such excuse."""
     N, R, M, A = 2000, 1024, 21500, 0.25
     J = I.sk_pm1(N, 0)
+    Jo = J.astype(np.float64)
     c = f32(1 / (2 * math.sqrt(N)))
     sign = variant in ("dsb", "gdsb")
+    n_pick = {"dsb": 64, "gdsb": 192}.get(variant, 16)
     st, pick, x0 = _sampled_50_steps(gsb.Problem.dense(J), None, variant, precision, N, R, M,
-                                     c, 1.25, A, 9, 48 if sign else 16)
-    ref = O.run(J.astype(np.float64), variant, x0, 0 * x0, c=c, dt=1.25, M=M, A=A, nsteps=50)
-    for k in ("x", "y", "p"):
-        assert_replicas_close(st[k][pick], ref[k], ref["margin"], rtol=RTOL_TRAJ, what=k,
-                              max_excused=0.75 if sign else 0.0)
+                                     c, 1.25, A, 9, n_pick)
+    if sign:
+        ref, tie = sign_tie_replicas(
+            lambda x, y, p, m0, n: O.run(Jo, variant, x, y, p=p, c=c, dt=1.25, M=M, A=A, m0=m0,
+                                         nsteps=n), x0, 50)
+        note_widened(f"50 steps {variant} {precision}", int(tie.sum()), len(tie),
+                     "excused: sign decision within 10x the FP32-storage deviation")
+        assert (~tie).sum() >= 8, f"only {(~tie).sum()} replicas without a near-tie"
+        margin = np.where(tie, 0.0, np.inf)
+        for k in ("x", "y", "p"):
+            assert_replicas_close(st[k][pick], ref[k], margin, rtol=RTOL_TRAJ, what=k,
+                                  max_excused=1.0)
+    else:
+        ref = O.run(Jo, variant, x0, 0 * x0, c=c, dt=1.25, M=M, A=A, nsteps=50)
+        for k in ("x", "y", "p"):
+            assert_replicas_close(st[k][pick], ref[k], ref["margin"], rtol=RTOL_TRAJ, what=k,
+                                  max_excused=0.0)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_full_size_one_step_resync_every_element(variant):
+    """The timed shape, N = 2000 +-1 complete graph, R = 1024, M = 2000, on the
+    tensor-core path the bench times (the persistent FP8 kernel for the sgn
+    couplings, FX32 for x). At steps m = 0, 50, 1000 and 1999 the GPU's FP32
+    state is handed to the oracle, both advance one step (the GPU in a
+    one-step launch of the same kernel), and every element of x, y, p of every
+    replica is compared with the operand-magnitude bound of one FP32 step. The
+    coupling signs are then the same on both sides, so only a wall test within
+    rounding of |x| = 1 can excuse a replica, at most 10 % of them."""
+    N, R, M, A = 2000, 1024, 2000, 0.25
+    J = I.sk_pm1(N, 0)
+    Jo = J.astype(np.float64)
+    c = f32(1 / (2 * math.sqrt(N)))
+    P = gsb.Problem.dense(J)
+    run = P.run(variant, M=M, R=R, c=c, dt=1.25, A=A, seed=21, defer=True)
+    want = "k_tc_persist" if variant in ("dsb", "gdsb") else "k_fx32"
+    assert run.kernel().startswith(want), run.kernel()
+    done = 0
+    for m in (0, 50, 1000, 1999):
+        if m > done:
+            run.steps(m - done)
+        s0 = run.state()
+        run.steps(1)
+        done = m + 1
+        s1 = run.state()
+        ref = O.run(Jo, variant, s0["x"].astype(np.float64), s0["y"].astype(np.float64),
+                    c=c, dt=1.25, M=M, A=A, p=s0["p"].astype(np.float64), m0=m, nsteps=1)
+        assert_one_step_close(s0, s1, ref, Jo, variant, c, 1.25, ref["wall_margin"],
+                              what=f"full size {variant} m={m}", max_excused=0.1)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "auto"])
@@ -131,7 +183,9 @@ def _one_step_resync(P, Jo, variant, N, R, M, m, **kw):
     ref = O.run(Jo, variant, s0["x"].astype(np.float64), s0["y"].astype(np.float64),
                 c=kw["c"], dt=kw["dt"], M=M, A=kw.get("A", 0.0), p=s0["p"].astype(np.float64),
                 m0=m, nsteps=1)
-    assert_one_step_close(s0, s1, ref, Jo, variant, kw["c"], kw["dt"], ref["margin"],
+    # the coupling signs come from the same FP32 state on both sides: only a
+    # wall test can be a near-tie
+    assert_one_step_close(s0, s1, ref, Jo, variant, kw["c"], kw["dt"], ref["wall_margin"],
                           what=f"{variant} m={m}")
 
 
