@@ -40,6 +40,11 @@ WORKLOAD = ("N=2000 +-1 complete graph (seed 0), R=1024 replicas, M=2000 steps, 
             "A swept over 8 values x 128 replicas, J.sgn(x) + Eq. 7 control on FP8 tcgen05")
 
 
+# DRAM bytes (read + write) of one launch of the headline kernel on the N = 2000,
+# R = 1024 shape, from the ncu captures summarised in profiles/
+KNOWN_TRAFFIC = {}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,11 +282,11 @@ def gpu_arm(args, world, rank, local):
                 "kernel": f"{kernel_name} (GdSB: e4m3 J.sgn(x) + Eqs. 3-7)",
                 "achieved": round(achieved, 1), "peak": round(fp8_peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / fp8_peak, 4),
-                # dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_persist launch
-                # of this shape (100 steps; profiles/k_tc_persist_N2000_R1024_M100.md):
-                # the state, J and V read once per launch, whatever its step count --
-                # the steps themselves run from L2 and TMEM
-                "traffic": 31493376 + 890112,
+                # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
+                # kernel and shape from an ncu capture (a 100-step launch: the state,
+                # J and V are read once per launch, whatever its step count -- the
+                # steps run from L2, shared memory and TMEM); None until captured
+                "traffic": KNOWN_TRAFFIC.get(kernel_name),
                 "traffic_note": "DRAM bytes per launch, measured on a 100-step launch of the "
                                 "same kernel and shape; independent of the steps per launch",
                 "peak_source": f"{how}: 2 x bf16 {peak_kind} (e4m3/bf16 nominal ratio; burst "
