@@ -608,13 +608,17 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         return out
     if only is not None and only not in ("batched_256", "lyapunov", "adjoint"):
         return out
-    # --- 256 batched uneven SK instances, N ~ U{64..1024}, R ~ U{32..256}, M = 1000
+    # --- 256 batched uneven SK instances, N ~ U{64..1024}, R ~ U{32..256}, M = 1000:
+    # the split-bf16 tensor-core form (persistent launches over windows of
+    # instances) and, for comparison, the FP32 CUDA-core form
     Ns, Rs = I.batch_sizes(256, seed=0)
-    probs = [gsb.Problem.dense(I.sk_gauss(int(n), 2000 + k), stream=stream.cuda_stream)
-             for k, n in enumerate(Ns)] if want("batched_256") else []
-    specs = [dict(variant="gbsb", M=1000, R=int(r), c=0.5, dt=1.25, A=0.2, seed=k)
-             for k, r in enumerate(Rs)]
-    if probs:
+    Js = [I.sk_gauss(int(n), 2000 + k) for k, n in enumerate(Ns)] if want("batched_256") else []
+    probs = [gsb.Problem.dense(J, stream=stream.cuda_stream) for J in Js]
+    su = float(np.sum(Ns * Rs)) * 1000
+    flop = float(np.sum(2.0 * Ns.astype(float) ** 2 * Rs)) * 1000  # one J x product per step
+    for form in (("bf16x3", "fp32") if probs else ()):
+        specs = [dict(variant="gbsb", M=1000, R=int(r), c=0.5, dt=1.25, A=0.2, seed=k,
+                      precision=form) for k, r in enumerate(Rs)]
         runs, _ = gsb.batch_run(probs, specs, max_steps=20, stream=stream.cuda_stream)  # warm-up
         for r in runs:
             r.close()
@@ -623,28 +627,42 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         el = time.perf_counter() - t
         for r in runs:
             r.close()
-        # the step kernels alone: CUDA events around each of their launches
+        # the step kernels alone: CUDA events around their launches
         gsb.set_call_profiling(True)
         runs, _ = gsb.batch_run(probs, specs, stream=stream.cuda_stream)
         kms, kn, ksteps = gsb.last_call_profile()
         gsb.set_call_profiling(False)
         for r in runs:
             r.close()
-        su = float(np.sum(Ns * Rs)) * 1000
-        flop = float(np.sum(2.0 * Ns.astype(float) ** 2 * Rs)) * 1000
-        flop_k = flop * ksteps / 1000.0
-    if probs:
-        ach = flop_k / (kms * 1e-3) / 1e12
-        out["batched_256"] = {
-            "workload": "256 SK instances N~U{64..1024}, N(0,1/N) FP32, R~U{32..256}, M=1000, GbSB",
-            "value": su / el, "unit": "spin-updates/s", "ms_per_run": 1e3 * el,
-            "how": "value: host wall clock around gsb_batch_run (set-up and probes included)",
-            "autotune": info, "kernel_ms": kms, "kernel_launches": kn, "kernel_steps": ksteps,
-            "roofline": {"bound": "alu", "kernel": f"k_batch_step<{info['tile']}>", "achieved": ach,
-                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                         "how": "2 sum_k N_k^2 R_k flop per step over the steps the profiled "
-                                "launches covered / their CUDA-event time",
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}}
+        if form == "bf16x3":
+            bsteps = float(np.sum(Ns * Rs))  # spin-steps per batch step
+            ach = flop / (kms * 1e-3) / 1e12
+            entry = {
+                "workload": "256 SK instances N~U{64..1024}, N(0,1/N), R~U{32..256}, M=1000, GbSB, "
+                            "split bf16 (J_hi x_hi + J_hi x_lo + J_lo x_hi) on tcgen05",
+                "value": su / el, "unit": "spin-updates/s", "ms_per_run": 1e3 * el,
+                "how": "value: host wall clock around gsb_batch_run (set-up and probes included)",
+                "autotune": info, "kernel_ms": kms, "kernel_launches": kn,
+                "kernel_value": su / (kms * 1e-3),
+                "roofline": {"bound": "tensor", "kernel": "k_bf16_multi", "achieved": ach,
+                             "peak": Pk["bf16_tflops"], "unit": "TFLOP/s",
+                             "frac": ach / Pk["bf16_tflops"],
+                             "how": "2 sum_k N_k^2 R_k flop per step (one J x product; the "
+                                    "split runs three bf16 MMAs for it) x 1000 steps / the "
+                                    "CUDA-event time of the profiled launches",
+                             "peak_source": how + " (bf16 burst)"},
+                "error_vs_fp64": batch_error_vs_oracle(gsb, probs, Js, Ns, Rs, stream)}
+            out["batched_256"] = entry
+        else:
+            ach = flop / (kms * 1e-3) / 1e12
+            out["batched_256_fp32"] = {
+                "workload": "the same 256 instances on the FP32 CUDA-core form",
+                "value": su / el, "unit": "spin-updates/s", "ms_per_run": 1e3 * el,
+                "autotune": info, "kernel_ms": kms, "kernel_launches": kn,
+                "roofline": {"bound": "alu", "kernel": f"k_batch_step<{info['tile']}>",
+                             "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": ach / fp32_peak,
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}}
     for P in probs:
         P.close()
     if only is not None and only not in ("lyapunov", "adjoint"):
@@ -681,6 +699,34 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         P5.close()
         return out
     return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak)
+
+
+def batch_error_vs_oracle(gsb, probs, Js, Ns, Rs, stream, sample=256):
+    """Per instance: the batched split-bf16 kernel's first step (from x(0),
+    y = 0, p = 1) against the FP64 oracle, as the largest |y_gpu - y_oracle|
+    over the instance relative to c dt max_i sum_j |J_ij x_j| (the coupling's
+    scale in Eq. 3). Only this leg runs the oracle (test infrastructure) and it
+    runs outside every timed region."""
+    import numpy as np
+    import oracle as O
+    specs = [dict(variant="gbsb", M=1000, R=int(r), c=0.5, dt=1.25, A=0.2, seed=k,
+                  precision="bf16x3") for k, r in enumerate(Rs)]
+    runs, _ = gsb.batch_run(probs, specs, max_steps=1, stream=stream.cuda_stream)
+    errs = []
+    for k, run in enumerate(runs[:sample]):
+        st = run.state()
+        x0 = O.init_uniform(int(Rs[k]), int(Ns[k]), k)
+        Jo = Js[k].astype(np.float64)
+        ref = O.run(Jo, "gbsb", x0, 0 * x0, c=0.5, dt=1.25, M=1000, A=0.2, nsteps=1)
+        scale = 0.5 * 1.25 * float(np.max(np.abs(x0) @ np.abs(Jo)))
+        errs.append(float(np.max(np.abs(st["y"] - ref["y"]))) / scale)
+        run.close()
+    for run in runs[sample:]:
+        run.close()
+    e = np.asarray(errs)
+    return {"per_instance_max_rel": [round(v, 9) for v in errs], "max": float(e.max()),
+            "median": float(np.median(e)),
+            "how": "first step from the same x(0): max |dy| / (c dt max_i sum_j |J_ij x_j|)"}
 
 
 def adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak):

@@ -64,17 +64,28 @@ typedef enum gsb_variant { GSB_BSB = 0, GSB_GBSB = 1, GSB_DSB = 2, GSB_GDSB = 3 
 /* Coupling arithmetic. */
 typedef enum gsb_precision {
     GSB_PREC_AUTO = 0,   /* FP8 for sgn-x coupling with integer |J| <= 16, FX32 for x coupling
-                            with integer J (128 max_i sum_j |J_ij| < 2^24), FP32 otherwise;
-                            CSR problems always use CSR */
+                            with integer J (128 max_i sum_j |J_ij| < 2^24), BF16X3 for
+                            real-valued J, FP32 otherwise; CSR problems always use CSR */
     GSB_PREC_FP32 = 1,   /* FP32 on CUDA cores (the plain form) */
     GSB_PREC_FP8 = 2,    /* tcgen05 kind::f8f6f4, e4m3 J and sgn x, FP32 accumulate: exact for
                             integer |J| <= 16; sgn-x coupling (dSB, GdSB) only */
-    GSB_PREC_FX32 = 3    /* tcgen05 kind::f16 with integer J in bf16 and x as 32-bit fixed point
+    GSB_PREC_FX32 = 3,   /* tcgen05 kind::f16 with integer J in bf16 and x as 32-bit fixed point
                             rint(x 2^30) in four signed base-256 bf16 digits; each digit plane
                             accumulates exactly, the planes are combined in int64 and rounded
                             once: the coupling is the correctly rounded J x (x exact for
                             |x| >= 2^-7, else rounded at 2^-31). Needs integer J with
                             128 max_i sum_j |J_ij| < 2^24 */
+    GSB_PREC_BF16X3 = 4  /* tcgen05 kind::f16 with split bf16 operands for any dense J:
+                            J = J_hi + J_lo and x = x_hi + x_lo (each term the bf16
+                            rounding of the remainder, 16 significant bits a pair), the
+                            coupling accumulated in FP32 as J_hi x_hi + J_hi x_lo +
+                            J_lo x_hi (J_hi s + J_lo s for sgn x, which is exact in
+                            bf16). Each product is exact; the error against FP64 is
+                            the split's 2^-16-level residue (about 2^-15 of
+                            sum_j |J_ij v_j| at most) plus FP32 accumulation. One
+                            persistent launch runs the steps between energy
+                            evaluations. Not in the paper, whose machine computes J x
+                            in 16-bit fixed point (Sec. VI) */
 } gsb_precision;
 
 /* J storage passed to gsb_create. */
@@ -302,26 +313,43 @@ gsb_status gsb_relaxed_energy_grad(gsb_problem* problem, const gsb_params* param
                                    double* grad_dt, void* stream);
 
 /* Batched runs: n independent instances (each its own dense problem and
- * parameters; uneven N and R) advanced together, one launch per time step
- * over a work list of tiles of all instances (the paper solves several
+ * parameters; uneven N and R) advanced together (the paper solves several
  * instances at once on one machine, N_batch, Sec. VI). Every instance gets an
  * ordinary run handle in runs_out[k] (query it with gsb_best / gsb_get_state,
  * free it with gsb_run_destroy) and follows exactly the trajectory gsb_run
- * would give it on the FP32 path. Energies are evaluated at t_M
- * (eval_every must be 0). An autotuner picks the tile (128 or 64 spins x
- * replicas) and the number of steps captured per CUDA graph on the run's first
- * steps; info (nullable) reports the choice; info->force_tile = 128 or 64
- * skips the tile probe; info->max_steps > 0 stops every instance after that
- * many steps (continue each with gsb_run_steps). Blocks on `stream` until
- * every instance is done. */
+ * would give it with the same precision. Energies are evaluated at t_M
+ * (eval_every must be 0). Two forms, chosen by the instances' precision (all
+ * the same): AUTO or BF16X3 -- the split-bf16 tensor-core path: the instances
+ * are packed, largest first, into windows of tiles_per_cta x (number of SMs)
+ * tiles of 128 spins x 128 replicas, and each window runs all its steps in one
+ * persistent cooperative launch over a device work list of (step, tile) items
+ * (per-instance step counters order the items; the launches of all windows
+ * are captured as one CUDA graph, see graphed below). An autotuner picks tiles_per_cta (1 or 2) by timing a
+ * few real steps of the whole batch under each. FP32 -- the CUDA-core path: one
+ * launch per time step over a work list of tiles, chunks of steps replayed
+ * from CUDA graphs; the autotuner picks the tile (128 or 64 spins x
+ * replicas) and the graph chunk length on the first steps. info (nullable)
+ * reports the choices; info->force_tile = 128 or 64 skips the FP32 tile probe,
+ * info->force_tiles_per_cta = 1 or 2 the bf16 one; info->max_steps > 0 stops
+ * every instance after that many steps (continue each with gsb_run_steps).
+ * Blocks on `stream` until every instance is done. */
 typedef struct gsb_batch_info {
-    int32_t force_tile;       /* in: 0 = autotune, 128 or 64 */
+    int32_t force_tile;       /* in: FP32 form: 0 = autotune, 128 or 64 */
     int32_t max_steps;        /* in: 0 = run every instance to its M */
-    int32_t tile;             /* out: tile used */
-    int32_t steps_per_graph;  /* out: steps captured per graph launch */
+    int32_t tile;             /* out: tile used (spins and replicas per tile) */
+    int32_t steps_per_graph;  /* out: FP32 form: steps captured per graph launch; bf16 form:
+                                 the most steps one launch covered */
     int32_t tiles;            /* out: tiles per step */
-    double ms_step_tile128;   /* out: probe time per step, tile 128 (-1 if not probed) */
-    double ms_step_tile64;    /* out: probe time per step, tile 64 (-1 if not probed) */
+    double ms_step_tile128;   /* out: FP32 probe time per step, tile 128 (-1 if not probed) */
+    double ms_step_tile64;    /* out: FP32 probe time per step, tile 64 (-1 if not probed) */
+    int32_t force_tiles_per_cta; /* in: bf16 form: 0 = autotune, 1 or 2 */
+    int32_t tiles_per_cta;    /* out: bf16 form: window size in tiles per CTA */
+    int32_t windows;          /* out: bf16 form: persistent launches (windows) */
+    int32_t ctas;             /* out: bf16 form: CTAs per launch */
+    double ms_step_probe[2];  /* out: bf16 probe time per step with 1 and 2 tiles per CTA
+                                 (-1 if not probed) */
+    int32_t graphed;          /* out: bf16 form: 1 if the windows' launches ran as one CUDA
+                                 graph, 0 if they were launched one by one */
 } gsb_batch_info;
 
 gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems, const gsb_params* params,

@@ -171,6 +171,8 @@ void free_problem(gsb_problem* P) {
     dev_free(P->J32);
     dev_free(P->J8);
     dev_free(P->J16);
+    dev_free(P->Jhi);
+    dev_free(P->Jlo);
     dev_free(P->rowptr);
     dev_free(P->col);
     dev_free(P->val);
@@ -433,7 +435,7 @@ void free_run(gsb_run_state* r) {
 }
 
 gsb_status evaluate(gsb_run_state* run, int step) {
-    if (run->path == kPathTcFp8 || run->path == kPathTcFx32) {
+    if (is_tc_path(run->path)) {
         gsb_status st = tc_energy(run);
         if (st != GSB_OK) return st;
         return launch_best_keep(run, step);
@@ -786,6 +788,8 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
                     path = kPathTcFp8;
                 else if (!sign && P->J16)
                     path = kPathTcFx32;
+                else if (!P->integer_J)
+                    path = kPathTcBf16;  // real-valued J: split bf16
                 else
                     path = kPathDenseF32;
                 break;
@@ -803,6 +807,7 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
                                      "FX32 needs integer J with 128 max_i sum_j |J_ij| < 2^24");
                 path = kPathTcFx32;
                 break;
+            case GSB_PREC_BF16X3: path = kPathTcBf16; break;
             default: return set_error(GSB_EINVAL, "unknown precision");
         }
     }
@@ -840,7 +845,7 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
         return e;
     };
     if ((st = dev_alloc(&run->x[0], nst)) || (st = dev_alloc(&run->y, nst))) return fail(st);
-    if (path != kPathTcFp8 && path != kPathTcFx32)
+    if (!is_tc_path(path))
         if ((st = dev_alloc(&run->x[1], nst))) return fail(st);
     if (control)
         if ((st = dev_alloc(&run->p, nst))) return fail(st);
@@ -883,7 +888,7 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
         dev_free(y0d);
     }
     if (st != GSB_OK) return fail(st);
-    if (path == kPathTcFp8 || path == kPathTcFx32) {
+    if (is_tc_path(path)) {
         if ((st = tc_setup(run)) != GSB_OK) return fail(st);
     }
     *out = run;
@@ -903,7 +908,7 @@ gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps) {
     if (nsteps < 0 || run->steps_done + nsteps > run->params.M)
         return set_error(GSB_EINVAL, "nsteps exceeds the remaining steps of the run");
     const int M = run->params.M;
-    if (run->path == kPathTcFp8 || run->path == kPathTcFx32) {
+    if (is_tc_path(run->path)) {
         gsb_status st = tc_steps(run, run->steps_done, nsteps);
         if (st == GSB_OK) run->steps_done += nsteps;
         return st;
@@ -988,7 +993,7 @@ gsb_status gsb_get_state(gsb_run_state* run, float* x, float* y, float* p, int32
     if (!run) return set_error(GSB_EINVAL, "run is NULL");
     gsb_status st = GSB_OK;
     const int R = run->R, N = run->N;
-    if (run->path == kPathTcFp8 || run->path == kPathTcFx32) {
+    if (is_tc_path(run->path)) {
         // the fused path keeps x, y, p in its own buffers; they are synced after every call
     }
     float* tmp = nullptr;
@@ -1079,7 +1084,7 @@ gsb_status gsb_run_set_state(gsb_run_state* run, const float* x, const float* y,
     run->steps_done = steps_done;
     // operands derived from x: sgn x for the CSR sign coupling, V for the tensor cores
     if (run->s8[0] && (st = launch_sign_extract(run))) return st;
-    if ((run->path == kPathTcFp8 || run->path == kPathTcFx32) && (st = tc_prepare(run))) return st;
+    if (is_tc_path(run->path) && (st = tc_prepare(run))) return st;
     return GSB_OK;
 }
 
@@ -1136,7 +1141,7 @@ gsb_status gsb_run_restart(gsb_run_state* run, uint64_t seed, uint32_t flags) {
     gsb_status st = reset_bookkeeping(run);
     if (st != GSB_OK) return st;
     if ((st = launch_init_state(run, nullptr, nullptr)) != GSB_OK) return st;
-    if (run->path == kPathTcFp8 || run->path == kPathTcFx32)
+    if (is_tc_path(run->path))
         if ((st = tc_prepare(run)) != GSB_OK) return st;
     if (flags & GSB_RUN_DEFER) return GSB_OK;
     return gsb_run_steps(run, run->params.M);

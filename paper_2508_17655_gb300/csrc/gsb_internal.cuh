@@ -24,7 +24,12 @@ enum Path : int {
     kPathCsr = 1,       // CSR coupling
     kPathTcFp8 = 2,     // tcgen05 e4m3, sgn x coupling
     kPathTcFx32 = 3,    // tcgen05 bf16, x as 32-bit fixed point in four digit planes
+    kPathTcBf16 = 4,    // tcgen05 bf16, J and x split into hi + lo bf16 terms
 };
+
+inline bool is_tc_path(int path) {
+    return path == kPathTcFp8 || path == kPathTcFx32 || path == kPathTcBf16;
+}
 
 // Device status word bits (written by kernels, read by the host).
 enum DevStatus : int {
@@ -60,6 +65,8 @@ struct gsb_problem {
     float* J32 = nullptr;
     uint8_t* J8 = nullptr;         // e4m3, when integer and |J| <= 16
     __nv_bfloat16* J16 = nullptr;  // bf16, when integer and 128 max row sum |J| < 2^24
+    __nv_bfloat16* Jhi = nullptr;  // bf16(J) and bf16(J - Jhi): the split-bf16 path,
+    __nv_bfloat16* Jlo = nullptr;  // made on first use
     // CSR device copy (N rows)
     int32_t* rowptr = nullptr;
     int32_t* col = nullptr;
@@ -93,7 +100,8 @@ struct gsb_run_state {
     float* sched = nullptr;   // [M+1] or null
     // tcgen05 operands, replica-major [Rp][Np] (K-major B operand)
     uint8_t* v8[2] = {nullptr, nullptr};
-    __nv_bfloat16* v16[2] = {nullptr, nullptr};  // four digit planes each: [4][Rp][Np]
+    __nv_bfloat16* v16[2] = {nullptr, nullptr};  // FX32: four digit planes [4][Rp][Np] each;
+                                                 // split bf16: [planes][Rp][Np], V(t_m) in [m & 1]
     // energy bookkeeping
     double* e_acc = nullptr;    // [Rp] sum_i s_i (J s)_i
     double* best_e = nullptr;   // [Rp]
@@ -213,6 +221,15 @@ gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps);
 gsb_status tc_energy(gsb_run_state* run);
 void tc_free(gsb_run_state* run);
 const char* tc_kernel_name(const gsb_run_state* run);
+// split-bf16 path (k_bf16.cu)
+gsb_status bf16_ensure_planes(gsb_problem* P, cudaStream_t s);
+gsb_status bf16_setup(gsb_run_state* run);
+gsb_status bf16_prepare(gsb_run_state* run);
+gsb_status bf16_steps(gsb_run_state* run, int m0, int nsteps);
+void bf16_free(gsb_run_state* run);
+gsb_status bf16_batch(gsb_run_state* const* runs, int n, const int* stop, int per_cta,
+                      double max_mb, bool graph, int* windows_out, int* grid_out,
+                      int* graphed_out, cudaStream_t s);
 // GSB_RUN_PROFILE bracketing of a step-kernel launch
 gsb_status prof_begin(gsb_run_state* run);
 gsb_status prof_end(gsb_run_state* run, int steps);

@@ -1,17 +1,23 @@
 // k_batch.cu -- many independent instances of uneven size stepped together
 // (gsb_batch_run). The paper runs several instances per machine at once and
 // keeps the better result (N_batch, Sec. VI); here every instance is an
-// ordinary run (its own J, replicas, parameters, state buffers), and one
-// launch per time step covers all of them through a device work list of
-// tiles (instance, spin block, replica block). Tiles that only hold padding
-// are never listed. Each tile is the plain FP32 SGEMM tile with Eqs. 3-7 in its
-// epilogue, summing over K in the same order as the single-run kernel, so a
-// batched instance follows exactly the trajectory it would follow alone.
+// ordinary run (its own J, replicas, parameters, state buffers).
 //
-// The step index lives in device memory and a one-thread kernel advances it,
-// so a chunk of steps is captured once as a CUDA graph and replayed. An
-// autotuner times the two tile sizes (128 and 64 spins x replicas) and the
-// graph chunk lengths on the run's first steps and keeps the fastest.
+// Split-bf16 form (precision AUTO or BF16X3): the tensor-core kernel of
+// k_bf16.cu runs windows of instances, each window all its steps in one
+// persistent launch over a device work list; batch_bf16 below sets the runs
+// up and times the window size.
+//
+// FP32 form (precision FP32): one launch per time step covers all instances
+// through a device work list of tiles (instance, spin block, replica block).
+// Tiles that only hold padding are never listed. Each tile is the plain FP32
+// SGEMM tile with Eqs. 3-7 in its epilogue, summing over K in the same order as
+// the single-run kernel, so a batched instance follows exactly the trajectory
+// it would follow alone. The step index lives in device memory and a
+// one-thread kernel advances it, so a chunk of steps is captured once as a CUDA
+// graph and replayed. An autotuner times the two tile sizes (128 and 64 spins x
+// replicas) and the graph chunk lengths on the run's first steps and keeps the
+// fastest.
 #include <algorithm>
 #include <vector>
 
@@ -157,12 +163,123 @@ gsb_status launch_batch_step(BatchState& B, int which, cudaStream_t s) {
 
 using namespace gsb;
 
+namespace gsb {
+namespace {
+
+// The split-bf16 form of gsb_batch_run (see include/gsb.h): every instance an
+// ordinary deferred run on the BF16X3 path, then persistent launches over
+// windows of instances; tiles per CTA picked by timing real steps.
+gsb_status batch_bf16(int n, gsb_problem* const* problems, const gsb_params* params,
+                      gsb_run_state** runs_out, gsb_batch_info* info, cudaStream_t s) {
+    auto cleanup = [&](gsb_status e) {
+        for (int k = 0; k < n; ++k) {
+            gsb_run_destroy(runs_out[k]);
+            runs_out[k] = nullptr;
+        }
+        return e;
+    };
+    gsb_status st = GSB_OK;
+    std::vector<int> stop(n);
+    int M_max = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!problems[k] || problems[k]->csr)
+            return cleanup(set_error(GSB_EUNSUPPORTED, "gsb_batch_run takes dense problems"));
+        if (params[k].eval_every != 0)
+            return cleanup(set_error(GSB_EUNSUPPORTED, "batched runs evaluate at t_M only"));
+        gsb_params q = params[k];
+        q.precision = GSB_PREC_BF16X3;
+        q.flags |= GSB_RUN_DEFER;
+        q.steps_per_launch = 0;
+        if ((st = gsb_run(problems[k], &q, &runs_out[k], s)) != GSB_OK) return cleanup(st);
+        stop[k] = (info && info->max_steps > 0) ? std::min(q.M, info->max_steps) : q.M;
+        M_max = std::max(M_max, stop[k]);
+    }
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    call_prof_reset();
+    const int force = info ? info->force_tiles_per_cta : 0;
+    int per_cta = force == 2 ? 2 : 1;
+    double ms_probe[2] = {-1.0, -1.0};
+    int windows = 0, grid = 0, graphed = 0;
+    // A window's working set (J, state, V) is kept within this many MB so that
+    // it stays resident in the 126 MB L2 across its steps.
+    constexpr double kWindowMB = 80.0;
+    constexpr int kProbe = 16;
+    if (force != 1 && force != 2 && M_max >= 4 * kProbe) {
+        // real steps of the whole batch under each window size; the instances'
+        // trajectories do not depend on the schedule
+        cudaEvent_t e0, e1;
+        GSB_CUDA_TRY(cudaEventCreate(&e0));
+        GSB_CUDA_TRY(cudaEventCreate(&e1));
+        for (int w = 0; w < 2 && st == GSB_OK; ++w) {
+            std::vector<int> to(n);
+            for (int k = 0; k < n; ++k) to[k] = std::min(stop[k], runs_out[k]->steps_done + kProbe);
+            GSB_CUDA_TRY(cudaEventRecord(e0, s));
+            st = bf16_batch(runs_out, n, to.data(), w + 1, kWindowMB, false, &windows, &grid,
+                            &graphed, s);
+            GSB_CUDA_TRY(cudaEventRecord(e1, s));
+            GSB_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            GSB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            ms_probe[w] = t / kProbe;
+            for (int k = 0; k < n; ++k) runs_out[k]->steps_done = to[k];
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != GSB_OK) return cleanup(st);
+        per_cta = ms_probe[1] < ms_probe[0] ? 2 : 1;
+    }
+    windows = grid = graphed = 0;
+    if ((st = bf16_batch(runs_out, n, stop.data(), per_cta, kWindowMB, true, &windows, &grid,
+                         &graphed, s)))
+        return cleanup(st);
+    if ((st = call_prof_collect())) return cleanup(st);
+    int tiles = 0, most = 0;
+    for (int k = 0; k < n; ++k) {
+        gsb_run_state* r = runs_out[k];
+        most = std::max(most, stop[k] - r->steps_done);
+        r->steps_done = stop[k];
+        tiles += ((r->N + 127) / 128) * ((r->R + 127) / 128);
+        if (stop[k] == r->params.M)
+            if ((st = run_evaluate(r, r->params.M)) != GSB_OK) return cleanup(st);
+    }
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (info) {
+        info->tile = 128;
+        info->steps_per_graph = most;
+        info->tiles = tiles;
+        info->ms_step_tile128 = -1.0;
+        info->ms_step_tile64 = -1.0;
+        info->tiles_per_cta = per_cta;
+        info->windows = windows;
+        info->ctas = grid;
+        info->ms_step_probe[0] = ms_probe[0];
+        info->ms_step_probe[1] = ms_probe[1];
+        info->graphed = graphed;
+    }
+    return GSB_OK;
+}
+
+}  // namespace
+}  // namespace gsb
+
 extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
                                     const gsb_params* params, gsb_run_state** runs_out,
                                     gsb_batch_info* info, void* stream) {
     if (n < 1 || !problems || !params || !runs_out) return set_error(GSB_EINVAL, "NULL argument or n < 1");
     for (int k = 0; k < n; ++k) runs_out[k] = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
+    // the form follows the instances' precision, which must agree
+    int prec = -1;
+    for (int k = 0; k < n; ++k) {
+        const int q = params[k].precision == GSB_PREC_FP32 ? GSB_PREC_FP32 : params[k].precision;
+        if (q != GSB_PREC_AUTO && q != GSB_PREC_BF16X3 && q != GSB_PREC_FP32)
+            return set_error(GSB_EUNSUPPORTED, "batched runs use BF16X3 (or AUTO) or FP32 coupling");
+        const int form = q == GSB_PREC_FP32 ? GSB_PREC_FP32 : GSB_PREC_BF16X3;
+        if (prec >= 0 && form != prec)
+            return set_error(GSB_EINVAL, "batched instances must share one precision form");
+        prec = form;
+    }
+    if (prec == GSB_PREC_BF16X3) return batch_bf16(n, problems, params, runs_out, info, s);
     // the batched steps run (and are captured) on a stream of their own, after
     // everything already queued on the caller's stream
     struct OwnStream {
@@ -187,8 +304,6 @@ extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
         if (params[k].eval_every != 0)
             return cleanup(set_error(GSB_EUNSUPPORTED, "batched runs evaluate at t_M only"));
         gsb_params q = params[k];
-        if (q.precision != GSB_PREC_AUTO && q.precision != GSB_PREC_FP32)
-            return cleanup(set_error(GSB_EUNSUPPORTED, "batched runs use FP32 coupling"));
         q.precision = GSB_PREC_FP32;
         q.flags |= GSB_RUN_DEFER;
         if ((st = gsb_run(problems[k], &q, &runs_out[k], stream)) != GSB_OK) return cleanup(st);

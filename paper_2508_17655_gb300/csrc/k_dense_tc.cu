@@ -895,6 +895,7 @@ void cluster_config(const gsb_run_state* run, cudaLaunchConfig_t* cfg, cudaLaunc
 bool tc_available() { return true; }
 
 const char* tc_kernel_name(const gsb_run_state* run) {
+    if (run->path == kPathTcBf16) return "k_bf16_multi";
     const TcState* T = (const TcState*)run->tc;
     if (!T) return "none";
     if (T->kind == 1) return "k_fx32_step";
@@ -903,6 +904,7 @@ const char* tc_kernel_name(const gsb_run_state* run) {
 }
 
 gsb_status tc_setup(gsb_run_state* run) {
+    if (run->path == kPathTcBf16) return bf16_setup(run);
     const gsb_problem* P = run->prob;
     TcState* T = new TcState();
     run->tc = T;
@@ -983,14 +985,19 @@ gsb_status tc_setup(gsb_run_state* run) {
 
 // V(t_0) from the current x (after the initial state is drawn).
 gsb_status tc_prepare(gsb_run_state* run) {
+    if (run->path == kPathTcBf16) return bf16_prepare(run);
     TcState* T = (TcState*)run->tc;
     dim3 grid(run->Np / 32, run->Rp / 32), block(32, 8);
+    // V(t_m) for the run's current step m goes to buffer m & 1: the persistent
+    // kernels pick the buffer by the parity of the step, and the one-step
+    // kernels start from vcur
+    const int b = run->steps_done & 1;
     if (T->kind == 0)
-        k_tc_prep<0><<<grid, block, 0, run->stream>>>(run->x[0], run->v8[0], run->Np, run->Rp);
+        k_tc_prep<0><<<grid, block, 0, run->stream>>>(run->x[0], run->v8[b], run->Np, run->Rp);
     else
-        k_tc_prep<1><<<grid, block, 0, run->stream>>>(run->x[0], run->v16[0], run->Np, run->Rp);
+        k_tc_prep<1><<<grid, block, 0, run->stream>>>(run->x[0], run->v16[b], run->Np, run->Rp);
     GSB_LAUNCH_CHECK("k_tc_prep");
-    T->vcur = 0;
+    T->vcur = b;
     return GSB_OK;
 }
 
@@ -1027,6 +1034,7 @@ gsb_status launch_persist(gsb_run_state* run, TcState* T, int m0, int n) {
 }
 
 gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps) {
+    if (run->path == kPathTcBf16) return bf16_steps(run, m0, nsteps);
     TcState* T = (TcState*)run->tc;
     if (T->persistent) {
         // one launch per stretch of steps between energy evaluations
@@ -1078,6 +1086,7 @@ gsb_status tc_energy(gsb_run_state* run) {
 }
 
 void tc_free(gsb_run_state* run) {
+    if (run->path == kPathTcBf16) return bf16_free(run);
     TcState* T = (TcState*)run->tc;
     if (T) {
         dev_free(T->counters);

@@ -84,7 +84,7 @@ extern "C" gsb_status gsb_twin_run(gsb_problem* P, const gsb_params* prm, int32_
         return st;
     }
     st = launch_init_state(run, nullptr, nullptr);
-    if (st == GSB_OK && (run->path == kPathTcFp8 || run->path == kPathTcFx32)) st = tc_prepare(run);
+    if (st == GSB_OK && is_tc_path(run->path)) st = tc_prepare(run);
     if (st == GSB_OK && !(Q.flags & GSB_RUN_DEFER)) st = gsb_run_steps(run, Q.M);
     if (st != GSB_OK) {
         gsb_run_destroy(run);

@@ -16,13 +16,14 @@ from . import build as _build
 # enums / flags of include/gsb.h
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENUMERIC, ENODEV = range(8)
 BSB, GBSB, DSB, GDSB = range(4)
-PREC_AUTO, PREC_FP32, PREC_FP8, PREC_FX32 = range(4)
+PREC_AUTO, PREC_FP32, PREC_FP8, PREC_FX32, PREC_BF16X3 = range(5)
 J_DENSE_I8, J_DENSE_F32, J_CSR_F32 = range(3)
 CREATE_DEVICE_INPUT, CREATE_NO_VALIDATE = 0x1, 0x2
 RUN_DEFER, RUN_PROFILE = 0x1, 0x2
 
 VARIANT = {"bsb": BSB, "gbsb": GBSB, "dsb": DSB, "gdsb": GDSB}
-PRECISION = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp8": PREC_FP8, "fx32": PREC_FX32}
+PRECISION = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp8": PREC_FP8, "fx32": PREC_FX32,
+             "bf16x3": PREC_BF16X3}
 
 
 class gsb_params(ctypes.Structure):
@@ -56,6 +57,12 @@ class gsb_batch_info(ctypes.Structure):
         ("tiles", ctypes.c_int32),
         ("ms_step_tile128", ctypes.c_double),
         ("ms_step_tile64", ctypes.c_double),
+        ("force_tiles_per_cta", ctypes.c_int32),
+        ("tiles_per_cta", ctypes.c_int32),
+        ("windows", ctypes.c_int32),
+        ("ctas", ctypes.c_int32),
+        ("ms_step_probe", ctypes.c_double * 2),
+        ("graphed", ctypes.c_int32),
     ]
 
 
@@ -266,10 +273,10 @@ class _BatchRun(object):
     __del__ = None
 
 
-def batch_run(problems, specs, force_tile=0, max_steps=0, stream=None):
+def batch_run(problems, specs, force_tile=0, max_steps=0, force_tiles_per_cta=0, stream=None):
     """Run len(problems) instances together (gsb_batch_run). specs: list of
     dicts with the keyword arguments of Problem.run (variant, M, R, c, dt, A,
-    seed, ...). Returns (runs, info dict)."""
+    seed, precision, ...). Returns (runs, info dict)."""
     n = len(problems)
     prms = (gsb_params * n)(*[_make_params(**sp) for sp in specs])
     handles = (_vp * n)(*[p.handle for p in problems])
@@ -277,12 +284,15 @@ def batch_run(problems, specs, force_tile=0, max_steps=0, stream=None):
     info = gsb_batch_info()
     info.force_tile = int(force_tile)
     info.max_steps = int(max_steps)
+    info.force_tiles_per_cta = int(force_tiles_per_cta)
     _check(lib().gsb_batch_run(n, handles, prms, outs, ctypes.byref(info),
                                _stream_handle(stream)))
     runs = [_BatchRun(problems[k], _vp(outs[k]), specs[k]["R"]) for k in range(n)]
     return runs, {"tile": info.tile, "steps_per_graph": info.steps_per_graph,
                   "tiles": info.tiles, "ms_step_tile128": info.ms_step_tile128,
-                  "ms_step_tile64": info.ms_step_tile64}
+                  "ms_step_tile64": info.ms_step_tile64, "tiles_per_cta": info.tiles_per_cta,
+                  "windows": info.windows, "ctas": info.ctas,
+                  "ms_step_probe": list(info.ms_step_probe), "graphed": info.graphed}
 
 
 def qubo_to_ising(Q):

@@ -91,9 +91,21 @@ def assert_one_step_close(state0, gpu1, ref1, J, variant, c, dt, margin, eps=1e-
     # Eq. 7 subtracts (1 - A x^2) p / (M - m) from p: its operands bound the error
     p0 = np.asarray(state0["p"], np.float64)
     mag_p = np.abs(p0) + np.abs(p0 - p1) + np.abs(p1)
+    # an element whose wall test (Eq. 5) one side took and the other side missed
+    # by less than the bar itself (eps x its operand magnitude) is a tie of the
+    # arithmetic's precision, not an error: excused element by element, counted
+    xg = np.asarray(gpu1["x"], np.float64)
+    yg = np.asarray(gpu1["y"], np.float64)
+    xr = np.asarray(ref1["x"], np.float64)
+    yr = np.asarray(ref1["y"], np.float64)
+    near = lambda v: np.abs(np.abs(v) - 1.0) <= eps * mag_x
+    walled = lambda v, w: (np.abs(v) == 1.0) & (w == 0.0)
+    tie = (walled(xg, yg) & ~walled(xr, yr) & near(xr)) | (walled(xr, yr) & ~walled(xg, yg) & near(xg))
+    if tie.any():
+        note_widened(what, int(tie.sum()), tie.size, "elements excused: wall test within the bar")
     for k, mag in (("y", mag_y), ("x", mag_x), ("p", mag_p)):
         err = np.abs(np.asarray(gpu1[k], np.float64) - np.asarray(ref1[k], np.float64))
-        bad = (err > eps * mag + 1e-30) & checked[:, None]
+        bad = (err > eps * mag + 1e-30) & checked[:, None] & ~tie
         assert not bad.any(), (f"{what} {k}: {int(bad.sum())} elements exceed {eps:g} x operand "
                                f"magnitude; worst ratio {float((err / (mag + 1e-30))[checked].max()):.3e}")
 
@@ -148,3 +160,18 @@ def sign_tie_replicas(step_oracle, x0, nsteps, factor=10.0):
         dev = np.max(np.abs(xa - xb), axis=1)
         tie |= a["margin"] < factor * dev
     return {"x": xa, "y": ya, "p": pa}, tie
+
+
+def coupling_scale_drift(run_oracle, x0, nsteps, rel=2.0 ** -16):
+    """Norm-wise relative drift, per replica, that a systematic relative error
+    rel of the coupling causes by itself over nsteps: the FP64 oracle with c
+    against the same oracle with c (1 - rel). run_oracle(x0, scale, nsteps)
+    runs the oracle with c scaled by `scale`. A split-bf16 coupling has such a
+    residue: J_hi + J_lo - J and the dropped J_lo x_lo term are each within
+    2^-16 of the products, and the tensor core's FP32 accumulation adds a
+    bias of the same order. Oracle-only."""
+    ref = run_oracle(x0, 1.0, nsteps)
+    pert = run_oracle(x0, 1.0 - rel, nsteps)
+    d = np.linalg.norm(pert["x"] - ref["x"], axis=1) / np.maximum(
+        np.linalg.norm(ref["x"], axis=1), 1e-30)
+    return ref, d

@@ -1,6 +1,8 @@
-"""Batched runs of uneven instances (gsb_batch_run): each instance follows
-the trajectory it follows alone, whatever tile the autotuner picks, and its
-error against the FP64 oracle stays within the single-run bars."""
+"""Batched runs of uneven instances (gsb_batch_run), in both forms: the
+split-bf16 tensor-core form (persistent launches over windows of instances)
+and the FP32 CUDA-core form. Each instance follows the trajectory it follows
+alone with the same precision, whatever the autotuner picks, and its error
+against the FP64 oracle stays within that precision's one-step bar."""
 import math
 
 import numpy as np
@@ -8,7 +10,7 @@ import pytest
 
 import oracle as O
 from paper_2508_17655_gb300 import gsb, inputs as I
-from tests._parity import assert_one_step_close
+from tests._parity import assert_one_step_close, coupling_scale_drift, note_widened
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +25,7 @@ def _built():
     build.build()
 
 
-def _instances():
+def _instances(precision):
     Ns = [70, 129, 200, 257, 300, 64, 100, 511, 128, 90]
     Rs = [33, 64, 100, 129, 40, 200, 17, 50, 128, 77]
     variants = ["gbsb", "gdsb", "bsb", "dsb", "gbsb", "gdsb", "gbsb", "dsb", "bsb", "gbsb"]
@@ -33,18 +35,32 @@ def _instances():
         J = I.sk_gauss(N, 100 + k) if k % 2 == 0 else I.sk_pm1(N, 100 + k)
         probs.append(gsb.Problem.dense(J))
         c = f32(0.5 if k % 2 == 0 else 1 / (2 * math.sqrt(N)))
-        specs.append(dict(variant=v, M=M, R=R, c=c, dt=f32(1.0), A=0.1 + 0.02 * k, seed=7 + k))
+        specs.append(dict(variant=v, M=M, R=R, c=c, dt=f32(1.0), A=0.1 + 0.02 * k, seed=7 + k,
+                          precision=precision))
     return probs, specs
 
 
-@pytest.mark.parametrize("force", [0, 128, 64])
-def test_batched_instances_match_their_single_runs_bit_exact(force):
-    probs, specs = _instances()
-    runs, info = gsb.batch_run(probs, specs, force_tile=force)
-    if force:
-        assert info["tile"] == force
+@pytest.mark.parametrize("form,force", [("fp32", 0), ("fp32", 128), ("fp32", 64),
+                                        ("bf16x3", 0), ("bf16x3", 1), ("bf16x3", 2)])
+def test_batched_instances_match_their_single_runs_bit_exact(form, force):
+    """Ten instances of uneven N (64..511) and R (17..200), all four variants,
+    Gaussian and +-1 couplings, uneven M (60..120): each batched instance ends
+    bit-identical to its single run. bf16x3: the window size forced to 1 or 2
+    tiles per CTA or autotuned (several windows, several CTAs per instance
+    and step)."""
+    probs, specs = _instances(form)
+    if form == "fp32":
+        runs, info = gsb.batch_run(probs, specs, force_tile=force)
+        if force:
+            assert info["tile"] == force
+    else:
+        runs, info = gsb.batch_run(probs, specs, force_tiles_per_cta=force)
+        if force:
+            assert info["tiles_per_cta"] == force
+        assert info["windows"] >= 1 and info["ctas"] >= 1
     for P, sp, run in zip(probs, specs, runs):
-        alone = P.run(precision="fp32", **sp)
+        alone = P.run(**sp)
+        assert alone.kernel() == ("k_dense_f32_step" if form == "fp32" else "k_bf16_multi")
         a, b = run.state(), alone.state()
         for k in ("x", "y", "p"):
             assert np.array_equal(a[k], b[k]), (sp, k)
@@ -53,19 +69,28 @@ def test_batched_instances_match_their_single_runs_bit_exact(force):
         assert np.all(ba["step"] == sp["M"])
 
 
-def test_batched_config4_shape_one_step_parity():
+# one-step bars relative to each update's operand magnitudes: FP32 sums for the
+# CUDA-core form; for split bf16, the split's residue (x_hi + x_lo and J_hi +
+# J_lo each within 2^-16 relative, the dropped J_lo x_lo term below 2^-16: at
+# most 3 x 2^-16 = 4.6e-5 of sum_j |J_ij x_j|) plus FP32 accumulation
+EPS_FORM = {"fp32": 1e-5, "bf16x3": 1e-4}
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+def test_batched_config4_shape_one_step_parity(form):
     """Config-4 shape: SK instances with N ~ U{64..1024}, Gaussian couplings
     N(0, 1/N), R ~ U{32..256}, c = 1/2, dt = 1.25, M = 1000. For every instance,
     the batched kernel's step m -> m+1 (m = 0 and 37) against the FP64 oracle
     started from the batched kernel's FP32 state at m: every element within
-    1e-5 of its update's operand magnitudes (the single-run bar)."""
+    the form's bar of its update's operand magnitudes."""
     Ns, Rs = I.batch_sizes(12, seed=4)
     probs, specs, Js = [], [], []
     for k, (N, R) in enumerate(zip(Ns.tolist(), Rs.tolist())):
         J = I.sk_gauss(N, 1000 + k)
         Js.append(J.astype(np.float64))
         probs.append(gsb.Problem.dense(J))
-        specs.append(dict(variant="gbsb", M=1000, R=R, c=0.5, dt=1.25, A=0.2, seed=k))
+        specs.append(dict(variant="gbsb", M=1000, R=R, c=0.5, dt=1.25, A=0.2, seed=k,
+                          precision=form))
     for m in (0, 37):
         s0 = [r.state() for r in gsb.batch_run(probs, specs, max_steps=m)[0]] if m else None
         s1 = [r.state() for r in gsb.batch_run(probs, specs, max_steps=m + 1)[0]]
@@ -79,14 +104,16 @@ def test_batched_config4_shape_one_step_parity():
             ref = O.run(Js[k], "gbsb", np.asarray(st0["x"], np.float64),
                         np.asarray(st0["y"], np.float64), c=0.5, dt=1.25, M=1000, A=0.2,
                         p=np.asarray(st0["p"], np.float64), m0=m, nsteps=1)
-            assert_one_step_close(st0, s1[k], ref, Js[k], "gbsb", 0.5, 1.25, ref["margin"],
-                                  what=f"instance {k} (N={N}, R={R}) m={m}")
+            assert_one_step_close(st0, s1[k], ref, Js[k], "gbsb", 0.5, 1.25, ref["wall_margin"],
+                                  eps=EPS_FORM[form],
+                                  what=f"{form} instance {k} (N={N}, R={R}) m={m}")
 
 
-def test_batched_config4_shape_50_step_error_and_energies():
+@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+def test_batched_config4_shape_50_step_error_and_energies(form):
     """The same instances over the first 50 steps: per-instance error against
-    the FP64 oracle (sampled replicas), which FP32 sequential coupling sums and
-    the instability of the top modes (c lambda_max >= 1 for these N) grow to
+    the FP64 oracle (sampled replicas), which the coupling arithmetic and the
+    instability of the top modes (c lambda_max >= 1 for these N) grow to
     ~1e-4 on some instances -- bounded here by 1e-3 -- and after finishing each
     run alone, best energies equal to the oracle energies of the best spins."""
     Ns, Rs = I.batch_sizes(12, seed=4)
@@ -95,7 +122,8 @@ def test_batched_config4_shape_50_step_error_and_energies():
         J = I.sk_gauss(N, 1000 + k)
         Js.append(J.astype(np.float64))
         probs.append(gsb.Problem.dense(J))
-        specs.append(dict(variant="gbsb", M=1000, R=R, c=0.5, dt=1.25, A=0.2, seed=k))
+        specs.append(dict(variant="gbsb", M=1000, R=R, c=0.5, dt=1.25, A=0.2, seed=k,
+                          precision=form))
     runs, info = gsb.batch_run(probs, specs, max_steps=50)
     worst = 0.0
     for k, run in enumerate(runs):
@@ -104,12 +132,20 @@ def test_batched_config4_shape_50_step_error_and_energies():
         assert st["steps"] == 50
         pick = np.linspace(0, R - 1, 4).astype(int)
         x0 = O.init_uniform(R, N, k)[pick]
-        ref = O.run(Js[k], "gbsb", x0, 0 * x0, c=0.5, dt=1.25, M=1000, A=0.2, nsteps=50)
+        step = lambda x, y, p, m0, n: O.run(Js[k], "gbsb", x, y, p=p, c=0.5, dt=1.25, M=1000,
+                                            A=0.2, m0=m0, nsteps=n)
+        if form == "bf16x3":
+            ref, drift = coupling_scale_drift(
+                lambda x, scale, n: O.run(Js[k], "gbsb", x, 0 * x, c=0.5 * scale, dt=1.25,
+                                          M=1000, A=0.2, nsteps=n), x0, 50)
+            bound = np.maximum(1e-5, 3.0 * drift)
+        else:
+            ref, bound = step(x0, 0 * x0, None, 0, 50), np.full(len(pick), 1e-3)
         ok = ref["margin"] >= 2e-6
         err = np.linalg.norm(st["x"][pick] - ref["x"], axis=1) / np.linalg.norm(ref["x"], axis=1)
+        assert not (ok & (err > bound)).any(), (k, err, bound)
         worst = max(worst, float(err[ok].max()) if ok.any() else 0.0)
         run.steps(950)  # finish the run alone; energies at t_M
         b = run.best()
         np.testing.assert_allclose(b["E"], O.energy(Js[k], b["s"]), rtol=1e-6, atol=1e-6)
-    print(f"worst per-instance 50-step error vs FP64: {worst:.2e}")
-    assert worst <= 1e-3
+    note_widened(f"batched {form} worst 50-step error {worst:.2e}", 0, len(runs), "reported")
