@@ -84,3 +84,40 @@ def test_mean_best_energy_sparse(variant):
     m1, m2 = float(np.mean(e_gpu)), float(np.mean(e_ref))
     bound = Z99 * math.sqrt(np.var(e_gpu, ddof=1) / R + np.var(e_ref, ddof=1) / R)
     assert abs(m1 - m2) <= bound, f"mean E gpu {m1:.3f} vs oracle {m2:.3f} (bound {bound:.3f})"
+
+
+def _stats_golden():
+    path = os.path.join(os.path.dirname(__file__), "golden", "stats_N2000.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def _cells():
+    return [(c["variant"], c["A"]) for c in _stats_golden()["cells"]]
+
+
+@pytest.mark.parametrize("variant,A", _cells())
+@pytest.mark.parametrize("precision", ["auto", "fp32"])
+def test_headline_shape_statistics_match_oracle(variant, A, precision):
+    """The dense precision workload itself: N = 2000 +-1 complete graph (seed
+    0), M = 2000, dt = 1.25, c = 1/(2 sqrt N), R = 1024 replicas from x(0)
+    uniform in [-0.1, 0.1), y(0) = 0 (App. A), energy at t_M (Sec. III). The
+    FP64 oracle's 1024 final energies per (variant, A) come from
+    tests/golden/make_stats_N2000.py; the GPU draws its own 1024 replicas
+    (another seed) on the path the bench times ("auto": the persistent FP8
+    kernel for GdSB, FX32 digit planes for GbSB) and on the plain FP32 form.
+    Within the 99 % bounds: P_S at the oracle target energy (two-proportion),
+    P(E <= the oracle's median energy), and the mean best energy (Welch)."""
+    g = _stats_golden()
+    cell = next(c for c in g["cells"] if c["variant"] == variant and c["A"] == A)
+    e_ref = np.asarray(cell["energies"], dtype=np.float64)
+    N, R, M, dt = g["N"], g["R"], g["M"], g["dt"]
+    c = float(np.float32(g["c"]))
+    run = gsb.Problem.dense(I.sk_pm1(N, 0)).run(variant, M=M, R=R, c=c, dt=dt, A=A,
+                                                 seed=88000 + int(1000 * A), precision=precision)
+    if precision == "auto":
+        assert run.kernel().startswith("k_tc_persist" if variant == "gdsb" else "k_fx32")
+    e_gpu = run.best()["E"]
+    target = _target("sk_pm1_N2000_seed0")
+    _compare(e_gpu, e_ref, target)
+    _compare(e_gpu, e_ref, float(np.median(e_ref)))
