@@ -324,6 +324,20 @@ def gpu_arm(args, world, rank, local):
                             "tensor_frac_bf16": (2.0 * N_SPINS ** 2 * R_REPLICAS /
                                                  (us2 / 1e6) / 1e12) / Pk["bf16_tflops"],
                             "success": success_report(e2, A, 2, E, fx_ms)}
+        # the paper's GbSB with its FPGA's 16-bit fixed-point JX (Sec. VI): FX16,
+        # persistent, e4m3 digit planes
+        t5, (k5ms, k5n, k5st), e5, _, k5name = timed_runs("gbsb", "fx16", 2, 1, 7500)
+        fx16_ms = sum(t5) / len(t5)
+        us5 = 1e3 * k5ms / k5st
+        ach5 = 2.0 * N_SPINS ** 2 * R_REPLICAS / (us5 * 1e-6) / 1e12
+        out["gbsb_fx16"] = {"value": N_SPINS * R_REPLICAS * M_STEPS / (fx16_ms / 1e3),
+                            "ms_per_step": fx16_ms, "us_per_time_step": us5, "kernel": k5name,
+                            "roofline": {"bound": "tensor", "achieved": ach5, "unit": "TFLOP/s",
+                                         "peak": fp8_peak, "frac": ach5 / fp8_peak,
+                                         "how": "one J x product (2 N^2 R flop) per step; "
+                                                "the kernel runs it as four e4m3 digit "
+                                                "planes"},
+                            "success": success_report(e5, A, 2, E, fx16_ms)}
         # the plain FP32 form, same workload: three runs, their P_S beside the
         # fused form's (the comparison is at equal success probability)
         t3, _, e3, _, _ = timed_runs("gdsb", "fp32", 3, 1, 9000, profile=False)

@@ -75,7 +75,7 @@ typedef enum gsb_precision {
                             once: the coupling is the correctly rounded J x (x exact for
                             |x| >= 2^-7, else rounded at 2^-31). Needs integer J with
                             128 max_i sum_j |J_ij| < 2^24 */
-    GSB_PREC_BF16X3 = 4  /* tcgen05 kind::f16 with split bf16 operands for any dense J:
+    GSB_PREC_BF16X3 = 4, /* tcgen05 kind::f16 with split bf16 operands for any dense J:
                             J = J_hi + J_lo and x = x_hi + x_lo (each term the bf16
                             rounding of the remainder, 16 significant bits a pair), the
                             coupling accumulated in FP32 as J_hi x_hi + J_hi x_lo +
@@ -86,6 +86,15 @@ typedef enum gsb_precision {
                             persistent launch runs the steps between energy
                             evaluations. Not in the paper, whose machine computes J x
                             in 16-bit fixed point (Sec. VI) */
+    GSB_PREC_FX16 = 5    /* the paper's 16-bit fixed-point JX (Sec. VI, Fig. 2 caption):
+                            x enters the coupling as q = rint(x 2^15) (half to even),
+                            four signed base-16 digits in e4m3 planes on tcgen05
+                            kind::f8f6f4, the planes paired into two exact FP32
+                            accumulators; f is the correctly rounded J q 2^-15. The
+                            state stays FP32. x coupling (bSB, GbSB) with integer
+                            |J| <= 16 and 136 max_i sum_j |J_ij| < 2^24; one persistent
+                            cooperative launch of (N/128) x (R/128) CTAs, which must
+                            fit on the GPU at once (else GSB_EUNSUPPORTED) */
 } gsb_precision;
 
 /* J storage passed to gsb_create. */
@@ -221,7 +230,8 @@ gsb_status gsb_kernel_time(gsb_run_state* run, double* ms, int64_t* launches, in
  * (FP8, many steps per launch, one thread-block cluster per 128 replicas),
  * "k_tc_persist<grid>" (the same, one cooperative launch), "k_tc_step<e4m3>"
  * (FP8, one step per launch), "k_fx32_step" (FX32 digit planes, one step per
- * launch), "k_dense_f32_step" or "k_csr_step". A static string owned by the
+ * launch), "k_fx16_persist" (FX16, many steps per launch), "k_bf16_multi"
+ * (split bf16, many steps per launch), "k_dense_f32_step" or "k_csr_step". A static string owned by the
  * library; "" for NULL. No GPU work. */
 const char* gsb_run_kernel(const gsb_run_state* run);
 

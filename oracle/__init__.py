@@ -189,16 +189,23 @@ VARIANTS = {
 
 
 def run(J, variant, x, y, *, c, dt, M, A=0.0, p=None, sched=None, m0=0, nsteps=None,
-        eval_every=0, best=None, nthreads=0):
+        eval_every=0, best=None, nthreads=0, jx16=False):
     """Advance R replicas from step m0 by nsteps (default: to M).
 
     x, y: R x N arrays (copied). p: R x N (default: ones = p(0), App. A).
-    A: scalar or per-replica control strength. Returns a dict with x, y, p, the
-    best-state record (E, s, step) and per-replica decision margins (the
-    smallest distance of a wall test or a sign from its threshold; wall_margin:
-    of a wall test alone)."""
+    A: scalar or per-replica control strength. jx16: the coupling takes x on the
+    16-bit fixed-point grid of the paper's JX module (Sec. VI, Fig. 2 caption).
+    Returns a dict with x, y, p, the best-state record (E, s, step) and
+    per-replica decision margins (the smallest distance of a wall test, a sign
+    or a grid rounding from its threshold; wall_margin: of a wall test alone)."""
     C = as_coupling(J)
     coupling, control = VARIANTS[variant]
+    if jx16:
+        # the paper's 16-bit fixed-point JX (Sec. VI): x on the 2^-15 grid in the
+        # coupling only; the x-coupled variants only
+        if coupling != 0:
+            raise ValueError("jx16 applies to the x coupling (bSB, GbSB)")
+        coupling = 2
     x = np.array(x, dtype=np.float64, copy=True, order="C")
     y = np.array(y, dtype=np.float64, copy=True, order="C")
     R, N = x.shape

@@ -37,7 +37,9 @@
  *   orc_bruteforce ....... pinned (closed-form max-cut graphs, exhaustive numpy)
  *   orc_run .............. pinned (Eq. 10 closed form, A=0 -> bSB (Eq. 6),
  *                          Eq. 7 product formula, time reversal, sign and
- *                          gauge symmetry, ground states of small instances)
+ *                          gauge symmetry, ground states of small instances;
+ *                          the 16-bit JX grid by a hand-computed step on
+ *                          grid midpoints and its quantisation bound)
  *   orc_lambda_extremes .. pinned (LAPACK eigvalsh on small matrices)
  *   orc_tangent_run ...... pinned (central finite differences of orc_run, the
  *                          closed-form growth rate about the x = 0 equilibrium)
@@ -215,6 +217,11 @@ double orc_bruteforce(int32_t N, const double* J, int8_t* s_best) {
  *
  *   coupling: 0 -> J x   (bSB, GbSB; Eq. 3)
  *             1 -> J sgn(x)   (dSB; Sec. VI)
+ *             2 -> J x with x taken on the 16-bit fixed-point grid of the
+ *                  paper's JX module (Sec. VI, Fig. 2 caption: the many-body
+ *                  term is computed in 16-bit fixed point, the rest in FP32):
+ *                  x -> rint(x 2^15) 2^-15, rounding half to even; |x| <= 1
+ *                  after the wall, so 16 bits with the sign
  *   control:  0 -> one shared bifurcation parameter: sched[m+1] if sched is
  *                  given, else 1 - (m+1)/M (Eq. 6)
  *             1 -> individual parameters p_i controlled by Eq. 7 with the
@@ -226,8 +233,9 @@ double orc_bruteforce(int32_t N, const double* J, int8_t* s_best) {
  * best_step (best_E must be initialised by the caller, e.g. to +inf).
  * margin (nullable, length R) receives, per replica, the smallest distance of
  * any floating-point decision from its threshold over this segment: | |x| - 1 |
- * before the wall test of Eq. 5, and |x| where sgn x enters the coupling. It
- * only observes the iteration; a decision closer than rounding error to its
+ * before the wall test of Eq. 5, |x| where sgn x enters the coupling, and the
+ * distance of x from a rounding midpoint of the fixed-point grid (coupling 2).
+ * It only observes the iteration; a decision closer than rounding error to its
  * threshold may go either way in another precision. wall_margin (nullable,
  * length R) receives the wall tests' part of it alone.
  * Returns 0, or -1 on bad arguments. */
@@ -240,6 +248,7 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
     if (N <= 0 || R <= 0 || M <= 0 || m0 < 0 || nsteps < 0 || m0 + nsteps > M) return -1;
     if (!J && !(rowptr && col && val)) return -1;
     if (control == 1 && !A) return -1;
+    if (coupling < 0 || coupling > 2) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -266,8 +275,18 @@ int orc_run(int32_t N, const double* J, const int32_t* rowptr, const int32_t* co
             }
             /* JX: many-body term of x(t_m) or of its signs */
             for (int32_t j = 0; j < N; ++j) {
-                v[j] = coupling ? orc_sgn(xr[j]) : xr[j];
-                if (coupling && fabs(xr[j]) < mrg) mrg = fabs(xr[j]);
+                if (coupling == 1) {
+                    v[j] = orc_sgn(xr[j]);
+                    if (fabs(xr[j]) < mrg) mrg = fabs(xr[j]);
+                } else if (coupling == 2) {
+                    const double u = xr[j] * 32768.0; /* exact: a power of two */
+                    v[j] = rint(u) / 32768.0;
+                    /* distance from the nearest midpoint k + 1/2, in units of x */
+                    const double d = fabs(fabs(u - floor(u)) - 0.5) / 32768.0;
+                    if (d < mrg) mrg = d;
+                } else {
+                    v[j] = xr[j];
+                }
             }
             orc_coupling(N, J, rowptr, col, val, v, f);
             /* Eq. 3: momentum, with p(t_{m+1}) and x(t_m) */
@@ -394,6 +413,7 @@ int orc_tangent_run(int32_t N, const double* J, const int32_t* rowptr, const int
     if (!J && !(rowptr && col && val)) return -1;
     if (control == 1 && !A) return -1;
     if (renorm_every <= 0) return -1;
+    if (coupling != 0 && coupling != 1) return -1;  /* no tangent through the grid rounding */
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -498,6 +518,7 @@ int orc_relaxed_energy_grad(int32_t N, const double* J, int32_t coupling, int32_
                             int32_t R, const double* x0, double* E, double* gx0, double* gA,
                             double* gdt, int32_t nthreads, int32_t f32_state) {
     if (N <= 0 || R <= 0 || M <= 0 || W < 0 || W > M || !J) return -1;
+    if (coupling != 0 && coupling != 1) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else

@@ -808,6 +808,15 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
                 path = kPathTcFx32;
                 break;
             case GSB_PREC_BF16X3: path = kPathTcBf16; break;
+            case GSB_PREC_FX16:
+                if (sign)
+                    return set_error(GSB_EUNSUPPORTED, "FX16 serves the x coupling (bSB, GbSB)");
+                if (!P->J8 || !(136.0 * P->max_row_abs < 16777216.0))
+                    return set_error(GSB_EUNSUPPORTED,
+                                     "FX16 needs integer J with |J| <= 16 and "
+                                     "136 max_i sum_j |J_ij| < 2^24");
+                path = kPathTcFx16;
+                break;
             default: return set_error(GSB_EINVAL, "unknown precision");
         }
     }

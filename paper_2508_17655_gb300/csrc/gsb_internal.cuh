@@ -25,10 +25,12 @@ enum Path : int {
     kPathTcFp8 = 2,     // tcgen05 e4m3, sgn x coupling
     kPathTcFx32 = 3,    // tcgen05 bf16, x as 32-bit fixed point in four digit planes
     kPathTcBf16 = 4,    // tcgen05 bf16, J and x split into hi + lo bf16 terms
+    kPathTcFx16 = 5,    // tcgen05 e4m3, x on the 16-bit fixed-point grid in four digit planes
 };
 
 inline bool is_tc_path(int path) {
-    return path == kPathTcFp8 || path == kPathTcFx32 || path == kPathTcBf16;
+    return path == kPathTcFp8 || path == kPathTcFx32 || path == kPathTcBf16 ||
+           path == kPathTcFx16;
 }
 
 // Device status word bits (written by kernels, read by the host).
@@ -99,7 +101,7 @@ struct gsb_run_state {
     double* twin_part = nullptr;  // partial sums of Eq. 8, [chunks][twin_pairs] + [twin_pairs]
     float* sched = nullptr;   // [M+1] or null
     // tcgen05 operands, replica-major [Rp][Np] (K-major B operand)
-    uint8_t* v8[2] = {nullptr, nullptr};
+    uint8_t* v8[2] = {nullptr, nullptr};     // FP8: sgn x [Rp][Np]; FX16: four digit planes [4][Rp][Np]
     __nv_bfloat16* v16[2] = {nullptr, nullptr};  // FX32: four digit planes [4][Rp][Np] each;
                                                  // split bf16: [planes][Rp][Np], V(t_m) in [m & 1]
     // energy bookkeeping

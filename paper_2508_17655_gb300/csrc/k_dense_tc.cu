@@ -565,6 +565,308 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     if (CLUSTER) cluster_sync();
 }
 
+// ---------------------------------------------------------------------------
+// FX16 (GSB_PREC_FX16): the x coupling with x on the 16-bit fixed-point grid of
+// the paper's JX module (Sec. VI, Fig. 2 caption), q = rint(x 2^15), written
+// as four signed base-16 digits q = d0 + 16 d1 + 256 d2 + 4096 d3 with
+// d0..d2 in [-8, 7] and d3 in [-8, 8]. The planes hold d0, 16 d1, d2, 16 d3 in
+// e4m3 (integers of at most four significant bits times a power of two:
+// exact), and the pairs share an FP32 accumulator: A0 = J (d0 + 16 d1),
+// A1 = J (d2 + 16 d3), every partial sum an integer below
+// 136 max_i sum_j |J_ij| < 2^24, exact in any order. The epilogue forms
+// A0 + 256 A1 in int32 and rounds 2^-15 times it once: f is the correctly
+// rounded J x_q.
+//
+// Persistent over many steps like k_tc_persist's grid form (cooperative
+// launch, a replica-column counter between steps): TMEM holds the two
+// accumulators and x, y ([0,128) A0, [128,256) A1, [256,512) x and y of each 16
+// spins side by side); p lives in shared memory. A ring stage is one 128-byte
+// K atom of J and of the four digit planes (80 KB), two stages.
+constexpr int kStagesX = 2;
+constexpr int kStageBytesX = 5 * BM * KB;
+__host__ __device__ constexpr int smem_bytes_fx16() {
+    return 1024 + kStagesX * kStageBytesX + BM * BN * 4 /* p */ + 512;
+}
+
+// e4m3 bytes of two small integers of at most four significant bits (exact).
+__device__ __forceinline__ uint32_t e4m3x2(int lo, int hi) {
+    return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2((float)lo, (float)hi), __NV_SATFINITE,
+                                              __NV_E4M3);
+}
+
+// The four digit-plane bytes of x: d0, 16 d1, d2, 16 d3 of q = rint(x 2^15).
+// With u = q + 0x888 (8 (1 + 16 + 256)), d_k = nibble_k(u) - 8 for k < 3 and
+// d3 = u >> 12 (arithmetic), in [-8, 8] for |x| <= 1.
+__device__ __forceinline__ void fx16_digits(float x, int (&d)[4]) {
+    const int u = __float2int_rn(x * 32768.0f) + 0x888;
+    d[0] = (u & 15) - 8;
+    d[1] = 16 * (((u >> 4) & 15) - 8);
+    d[2] = ((u >> 8) & 15) - 8;
+    d[3] = 16 * (u >> 12);
+}
+
+template <bool CONTROL>
+__global__ void __launch_bounds__(kThreadsP, 1)
+    k_fx16_persist(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmV0,
+                   const __grid_constant__ CUtensorMap tmV1, int Np, int Rp,
+                   float* __restrict__ x, float* __restrict__ y, float* __restrict__ p,
+                   const float* __restrict__ A, uint8_t* __restrict__ v0,
+                   uint8_t* __restrict__ v1, float c, float dt,
+                   const float* __restrict__ p_sched, int M, int m0, int nsteps,
+                   uint32_t* __restrict__ counters, int* status) {
+    constexpr int S = kStagesX;
+    constexpr int A1 = BM * KB;  // one K atom of 128 rows
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float* ps_sh = (float*)(smem + S * kStageBytesX);  // p [128 spins][128 replicas]
+    uint64_t* full = (uint64_t*)(ps_sh + BM * BN);
+    uint64_t* empty = full + S;
+    uint64_t* accf = empty + S;
+    uint64_t* acce = accf + 1;
+    uint64_t* drain = acce + 1;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    // stage st: J atom, then the four digit-plane atoms
+    auto stage = [&](uint32_t st, int q) { return smem + st * kStageBytesX + q * A1; };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = Np / KB;
+    const int rb = blockIdx.x, own = blockIdx.y;
+    const int i0 = own * BM, r0 = rb * BN;
+    uint32_t* ctr = counters + rb;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_init(acce, 1);
+        mbar_init(drain, 1);
+        tmem_slot[1] = 0u;  // epilogue abort flag
+        fence_barrier_init();
+        tma_prefetch_desc(&tmJ);
+        tma_prefetch_desc(&tmV0);
+        tma_prefetch_desc(&tmV1);
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0, armed = 0;
+            bool ok = true;
+            constexpr uint32_t bytes = 5 * A1;
+            for (int s = 0; s < nsteps && ok; ++s) {
+                const CUtensorMap* tv = ((m0 + s) & 1) ? &tmV1 : &tmV0;
+                const int pre = nk < S ? nk : S;
+                // J of the first stages does not depend on the other CTAs
+                for (int u = 0; u < pre; ++u) {
+                    const uint32_t gg = g + u, st = gg % S, ph = (gg / S) & 1u;
+                    if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[st], bytes);
+                    tma_load_2d(stage(st, 0), &tmJ, &full[st], u * KB, i0);
+                    armed = gg + 1;
+                }
+                // V(t_m) of the column is complete once its counter reached nk per step
+                if (ok && s > 0) {
+                    ok = wait_counter(ctr, (uint32_t)nk * (uint32_t)s, status);
+                    if (ok) fence_proxy_async();
+                }
+                // the planes of the stages armed above -- after a failed wait too, so
+                // every armed barrier completes its phase (the results are void then)
+                for (uint32_t gg = g; gg < armed; ++gg)
+                    for (int q = 0; q < 4; ++q)
+                        tma_load_2d(stage(gg % S, 1 + q), tv, &full[gg % S], (int)(gg - g) * KB,
+                                    q * Rp + r0);
+                if (!ok) break;
+                for (int u = pre; u < nk; ++u) {
+                    const uint32_t gg = g + u, st = gg % S, ph = (gg / S) & 1u;
+                    if (gg >= (uint32_t)S && !mbar_wait(&empty[st], ph ^ 1u, status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[st], bytes);
+                    tma_load_2d(stage(st, 0), &tmJ, &full[st], u * KB, i0);
+                    for (int q = 0; q < 4; ++q)
+                        tma_load_2d(stage(st, 1 + q), tv, &full[st], u * KB, q * Rp + r0);
+                    armed = gg + 1;
+                }
+                g += (uint32_t)nk;
+            }
+            // no copy is in flight when the CTA leaves
+            for (uint32_t gg = armed > (uint32_t)S ? armed - S : 0u; gg < armed; ++gg)
+                mbar_wait(&full[gg % S], (gg / S) & 1u, status, kDrainLimitCycles);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_make(0u, BM, BN);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int s = 0; s < nsteps && ok; ++s) {
+                if (s > 0 && !mbar_wait(acce, (uint32_t)(s - 1) & 1u, status)) break;
+                fence_after_sync();
+                for (int u = 0; u < nk; ++u, ++g) {
+                    const uint32_t st = g % S, ph = (g / S) & 1u;
+                    if (!mbar_wait(&full[st], ph, status)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+                    const uint32_t jb = smem_u32(stage(st, 0));
+#pragma unroll
+                    for (int k = 0; k < KB / 32; ++k) {  // 32 bytes of K per MMA
+                        const uint64_t jd = sdesc_sw128(jb + k * 32);
+                        const uint32_t first = (u | k) != 0;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            mma_f8f6f4(tmem + (q >> 1) * 128,
+                                       sdesc_sw128(smem_u32(stage(st, 1 + q)) + k * 32), jd, idesc,
+                                       (q & 1) ? 1u : first);
+                    }
+                    mma_commit(&empty[st]);
+                }
+                if (ok) mma_commit(accf);
+            }
+            mma_commit(drain);
+            mbar_wait(drain, 0, status, kDrainLimitCycles);
+        }
+    } else {
+        const int ew = warp - 2;
+        const int quarter = warp & 3;
+        const int c0 = (ew >> 2) * 64;
+        const int rl = quarter * 32 + lane;  // the thread's replica in the tile (TMEM lane)
+        const int r = r0 + rl;
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+        const float a_r = CONTROL ? A[r] : 0.f;
+        // state of this thread's replica, spins i0 + c0 .. +63: x, y into TMEM, p
+        // into shared memory
+#pragma unroll 1
+        for (int cb = c0; cb < c0 + 64; cb += 16) {
+            const size_t o = (size_t)(i0 + cb) * Rp + r;
+            float v[16], w[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                v[k] = x[o + (size_t)k * Rp];
+                w[k] = y[o + (size_t)k * Rp];
+                if (CONTROL) ps_sh[(cb + k) * BN + rl] = p[o + (size_t)k * Rp];
+            }
+            tmem_st32(tl + 256 + 2 * cb, v, w);
+        }
+        tmem_wait_st();
+        volatile uint32_t* abort_flag = tmem_slot + 1;
+        for (int s = 0; s < nsteps; ++s) {
+            const int m = m0 + s;
+            bool ok = *abort_flag == 0u;
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(accf, (uint32_t)s & 1u, status));
+            if (!ok) {
+                *abort_flag = 1u;
+                named_barrier_sync(1, kEpiThreadsP);
+                break;
+            }
+            fence_after_sync();
+            const float inv_rem = __frcp_rn((float)(M - m));
+            const float p_shared = CONTROL ? 0.f : p_sched[s];
+            // V(t_{m+1}) goes to buffer (m + 1) & 1: four planes [4][Rp][Np]
+            uint8_t* vrow = ((m & 1) ? v0 : v1) + (size_t)r * Np + i0;
+            const size_t plane = (size_t)Rp * Np;
+#pragma unroll 1
+            for (int cb = c0; cb < c0 + 64; cb += 16) {
+                float f[16], xs[16], ys[16], ps[16];
+                {
+                    uint32_t ra[16], rb2[16], rx[16], ry[16];
+                    tmem_ld16_async(tl + cb, ra);
+                    tmem_ld16_async(tl + 128 + cb, rb2);
+                    tmem_ld32_async(tl + 256 + 2 * cb, rx, ry);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        ps[k] = CONTROL ? ps_sh[(cb + k) * BN + rl] : 0.f;
+                    tmem_wait_ld(ra);
+                    tmem_wait_ld(rb2);
+                    tmem_wait_ld(rx);
+                    tmem_wait_ld(ry);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        // exact integers below 2^24 in FP32; their int32 combination
+                        // is exact, rounded once to FP32 (2^-15 is exact)
+                        const int q = __float2int_rn(__uint_as_float(ra[k])) +
+                                      256 * __float2int_rn(__uint_as_float(rb2[k]));
+                        f[k] = __int2float_rn(q) * 3.0517578125e-05f;
+                        xs[k] = __uint_as_float(rx[k]);
+                        ys[k] = __uint_as_float(ry[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    float2 x2 = make_float2(xs[k], xs[k + 1]), y2 = make_float2(ys[k], ys[k + 1]);
+                    float2 p2 = make_float2(ps[k], ps[k + 1]);
+                    sb_update2<CONTROL>(x2, y2, p2, make_float2(f[k], f[k + 1]), a_r, c, dt,
+                                        p_shared, inv_rem);
+                    xs[k] = x2.x, xs[k + 1] = x2.y, ys[k] = y2.x, ys[k + 1] = y2.y;
+                    ps[k] = p2.x, ps[k + 1] = p2.y;
+                }
+                tmem_st32(tl + 256 + 2 * cb, xs, ys);
+                if (CONTROL) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) ps_sh[(cb + k) * BN + rl] = ps[k];
+                }
+                // the next step's digit planes, 16 bytes of the replica's row each
+                uint32_t w[4][4];
+#pragma unroll
+                for (int k = 0; k < 16; k += 4) {
+                    int da[4], db[4], dc[4], dd[4];
+                    fx16_digits(xs[k], da);
+                    fx16_digits(xs[k + 1], db);
+                    fx16_digits(xs[k + 2], dc);
+                    fx16_digits(xs[k + 3], dd);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        w[q][k / 4] = e4m3x2(da[q], db[q]) | (e4m3x2(dc[q], dd[q]) << 16);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4*>(vrow + q * plane + cb) =
+                        make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            }
+            tmem_wait_st();
+            fence_before_sync();
+            named_barrier_sync(1, kEpiThreadsP);
+            if (*abort_flag) break;
+            if (ew == 0 && lane == 0) {
+                mbar_arrive(acce);
+                red_release_add(ctr, 1u);
+            }
+        }
+        // state back to global memory
+#pragma unroll 1
+        for (int cb = c0; cb < c0 + 64; cb += 16) {
+            const size_t o = (size_t)(i0 + cb) * Rp + r;
+            float v[16];
+            tmem_ld16(tl + 256 + 2 * cb, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) x[o + (size_t)k * Rp] = v[k];
+            tmem_ld16(tl + 256 + 2 * cb + 16, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) y[o + (size_t)k * Rp] = v[k];
+            if (CONTROL) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) p[o + (size_t)k * Rp] = ps_sh[(cb + k) * BN + rl];
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // V(t_0) from x(t_0): spin-major x [Np][Rp] -> replica-major operand planes.
 template <int KIND>
 __global__ void k_tc_prep(const float* __restrict__ x, void* __restrict__ v, int Np, int Rp) {
@@ -579,6 +881,13 @@ __global__ void k_tc_prep(const float* __restrict__ x, void* __restrict__ v, int
         const size_t vo = (size_t)r * Np + i;
         if (KIND == 0) {
             reinterpret_cast<uint8_t*>(v)[vo] = e4m3_sign(xv);
+        } else if (KIND == 2) {
+            int d[4];
+            fx16_digits(xv, d);
+            uint8_t* vb = reinterpret_cast<uint8_t*>(v);
+            const size_t plane = (size_t)Rp * Np;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vb[q * plane + vo] = (uint8_t)(e4m3x2(d[q], 0) & 0xFFu);
         } else {
             uint16_t d[4];
             fx32_digit_bits(xv, d);
@@ -899,6 +1208,7 @@ const char* tc_kernel_name(const gsb_run_state* run) {
     const TcState* T = (const TcState*)run->tc;
     if (!T) return "none";
     if (T->kind == 1) return "k_fx32_step";
+    if (T->kind == 2) return "k_fx16_persist";
     if (T->persistent) return T->cluster ? "k_tc_persist<cluster>" : "k_tc_persist<grid>";
     return "k_tc_step<e4m3>";
 }
@@ -908,7 +1218,7 @@ gsb_status tc_setup(gsb_run_state* run) {
     const gsb_problem* P = run->prob;
     TcState* T = new TcState();
     run->tc = T;
-    T->kind = run->path == kPathTcFp8 ? 0 : 1;
+    T->kind = run->path == kPathTcFp8 ? 0 : (run->path == kPathTcFx16 ? 2 : 1);
     const size_t n = (size_t)run->Np * run->Rp;
     gsb_status st;
     if (T->kind == 0) {
@@ -919,6 +1229,31 @@ gsb_status tc_setup(gsb_run_state* run) {
             if ((st = make_map(&T->tmB[b], run->v8[b], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, run->Np,
                                run->Rp)))
                 return st;
+    } else if (T->kind == 2) {
+        for (int b = 0; b < 2; ++b)
+            if ((st = dev_alloc(&run->v8[b], 4 * n))) return st;
+        if ((st = make_map(&T->tmA, P->J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P->Np, P->Np))) return st;
+        for (int b = 0; b < 2; ++b)
+            if ((st = make_map(&T->tmB[b], run->v8[b], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, run->Np,
+                               4 * (uint64_t)run->Rp)))
+                return st;
+        // persistent grid form only: the whole grid resident at once
+        int dev = 0, sms = 0, per_sm = 0, coop = 0;
+        GSB_CUDA_TRY(cudaGetDevice(&dev));
+        GSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        GSB_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        auto kern = run->control ? (const void*)k_fx16_persist<true> : (const void*)k_fx16_persist<false>;
+        GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          smem_bytes_fx16()));
+        GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsP,
+                                                                   smem_bytes_fx16()));
+        const int nrb = run->Rp / BN;
+        if (!coop || per_sm < 1 || (long)nrb * (run->Np / BM) > (long)per_sm * sms)
+            return set_error(GSB_EUNSUPPORTED,
+                             "FX16 runs as one cooperative grid of (N/128) x (R/128) CTAs, "
+                             "which must fit on the GPU at once");
+        if ((st = dev_alloc(&T->counters, (size_t)nrb))) return st;
+        T->persistent = true;
     } else {
         for (int b = 0; b < 2; ++b)
             if ((st = dev_alloc(&run->v16[b], 4 * n))) return st;
@@ -994,6 +1329,8 @@ gsb_status tc_prepare(gsb_run_state* run) {
     const int b = run->steps_done & 1;
     if (T->kind == 0)
         k_tc_prep<0><<<grid, block, 0, run->stream>>>(run->x[0], run->v8[b], run->Np, run->Rp);
+    else if (T->kind == 2)
+        k_tc_prep<2><<<grid, block, 0, run->stream>>>(run->x[0], run->v8[b], run->Np, run->Rp);
     else
         k_tc_prep<1><<<grid, block, 0, run->stream>>>(run->x[0], run->v16[b], run->Np, run->Rp);
     GSB_LAUNCH_CHECK("k_tc_prep");
@@ -1008,7 +1345,18 @@ gsb_status launch_persist(gsb_run_state* run, TcState* T, int m0, int n) {
     int Np = run->Np, Rp = run->Rp, M = run->params.M;
     float c = run->c, dt = run->dt;
     const float* ps = T->p_sched + m0;
-    if (T->cluster) {
+    if (T->kind == 2) {
+        const int nrb = run->Rp / BN;
+        GSB_CUDA_TRY(cudaMemsetAsync(T->counters, 0, sizeof(uint32_t) * nrb, run->stream));
+        dim3 grid(nrb, run->Np / BM);
+        void* args[] = {(void*)&T->tmA, (void*)&T->tmB[0], (void*)&T->tmB[1], &Np, &Rp,
+                        (void*)&run->x[0], (void*)&run->y, (void*)&run->p, (void*)&run->A,
+                        (void*)&run->v8[0], (void*)&run->v8[1], &c, &dt, (void*)&ps, &M, &m0, &n,
+                        (void*)&T->counters, (void*)&run->status};
+        GSB_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_fx16_persist<CONTROL>, grid,
+                                                 dim3(kThreadsP), args, smem_bytes_fx16(),
+                                                 run->stream));
+    } else if (T->cluster) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
         cluster_config(run, &cfg, at);

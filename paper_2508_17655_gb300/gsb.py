@@ -16,14 +16,14 @@ from . import build as _build
 # enums / flags of include/gsb.h
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENUMERIC, ENODEV = range(8)
 BSB, GBSB, DSB, GDSB = range(4)
-PREC_AUTO, PREC_FP32, PREC_FP8, PREC_FX32, PREC_BF16X3 = range(5)
+PREC_AUTO, PREC_FP32, PREC_FP8, PREC_FX32, PREC_BF16X3, PREC_FX16 = range(6)
 J_DENSE_I8, J_DENSE_F32, J_CSR_F32 = range(3)
 CREATE_DEVICE_INPUT, CREATE_NO_VALIDATE = 0x1, 0x2
 RUN_DEFER, RUN_PROFILE = 0x1, 0x2
 
 VARIANT = {"bsb": BSB, "gbsb": GBSB, "dsb": DSB, "gdsb": GDSB}
 PRECISION = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp8": PREC_FP8, "fx32": PREC_FX32,
-             "bf16x3": PREC_BF16X3}
+             "bf16x3": PREC_BF16X3, "fx16": PREC_FX16}
 
 
 class gsb_params(ctypes.Structure):

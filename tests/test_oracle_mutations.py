@@ -27,8 +27,14 @@ MUTATIONS = [
      [lambda: P.test_energy_cut_identity("pm1")]),
     ("wall keeps momentum", "yr[i] = 0.0;", "yr[i] = yr[i];",
      [lambda: P.test_eq7_product_formula_with_pinned_walls(0.3)]),
-    ("dsb coupling uses x", "v[j] = coupling ? orc_sgn(xr[j]) : xr[j];", "v[j] = xr[j];",
+    ("dsb coupling uses x", "v[j] = orc_sgn(xr[j]);", "v[j] = xr[j];",
      [lambda: P.test_time_reversal_of_wall_free_step("dsb")]),
+    ("jx16 grid scale", "v[j] = rint(u) / 32768.0;", "v[j] = rint(u) / 16384.0;",
+     [P.test_jx16_grid_scale_and_rounding_by_hand]),
+    ("jx16 rounds half up", "v[j] = rint(u) / 32768.0;", "v[j] = floor(u + 0.5) / 32768.0;",
+     [P.test_jx16_grid_scale_and_rounding_by_hand]),
+    ("jx16 coupling exact", "v[j] = rint(u) / 32768.0;", "v[j] = xr[j];",
+     [P.test_jx16_grid_scale_and_rounding_by_hand]),
     ("best keeps latest tie", "if (e < best_E[r]) {", "if (e <= best_E[r]) {",
      [P.test_walls_and_best_keeping]),
     ("control uses new x", None, None, [lambda: P.test_time_reversal_of_wall_free_step("gbsb")]),

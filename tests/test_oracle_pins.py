@@ -544,3 +544,48 @@ def test_adjoint_dot_product_identity_with_tangent():
     lhs = np.sum(gx * u, axis=1)
     rhs = np.sum(-(t["x"] @ J) * du, axis=1)
     np.testing.assert_allclose(lhs, rhs, rtol=1e-10)
+
+
+# ------------------------------------------------------------- 16-bit JX grid
+
+def test_jx16_grid_scale_and_rounding_by_hand():
+    """The paper's JX module works in 16-bit fixed point (Sec. VI, Fig. 2
+    caption): x enters the coupling as rint(x 2^15) 2^-15. A coupled pair
+    (J = [[0, 1], [1, 0]]) started on grid midpoints x0 = (3, 5) 2^-16 takes
+    v = (rint 1.5, rint 2.5) 2^-15 = (2, 2) 2^-15 (half to even), so after one
+    bSB step y1 = -(p(t_1) x0 - c v_swap) dt, computed here by hand."""
+    J = np.array([[0.0, 1.0], [1.0, 0.0]])
+    x0 = np.array([[3.0, 5.0]]) * 2.0 ** -16
+    c, dt, M = 0.5, 0.25, 10
+    o = O.run(J, "bsb", x0, 0 * x0, c=c, dt=dt, M=M, nsteps=1, jx16=True)
+    p1 = 1.0 - 1.0 / M
+    v = np.array([2.0, 2.0]) * 2.0 ** -15
+    y1 = -(p1 * x0[0] - c * v[::-1]) * dt
+    np.testing.assert_array_equal(o["y"][0], y1)
+    np.testing.assert_array_equal(o["x"][0], x0[0] + y1 * dt)
+    # the exact coupling differs: (x1, x0) instead of the rounded grid values
+    e = O.run(J, "bsb", x0, 0 * x0, c=c, dt=dt, M=M, nsteps=1)
+    assert not np.array_equal(e["y"], o["y"])
+
+
+def test_jx16_equals_exact_coupling_on_the_grid_and_bounds_the_error_off_it():
+    """x on the 2^-15 grid: the 16-bit coupling is the exact one (first step
+    bit-identical). x anywhere: one step's y differs from the exact coupling's
+    by at most c dt 2^-16 sum_j |J_ij| (half a grid step per term), and by more
+    than a quarter of that somewhere (the grid really is 2^-15)."""
+    N, R = 64, 8
+    J = I.sk_pm1(N, 3).astype(np.float64)
+    c, dt, M = 0.1, 0.5, 100
+    xg = np.round(O.init_uniform(R, N, 4) * 2.0 ** 15) * 2.0 ** -15
+    a = O.run(J, "gbsb", xg, 0 * xg, c=c, dt=dt, M=M, A=0.2, nsteps=1, jx16=True)
+    b = O.run(J, "gbsb", xg, 0 * xg, c=c, dt=dt, M=M, A=0.2, nsteps=1)
+    np.testing.assert_array_equal(a["x"], b["x"])
+    x0 = O.init_uniform(R, N, 5)
+    a = O.run(J, "bsb", x0, 0 * x0, c=c, dt=dt, M=M, nsteps=1, jx16=True)
+    b = O.run(J, "bsb", x0, 0 * x0, c=c, dt=dt, M=M, nsteps=1)
+    bound = c * dt * 2.0 ** -16 * np.abs(J).sum(axis=1)
+    d = np.abs(a["y"] - b["y"])
+    assert np.all(d <= bound[None, :] * (1 + 1e-12))
+    assert d.max() > 0.25 * bound.max() * 2.0 ** -3  # well above FP64 rounding
+    with pytest.raises(ValueError):
+        O.run(J, "dsb", x0, 0 * x0, c=c, dt=dt, M=M, nsteps=1, jx16=True)
