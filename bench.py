@@ -42,7 +42,12 @@ WORKLOAD = ("N=2000 +-1 complete graph (seed 0), R=1024 replicas, M=2000 steps, 
 
 # DRAM bytes (read + write) of one launch of the headline kernel on the N = 2000,
 # R = 1024 shape, from the ncu captures summarised in profiles/
-KNOWN_TRAFFIC = {}
+KNOWN_TRAFFIC = {
+    # profiles/k_tc_persist_N2000_R1024_M100.md
+    "k_tc_persist<grid>": 31493376 + 890112,
+    # profiles/k_fx16_persist_N2000_R1024_M100.md
+    "k_fx16_persist": 37800192 + 2225152,
+}
 
 
 def parse_args():
@@ -334,6 +339,7 @@ def gpu_arm(args, world, rank, local):
                             "ms_per_step": fx16_ms, "us_per_time_step": us5, "kernel": k5name,
                             "roofline": {"bound": "tensor", "achieved": ach5, "unit": "TFLOP/s",
                                          "peak": fp8_peak, "frac": ach5 / fp8_peak,
+                                         "traffic": KNOWN_TRAFFIC.get(k5name),
                                          "how": "one J x product (2 N^2 R flop) per step; "
                                                 "the kernel runs it as four e4m3 digit "
                                                 "planes"},
@@ -439,7 +445,7 @@ def _events(torch, stream):
     return e0, e1
 
 
-LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "adjoint", "fx32",
+LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "adjoint", "fx32", "fx16",
         "twin_delta", "grid", "twin_valley")
 
 
@@ -530,6 +536,19 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
                        "tensor_frac_bf16": (2.0 * N_SPINS ** 2 * R_REPLICAS / (us * 1e-6)
                                             / 1e12) / Pk["bf16_tflops"]}
         run.close()
+        P.close()
+    # --- FX16 (GbSB, the 16-bit fixed-point JX of Sec. VI, persistent), headline shape
+    if only == "fx16":
+        J = I.sk_pm1(N_SPINS, 0)
+        A = np.repeat(np.array(A_VALUES, np.float32), R_REPLICAS // len(A_VALUES))
+        P = gsb.Problem.dense(J, stream=stream.cuda_stream)
+        M = leg_M or M_STEPS
+        mk = lambda m, prof: P.run("gbsb", M=m, R=R_REPLICAS, c=1.0 / (2.0 * math.sqrt(N_SPINS)),
+                                   dt=DT, A=A, seed=1, precision="fx16", defer=True,
+                                   profile=prof, stream=stream.cuda_stream)
+        us = kernel_us(mk, M)
+        out["fx16"] = {"workload": f"{WORKLOAD}, GbSB on FX16, M={M}", "us_per_step": us,
+                       "kernel": "k_fx16_persist"}
         P.close()
     # --- twin trajectories (Sec. IV, Eq. 8): delta(t_M) over A on the K2000 shape
     # at the step count of Fig. 1(d) (M = 21,500), 100 pairs per A, GbSB
@@ -628,11 +647,15 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
     Ns, Rs = I.batch_sizes(256, seed=0)
     Js = [I.sk_gauss(int(n), 2000 + k) for k, n in enumerate(Ns)] if want("batched_256") else []
     probs = [gsb.Problem.dense(J, stream=stream.cuda_stream) for J in Js]
-    su = float(np.sum(Ns * Rs)) * 1000
-    flop = float(np.sum(2.0 * Ns.astype(float) ** 2 * Rs)) * 1000  # one J x product per step
+    small = only == "batched_256" and leg_M > 0  # a short batch, for profiling
+    Mb = leg_M if small else 1000
+    su = float(np.sum(Ns * Rs)) * Mb
+    flop = float(np.sum(2.0 * Ns.astype(float) ** 2 * Rs)) * Mb  # one J x product per step
     for form in (("bf16x3", "fp32") if probs else ()):
-        specs = [dict(variant="gbsb", M=1000, R=int(r), c=0.5, dt=1.25, A=0.2, seed=k,
-                      precision=form) for k, r in enumerate(Rs)]
+        if small and form == "fp32":
+            continue
+        specs = [dict(variant="gbsb", M=Mb, R=int(r), c=0.5, dt=1.25,
+                      A=0.2, seed=k, precision=form) for k, r in enumerate(Rs)]
         runs, _ = gsb.batch_run(probs, specs, max_steps=20, stream=stream.cuda_stream)  # warm-up
         for r in runs:
             r.close()
@@ -665,7 +688,8 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
                                     "split runs three bf16 MMAs for it) x 1000 steps / the "
                                     "CUDA-event time of the profiled launches",
                              "peak_source": how + " (bf16 burst)"},
-                "error_vs_fp64": batch_error_vs_oracle(gsb, probs, Js, Ns, Rs, stream)}
+                "error_vs_fp64": None if small else
+                batch_error_vs_oracle(gsb, probs, Js, Ns, Rs, stream)}
             out["batched_256"] = entry
         else:
             ach = flop / (kms * 1e-3) / 1e12
