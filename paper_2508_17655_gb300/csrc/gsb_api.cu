@@ -436,7 +436,7 @@ void free_run(gsb_run_state* r) {
 
 gsb_status evaluate(gsb_run_state* run, int step) {
     if (is_tc_path(run->path)) {
-        gsb_status st = tc_energy(run);
+        gsb_status st = tc_energy(run, step);
         if (st != GSB_OK) return st;
         return launch_best_keep(run, step);
     }

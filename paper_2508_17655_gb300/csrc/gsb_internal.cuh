@@ -220,7 +220,7 @@ bool tc_available();
 gsb_status tc_setup(gsb_run_state* run);
 gsb_status tc_prepare(gsb_run_state* run);
 gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps);
-gsb_status tc_energy(gsb_run_state* run);
+gsb_status tc_energy(gsb_run_state* run, int step);  // energies of sgn x(t_step)
 void tc_free(gsb_run_state* run);
 const char* tc_kernel_name(const gsb_run_state* run);
 // split-bf16 path (k_bf16.cu)

@@ -224,6 +224,127 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Ising energies (Eq. 1) on the FP8 tensor cores, for the sgn coupling's runs:
+// e_acc[r] += sum_i s_ri (J s_r)_i over the CTA's 128 spins, with
+// s = sgn x(t_m) read from the e4m3 operand V(t_m) that the step kernels leave
+// in the buffer of the step's parity. The tile is transposed as in
+// k_tc_persist (a TMEM lane is a replica), so each epilogue thread reduces its
+// replica's products over the spins in registers; the products and sums are
+// integers (exact), added in FP64 across the CTAs of a replica column.
+// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2-5 epilogue.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_energy(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const uint8_t* __restrict__ v, int Np, double* __restrict__ e_acc, int* status) {
+    constexpr int S = kStagesS;
+    constexpr int SA = BM * KB;
+    constexpr int SB = BN * KB;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + S * SA;
+    uint64_t* full = (uint64_t*)(sB + S * SB);
+    uint64_t* empty = full + S;
+    uint64_t* accf = empty + S;
+    uint64_t* drain = accf + 1;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * BN, i0 = blockIdx.y * BM;
+    const int nk = Np / KB;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_init(drain, 1);
+        fence_barrier_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    constexpr uint32_t kTmemCols = 128;
+    if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int armed = 0;
+            for (int kc = 0; kc < nk; ++kc) {
+                const int st = kc % S;
+                const uint32_t ph = (uint32_t)(kc / S) & 1u;
+                if (kc >= S && !mbar_wait(&empty[st], ph ^ 1u, status)) break;
+                mbar_arrive_expect_tx(&full[st], SA + SB);
+                tma_load_2d(sA + st * SA, &tmA, &full[st], kc * KB, i0);
+                tma_load_2d(sB + st * SB, &tmB, &full[st], kc * KB, r0);
+                armed = kc + 1;
+            }
+            for (int kc = armed > S ? armed - S : 0; kc < armed; ++kc)
+                mbar_wait(&full[kc % S], (uint32_t)(kc / S) & 1u, status, kDrainLimitCycles);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_make(0u, BN, BM);
+            bool ok = true;
+            for (int kc = 0; kc < nk && ok; ++kc) {
+                const int st = kc % S;
+                const uint32_t ph = (uint32_t)(kc / S) & 1u;
+                if (!mbar_wait(&full[st], ph, status)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t a0 = smem_u32(sA + st * SA);
+                const uint32_t b0 = smem_u32(sB + st * SB);
+#pragma unroll
+                for (int k = 0; k < KB / 32; ++k)
+                    mma_f8f6f4(tmem, sdesc_sw128(b0 + k * 32), sdesc_sw128(a0 + k * 32), idesc,
+                               (kc | k) != 0);
+                mma_commit(&empty[st]);
+            }
+            if (ok) mma_commit(accf);
+            mma_commit(drain);
+            mbar_wait(drain, 0, status, kDrainLimitCycles);
+        }
+    } else {
+        const int quarter = warp & 3;
+        const int r = r0 + quarter * 32 + lane;  // this thread's replica (TMEM lane)
+        const bool ready = __all_sync(0xffffffffu, mbar_wait(accf, 0, status));
+        if (ready) {
+            fence_after_sync();
+            const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+            const uint8_t* srow = v + (size_t)r * Np + i0;
+            // each (J s)_i is an exact integer in FP32 (the FP8 path's condition);
+            // the products with s_i = +-1 are summed in int64
+            long long part = 0;
+#pragma unroll 1
+            for (int cb = 0; cb < BM; cb += 16) {
+                float f[16];
+                tmem_ld16(tl + cb, f);
+                const uint4 b = *reinterpret_cast<const uint4*>(srow + cb);
+                const uint32_t w[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    // e4m3 +-1: the sign bit of each byte
+                    const bool neg = (w[k >> 2] >> (8 * (k & 3) + 7)) & 1u;
+                    const int fi = __float2int_rn(f[k]);
+                    part += neg ? -fi : fi;
+                }
+            }
+            atomicAdd(&e_acc[r], (double)part);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Persistent form of the FP8 step: one launch runs many steps.
 // The tile is transposed against k_tc_step: the MMA forms F^T = V J^T, so a
@@ -1428,8 +1549,24 @@ gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps) {
     return GSB_OK;
 }
 
-gsb_status tc_energy(gsb_run_state* run) {
+gsb_status tc_energy(gsb_run_state* run, int step) {
     GSB_CUDA_TRY(cudaMemsetAsync(run->e_acc, 0, sizeof(double) * run->Rp, run->stream));
+    const TcState* T = (const TcState*)run->tc;
+    if (run->path == kPathTcFp8 && T) {
+        // sgn x(t_step) is the e4m3 operand the steps left in buffer step & 1
+        const int b = step & 1;
+        static bool attr_set = false;
+        if (!attr_set) {
+            GSB_CUDA_TRY(cudaFuncSetAttribute(k_tc_energy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              smem_bytes_step()));
+            attr_set = true;
+        }
+        dim3 grid(run->Rp / BN, run->Np / BM);
+        k_tc_energy<<<grid, kThreads, smem_bytes_step(), run->stream>>>(
+            T->tmA, T->tmB[b], run->v8[b], run->Np, run->e_acc, run->status);
+        GSB_LAUNCH_CHECK("k_tc_energy");
+        return GSB_OK;
+    }
     return launch_dense_f32_energy(run->prob, run->x[0], run->Rp, run->e_acc, run->stream);
 }
 
