@@ -330,17 +330,19 @@ gsb_status gsb_relaxed_energy_grad(gsb_problem* problem, const gsb_params* param
  * would give it with the same precision. Energies are evaluated at t_M
  * (eval_every must be 0). Two forms, chosen by the instances' precision (all
  * the same): AUTO or BF16X3 -- the split-bf16 tensor-core path: the instances
- * are packed, largest first, into windows of tiles_per_cta x (number of SMs)
- * tiles of 128 spins x 128 replicas, and each window runs all its steps in one
+ * are packed, largest first, into windows of at most tiles_per_cta x (number of
+ * SMs) tiles of 128 spins x 128 replicas and a working set (J, state, operands)
+ * of 80, 120, 160 or 240 MB for 1, 2, 4 or 8 tiles per CTA (the smallest stays
+ * resident in the L2), and each window runs all its steps in one
  * persistent cooperative launch over a device work list of (step, tile) items
  * (per-instance step counters order the items; the launches of all windows
- * are captured as one CUDA graph, see graphed below). An autotuner picks tiles_per_cta (1 or 2) by timing a
- * few real steps of the whole batch under each. FP32 -- the CUDA-core path: one
+ * are captured as one CUDA graph, see graphed below). An autotuner picks tiles_per_cta (1, 2, 4
+ * or 8) by timing a few real steps of the whole batch under each. FP32 -- the CUDA-core path: one
  * launch per time step over a work list of tiles, chunks of steps replayed
  * from CUDA graphs; the autotuner picks the tile (128 or 64 spins x
  * replicas) and the graph chunk length on the first steps. info (nullable)
  * reports the choices; info->force_tile = 128 or 64 skips the FP32 tile probe,
- * info->force_tiles_per_cta = 1 or 2 the bf16 one; info->max_steps > 0 stops
+ * info->force_tiles_per_cta = 1, 2, 4 or 8 the bf16 one; info->max_steps > 0 stops
  * every instance after that many steps (continue each with gsb_run_steps).
  * Blocks on `stream` until every instance is done. */
 typedef struct gsb_batch_info {
@@ -352,12 +354,12 @@ typedef struct gsb_batch_info {
     int32_t tiles;            /* out: tiles per step */
     double ms_step_tile128;   /* out: FP32 probe time per step, tile 128 (-1 if not probed) */
     double ms_step_tile64;    /* out: FP32 probe time per step, tile 64 (-1 if not probed) */
-    int32_t force_tiles_per_cta; /* in: bf16 form: 0 = autotune, 1 or 2 */
+    int32_t force_tiles_per_cta; /* in: bf16 form: 0 = autotune, 1, 2, 4 or 8 */
     int32_t tiles_per_cta;    /* out: bf16 form: window size in tiles per CTA */
     int32_t windows;          /* out: bf16 form: persistent launches (windows) */
     int32_t ctas;             /* out: bf16 form: CTAs per launch */
-    double ms_step_probe[2];  /* out: bf16 probe time per step with 1 and 2 tiles per CTA
-                                 (-1 if not probed) */
+    double ms_step_probe[4];  /* out: bf16 probe time per step with 1, 2, 4 and 8 tiles per
+                                 CTA (-1 if not probed) */
     int32_t graphed;          /* out: bf16 form: 1 if the windows' launches ran as one CUDA
                                  graph, 0 if they were launched one by one */
 } gsb_batch_info;

@@ -197,24 +197,29 @@ gsb_status batch_bf16(int n, gsb_problem* const* problems, const gsb_params* par
     GSB_CUDA_TRY(cudaStreamSynchronize(s));
     call_prof_reset();
     const int force = info ? info->force_tiles_per_cta : 0;
-    int per_cta = force == 2 ? 2 : 1;
-    double ms_probe[2] = {-1.0, -1.0};
-    int windows = 0, grid = 0, graphed = 0;
-    // A window's working set (J, state, V) is kept within this many MB so that
-    // it stays resident in the 126 MB L2 across its steps.
-    constexpr double kWindowMB = 80.0;
+    // Window budgets the autotuner tries: tiles per CTA per step, and the MB of
+    // working set (J, state, V) a window may hold -- within the 129 MB L2 it
+    // stays resident across its steps, beyond it more tiles run at once.
+    constexpr int kCands[4] = {1, 2, 4, 8};
+    constexpr double kCandMB[4] = {80.0, 120.0, 160.0, 240.0};
     constexpr int kProbe = 16;
-    if (force != 1 && force != 2 && M_max >= 4 * kProbe) {
+    int cand = force == 2 ? 1 : force == 4 ? 2 : force == 8 ? 3 : 0;
+    int per_cta = kCands[cand];
+    double window_mb = kCandMB[cand];
+    double ms_probe[4] = {-1.0, -1.0, -1.0, -1.0};
+    int windows = 0, grid = 0, graphed = 0;
+    if (per_cta != force && M_max >= 8 * kProbe) {
         // real steps of the whole batch under each window size; the instances'
         // trajectories do not depend on the schedule
         cudaEvent_t e0, e1;
         GSB_CUDA_TRY(cudaEventCreate(&e0));
         GSB_CUDA_TRY(cudaEventCreate(&e1));
-        for (int w = 0; w < 2 && st == GSB_OK; ++w) {
+        double best = 1e300;
+        for (int w = 0; w < 4 && st == GSB_OK; ++w) {
             std::vector<int> to(n);
             for (int k = 0; k < n; ++k) to[k] = std::min(stop[k], runs_out[k]->steps_done + kProbe);
             GSB_CUDA_TRY(cudaEventRecord(e0, s));
-            st = bf16_batch(runs_out, n, to.data(), w + 1, kWindowMB, false, &windows, &grid,
+            st = bf16_batch(runs_out, n, to.data(), kCands[w], kCandMB[w], false, &windows, &grid,
                             &graphed, s);
             GSB_CUDA_TRY(cudaEventRecord(e1, s));
             GSB_CUDA_TRY(cudaEventSynchronize(e1));
@@ -222,14 +227,18 @@ gsb_status batch_bf16(int n, gsb_problem* const* problems, const gsb_params* par
             GSB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
             ms_probe[w] = t / kProbe;
             for (int k = 0; k < n; ++k) runs_out[k]->steps_done = to[k];
+            if (ms_probe[w] < best) {
+                best = ms_probe[w];
+                per_cta = kCands[w];
+                window_mb = kCandMB[w];
+            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (st != GSB_OK) return cleanup(st);
-        per_cta = ms_probe[1] < ms_probe[0] ? 2 : 1;
     }
     windows = grid = graphed = 0;
-    if ((st = bf16_batch(runs_out, n, stop.data(), per_cta, kWindowMB, true, &windows, &grid,
+    if ((st = bf16_batch(runs_out, n, stop.data(), per_cta, window_mb, true, &windows, &grid,
                          &graphed, s)))
         return cleanup(st);
     if ((st = call_prof_collect())) return cleanup(st);
@@ -252,8 +261,7 @@ gsb_status batch_bf16(int n, gsb_problem* const* problems, const gsb_params* par
         info->tiles_per_cta = per_cta;
         info->windows = windows;
         info->ctas = grid;
-        info->ms_step_probe[0] = ms_probe[0];
-        info->ms_step_probe[1] = ms_probe[1];
+        for (int w = 0; w < 4; ++w) info->ms_step_probe[w] = ms_probe[w];
         info->graphed = graphed;
     }
     return GSB_OK;

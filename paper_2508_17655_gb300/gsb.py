@@ -61,7 +61,7 @@ class gsb_batch_info(ctypes.Structure):
         ("tiles_per_cta", ctypes.c_int32),
         ("windows", ctypes.c_int32),
         ("ctas", ctypes.c_int32),
-        ("ms_step_probe", ctypes.c_double * 2),
+        ("ms_step_probe", ctypes.c_double * 4),
         ("graphed", ctypes.c_int32),
     ]
 

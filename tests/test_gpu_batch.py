@@ -41,11 +41,12 @@ def _instances(precision):
 
 
 @pytest.mark.parametrize("form,force", [("fp32", 0), ("fp32", 128), ("fp32", 64),
-                                        ("bf16x3", 0), ("bf16x3", 1), ("bf16x3", 2)])
+                                        ("bf16x3", 0), ("bf16x3", 1), ("bf16x3", 2),
+                                        ("bf16x3", 8)])
 def test_batched_instances_match_their_single_runs_bit_exact(form, force):
     """Ten instances of uneven N (64..511) and R (17..200), all four variants,
     Gaussian and +-1 couplings, uneven M (60..120): each batched instance ends
-    bit-identical to its single run. bf16x3: the window size forced to 1 or 2
+    bit-identical to its single run. bf16x3: the window size forced to 1, 2 or 8
     tiles per CTA or autotuned (several windows, several CTAs per instance
     and step)."""
     probs, specs = _instances(form)
