@@ -348,12 +348,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ---------------------------------------------------------------------------
 // Persistent form of the FP8 step: one launch runs many steps.
 // The tile is transposed against k_tc_step: the MMA forms F^T = V J^T, so a
-// TMEM lane is a replica and a column a spin. Each CTA keeps its tile's x, y
-// (and p) in TMEM next to the accumulator (columns [0,128) F; [128,384) x and
-// y of each 16 spins side by side, 32 columns per chunk, so one 32-column
-// load or store moves both; [384,512) p), so a step moves no state through
-// global memory: only the 16 KB of the next V tile leave the SM, each thread
-// writing 16 consecutive bytes of its replica's row of V at a time. The
+// TMEM lane is a replica and a column a spin. Each CTA keeps its tile's x and
+// y in TMEM next to the accumulator (columns [0,128) F; [128,384) x and y of
+// each 16 spins side by side, 32 columns per chunk, so one 32-column load or
+// store moves both) and p (individual control) in the registers of the
+// epilogue thread that owns the oscillator, 64 per thread -- a third less
+// TMEM traffic per step than with p in TMEM -- so a step moves no state
+// through global memory: only the 16 KB of the next V tile leave the SM, each
+// thread writing 16 consecutive bytes of its replica's row of V at a time. The
 // products are +-J_ij and the sums integers, so F is bit-identical to
 // k_tc_step's whatever the order of the K slices.
 //
@@ -373,6 +375,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 // J does not change, so the producer issues the first ring stages' J tiles
 // before it waits.
 //
+// FORM: kFormCluster is the cluster form above, kFormGrid the grid form, and
+// kFormPair the grid form on SM pairs: the CTAs of replica blocks 2q and
+// 2q + 1 (same spin block) are a cluster of two whose MMAs (cta_group::2,
+// M = 256) the even CTA issues. Each CTA stages its own 128 rows of V and
+// half of the spin block's J rows (64), so a K slice costs an SM 24 KB of
+// shared memory and of L2 reads instead of 32 KB: four stages of two slices
+// fit where three did, for the same 128 x 128 tile per SM. The even CTA's
+// full barriers count both CTAs' bytes (the odd CTA's loads signal them
+// across the pair), the MMA issuer's commits arrive on both CTAs' barriers,
+// and both epilogues release the accumulator on the even CTA's barrier. The
+// exchange of V between steps is the grid form's, per replica block.
+//
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2-9 epilogue (warp w
 // reads TMEM lanes 32 (w % 4).. -- its 32 replicas -- and columns 64 ((w - 2)
 // / 4) .. +63 -- 64 spins).
@@ -384,12 +398,15 @@ constexpr int kEpiThreadsP = 256;
 constexpr int kAtomsP = 2;
 constexpr int kStagesP = 3;
 constexpr int kMaxClusterP = 16;  // the largest (non-portable) cluster
+constexpr int kStagesQ = 4;       // ring stages of the pair form
+enum : int { kFormGrid = 0, kFormCluster = 1, kFormPair = 2 };
 
-__host__ __device__ constexpr int smem_bytes_persist() {
-    return 1024 + kStagesP * kAtomsP * 2 * BM * KB + 512;
+__host__ __device__ constexpr int smem_bytes_persist(int form = kFormGrid) {
+    return form == kFormPair ? 1024 + kStagesQ * kAtomsP * (BN + BM / 2) * KB + 512
+                             : 1024 + kStagesP * kAtomsP * 2 * BM * KB + 512;
 }
 
-template <bool CONTROL, bool CLUSTER>
+template <bool CONTROL, int FORM>
 __global__ void __launch_bounds__(kThreadsP, 1)
     k_tc_persist(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmV0,
                  const __grid_constant__ CUtensorMap tmV1, int Np, int Rp, float* __restrict__ x,
@@ -397,8 +414,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                  uint8_t* __restrict__ v0, uint8_t* __restrict__ v1, float c, float dt,
                  const float* __restrict__ p_sched, int M, int m0, int nsteps,
                  uint32_t* __restrict__ counters, int* status) {
-    constexpr int S = kStagesP;
-    constexpr int SA1 = BM * KB, SB1 = BN * KB;  // one K atom of J / of V
+    constexpr bool CLUSTER = FORM == kFormCluster, PAIR = FORM == kFormPair;
+    constexpr int S = PAIR ? kStagesQ : kStagesP;
+    constexpr int JR = PAIR ? BM / 2 : BM;       // J rows this CTA stages
+    constexpr int SA1 = JR * KB, SB1 = BN * KB;  // one K atom of J / of V
     constexpr int SA = kAtomsP * SA1, SB = kAtomsP * SB1;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -420,6 +439,9 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     const int rb = CLUSTER ? (int)blockIdx.y : (int)blockIdx.x;
     const int i0 = own * BM, r0 = rb * BN;
     uint32_t* ctr = counters + rb;
+    // pair form: this CTA's rank in its pair (0 issues the MMAs)
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0u;
     // the k-th K atom of a step: rotated from the CTA's own slice in the cluster form
     auto atom = [&](int k) { return CLUSTER ? (own + k) % nk : k; };
 
@@ -429,7 +451,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             mbar_init(&empty[st], 1);
         }
         mbar_init(accf, 1);
-        mbar_init(acce, 1);
+        mbar_init(acce, PAIR ? 2u : 1u);  // pair form: both epilogues, on the even CTA
         mbar_init(&vready[0], (uint32_t)nk);
         mbar_init(&vready[1], (uint32_t)nk);
         mbar_init(drain, 1);
@@ -439,12 +461,18 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         tma_prefetch_desc(&tmV0);
         tma_prefetch_desc(&tmV1);
     }
-    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    if (warp == 1) {
+        if (PAIR)
+            tmem_alloc_pair(tmem_slot, 512);
+        else
+            tmem_alloc(tmem_slot, 512);
+    }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    // every CTA's barriers exist before any CTA arrives on them
-    if (CLUSTER) cluster_sync();
+    // every CTA's barriers (and, in pairs, both TMEM allocations) exist before
+    // any CTA arrives on them or issues an MMA
+    if (CLUSTER || PAIR) cluster_sync();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
@@ -454,16 +482,32 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             bool ok = true;
             // K atoms u kAtomsP .. of a step go to stage u
             auto atoms = [&](int u) { return nk - u * kAtomsP < kAtomsP ? nk - u * kAtomsP : kAtomsP; };
+            // pair form: every load signals the even CTA's full barrier,
+            // which expects both CTAs' bytes
+            const uint32_t full_pair = PAIR ? mapa_u32(smem_u32(full), 0u) : 0u;
             auto load_j = [&](int u, uint32_t st) {
-                mbar_arrive_expect_tx(&full[st], (uint32_t)atoms(u) * (SA1 + SB1));
-                for (int a = 0; a < atoms(u); ++a)
-                    tma_load_2d(sA + st * SA + a * SA1, &tmA, &full[st], atom(u * kAtomsP + a) * KB,
-                                i0);
+                if (!PAIR) {
+                    mbar_arrive_expect_tx(&full[st], (uint32_t)atoms(u) * (SA1 + SB1));
+                    for (int a = 0; a < atoms(u); ++a)
+                        tma_load_2d(sA + st * SA + a * SA1, &tmA, &full[st],
+                                    atom(u * kAtomsP + a) * KB, i0);
+                } else {
+                    if (leader)
+                        mbar_arrive_expect_tx(&full[st], 2u * (uint32_t)atoms(u) * (SA1 + SB1));
+                    for (int a = 0; a < atoms(u); ++a)
+                        tma_load_2d_pair(sA + st * SA + a * SA1, &tmA, full_pair + 8u * st,
+                                         atom(u * kAtomsP + a) * KB, i0 + (int)rank * JR);
+                }
             };
             auto load_v = [&](int u, uint32_t st, const CUtensorMap* tv) {
-                for (int a = 0; a < atoms(u); ++a)
-                    tma_load_2d(sB + st * SB + a * SB1, tv, &full[st], atom(u * kAtomsP + a) * KB,
-                                r0);
+                for (int a = 0; a < atoms(u); ++a) {
+                    if (PAIR)
+                        tma_load_2d_pair(sB + st * SB + a * SB1, tv, full_pair + 8u * st,
+                                         atom(u * kAtomsP + a) * KB, r0);
+                    else
+                        tma_load_2d(sB + st * SB + a * SB1, tv, &full[st],
+                                    atom(u * kAtomsP + a) * KB, r0);
+                }
             };
             uint32_t armed = 0;  // ring positions whose full barrier has been armed
             for (int s = 0; s < nsteps && ok; ++s) {
@@ -507,17 +551,22 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                 g += ns;
             }
             // no copy is in flight when the CTA leaves: the last phase armed on
-            // every stage has landed
-            for (uint32_t gg = armed > (uint32_t)S ? armed - S : 0u; gg < armed; ++gg)
-                mbar_wait(&full[gg % S], (gg / S) & 1u, status, kDrainLimitCycles);
+            // every stage has landed (in pairs, the even CTA's full barriers
+            // count the odd CTA's copies too, and both leave together)
+            if (leader)
+                for (uint32_t gg = armed > (uint32_t)S ? armed - S : 0u; gg < armed; ++gg)
+                    mbar_wait(&full[gg % S], (gg / S) & 1u, status, kDrainLimitCycles);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_make(0u, BM, BN);
+        if (lane == 0 && leader) {
+            constexpr uint32_t idesc = idesc_make(0u, PAIR ? 2 * BN : BN, BM);
             uint32_t g = 0;
             bool ok = true;
             for (int s = 0; s < nsteps && ok; ++s) {
-                if (s > 0 && !mbar_wait(acce, (uint32_t)(s - 1) & 1u, status)) break;
+                // pair form: the odd CTA's epilogue arrives from across the pair
+                if (s > 0 && !(PAIR ? mbar_wait_cluster(acce, (uint32_t)(s - 1) & 1u, status)
+                                    : mbar_wait(acce, (uint32_t)(s - 1) & 1u, status)))
+                    break;
                 fence_after_sync();
                 for (int u = 0; u < ns; ++u, ++g) {
                     const uint32_t st = g % S, ph = (g / S) & 1u;
@@ -531,16 +580,32 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                         const uint32_t a0 = smem_u32(sA + st * SA + a * SA1);
                         const uint32_t b0 = smem_u32(sB + st * SB + a * SB1);
 #pragma unroll
-                        for (int k = 0; k < KB / 32; ++k)
-                            mma_f8f6f4(tmem, sdesc_sw128(b0 + k * 32), sdesc_sw128(a0 + k * 32),
-                                       idesc, (u | a | k) != 0);
+                        for (int k = 0; k < KB / 32; ++k) {
+                            if (PAIR)
+                                mma_f8f6f4_pair(tmem, sdesc_sw128(b0 + k * 32),
+                                                sdesc_sw128(a0 + k * 32), idesc, (u | a | k) != 0);
+                            else
+                                mma_f8f6f4(tmem, sdesc_sw128(b0 + k * 32), sdesc_sw128(a0 + k * 32),
+                                           idesc, (u | a | k) != 0);
+                        }
                     }
-                    mma_commit(&empty[st]);
+                    if (PAIR)
+                        mma_commit_pair(&empty[st]);
+                    else
+                        mma_commit(&empty[st]);
                 }
-                if (ok) mma_commit(accf);
+                if (ok) {
+                    if (PAIR)
+                        mma_commit_pair(accf);
+                    else
+                        mma_commit(accf);
+                }
             }
             // every MMA issued has finished before TMEM is released
-            mma_commit(drain);
+            if (PAIR)
+                mma_commit_pair(drain);
+            else
+                mma_commit(drain);
             mbar_wait(drain, 0, status, kDrainLimitCycles);
         }
     } else {
@@ -550,7 +615,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         const int r = r0 + quarter * 32 + lane;  // this thread's replica (TMEM lane)
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         const float a_r = CONTROL ? A[r] : 0.f;
-        // state of this thread's replica, spins i0 + c0 .. +63, into TMEM
+        // state of this thread's replica, spins i0 + c0 .. +63: x and y into
+        // TMEM, p (individual control) into registers -- a step's TMEM traffic
+        // is then F, x, y in and x, y out
+        float pr[CONTROL ? 64 : 1];
 #pragma unroll 1
         for (int cb = c0; cb < c0 + 64; cb += 16) {
             const size_t o = (size_t)(i0 + cb) * Rp + r;
@@ -562,11 +630,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                 w[k] = y[o + (size_t)k * Rp];
             }
             tmem_st32(tl + 128 + 2 * cb, v, w);
-            if (CONTROL) {
+        }
+        if (CONTROL) {
 #pragma unroll
-                for (int k = 0; k < 16; ++k) v[k] = p[o + (size_t)k * Rp];
-                tmem_st16(tl + 384 + cb, v);
-            }
+            for (int k = 0; k < 64; ++k) pr[k] = p[(size_t)(i0 + c0 + k) * Rp + r];
         }
         tmem_wait_st();
         // Every epilogue warp passes the same named barriers: a timeout in one of
@@ -587,25 +654,24 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             // V(t_{m+1}) goes to buffer (m + 1) & 1; this thread's 16 spins of a
             // chunk are 16 consecutive bytes of its replica's row
             uint8_t* vrow = ((m & 1) ? v0 : v1) + (size_t)r * Np + i0;
-#pragma unroll 1
-            for (int cb = c0; cb < c0 + 64; cb += 16) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cb = c0 + 16 * j;
                 float f[16], xs[16], ys[16], ps[16];
                 {
-                    // the four loads in flight together, one wait
-                    uint32_t rf[16], rx[16], ry[16], rp[16];
+                    // the loads in flight together, one wait
+                    uint32_t rf[16], rx[16], ry[16];
                     tmem_ld16_async(tl + cb, rf);
                     tmem_ld32_async(tl + 128 + 2 * cb, rx, ry);
-                    if (CONTROL) tmem_ld16_async(tl + 384 + cb, rp);
                     tmem_wait_ld(rf);
                     tmem_wait_ld(rx);
                     tmem_wait_ld(ry);
-                    if (CONTROL) tmem_wait_ld(rp);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         f[k] = __uint_as_float(rf[k]);
                         xs[k] = __uint_as_float(rx[k]);
                         ys[k] = __uint_as_float(ry[k]);
-                        ps[k] = CONTROL ? __uint_as_float(rp[k]) : 0.f;
+                        ps[k] = CONTROL ? pr[16 * j + k] : 0.f;
                     }
                 }
 #pragma unroll
@@ -618,7 +684,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     ps[k] = p2.x, ps[k + 1] = p2.y;
                 }
                 tmem_st32(tl + 128 + 2 * cb, xs, ys);
-                if (CONTROL) tmem_st16(tl + 384 + cb, ps);
+                if (CONTROL) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) pr[16 * j + k] = ps[k];
+                }
                 // e4m3 sgn x, 0x38 (+1) or 0xB8 (-1): the sign bit of x + 0 (which
                 // turns -0 into +0, so sgn 0 = +1) in the top byte of each word,
                 // four gathered per word
@@ -647,7 +716,12 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             named_barrier_sync(1, kEpiThreadsP);
             if (*abort_flag) break;
             if (ew == 0) {
-                if (lane == 0) mbar_arrive(acce);
+                if (lane == 0) {
+                    if (PAIR && !leader)
+                        mbar_arrive_remote(acce, 0u);
+                    else
+                        mbar_arrive(acce);
+                }
                 if (!CLUSTER) {
                     if (lane == 0) red_release_add(ctr, 1u);
                 } else if (s + 1 < nsteps && lane < nk) {
@@ -669,18 +743,30 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             tmem_ld16(tl + 128 + 2 * cb + 16, v);
 #pragma unroll
             for (int k = 0; k < 16; ++k) y[o + (size_t)k * Rp] = v[k];
-            if (CONTROL) {
-                tmem_ld16(tl + 384 + cb, v);
+        }
+        if (CONTROL) {
 #pragma unroll
-                for (int k = 0; k < 16; ++k) p[o + (size_t)k * Rp] = v[k];
-            }
+            for (int k = 0; k < 64; ++k) p[(size_t)(i0 + c0 + k) * Rp + r] = pr[k];
         }
     }
     fence_before_sync();
     __syncthreads();
+    if (PAIR) {
+        // the even CTA's MMAs have written this CTA's TMEM for the last time
+        // (its own MMA warp waited for the same commit), and neither CTA
+        // releases TMEM or leaves while the other may still use it
+        if (!leader && warp == 1) {
+            if (lane == 0) mbar_wait(drain, 0, status, kDrainLimitCycles);
+            __syncwarp();
+        }
+        cluster_sync();
+    }
     if (warp == 1) {
         fence_after_sync();
-        tmem_dealloc(tmem, 512);
+        if (PAIR)
+            tmem_dealloc_pair(tmem, 512);
+        else
+            tmem_dealloc(tmem, 512);
     }
     // no CTA leaves while another may still arrive on its barriers
     if (CLUSTER) cluster_sync();
@@ -1027,6 +1113,8 @@ struct TcState {
     int kind = 0;
     bool persistent = false;     // a multi-step kernel runs this shape
     bool cluster = false;        // ... in its cluster form (else the cooperative grid form)
+    bool pair = false;           // ... in the grid form on SM pairs
+    CUtensorMap tmA_half;        // J in tiles of 64 rows (the pair form)
     uint32_t* counters = nullptr;  // one per replica block
     float* p_sched = nullptr;      // p(t_{m+1}) for m = 0..M-1 (shared schedule)
 };
@@ -1047,12 +1135,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 // 2D K-major tensor map: inner dimension K (contiguous), outer rows; box of
 // one 128-byte K slice by 128 rows, 128-byte swizzle.
 gsb_status make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, int elem_bytes,
-                    uint64_t inner, uint64_t outer) {
+                    uint64_t inner, uint64_t outer, uint32_t box_rows = 128u) {
     auto encode = get_encode();
     if (!encode) return set_error(GSB_ECUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {inner, outer};
     cuuint64_t strides[1] = {inner * (cuuint64_t)elem_bytes};
-    cuuint32_t box[2] = {(cuuint32_t)(KB / elem_bytes), 128u};
+    cuuint32_t box[2] = {(cuuint32_t)(KB / elem_bytes), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1u, 1u};
     CUresult r = encode(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1305,6 +1393,24 @@ gsb_status launch_step(gsb_run_state* run, TcState* T, float p_shared, float inv
     return GSB_OK;
 }
 
+// Pair form: grid (replica blocks, spin blocks), clusters of two replica
+// blocks, launched cooperatively (the column counters need the whole grid
+// resident).
+void pair_config(const gsb_run_state* run, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at) {
+    cfg->gridDim = dim3(run->Rp / BN, run->Np / BM);
+    cfg->blockDim = dim3(kThreadsP);
+    cfg->dynamicSmemBytes = smem_bytes_persist(kFormPair);
+    cfg->stream = run->stream;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    cfg->attrs = at;
+    cfg->numAttrs = 2;
+}
+
 // Cluster form: grid (spin blocks, replica blocks), one cluster per replica block.
 void cluster_config(const gsb_run_state* run, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at) {
     const int nk = run->Np / BM;
@@ -1330,7 +1436,8 @@ const char* tc_kernel_name(const gsb_run_state* run) {
     if (!T) return "none";
     if (T->kind == 1) return "k_fx32_step";
     if (T->kind == 2) return "k_fx16_persist";
-    if (T->persistent) return T->cluster ? "k_tc_persist<cluster>" : "k_tc_persist<grid>";
+    if (T->persistent)
+        return T->cluster ? "k_tc_persist<cluster>" : T->pair ? "k_tc_persist<pair>" : "k_tc_persist<grid>";
     return "k_tc_step<e4m3>";
 }
 
@@ -1386,15 +1493,17 @@ gsb_status tc_setup(gsb_run_state* run) {
                 return st;
     }
     if (T->kind == 0 && run->params.steps_per_launch != 1) {
-        // Two multi-step forms. The cluster form (one cluster of Np/128 CTAs per
-        // replica block, Np <= 16 x 128) runs in waves when not every cluster
-        // fits at once; the grid form needs the whole grid co-resident. Take the
-        // cluster form if all its clusters fit (its exchange is cheaper), else
-        // the grid form if it fits, else the cluster form in waves.
+        // Three multi-step forms. The cluster form (one cluster of Np/128 CTAs
+        // per replica block, Np <= 16 x 128) runs in waves when not every
+        // cluster fits at once; the grid form and its SM-pair variant need the
+        // whole grid co-resident. Take the cluster form if all its clusters fit
+        // (its exchange is cheaper), else -- with GSB_RUN_SM_PAIRS -- the pair
+        // form if it fits (an even number of replica blocks), else the grid
+        // form if it fits, else the cluster form in waves.
         const int nrb = run->Rp / BN;
         int nclusters = 0;
         if (run->Np / BM <= kMaxClusterP) {
-            auto kern = run->control ? k_tc_persist<true, true> : k_tc_persist<false, true>;
+            auto kern = run->control ? k_tc_persist<true, kFormCluster> : k_tc_persist<false, kFormCluster>;
             GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               smem_bytes_persist()));
             if (run->Np / BM > 8)
@@ -1408,22 +1517,43 @@ gsb_status tc_setup(gsb_run_state* run) {
                 nclusters = 0;
             }
         }
-        bool grid_fits = false;
+        bool grid_fits = false, pair_fits = false;
         {
             int dev = 0, sms = 0, per_sm = 0, coop = 0;
             GSB_CUDA_TRY(cudaGetDevice(&dev));
             GSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             GSB_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-            auto kern = run->control ? (const void*)k_tc_persist<true, false>
-                                     : (const void*)k_tc_persist<false, false>;
+            auto kern = run->control ? (const void*)k_tc_persist<true, kFormGrid>
+                                     : (const void*)k_tc_persist<false, kFormGrid>;
             GSB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               smem_bytes_persist()));
             GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsP,
                                                                        smem_bytes_persist()));
             grid_fits = coop && per_sm >= 1 && (long)nrb * (run->Np / BM) <= (long)per_sm * sms;
+            if (coop && nrb % 2 == 0 && (run->params.flags & GSB_RUN_SM_PAIRS)) {
+                auto kp = run->control ? k_tc_persist<true, kFormPair> : k_tc_persist<false, kFormPair>;
+                GSB_CUDA_TRY(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  smem_bytes_persist(kFormPair)));
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute at[2];
+                pair_config(run, &cfg, at);
+                cfg.numAttrs = 1;  // the occupancy query takes the cluster shape only
+                int npairs = 0;
+                if (cudaOccupancyMaxActiveClusters(&npairs, kp, &cfg) != cudaSuccess) {
+                    cudaGetLastError();
+                    npairs = 0;
+                }
+                pair_fits = 2L * npairs >= (long)nrb * (run->Np / BM);
+            }
         }
-        if (nclusters >= nrb || (nclusters >= 1 && !grid_fits)) {
+        if (nclusters >= nrb || (nclusters >= 1 && !grid_fits && !pair_fits)) {
             T->persistent = T->cluster = true;
+        } else if (pair_fits) {
+            T->persistent = T->pair = true;
+            if ((st = make_map(&T->tmA_half, P->J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P->Np, P->Np,
+                               BM / 2)))
+                return st;
+            if ((st = dev_alloc(&T->counters, (size_t)nrb))) return st;
         } else if (grid_fits) {
             T->persistent = true;
             if ((st = dev_alloc(&T->counters, (size_t)nrb))) return st;
@@ -1477,11 +1607,21 @@ gsb_status launch_persist(gsb_run_state* run, TcState* T, int m0, int n) {
         GSB_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_fx16_persist<CONTROL>, grid,
                                                  dim3(kThreadsP), args, smem_bytes_fx16(),
                                                  run->stream));
+    } else if (T->pair) {
+        const int nrb = run->Rp / BN;
+        GSB_CUDA_TRY(cudaMemsetAsync(T->counters, 0, sizeof(uint32_t) * nrb, run->stream));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[2];
+        pair_config(run, &cfg, at);
+        GSB_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_persist<CONTROL, kFormPair>, T->tmA_half,
+                                        T->tmB[0], T->tmB[1], Np, Rp, run->x[0], run->y, run->p,
+                                        (const float*)run->A, run->v8[0], run->v8[1], c, dt, ps, M,
+                                        m0, n, T->counters, run->status));
     } else if (T->cluster) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
         cluster_config(run, &cfg, at);
-        GSB_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_persist<CONTROL, true>, T->tmA, T->tmB[0],
+        GSB_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_persist<CONTROL, kFormCluster>, T->tmA, T->tmB[0],
                                         T->tmB[1], Np, Rp, run->x[0], run->y, run->p,
                                         (const float*)run->A, run->v8[0], run->v8[1], c, dt, ps, M,
                                         m0, n, (uint32_t*)nullptr, run->status));
@@ -1493,7 +1633,7 @@ gsb_status launch_persist(gsb_run_state* run, TcState* T, int m0, int n) {
                         (void*)&run->x[0], (void*)&run->y, (void*)&run->p, (void*)&run->A,
                         (void*)&run->v8[0], (void*)&run->v8[1], &c, &dt, (void*)&ps, &M, &m0, &n,
                         (void*)&T->counters, (void*)&run->status};
-        GSB_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_tc_persist<CONTROL, false>, grid,
+        GSB_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_tc_persist<CONTROL, kFormGrid>, grid,
                                                  dim3(kThreadsP), args, smem_bytes_persist(),
                                                  run->stream));
     }

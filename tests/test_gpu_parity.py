@@ -454,20 +454,23 @@ def test_lambda_extremes_match_dense_eigensolver(case):
 
 @pytest.mark.parametrize("variant", ["dsb", "gdsb"])
 @pytest.mark.parametrize("N,R,form", [(100, 130, "cluster"), (300, 200, "cluster"),
-                                      (2000, 128, "cluster"), (2100, 129, "grid"),
+                                      (2000, 128, "cluster"), (2100, 129, "pair"),
+                                      (2100, 129, "grid"), (2000, 1024, "pair"),
                                       (2000, 1024, "grid")])
 def test_fp8_persistent_matches_per_step_launches_bit_exact(variant, N, R, form):
     """The persistent FP8 kernel (state in TMEM, many steps per launch; 1, 3,
     16 and 17 K atoms per step, so ring stages of two atoms and a last stage of
-    one; clusters of 1, 3 and 16 CTAs per replica block, and the cooperative
-    grid form above 16 spin blocks) and the one-step-per-launch FP8 kernel do
-    the same arithmetic: identical bits. N = 2000, R = 1024 is the timed shape
-    (8 replica blocks of 16 spin blocks: the grid form)."""
+    one; clusters of 1, 3 and 16 CTAs per replica block, the cooperative grid
+    form above 16 spin blocks, and that form on SM pairs (two replica blocks
+    per MMA, asked for with sm_pairs on an even number of replica blocks) and
+    the one-step-per-launch FP8 kernel do the same arithmetic: identical bits.
+    N = 2000, R = 1024 is the timed shape (8 replica blocks of 16 spin blocks:
+    the grid form)."""
     M = 120
     J = I.sk_pm1(N, 41)
     P = gsb.Problem.dense(J)
     kw = dict(M=M, R=R, c=f32(1 / (2 * math.sqrt(N))), dt=1.25, A=0.3, seed=8, precision="fp8",
-              eval_every=25)
+              eval_every=25, sm_pairs=form == "pair")
     outs = []
     for spl in (1, 0, 7):
         run = P.run(variant, steps_per_launch=spl, **kw)
