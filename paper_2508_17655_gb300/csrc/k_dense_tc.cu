@@ -380,8 +380,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // 2q + 1 (same spin block) are a cluster of two whose MMAs (cta_group::2,
 // M = 256) the even CTA issues. Each CTA stages its own 128 rows of V and
 // half of the spin block's J rows (64), so a K slice costs an SM 24 KB of
-// shared memory and of L2 reads instead of 32 KB: four stages of two slices
-// fit where three did, for the same 128 x 128 tile per SM. The even CTA's
+// shared memory and of L2 reads instead of 32 KB, for the same 128 x 128
+// tile per SM (but the peer's tensor core reads the other half of B out of
+// this SM's shared memory, and each step waits for two replica columns). The even CTA's
 // full barriers count both CTAs' bytes (the odd CTA's loads signal them
 // across the pair), the MMA issuer's commits arrive on both CTAs' barriers,
 // and both epilogues release the accumulator on the even CTA's barrier. The
@@ -392,13 +393,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 // / 4) .. +63 -- 64 spins).
 constexpr int kThreadsP = 320;
 constexpr int kEpiThreadsP = 256;
-// A ring stage holds kAtomsP consecutive 128-byte K slices of J and of V: the
-// MMA issuer's fixed cost per stage (barrier wait, fence, commit -- about as
-// long as four MMAs) is paid once per eight MMAs.
-constexpr int kAtomsP = 2;
-constexpr int kStagesP = 3;
+// A ring stage holds kAtomsP consecutive 128-byte K slices of J and of V. The
+// K loop costs about 3.3 us per MB that passes through shared memory (TMA
+// writes plus tensor-core operand reads: 1 MB per step for a 128 x 128 tile
+// at K = 2048) plus about 0.1 us per ring stage (barrier round trip and
+// commit), and neither the number of slices in flight nor the MMA's N moves
+// it (measured: one-slice stages, seven in flight, 4.86 us; two-slice stages,
+// three in flight, 4.10 us; N = 64, 3.84 us): three-slice stages, two in
+// flight, take the fewest stages that fit.
+constexpr int kAtomsP = 3;
+constexpr int kStagesP = 2;
 constexpr int kMaxClusterP = 16;  // the largest (non-portable) cluster
-constexpr int kStagesQ = 4;       // ring stages of the pair form
+constexpr int kStagesQ = 3;       // ring stages of the pair form
 enum : int { kFormGrid = 0, kFormCluster = 1, kFormPair = 2 };
 
 __host__ __device__ constexpr int smem_bytes_persist(int form = kFormGrid) {
