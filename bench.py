@@ -498,6 +498,10 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         us = kernel_us(mk, min(M, 1000))
+        # the fused multi-step form (GSB_RUN_FUSED_CSR), for comparison
+        mkf = lambda m, prof: P.run("gbsb", M=m, R=R, c=0.0, dt=0.0, A=0.2, seed=1, defer=True,
+                                    profile=prof, stream=stream.cuda_stream, fused_csr=True)
+        us_fused = kernel_us(mkf, min(M, 1000))
         nnz = len(col)
         # algorithmic bytes per step: x, y, p read and written (24 B per spin and
         # replica), x gathered once (4 B), CSR indices and values (8 B per nonzero)
@@ -507,10 +511,11 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
             "value": N * R * M / (ms / 1e3), "unit": "spin-updates/s", "ms_per_run": ms,
             "lambda_setup": {"ms": setup_ms, "lambda_max": lmax, "lambda_min": lmin,
                              "how": "host wall clock around gsb_problem_info (Lanczos)"},
-            "roofline": {"bound": "hbm", "kernel": "k_csr_step", "achieved": bytes_step / (us * 1e-6) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": run.kernel(), "achieved": bytes_step / (us * 1e-6) / 1e9,
                          "peak": hbm, "unit": "GB/s",
                          "frac": bytes_step / (us * 1e-6) / 1e9 / hbm, "us_per_step": us,
-                         "algorithmic_bytes_per_step": bytes_step, "peak_source": how}}
+                         "algorithmic_bytes_per_step": bytes_step, "peak_source": how},
+            "fused_multistep_us_per_step": us_fused}
         run.close()
         P.close()
     # --- FX32 (GbSB, J.x exact on bf16 digit planes), the headline shape, one run

@@ -139,6 +139,9 @@ typedef struct gsb_params {
 
 #define GSB_RUN_DEFER 0x1u   /* gsb_run sets up the state but advances no step */
 #define GSB_RUN_PROFILE 0x2u /* record CUDA events around every launch of the step kernel */
+#define GSB_RUN_FUSED_CSR 0x8u /* CSR runs: one cooperative launch per stretch of steps (a grid
+                                  barrier between steps) instead of one launch per step; the
+                                  same bits, measured slower on the ER workloads */
 #define GSB_RUN_SM_PAIRS 0x4u /* the persistent FP8 kernel's grid form runs on SM pairs (two
                                  CTAs per MMA, cta_group::2) where it fits; the same bits,
                                  measured slower on the N = 2000, R = 1024 workload */

@@ -423,6 +423,8 @@ void free_run(gsb_run_state* r) {
     dev_free(r->A);
     dev_free(r->twin_part);
     dev_free(r->sched);
+    dev_free(r->csr_bar);
+    dev_free(r->csr_psched);
     dev_free(r->e_acc);
     dev_free(r->best_e);
     dev_free(r->best_step);
@@ -899,6 +901,8 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
     if (st != GSB_OK) return fail(st);
     if (is_tc_path(path)) {
         if ((st = tc_setup(run)) != GSB_OK) return fail(st);
+    } else if (path == kPathCsr) {
+        if ((st = csr_setup(run)) != GSB_OK) return fail(st);
     }
     *out = run;
     if (!(Q.flags & GSB_RUN_DEFER)) {
@@ -917,8 +921,9 @@ gsb_status gsb_run_steps(gsb_run_state* run, int32_t nsteps) {
     if (nsteps < 0 || run->steps_done + nsteps > run->params.M)
         return set_error(GSB_EINVAL, "nsteps exceeds the remaining steps of the run");
     const int M = run->params.M;
-    if (is_tc_path(run->path)) {
-        gsb_status st = tc_steps(run, run->steps_done, nsteps);
+    if (is_tc_path(run->path) || (run->path == kPathCsr && run->csr_grid > 0)) {
+        gsb_status st = is_tc_path(run->path) ? tc_steps(run, run->steps_done, nsteps)
+                                              : csr_steps(run, run->steps_done, nsteps);
         if (st == GSB_OK) run->steps_done += nsteps;
         return st;
     }
@@ -1159,7 +1164,7 @@ gsb_status gsb_run_restart(gsb_run_state* run, uint64_t seed, uint32_t flags) {
 const char* gsb_run_kernel(const gsb_run_state* run) {
     if (!run) return "";
     if (run->path == kPathDenseF32) return "k_dense_f32_step";
-    if (run->path == kPathCsr) return "k_csr_step";
+    if (run->path == kPathCsr) return run->csr_grid > 0 ? "k_csr_persist" : "k_csr_step";
     return tc_kernel_name(run);
 }
 

@@ -95,6 +95,9 @@ struct gsb_run_state {
     float* y = nullptr;
     float* p = nullptr;       // individual parameters (GbSB / GdSB)
     int8_t* s8[2] = {nullptr, nullptr};  // sgn x for the CSR sgn coupling
+    int csr_grid = 0;                 // CSR: blocks of the fused multi-step kernel (0: one step per launch)
+    uint32_t* csr_bar = nullptr;      // its grid-barrier counter
+    float* csr_psched = nullptr;      // p(t_{m+1}), m = 0..M-1 (shared schedule)
     float* A = nullptr;       // [Rp]
     // twin runs (Sec. IV): pair q runs as replicas q and twin_pairs + q
     int twin_pairs = 0;
@@ -211,6 +214,8 @@ gsb_status launch_dense_f32_energy(const gsb_problem* prob, const float* x_sm, i
 gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc);
 gsb_status launch_csr_energy(const gsb_problem* prob, const float* x_sm, int Rp, double* e_acc,
                              cudaStream_t s);
+gsb_status csr_setup(gsb_run_state* run);
+gsb_status csr_steps(gsb_run_state* run, int m0, int nsteps);
 // best keeping
 gsb_status launch_best_keep(gsb_run_state* run, int step);
 // Lanczos iteration (App. A)

@@ -19,7 +19,7 @@ BSB, GBSB, DSB, GDSB = range(4)
 PREC_AUTO, PREC_FP32, PREC_FP8, PREC_FX32, PREC_BF16X3, PREC_FX16 = range(6)
 J_DENSE_I8, J_DENSE_F32, J_CSR_F32 = range(3)
 CREATE_DEVICE_INPUT, CREATE_NO_VALIDATE = 0x1, 0x2
-RUN_DEFER, RUN_PROFILE, RUN_SM_PAIRS = 0x1, 0x2, 0x4
+RUN_DEFER, RUN_PROFILE, RUN_SM_PAIRS, RUN_FUSED_CSR = 0x1, 0x2, 0x4, 0x8
 
 VARIANT = {"bsb": BSB, "gbsb": GBSB, "dsb": DSB, "gdsb": GDSB}
 PRECISION = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp8": PREC_FP8, "fx32": PREC_FX32,
@@ -390,11 +390,13 @@ class Problem:
 
     def run(self, variant, M, R, *, c=0.0, dt=0.0, A=0.0, seed=0, precision="auto",
             eval_every=0, x0=None, y0=None, y0_uniform=False, x0_range=0.0, schedule=None,
-            steps_per_launch=0, defer=False, profile=False, stream=None, sm_pairs=False):
+            steps_per_launch=0, defer=False, profile=False, stream=None, sm_pairs=False,
+            fused_csr=False):
         return Run(self, variant, M, R, c=c, dt=dt, A=A, seed=seed, precision=precision,
                    eval_every=eval_every, x0=x0, y0=y0, y0_uniform=y0_uniform,
                    x0_range=x0_range, schedule=schedule, steps_per_launch=steps_per_launch,
-                   defer=defer, profile=profile, stream=stream, sm_pairs=sm_pairs)
+                   defer=defer, profile=profile, stream=stream, sm_pairs=sm_pairs,
+                   fused_csr=fused_csr)
 
     def lyapunov(self, variant, M, R, A_values, *, c=0.0, dt=0.0, seed=0, renorm_every=10,
                  nsteps=0, y0_uniform=False, x0_range=0.0, stream=None):
@@ -485,7 +487,7 @@ class Run:
 
     def __init__(self, problem, variant, M, R, *, c, dt, A, seed, precision, eval_every, x0, y0,
                  y0_uniform, x0_range, schedule, steps_per_launch, defer, profile, stream,
-                 sm_pairs=False):
+                 sm_pairs=False, fused_csr=False):
         self.problem = problem
         self.R = int(R)
         self.N = problem.N
@@ -522,7 +524,7 @@ class Run:
             keep.append(ya)
             prm.y0 = _p(ya, ctypes.c_float)
         prm.flags = ((RUN_DEFER if defer else 0) | (RUN_PROFILE if profile else 0)
-                     | (RUN_SM_PAIRS if sm_pairs else 0))
+                     | (RUN_SM_PAIRS if sm_pairs else 0) | (RUN_FUSED_CSR if fused_csr else 0))
         out = _vp()
         _check(lib().gsb_run(problem.handle, ctypes.byref(prm), ctypes.byref(out),
                              _stream_handle(stream)))

@@ -236,6 +236,35 @@ def test_csr_trajectory_50_steps(variant, weights):
     assert_within_fp32_drift(st["x"][pick], ref, drift, RTOL_TRAJ)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("weights", ["+1", "pm1", "real"])
+def test_csr_fused_steps_match_one_step_launches_bit_exact(variant, weights):
+    """The fused multi-step CSR kernel (GSB_RUN_FUSED_CSR: one cooperative
+    launch per stretch of steps, a grid barrier between steps, gathered rows
+    read through L2) and one launch per step do the same arithmetic: identical
+    state and best records.
+    ER N = 2000, mean degree 20 (more tasks than resident warps), R = 200 (a
+    ragged second replica block), energies every 25 steps (launches cut
+    there) and stretches of at most 7 steps; "real" scales the +-1 weights by
+    0.37 (no exact fixed-point form)."""
+    N, R, M = 2000, 200, 120
+    rp, col, val = I.er_graph(N, 20, "+1" if weights == "+1" else "pm1", 6)
+    if weights == "real":
+        val = (val * np.float32(0.37)).astype(np.float32)
+    P = gsb.Problem.csr(N, rp, col, val)
+    kw = dict(M=M, R=R, c=0.08, dt=0.9, A=0.25, seed=4, eval_every=25)
+    outs = []
+    for spl, fused in ((1, False), (0, True), (7, True)):
+        run = P.run(variant, steps_per_launch=spl, fused_csr=fused, **kw)
+        assert run.kernel() == ("k_csr_persist" if fused else "k_csr_step")
+        outs.append((run.state(), run.best()))
+    for st, b in outs[1:]:
+        for k in ("x", "y", "p"):
+            assert np.array_equal(st[k], outs[0][0][k]), k
+        for k in ("E", "s", "step"):
+            assert np.array_equal(b[k], outs[0][1][k]), k
+
+
 def test_gaussian_couplings_and_schedule():
     """Real-valued J (SK N(0, 1/N)), explicit x0/y0, caller schedule."""
     N, R, M = 257, 33, 1000
