@@ -96,6 +96,7 @@ struct gsb_run_state {
     float* p = nullptr;       // individual parameters (GbSB / GdSB)
     int8_t* s8[2] = {nullptr, nullptr};  // sgn x for the CSR sgn coupling
     int csr_grid = 0;                 // CSR: blocks of the fused multi-step kernel (0: one step per launch)
+    bool csr_mlp4 = false;            // CSR per-step kernel: four gathers in flight
     uint32_t* csr_bar = nullptr;      // its grid-barrier counter
     float* csr_psched = nullptr;      // p(t_{m+1}), m = 0..M-1 (shared schedule)
     float* A = nullptr;       // [Rp]

@@ -41,7 +41,7 @@ __device__ __forceinline__ char4 load_s4(const int8_t* p) {
     return *reinterpret_cast<const char4*>(p);
 }
 
-template <bool SIGN, bool EXACT, bool CG = false>
+template <bool SIGN, bool EXACT, bool CG, bool MLP4>
 __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowptr,
                                                const int32_t* __restrict__ col,
                                                const float* __restrict__ val,
@@ -58,8 +58,8 @@ __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowpt
         const float wj = k < end ? val[k] : 0.f;
         const int cnt = min(32, end - kb);
         int t0 = 0;
-        if (CG && !SIGN) {
-            // four gathers in flight at once (fused kernel): the loads first,
+        if (MLP4 && !SIGN) {
+            // four gathers in flight at once (MLP4): the loads first,
             // then the sums in the nonzeros' order, so the result is the
             // one-at-a-time loop's bit for bit
             for (; t0 + 4 <= cnt; t0 += 4) {
@@ -124,7 +124,7 @@ __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowpt
 
 // Row i, replicas rlane .. rlane + 3 of one step: the coupling, then Eqs. 7,
 // 3, 4, 5 on the four oscillators, written to the next buffers.
-template <bool SIGN, bool CONTROL, bool EXACT, bool CG>
+template <bool SIGN, bool CONTROL, bool EXACT, bool CG, bool MLP4>
 __device__ __forceinline__ void csr_task(const int32_t* __restrict__ rowptr,
                                          const int32_t* __restrict__ col,
                                          const float* __restrict__ val, int Rp,
@@ -134,7 +134,7 @@ __device__ __forceinline__ void csr_task(const int32_t* __restrict__ rowptr,
                                          float* __restrict__ p, const float* __restrict__ A,
                                          float c, float dt, float p_shared, float inv_rem, int i,
                                          int rlane) {
-    const float4 f = row_coupling<SIGN, EXACT, CG>(rowptr, col, val, xc, sc, Rp, i, rlane);
+    const float4 f = row_coupling<SIGN, EXACT, CG, MLP4>(rowptr, col, val, xc, sc, Rp, i, rlane);
     const size_t o = (size_t)i * Rp + rlane;
     float4 x4 = *reinterpret_cast<const float4*>(xc + o);
     float4 y4 = *reinterpret_cast<const float4*>(y + o);
@@ -161,7 +161,11 @@ __device__ __forceinline__ void csr_task(const int32_t* __restrict__ rowptr,
     }
 }
 
-template <bool SIGN, bool CONTROL, bool EXACT>
+// MLP4: four gathers of a row in flight at once (more registers, fewer
+// resident warps); taken when the state fits in half the L2, where the gathers'
+// latency bounds the step: 12.7 -> 11.4 us per step at N = 2000, R = 512, and
+// 90 -> 92 us at N = 20000, where the state streams from HBM.
+template <bool SIGN, bool CONTROL, bool EXACT, bool MLP4>
 __global__ void __launch_bounds__(256) k_csr_step(
     const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const float* __restrict__ val, int N, int Rp, const float* __restrict__ xc,
@@ -176,8 +180,8 @@ __global__ void __launch_bounds__(256) k_csr_step(
     const int i = blockIdx.y * kWarpsPerBlock + (threadIdx.x >> 5);
     if (i >= N) return;
     const int rlane = blockIdx.x * kReplicasPerWarp + (threadIdx.x & 31) * 4;
-    csr_task<SIGN, CONTROL, EXACT, false>(rowptr, col, val, Rp, xc, sc, xn, sn, y, p, A, c, dt,
-                                          p_shared, inv_rem, i, rlane);
+    csr_task<SIGN, CONTROL, EXACT, false, MLP4>(rowptr, col, val, Rp, xc, sc, xn, sn, y, p, A, c,
+                                                dt, p_shared, inv_rem, i, rlane);
 }
 
 // Fused multi-step form (the steps of Sec. II repeated, one cooperative launch
@@ -216,8 +220,8 @@ __global__ void __launch_bounds__(256) k_csr_persist(
         for (int t = w0; t < ntask; t += W) {
             const int i = t / nrb;
             const int rlane = (t - i * nrb) * kReplicasPerWarp + lane * 4;
-            csr_task<SIGN, CONTROL, EXACT, true>(rowptr, col, val, Rp, xc, sc, xn, sn, y, p, A, c,
-                                                 dt, p_shared, inv_rem, i, rlane);
+            csr_task<SIGN, CONTROL, EXACT, true, true>(rowptr, col, val, Rp, xc, sc, xn, sn, y, p,
+                                                       A, c, dt, p_shared, inv_rem, i, rlane);
         }
         if (s + 1 == nsteps) break;
         // grid barrier: every CTA's writes of this step before any read of the next
@@ -295,7 +299,8 @@ gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc) {
     const int cur = run->cur;
     const float inv_rem = 1.0f / (float)(sc.M - sc.m);
 #define GSB_CSR_LAUNCH(S, C, E)                                                              \
-    GSB_CUDA_TRY(launch_pdl(k_csr_step<S, C, E>, grid, dim3(256), 0, run->stream, P->rowptr,   \
+    GSB_CUDA_TRY(launch_pdl(run->csr_mlp4 ? k_csr_step<S, C, E, true> : k_csr_step<S, C, E, false>, \
+                            grid, dim3(256), 0, run->stream, P->rowptr,                        \
                             P->col, P->val, run->N, run->Rp, (const float*)run->x[cur],      \
                             (const int8_t*)run->s8[cur], run->x[cur ^ 1], run->s8[cur ^ 1],  \
                             run->y, run->p, (const float*)run->A, sc.c, sc.dt, sc.p_next,    \
@@ -341,6 +346,14 @@ const void* csr_persist_kernel(const gsb_run_state* run) {
 // warp per task; its barrier counter and the shared p(t_{m+1}) of every step.
 gsb_status csr_setup(gsb_run_state* run) {
     run->csr_grid = 0;
+    {
+        // the per-step kernel's gathers: four in flight while the state (x
+        // twice, y, p) fits in half the L2
+        int dev = 0, l2 = 0;
+        GSB_CUDA_TRY(cudaGetDevice(&dev));
+        GSB_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        run->csr_mlp4 = 16.0 * run->Np * run->Rp <= 0.5 * l2;
+    }
     if (!(run->params.flags & GSB_RUN_FUSED_CSR) || run->params.steps_per_launch == 1)
         return GSB_OK;
     int dev = 0, sms = 0, coop = 0, per_sm = 0;

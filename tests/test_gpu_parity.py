@@ -265,6 +265,27 @@ def test_csr_fused_steps_match_one_step_launches_bit_exact(variant, weights):
             assert np.array_equal(b[k], outs[0][1][k]), k
 
 
+@pytest.mark.parametrize("variant", ["gbsb", "bsb"])
+def test_csr_gather_forms_agree_bit_exact_beyond_l2(variant):
+    """N = 20000 ER, R = 256: the state (x twice, y, p: 82 MB) exceeds half the
+    L2, so the per-step kernel gathers one row of x at a time, while the fused
+    kernel keeps four in flight; both sum in the nonzeros' order: identical
+    bits."""
+    N, R, M = 20000, 256, 20
+    rp, col, val = I.er_graph(N, 20, "pm1", 8)
+    P = gsb.Problem.csr(N, rp, col, val)
+    kw = dict(M=M, R=R, c=0.08, dt=0.9, A=0.25, seed=5, eval_every=10)
+    a = P.run(variant, **kw)
+    b = P.run(variant, fused_csr=True, **kw)
+    assert (a.kernel(), b.kernel()) == ("k_csr_step", "k_csr_persist")
+    sa, sb = a.state(), b.state()
+    for k in ("x", "y", "p"):
+        assert np.array_equal(sa[k], sb[k]), k
+    ba, bb = a.best(), b.best()
+    for k in ("E", "s", "step"):
+        assert np.array_equal(ba[k], bb[k]), k
+
+
 def test_gaussian_couplings_and_schedule():
     """Real-valued J (SK N(0, 1/N)), explicit x0/y0, caller schedule."""
     N, R, M = 257, 33, 1000
