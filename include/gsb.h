@@ -404,6 +404,29 @@ gsb_status gsb_energy_noalloc(const float* J, int32_t N, const int8_t* spins, in
  * context stays usable afterwards. Blocks on `stream`. */
 gsb_status gsb_wait_check(int32_t kind, int64_t limit_ns, void* stream);
 
+/* Debug build (not in the paper: a stand-in for a memory checker, which this
+ * library's test machines do not offer). The same sources built with
+ * -DGSB_DEBUG (paper_2508_17655_gb300/_build_debug/libgsb.so; the Python
+ * binding loads it when GSB_LIBRARY=debug) check on the device the indices
+ * that come from the caller's data -- CSR row ranges and column indices, the
+ * tile lists of batched runs -- and the launch geometry of the tensor-core and
+ * dense step kernels (grid against the padded shape, steps against M). A
+ * failed check skips the access it guards (a column out of range is read as
+ * row 0 with weight 0; a kernel with a wrong grid returns before its first
+ * barrier) and sets a bit in the run's status word, which gsb_best then
+ * reports as GSB_ECUDA ("a kernel detected an out-of-range index"). Nothing
+ * traps, so the CUDA context stays usable. In the release build the checks
+ * compile away. gsb_debug_build: 1 in the debug build, 0 in the release build
+ * (host only). */
+int32_t gsb_debug_build(void);
+/* Debug build only: runs two kernels on inputs planted to fail their checks --
+ * the CSR energy kernel on a 4-row matrix one of whose columns is out of range,
+ * and the FP8 energy kernel on a grid one spin block taller than its matrix --
+ * and returns GSB_OK when both checks fired (the status bit set, the access not
+ * made), GSB_ECUDA otherwise. In the release build GSB_EUNSUPPORTED, with
+ * nothing launched. Uses the current device and synchronises it. */
+gsb_status gsb_debug_selftest(void);
+
 /* Device-time profile of the library's own multi-launch calls (not in the
  * paper). After gsb_set_call_profiling(1) on a thread, each later
  * gsb_batch_run, gsb_lyapunov and gsb_relaxed_energy_grad on that thread

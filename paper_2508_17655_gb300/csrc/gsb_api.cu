@@ -445,7 +445,7 @@ gsb_status evaluate(gsb_run_state* run, int step) {
     GSB_CUDA_TRY(cudaMemsetAsync(run->e_acc, 0, sizeof(double) * run->Rp, run->stream));
     gsb_status st = run->path == kPathCsr
                         ? launch_csr_energy(run->prob, run->x[run->cur], run->Rp, run->e_acc,
-                                            run->stream)
+                                            run->stream, run->status)
                         : launch_dense_f32_energy(run->prob, run->x[run->cur], run->Rp,
                                                   run->e_acc, run->stream);
     if (st != GSB_OK) return st;
@@ -1188,6 +1188,43 @@ gsb_status gsb_run_destroy(gsb_run_state* run) {
     cudaStreamSynchronize(run->stream);
     free_run(run);
     return GSB_OK;
+}
+
+int32_t gsb_debug_build(void) {
+#ifdef GSB_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+gsb_status gsb_debug_selftest(void) {
+#ifndef GSB_DEBUG
+    return set_error(GSB_EUNSUPPORTED, "gsb_debug_selftest needs the GSB_DEBUG build");
+#else
+    cudaStream_t s = nullptr;
+    int* status = nullptr;
+    gsb_status st = dev_alloc(&status, 1);
+    if (st != GSB_OK) return st;
+    int got[2] = {0, 0};
+    for (int k = 0; k < 2 && st == GSB_OK; ++k) {
+        if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "debug self-test");
+            break;
+        }
+        st = k == 0 ? csr_debug_selftest(status, s) : tc_debug_selftest(status, s);
+        if (st == GSB_OK &&
+            cudaMemcpy(&got[k], status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = cuda_error(cudaGetLastError(), "debug self-test");
+    }
+    dev_free(status);
+    if (st != GSB_OK) return st;
+    if (!(got[0] & kDevBounds))
+        return set_error(GSB_ECUDA, "the CSR column check did not fire");
+    if (!(got[1] & kDevBounds))
+        return set_error(GSB_ECUDA, "the FP8 energy kernel's grid check did not fire");
+    return GSB_OK;
+#endif
 }
 
 }  // extern "C"

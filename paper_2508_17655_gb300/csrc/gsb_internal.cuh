@@ -41,6 +41,24 @@ enum DevStatus : int {
     kDevBounds = 4,
 };
 
+// Device-side bounds checks of the debug build (-DGSB_DEBUG, built beside the
+// release library as _build_debug/libgsb.so). GSB_DOK(cond, status) is cond,
+// and when cond is false the kDevBounds bit goes into *status; the caller skips
+// the access the check guards, without changing its control flow, so every
+// barrier is still reached by every thread. Checks made on kernel parameters
+// and the grid alone (the same in every thread) may return at a kernel's
+// entry, before its first barrier. Without GSB_DEBUG, GSB_DOK is the constant
+// true and compiles away.
+#ifdef GSB_DEBUG
+__device__ __forceinline__ bool gsb_dok(bool cond, int* status) {
+    if (!cond && status) atomicOr(status, (int)kDevBounds);
+    return cond;
+}
+#define GSB_DOK(cond, status) ::gsb::gsb_dok((cond), (status))
+#else
+#define GSB_DOK(cond, status) true
+#endif
+
 // Per-step scalars of Eqs. 3-7 shared by every kernel of a step.
 struct StepScalars {
     int m;        // step index; the step produces t_{m+1}
@@ -214,8 +232,12 @@ gsb_status launch_dense_f32_energy(const gsb_problem* prob, const float* x_sm, i
 // CSR path
 gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc);
 gsb_status launch_csr_energy(const gsb_problem* prob, const float* x_sm, int Rp, double* e_acc,
-                             cudaStream_t s);
+                             cudaStream_t s, int* status = nullptr);
 gsb_status csr_setup(gsb_run_state* run);
+// debug build: planted out-of-range inputs for the CSR and FP8 energy kernels
+// (status: a device word the kernels report into)
+gsb_status csr_debug_selftest(int* status, cudaStream_t s);
+gsb_status tc_debug_selftest(int* status, cudaStream_t s);
 gsb_status csr_steps(gsb_run_state* run, int m0, int nsteps);
 // best keeping
 gsb_status launch_best_keep(gsb_run_state* run, int step);

@@ -40,6 +40,7 @@ struct BatchInst {
     int stop;              // steps this batch advances the instance (<= M)
     float c, dt;
     const float* sched;    // p(t_m), m = 0..M (device) or null
+    int* status;           // the instance's run status word
 };
 
 struct BatchTile {
@@ -71,10 +72,16 @@ __device__ __forceinline__ void batch_update4(const BatchInst& I, const float* x
 template <int T>
 __global__ void __launch_bounds__(256) k_batch_step(const BatchInst* __restrict__ insts,
                                                     const BatchTile* __restrict__ tiles,
-                                                    const int* __restrict__ m_dev) {
+                                                    const int* __restrict__ m_dev, int ninst) {
     const int m = *m_dev;
     const BatchTile t = tiles[blockIdx.x];
+    // debug build: the tile names an instance of the batch and a whole T x T
+    // tile of it (one tile per block: a uniform return)
+    if (!GSB_DOK(t.inst >= 0 && t.inst < ninst, insts[0].status)) return;
     const BatchInst I = insts[t.inst];
+    if (!GSB_DOK(t.i0 >= 0 && t.r0 >= 0 && t.i0 + T <= I.Np && t.r0 + T <= I.Rp && I.stop <= I.M,
+                 I.status))
+        return;
     if (m >= I.stop) return;  // this instance has finished its steps
     const bool odd = m & 1;
     const float* xc = odd ? I.x1 : I.x0;
@@ -140,9 +147,9 @@ struct BatchState {
 gsb_status launch_batch_step_raw(BatchState& B, int which, cudaStream_t s) {
     if (B.ntiles[which] == 0) return GSB_OK;
     if (which == 0)
-        k_batch_step<128><<<B.ntiles[0], 256, 0, s>>>(B.d_inst, B.d_tiles[0], B.d_m);
+        k_batch_step<128><<<B.ntiles[0], 256, 0, s>>>(B.d_inst, B.d_tiles[0], B.d_m, B.n);
     else
-        k_batch_step<64><<<B.ntiles[1], 256, 0, s>>>(B.d_inst, B.d_tiles[1], B.d_m);
+        k_batch_step<64><<<B.ntiles[1], 256, 0, s>>>(B.d_inst, B.d_tiles[1], B.d_m, B.n);
     GSB_LAUNCH_CHECK("k_batch_step");
     k_batch_advance<<<1, 1, 0, s>>>(B.d_m);
     GSB_LAUNCH_CHECK("k_batch_advance");
@@ -338,6 +345,7 @@ extern "C" gsb_status gsb_batch_run(int32_t n, gsb_problem* const* problems,
         I.c = r->c;
         I.dt = r->dt;
         I.sched = nullptr;
+        I.status = r->status;
         if (!r->sched_host.empty()) {
             float* d = nullptr;
             GSB_CUDA_TRY(cudaMalloc(&d, sizeof(float) * r->sched_host.size()));

@@ -81,7 +81,7 @@ __device__ __forceinline__ uint16_t bf16_bits(float v) {
 
 __global__ void __launch_bounds__(kThreadsM, 1)
     k_bf16_multi(const MInst* __restrict__ insts, const MTile* __restrict__ tiles, int ntiles,
-                 int nsteps, uint32_t* __restrict__ counters, int* __restrict__ status) {
+                 int nsteps, uint32_t* __restrict__ counters, int ninst, int* __restrict__ status) {
     constexpr int S = kStagesM;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -97,6 +97,30 @@ __global__ void __launch_bounds__(kThreadsM, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long nitems = (long)nsteps * ntiles;
     const long G = gridDim.x;
+#ifdef GSB_DEBUG
+    // debug build: every tile of the list names an instance of the batch and a
+    // whole 128 x 128 tile of it, and every instance's steps lie within its run
+    // (the whole list, checked alike by every CTA before any barrier: a
+    // uniform return)
+    {
+        int bad = 0;
+        for (int k = threadIdx.x; k < ntiles; k += blockDim.x) {
+            const MTile T = tiles[k];
+            if (T.inst < 0 || T.inst >= ninst) {
+                bad = 1;
+                continue;
+            }
+            const MInst* I = insts + T.inst;
+            bad |= !(T.i0 >= 0 && T.r0 >= 0 && T.i0 % kT == 0 && T.r0 % kT == 0 &&
+                     T.i0 < I->Np && T.r0 < I->Rp && I->Np % kT == 0 && I->Rp % kT == 0 &&
+                     I->m0 >= 0 && I->m0 <= I->stop && I->stop <= I->M);
+        }
+        if (__syncthreads_or(bad)) {
+            GSB_DOK(false, status);
+            return;
+        }
+    }
+#endif
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < S; ++st) {
@@ -471,7 +495,7 @@ gsb_status launch_multi(const MInst* insts, const MTile* tiles, int ntiles, int 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     GSB_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_bf16_multi, insts, tiles, ntiles, nsteps, counters,
-                                    status));
+                                    ninst, status));
     count_launch();
     return GSB_OK;
 }

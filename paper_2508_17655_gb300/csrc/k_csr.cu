@@ -47,15 +47,24 @@ __device__ __forceinline__ float4 row_coupling(const int32_t* __restrict__ rowpt
                                                const float* __restrict__ val,
                                                const float* __restrict__ xv,
                                                const int8_t* __restrict__ sv, int Rp, int i,
-                                               int rlane) {
+                                               int rlane, int N, int* status) {
     const int lane = threadIdx.x & 31;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     long long qa[4] = {0, 0, 0, 0};
     const int beg = rowptr[i], end = rowptr[i + 1];
+#ifdef GSB_DEBUG
+    // the row's nonzeros within col / val (one warp, one row: a uniform return)
+    if (!GSB_DOK(beg >= 0 && beg <= end && end <= rowptr[N], status)) return acc;
+#endif
     for (int kb = beg; kb < end; kb += 32) {
         const int k = kb + lane;
-        const int cj = k < end ? col[k] : 0;
-        const float wj = k < end ? val[k] : 0.f;
+        int cj = k < end ? col[k] : 0;
+        float wj = k < end ? val[k] : 0.f;
+        // debug build: an out-of-range column reads row 0 with weight 0
+        if (!GSB_DOK(cj >= 0 && cj < N, status)) {
+            cj = 0;
+            wj = 0.f;
+        }
         const int cnt = min(32, end - kb);
         int t0 = 0;
         if (MLP4 && !SIGN) {
@@ -133,8 +142,9 @@ __device__ __forceinline__ void csr_task(const int32_t* __restrict__ rowptr,
                                          int8_t* __restrict__ sn, float* __restrict__ y,
                                          float* __restrict__ p, const float* __restrict__ A,
                                          float c, float dt, float p_shared, float inv_rem, int i,
-                                         int rlane) {
-    const float4 f = row_coupling<SIGN, EXACT, CG, MLP4>(rowptr, col, val, xc, sc, Rp, i, rlane);
+                                         int rlane, int N, int* status) {
+    const float4 f = row_coupling<SIGN, EXACT, CG, MLP4>(rowptr, col, val, xc, sc, Rp, i, rlane, N,
+                                                         status);
     const size_t o = (size_t)i * Rp + rlane;
     float4 x4 = *reinterpret_cast<const float4*>(xc + o);
     float4 y4 = *reinterpret_cast<const float4*>(y + o);
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(256) k_csr_step(
     const float* __restrict__ val, int N, int Rp, const float* __restrict__ xc,
     const int8_t* __restrict__ sc, float* __restrict__ xn, int8_t* __restrict__ sn,
     float* __restrict__ y, float* __restrict__ p, const float* __restrict__ A, float c, float dt,
-    float p_shared, float inv_rem) {
+    float p_shared, float inv_rem, int* status) {
     // launched with programmatic dependent launch: the next step may be
     // scheduled once every block of this one has started; everything below
     // reads or writes state the previous step touched, so it waits for it
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(256) k_csr_step(
     if (i >= N) return;
     const int rlane = blockIdx.x * kReplicasPerWarp + (threadIdx.x & 31) * 4;
     csr_task<SIGN, CONTROL, EXACT, false, MLP4>(rowptr, col, val, Rp, xc, sc, xn, sn, y, p, A, c,
-                                                dt, p_shared, inv_rem, i, rlane);
+                                                dt, p_shared, inv_rem, i, rlane, N, status);
 }
 
 // Fused multi-step form (the steps of Sec. II repeated, one cooperative launch
@@ -221,7 +231,8 @@ __global__ void __launch_bounds__(256) k_csr_persist(
             const int i = t / nrb;
             const int rlane = (t - i * nrb) * kReplicasPerWarp + lane * 4;
             csr_task<SIGN, CONTROL, EXACT, true, true>(rowptr, col, val, Rp, xc, sc, xn, sn, y, p,
-                                                       A, c, dt, p_shared, inv_rem, i, rlane);
+                                                       A, c, dt, p_shared, inv_rem, i, rlane, N,
+                                                       status);
         }
         if (s + 1 == nsteps) break;
         // grid barrier: every CTA's writes of this step before any read of the next
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(256) k_csr_energy(const int32_t* __restrict__ 
                                                     const int32_t* __restrict__ col,
                                                     const float* __restrict__ val, int N,
                                                     int Rp, const float* __restrict__ x,
-                                                    double* __restrict__ e_acc) {
+                                                    double* __restrict__ e_acc, int* status) {
     __shared__ float red[kWarpsPerBlock][kReplicasPerWarp];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rlane = blockIdx.x * kReplicasPerWarp + lane * 4;
@@ -257,11 +268,18 @@ __global__ void __launch_bounds__(256) k_csr_energy(const int32_t* __restrict__ 
         const int i = row0 + rr;
         if (i >= N) break;
         float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int beg = rowptr[i], end = rowptr[i + 1];
+        int beg = rowptr[i], end = rowptr[i + 1];
+#ifdef GSB_DEBUG
+        if (!GSB_DOK(beg >= 0 && beg <= end && end <= rowptr[N], status)) end = beg = 0;
+#endif
         for (int kb = beg; kb < end; kb += 32) {
             const int k = kb + lane;
-            const int cj = k < end ? col[k] : 0;
-            const float wj = k < end ? val[k] : 0.f;
+            int cj = k < end ? col[k] : 0;
+            float wj = k < end ? val[k] : 0.f;
+            if (!GSB_DOK(cj >= 0 && cj < N, status)) {
+                cj = 0;
+                wj = 0.f;
+            }
             const int cnt = min(32, end - kb);
             for (int t = 0; t < cnt; ++t) {
                 const int j = __shfl_sync(0xffffffffu, cj, t);
@@ -304,7 +322,7 @@ gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc) {
                             P->col, P->val, run->N, run->Rp, (const float*)run->x[cur],      \
                             (const int8_t*)run->s8[cur], run->x[cur ^ 1], run->s8[cur ^ 1],  \
                             run->y, run->p, (const float*)run->A, sc.c, sc.dt, sc.p_next,    \
-                            inv_rem))
+                            inv_rem, run->status))
     // exact fixed-point x coupling when J is integer and 2^30 sum_k |J_ik| fits in int64
     const bool exact = P->integer_J && P->max_row_abs < 4294967296.0;
     if (run->sign_coupling) {
@@ -418,11 +436,56 @@ gsb_status csr_steps(gsb_run_state* run, int m0, int nsteps) {
     return GSB_OK;
 }
 
+// Debug build: the CSR energy kernel on a 4-row matrix whose third row names
+// column 9; its check must skip that gather and report it.
+gsb_status csr_debug_selftest(int* status, cudaStream_t s) {
+#ifndef GSB_DEBUG
+    // the release kernel has no check: it must never see this matrix
+    (void)status;
+    (void)s;
+    return set_error(GSB_EUNSUPPORTED, "built without GSB_DEBUG");
+#endif
+    const int N = 4, Rp = kReplicasPerWarp;
+    const int32_t rowptr_h[N + 1] = {0, 1, 2, 3, 4};
+    const int32_t col_h[N] = {1, 0, 9, 2};
+    const float val_h[N] = {1.f, 1.f, 1.f, 1.f};
+    gsb_problem P;
+    P.N = N;
+    float* x = nullptr;
+    double* e = nullptr;
+    gsb_status st = GSB_OK;
+    if ((st = dev_alloc(&P.rowptr, N + 1)) || (st = dev_alloc(&P.col, N)) ||
+        (st = dev_alloc(&P.val, N)) || (st = dev_alloc(&x, (size_t)N * Rp)) ||
+        (st = dev_alloc(&e, Rp))) {
+    } else if (cudaMemcpyAsync(P.rowptr, rowptr_h, sizeof(rowptr_h), cudaMemcpyHostToDevice, s) ||
+               cudaMemcpyAsync(P.col, col_h, sizeof(col_h), cudaMemcpyHostToDevice, s) ||
+               cudaMemcpyAsync(P.val, val_h, sizeof(val_h), cudaMemcpyHostToDevice, s) ||
+               cudaMemsetAsync(x, 0, sizeof(float) * N * Rp, s) ||
+               cudaMemsetAsync(e, 0, sizeof(double) * Rp, s)) {
+        st = cuda_error(cudaGetLastError(), "debug self-test set-up");
+    } else {
+        st = launch_csr_energy(&P, x, Rp, e, s, status);
+        if (st == GSB_OK && cudaStreamSynchronize(s) != cudaSuccess)
+            st = cuda_error(cudaGetLastError(), "debug self-test");
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == GSB_OK)
+        st = cuda_error(cudaGetLastError(), "debug self-test");
+    dev_free(P.rowptr);
+    dev_free(P.col);
+    dev_free(P.val);
+    P.rowptr = nullptr;
+    P.col = nullptr;
+    P.val = nullptr;
+    dev_free(x);
+    dev_free(e);
+    return st;
+}
+
 gsb_status launch_csr_energy(const gsb_problem* P, const float* x, int Rp, double* e_acc,
-                             cudaStream_t s) {
+                             cudaStream_t s, int* status) {
     const int rows_per_block = kWarpsPerBlock * kRowsPerWarp;
     dim3 grid(Rp / kReplicasPerWarp, (P->N + rows_per_block - 1) / rows_per_block);
-    k_csr_energy<<<grid, 256, 0, s>>>(P->rowptr, P->col, P->val, P->N, Rp, x, e_acc);
+    k_csr_energy<<<grid, 256, 0, s>>>(P->rowptr, P->col, P->val, P->N, Rp, x, e_acc, status);
     GSB_LAUNCH_CHECK("k_csr_energy");
     return GSB_OK;
 }

@@ -18,8 +18,13 @@ template <bool SIGN, bool CONTROL>
 __global__ void __launch_bounds__(256) k_dense_f32_step(
     const float* __restrict__ J, int Np, int Rp, const float* __restrict__ xc,
     float* __restrict__ xn, float* __restrict__ y, float* __restrict__ p,
-    const float* __restrict__ A, float c, float dt, float p_shared, float inv_rem) {
+    const float* __restrict__ A, float c, float dt, float p_shared, float inv_rem, int* status) {
     __shared__ __align__(16) F32Smem sm;
+    // debug build: the grid covers the padded shape exactly (a uniform return)
+    if (!GSB_DOK(Np % BM == 0 && Rp % BN == 0 && (int)gridDim.x * BN == Rp &&
+                     (int)gridDim.y * BM == Np,
+                 status))
+        return;
     const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
     float acc[8][8];
     sgemm_tile<SIGN>(J, xc, Np, Rp, i0, r0, acc, sm);
@@ -95,7 +100,7 @@ gsb_status launch_dense_f32_step(gsb_run_state* run, const StepScalars& sc) {
 #define GSB_F32_LAUNCH(S, C)                                                                  \
     k_dense_f32_step<S, C><<<grid, 256, 0, run->stream>>>(P->J32, run->Np, run->Rp, xc, xn,   \
                                                           run->y, run->p, run->A, sc.c, sc.dt, \
-                                                          sc.p_next, inv_rem)
+                                                          sc.p_next, inv_rem, run->status)
     if (run->sign_coupling) {
         if (run->control) GSB_F32_LAUNCH(true, true); else GSB_F32_LAUNCH(true, false);
     } else {

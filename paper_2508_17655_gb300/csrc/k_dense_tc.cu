@@ -89,6 +89,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               int Np, int Rp, float* __restrict__ x, float* __restrict__ y,
               float* __restrict__ p, const float* __restrict__ A, uint8_t* __restrict__ vnext,
               float c, float dt, float p_shared, float inv_rem, int* status) {
+    // debug build: the grid covers the padded shape exactly (a uniform return)
+    if (!GSB_DOK(Np > 0 && Np % KB == 0 && Rp % BN == 0 && (int)gridDim.x * BN == Rp &&
+                     (int)gridDim.y * BM == Np,
+                 status))
+        return;
     constexpr int S = kStagesS;
     constexpr int SA = BM * KB;
     constexpr int SB = BN * KB;
@@ -235,6 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_energy(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const uint8_t* __restrict__ v, int Np, double* __restrict__ e_acc, int* status) {
+    if (!GSB_DOK(Np > 0 && Np % KB == 0 && (int)gridDim.y * BM == Np, status)) return;
     constexpr int S = kStagesS;
     constexpr int SA = BM * KB;
     constexpr int SB = BN * KB;
@@ -420,6 +426,17 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                  uint8_t* __restrict__ v0, uint8_t* __restrict__ v1, float c, float dt,
                  const float* __restrict__ p_sched, int M, int m0, int nsteps,
                  uint32_t* __restrict__ counters, int* status) {
+    // debug build: the grid and the steps match the shape and the run (checked
+    // by every thread alike, before any barrier: a uniform return)
+    if (!GSB_DOK(Np > 0 && Np % KB == 0 && Rp % BN == 0 && m0 >= 0 && nsteps >= 0 &&
+                     m0 + nsteps <= M &&
+                     (FORM == kFormCluster
+                          ? ((int)gridDim.x * BM == Np && (int)gridDim.y * BN == Rp &&
+                             Np / BM <= kMaxClusterP)
+                          : ((int)gridDim.x * BN == Rp && (int)gridDim.y * BM == Np &&
+                             (FORM != kFormPair || gridDim.x % 2 == 0))),
+                 status))
+        return;
     constexpr bool CLUSTER = FORM == kFormCluster, PAIR = FORM == kFormPair;
     constexpr int S = PAIR ? kStagesQ : kStagesP;
     constexpr int JR = PAIR ? BM / 2 : BM;       // J rows this CTA stages
@@ -827,6 +844,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                    uint8_t* __restrict__ v1, float c, float dt,
                    const float* __restrict__ p_sched, int M, int m0, int nsteps,
                    uint32_t* __restrict__ counters, int* status) {
+    if (!GSB_DOK(Np > 0 && Np % KB == 0 && Rp % BN == 0 && m0 >= 0 && nsteps >= 0 &&
+                     m0 + nsteps <= M && (int)gridDim.x * BN == Rp && (int)gridDim.y * BM == Np,
+                 status))
+        return;
     constexpr int S = kStagesX;
     constexpr int A1 = BM * KB;  // one K atom of 128 rows
     extern __shared__ uint8_t smem_raw[];
@@ -1180,6 +1201,10 @@ __global__ void __launch_bounds__(kThreadsF, 1)
                 float* __restrict__ p, const float* __restrict__ A,
                 __nv_bfloat16* __restrict__ vnext, float c, float dt, float p_shared,
                 float inv_rem, int* status) {
+    if (!GSB_DOK(Np > 0 && Np % (KB / 2) == 0 && Rp % BN == 0 && (int)gridDim.x * BN == Rp &&
+                     (int)gridDim.y * BM == Np,
+                 status))
+        return;
     constexpr int S = kStagesF;
     constexpr int SV1 = BN * KB, SV = 4 * SV1, SJ = BM * KB;  // bytes per stage
     constexpr int kElems = KB / 2;                          // bf16 elements of K per stage
@@ -1693,6 +1718,28 @@ gsb_status tc_steps(gsb_run_state* run, int m0, int nsteps) {
             if ((st = run_evaluate(run, m + 1)) != GSB_OK) return st;
     }
     return GSB_OK;
+}
+
+// Debug build: the FP8 energy kernel on a grid of two spin blocks over a
+// 128-spin matrix; its entry check must return before any barrier, copy or
+// MMA (the tensor maps are empty and the pointers null: nothing may touch them).
+gsb_status tc_debug_selftest(int* status, cudaStream_t s) {
+#ifndef GSB_DEBUG
+    // the release kernel has no check: it must never see this launch
+    (void)status;
+    (void)s;
+    return set_error(GSB_EUNSUPPORTED, "built without GSB_DEBUG");
+#else
+    CUtensorMap empty_map;
+    memset(&empty_map, 0, sizeof(empty_map));
+    GSB_CUDA_TRY(cudaFuncSetAttribute(k_tc_energy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem_bytes_step()));
+    k_tc_energy<<<dim3(1, 2), kThreads, smem_bytes_step(), s>>>(empty_map, empty_map, nullptr, BM,
+                                                                 nullptr, status);
+    GSB_LAUNCH_CHECK("k_tc_energy");
+    GSB_CUDA_TRY(cudaStreamSynchronize(s));
+    return GSB_OK;
+#endif
 }
 
 gsb_status tc_energy(gsb_run_state* run, int step) {

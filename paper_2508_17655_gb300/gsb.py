@@ -77,13 +77,15 @@ _vp = ctypes.c_void_p
 
 
 def library_path():
-    return _build.LIB
+    """The library this process loads: the release build, or the debug build
+    (device-side bounds checks, -DGSB_DEBUG) when GSB_LIBRARY=debug."""
+    return _build.LIB_DEBUG if os.environ.get("GSB_LIBRARY") == "debug" else _build.LIB
 
 
 def lib():
     global _LIB
     if _LIB is None:
-        path = _build.LIB
+        path = library_path()
         if not os.path.exists(path):
             raise RuntimeError(f"libgsb.so is not built ({path}); run "
                                "paper_2508_17655_gb300.build.build() first")
@@ -164,6 +166,10 @@ def _declare(L):
     L.gsb_release_cached_memory.restype = st
     L.gsb_wait_check.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp]
     L.gsb_wait_check.restype = st
+    L.gsb_debug_build.argtypes = []
+    L.gsb_debug_build.restype = ctypes.c_int32
+    L.gsb_debug_selftest.argtypes = []
+    L.gsb_debug_selftest.restype = st
     L.gsb_set_call_profiling.argtypes = [ctypes.c_int32]
     L.gsb_set_call_profiling.restype = st
     L.gsb_last_call_profile.argtypes = [ctypes.POINTER(ctypes.c_double),
@@ -218,6 +224,18 @@ def wait_check(kind, limit_ns, stream=None):
     both never satisfied; 2: a counter already at its target). Raises GsbError
     with status ETIMEOUT when the wait gives up."""
     _check(lib().gsb_wait_check(int(kind), int(limit_ns), _stream_handle(stream)))
+
+
+def debug_build():
+    """gsb_debug_build: True when this process loaded the -DGSB_DEBUG library
+    (device-side bounds checks; GSB_LIBRARY=debug)."""
+    return bool(lib().gsb_debug_build())
+
+
+def debug_selftest():
+    """gsb_debug_selftest (debug build): kernels run on inputs planted to fail
+    their bounds checks; raises GsbError unless both checks fired."""
+    _check(lib().gsb_debug_selftest())
 
 
 def set_call_profiling(on):
