@@ -45,6 +45,8 @@ WORKLOAD = ("N=2000 +-1 complete graph (seed 0), R=1024 replicas, M=2000 steps, 
 KNOWN_TRAFFIC = {
     # profiles/k_tc_persist_N2000_R1024_M100.md
     "k_tc_persist<grid>": 31505152 + 1446656,
+    # profiles/k_tc_persist_N2000_R1024_M100.md (the 112-spin grid form, 144 CTAs)
+    "k_tc_persist<grid112>": 31082752 + 1356288,
     # profiles/k_fx16_persist_N2000_R1024_M100.md
     "k_fx16_persist": 37800192 + 2225152,
 }

@@ -413,12 +413,67 @@ constexpr int kMaxClusterP = 16;  // the largest (non-portable) cluster
 constexpr int kStagesQ = 3;       // ring stages of the pair form
 enum : int { kFormGrid = 0, kFormCluster = 1, kFormPair = 2 };
 
-__host__ __device__ constexpr int smem_bytes_persist(int form = kFormGrid) {
+__host__ __device__ constexpr int smem_bytes_persist(int form = kFormGrid, int bs = BM) {
     return form == kFormPair ? 1024 + kStagesQ * kAtomsP * (BN + BM / 2) * KB + 512
-                             : 1024 + kStagesP * kAtomsP * 2 * BM * KB + 512;
+                             : 1024 + kStagesP * kAtomsP * (BN + bs) * KB + 512;
 }
 
-template <bool CONTROL, int FORM>
+// TMEM moves of an epilogue chunk of CH spins: F (CH columns at cf) and x, y
+// (2 CH columns at cxy, x first), the loads in flight together with one wait;
+// and the store of x, y.
+template <int CH>
+__device__ __forceinline__ void tmem_ld_fxy(uint32_t cf, uint32_t cxy, float (&f)[CH],
+                                            float (&xs)[CH], float (&ys)[CH]) {
+    if constexpr (CH == 16) {
+        uint32_t rf[16], rx[16], ry[16];
+        tmem_ld16_async(cf, rf);
+        tmem_ld32_async(cxy, rx, ry);
+        tmem_wait_ld(rf);
+        tmem_wait_ld(rx);
+        tmem_wait_ld(ry);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            f[k] = __uint_as_float(rf[k]);
+            xs[k] = __uint_as_float(rx[k]);
+            ys[k] = __uint_as_float(ry[k]);
+        }
+    } else {
+        static_assert(CH == 8, "chunk");
+        uint32_t rf[8], rxy[16];
+        tmem_ld8_async(cf, rf);
+        tmem_ld16_async(cxy, rxy);
+        tmem_wait_ld8(rf);
+        tmem_wait_ld(rxy);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            f[k] = __uint_as_float(rf[k]);
+            xs[k] = __uint_as_float(rxy[k]);
+            ys[k] = __uint_as_float(rxy[8 + k]);
+        }
+    }
+}
+template <int CH>
+__device__ __forceinline__ void tmem_st_xy(uint32_t cxy, const float (&v)[2 * CH]) {
+    if constexpr (CH == 16) {
+        float lo[16], hi[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            lo[k] = v[k];
+            hi[k] = v[16 + k];
+        }
+        tmem_st32(cxy, lo, hi);
+    } else {
+        tmem_st16(cxy, v);
+    }
+}
+
+// BS: spins per CTA (the MMA's N and the epilogue's width). 128, or 112 in the
+// grid form, where ceil(N / 112) spin blocks put more SMs to work on the same
+// step (N = 2000, R = 1024: 144 CTAs instead of 128, each with 6 % less
+// shared-memory traffic in its K loop and 56 instead of 64 oscillators per
+// epilogue thread). The spins past the last block (up to N_p) are padding:
+// J is zero there, so their V bytes never reach F.
+template <bool CONTROL, int FORM, int BS = BM>
 __global__ void __launch_bounds__(kThreadsP, 1)
     k_tc_persist(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmV0,
                  const __grid_constant__ CUtensorMap tmV1, int Np, int Rp, float* __restrict__ x,
@@ -433,13 +488,20 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                      (FORM == kFormCluster
                           ? ((int)gridDim.x * BM == Np && (int)gridDim.y * BN == Rp &&
                              Np / BM <= kMaxClusterP)
-                          : ((int)gridDim.x * BN == Rp && (int)gridDim.y * BM == Np &&
+                          : ((int)gridDim.x * BN == Rp &&
+                             (BS == BM ? (int)gridDim.y * BM == Np : (int)gridDim.y * BS <= Np) &&
                              (FORM != kFormPair || gridDim.x % 2 == 0))),
                  status))
         return;
     constexpr bool CLUSTER = FORM == kFormCluster, PAIR = FORM == kFormPair;
+    static_assert(BS == BM || FORM == kFormGrid, "narrow spin blocks: grid form only");
+    static_assert(BS % 16 == 0 && BS <= BM, "MMA N");
     constexpr int S = PAIR ? kStagesQ : kStagesP;
-    constexpr int JR = PAIR ? BM / 2 : BM;       // J rows this CTA stages
+    constexpr int JR = PAIR ? BM / 2 : BS;       // J rows this CTA stages
+    // epilogue: CH spins per chunk, NCH chunks per thread (half the block)
+    constexpr int CH = BS == BM ? 16 : 8;
+    constexpr int HW = BS / 2, NCH = HW / CH;
+    static_assert(NCH * CH == HW, "epilogue chunks");
     constexpr int SA1 = JR * KB, SB1 = BN * KB;  // one K atom of J / of V
     constexpr int SA = kAtomsP * SA1, SB = kAtomsP * SB1;
     extern __shared__ uint8_t smem_raw[];
@@ -460,7 +522,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     // spin block (the CTA's own K slice) and replica block
     const int own = CLUSTER ? (int)blockIdx.x : (int)blockIdx.y;
     const int rb = CLUSTER ? (int)blockIdx.y : (int)blockIdx.x;
-    const int i0 = own * BM, r0 = rb * BN;
+    const int i0 = own * BS, r0 = rb * BN;
     uint32_t* ctr = counters + rb;
     // pair form: this CTA's rank in its pair (0 issues the MMAs)
     const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
@@ -553,7 +615,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                 if (ok && s > 0) {
                     ok = CLUSTER ? mbar_wait_cluster(&vready[(s - 1) & 1],
                                                      (uint32_t)((s - 1) >> 1) & 1u, status)
-                                 : wait_counter(ctr, (uint32_t)nk * (uint32_t)s, status);
+                                 : wait_counter(ctr, gridDim.y * (uint32_t)s, status);
                     if (ok) fence_proxy_async();
                 }
                 // V of the stages whose J is out -- after a failed wait too, so that
@@ -582,7 +644,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {
-            constexpr uint32_t idesc = idesc_make(0u, PAIR ? 2 * BN : BN, BM);
+            constexpr uint32_t idesc = idesc_make(0u, PAIR ? 2 * BN : BN, PAIR ? BM : BS);
             uint32_t g = 0;
             bool ok = true;
             for (int s = 0; s < nsteps && ok; ++s) {
@@ -634,29 +696,29 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     } else {
         const int ew = warp - 2;
         const int quarter = warp & 3;
-        const int c0 = (ew >> 2) * 64;
+        const int c0 = (ew >> 2) * HW;
         const int r = r0 + quarter * 32 + lane;  // this thread's replica (TMEM lane)
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         const float a_r = CONTROL ? A[r] : 0.f;
-        // state of this thread's replica, spins i0 + c0 .. +63: x and y into
-        // TMEM, p (individual control) into registers -- a step's TMEM traffic
-        // is then F, x, y in and x, y out
-        float pr[CONTROL ? 64 : 1];
+        // state of this thread's replica, spins i0 + c0 .. + HW - 1: x and y
+        // into TMEM (x and y of each chunk side by side, 2 CH columns), p
+        // (individual control) into registers -- a step's TMEM traffic is then
+        // F, x, y in and x, y out
+        float pr[CONTROL ? HW : 1];
 #pragma unroll 1
-        for (int cb = c0; cb < c0 + 64; cb += 16) {
+        for (int cb = c0; cb < c0 + HW; cb += CH) {
             const size_t o = (size_t)(i0 + cb) * Rp + r;
-            float v[16];
-            float w[16];
+            float v[2 * CH];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
+            for (int k = 0; k < CH; ++k) {
                 v[k] = x[o + (size_t)k * Rp];
-                w[k] = y[o + (size_t)k * Rp];
+                v[CH + k] = y[o + (size_t)k * Rp];
             }
-            tmem_st32(tl + 128 + 2 * cb, v, w);
+            tmem_st_xy<CH>(tl + 128 + 2 * cb, v);
         }
         if (CONTROL) {
 #pragma unroll
-            for (int k = 0; k < 64; ++k) pr[k] = p[(size_t)(i0 + c0 + k) * Rp + r];
+            for (int k = 0; k < HW; ++k) pr[k] = p[(size_t)(i0 + c0 + k) * Rp + r];
         }
         tmem_wait_st();
         // Every epilogue warp passes the same named barriers: a timeout in one of
@@ -674,31 +736,20 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             fence_after_sync();
             const float inv_rem = __frcp_rn((float)(M - m));
             const float p_shared = CONTROL ? 0.f : p_sched[s];
-            // V(t_{m+1}) goes to buffer (m + 1) & 1; this thread's 16 spins of a
-            // chunk are 16 consecutive bytes of its replica's row
+            // V(t_{m+1}) goes to buffer (m + 1) & 1; this thread's CH spins of a
+            // chunk are CH consecutive bytes of its replica's row
             uint8_t* vrow = ((m & 1) ? v0 : v1) + (size_t)r * Np + i0;
+            uint2 pend = make_uint2(0u, 0u);  // an 8-spin chunk's bytes held for its neighbour
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int cb = c0 + 16 * j;
-                float f[16], xs[16], ys[16], ps[16];
-                {
-                    // the loads in flight together, one wait
-                    uint32_t rf[16], rx[16], ry[16];
-                    tmem_ld16_async(tl + cb, rf);
-                    tmem_ld32_async(tl + 128 + 2 * cb, rx, ry);
-                    tmem_wait_ld(rf);
-                    tmem_wait_ld(rx);
-                    tmem_wait_ld(ry);
+            for (int j = 0; j < NCH; ++j) {
+                const int cb = c0 + CH * j;
+                float f[CH], xs[CH], ys[CH], ps[CH];
+                // the loads in flight together, one wait
+                tmem_ld_fxy<CH>(tl + cb, tl + 128 + 2 * cb, f, xs, ys);
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        f[k] = __uint_as_float(rf[k]);
-                        xs[k] = __uint_as_float(rx[k]);
-                        ys[k] = __uint_as_float(ry[k]);
-                        ps[k] = CONTROL ? pr[16 * j + k] : 0.f;
-                    }
-                }
+                for (int k = 0; k < CH; ++k) ps[k] = CONTROL ? pr[CH * j + k] : 0.f;
 #pragma unroll
-                for (int k = 0; k < 16; k += 2) {
+                for (int k = 0; k < CH; k += 2) {
                     float2 x2 = make_float2(xs[k], xs[k + 1]), y2 = make_float2(ys[k], ys[k + 1]);
                     float2 p2 = make_float2(ps[k], ps[k + 1]);
                     sb_update2<CONTROL>(x2, y2, p2, make_float2(f[k], f[k + 1]), a_r, c, dt,
@@ -706,28 +757,53 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     xs[k] = x2.x, xs[k + 1] = x2.y, ys[k] = y2.x, ys[k + 1] = y2.y;
                     ps[k] = p2.x, ps[k + 1] = p2.y;
                 }
-                tmem_st32(tl + 128 + 2 * cb, xs, ys);
+                {
+                    float v[2 * CH];
+#pragma unroll
+                    for (int k = 0; k < CH; ++k) {
+                        v[k] = xs[k];
+                        v[CH + k] = ys[k];
+                    }
+                    tmem_st_xy<CH>(tl + 128 + 2 * cb, v);
+                }
                 if (CONTROL) {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) pr[16 * j + k] = ps[k];
+                    for (int k = 0; k < CH; ++k) pr[CH * j + k] = ps[k];
                 }
                 // e4m3 sgn x, 0x38 (+1) or 0xB8 (-1): the sign bit of x + 0 (which
                 // turns -0 into +0, so sgn 0 = +1) in the top byte of each word,
                 // four gathered per word
-                uint32_t b[16], w[4];
+                uint32_t b[CH], w[CH / 4];
 #pragma unroll
-                for (int k = 0; k < 16; k += 2) {
+                for (int k = 0; k < CH; k += 2) {
                     const float2 z = __fadd2_rn(make_float2(xs[k], xs[k + 1]), make_float2(0.f, 0.f));
                     b[k] = __float_as_uint(z.x);
                     b[k + 1] = __float_as_uint(z.y);
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < CH / 4; ++q) {
                     const uint32_t lo = __byte_perm(b[4 * q], b[4 * q + 1], 0x0073);
                     const uint32_t hi = __byte_perm(b[4 * q + 2], b[4 * q + 3], 0x0073);
                     w[q] = (__byte_perm(lo, hi, 0x5410) & 0x80808080u) | 0x38383838u;
                 }
-                *reinterpret_cast<uint4*>(vrow + cb) = make_uint4(w[0], w[1], w[2], w[3]);
+                if constexpr (CH == 16) {
+                    *reinterpret_cast<uint4*>(vrow + cb) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else {
+                    // 8-spin chunks: two neighbours go out as one 16-byte store
+                    // where the pair starts on a 16-byte boundary (fewer stores
+                    // for the release after the epilogue to wait for)
+                    if (((cb >> 3) & 1) == 0) {
+                        if (j + 1 < NCH)
+                            pend = make_uint2(w[0], w[1]);
+                        else
+                            *reinterpret_cast<uint2*>(vrow + cb) = make_uint2(w[0], w[1]);
+                    } else if (j > 0) {
+                        *reinterpret_cast<uint4*>(vrow + cb - 8) =
+                            make_uint4(pend.x, pend.y, w[0], w[1]);
+                    } else {
+                        *reinterpret_cast<uint2*>(vrow + cb) = make_uint2(w[0], w[1]);
+                    }
+                }
             }
             // The block barrier orders every thread's V bytes before the one
             // release (add or remote arrivals), which is cumulative over them;
@@ -757,19 +833,19 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         }
         // state back to global memory
 #pragma unroll 1
-        for (int cb = c0; cb < c0 + 64; cb += 16) {
+        for (int cb = c0; cb < c0 + HW; cb += CH) {
             const size_t o = (size_t)(i0 + cb) * Rp + r;
-            float v[16];
-            tmem_ld16(tl + 128 + 2 * cb, v);
+            float f[CH], xs[CH], ys[CH];
+            tmem_ld_fxy<CH>(tl + cb, tl + 128 + 2 * cb, f, xs, ys);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) x[o + (size_t)k * Rp] = v[k];
-            tmem_ld16(tl + 128 + 2 * cb + 16, v);
-#pragma unroll
-            for (int k = 0; k < 16; ++k) y[o + (size_t)k * Rp] = v[k];
+            for (int k = 0; k < CH; ++k) {
+                x[o + (size_t)k * Rp] = xs[k];
+                y[o + (size_t)k * Rp] = ys[k];
+            }
         }
         if (CONTROL) {
 #pragma unroll
-            for (int k = 0; k < 64; ++k) p[(size_t)(i0 + c0 + k) * Rp + r] = pr[k];
+            for (int k = 0; k < HW; ++k) p[(size_t)(i0 + c0 + k) * Rp + r] = pr[k];
         }
     }
     fence_before_sync();
@@ -1141,7 +1217,9 @@ struct TcState {
     bool persistent = false;     // a multi-step kernel runs this shape
     bool cluster = false;        // ... in its cluster form (else the cooperative grid form)
     bool pair = false;           // ... in the grid form on SM pairs
+    int bs = BM;                 // spins per CTA of the grid form (128, or 112: more CTAs)
     CUtensorMap tmA_half;        // J in tiles of 64 rows (the pair form)
+    CUtensorMap tmA_bs;          // J in tiles of bs rows (the narrow grid form)
     uint32_t* counters = nullptr;  // one per replica block
     float* p_sched = nullptr;      // p(t_{m+1}) for m = 0..M-1 (shared schedule)
 };
@@ -1468,7 +1546,10 @@ const char* tc_kernel_name(const gsb_run_state* run) {
     if (T->kind == 1) return "k_fx32_step";
     if (T->kind == 2) return "k_fx16_persist";
     if (T->persistent)
-        return T->cluster ? "k_tc_persist<cluster>" : T->pair ? "k_tc_persist<pair>" : "k_tc_persist<grid>";
+        return T->cluster ? "k_tc_persist<cluster>"
+               : T->pair  ? "k_tc_persist<pair>"
+               : T->bs != BM ? "k_tc_persist<grid112>"
+                             : "k_tc_persist<grid>";
     return "k_tc_step<e4m3>";
 }
 
@@ -1481,8 +1562,12 @@ gsb_status tc_setup(gsb_run_state* run) {
     const size_t n = (size_t)run->Np * run->Rp;
     gsb_status st;
     if (T->kind == 0) {
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 2; ++b) {
             if ((st = dev_alloc(&run->v8[b], n))) return st;
+            // zero (e4m3 0): spins past a narrow grid's last block keep this in
+            // the buffer the steps write, and their J columns are zero
+            GSB_CUDA_TRY(cudaMemsetAsync(run->v8[b], 0, n, run->stream));
+        }
         if ((st = make_map(&T->tmA, P->J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P->Np, P->Np))) return st;
         for (int b = 0; b < 2; ++b)
             if ((st = make_map(&T->tmB[b], run->v8[b], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, run->Np,
@@ -1548,7 +1633,11 @@ gsb_status tc_setup(gsb_run_state* run) {
                 nclusters = 0;
             }
         }
-        bool grid_fits = false, pair_fits = false;
+        bool grid_fits = false, pair_fits = false, narrow_fits = false;
+        // the narrow grid form: ceil(N / 112) spin blocks of 112, when that is
+        // more CTAs than the 128-wide grid and they are all resident at once
+        constexpr int kNarrow = 112;
+        const int nsb_narrow = (run->N + kNarrow - 1) / kNarrow;
         {
             int dev = 0, sms = 0, per_sm = 0, coop = 0;
             GSB_CUDA_TRY(cudaGetDevice(&dev));
@@ -1561,6 +1650,17 @@ gsb_status tc_setup(gsb_run_state* run) {
             GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsP,
                                                                        smem_bytes_persist()));
             grid_fits = coop && per_sm >= 1 && (long)nrb * (run->Np / BM) <= (long)per_sm * sms;
+            if (coop && nsb_narrow > run->Np / BM && nsb_narrow * kNarrow <= run->Np) {
+                auto kn = run->control ? (const void*)k_tc_persist<true, kFormGrid, kNarrow>
+                                       : (const void*)k_tc_persist<false, kFormGrid, kNarrow>;
+                const int sm_n = smem_bytes_persist(kFormGrid, kNarrow);
+                int per_sm_n = 0;
+                GSB_CUDA_TRY(cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  sm_n));
+                GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_n, kn, kThreadsP,
+                                                                           sm_n));
+                narrow_fits = per_sm_n >= 1 && (long)nrb * nsb_narrow <= (long)per_sm_n * sms;
+            }
             if (coop && nrb % 2 == 0 && (run->params.flags & GSB_RUN_SM_PAIRS)) {
                 auto kp = run->control ? k_tc_persist<true, kFormPair> : k_tc_persist<false, kFormPair>;
                 GSB_CUDA_TRY(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1583,6 +1683,13 @@ gsb_status tc_setup(gsb_run_state* run) {
             T->persistent = T->pair = true;
             if ((st = make_map(&T->tmA_half, P->J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P->Np, P->Np,
                                BM / 2)))
+                return st;
+            if ((st = dev_alloc(&T->counters, (size_t)nrb))) return st;
+        } else if (narrow_fits) {
+            T->persistent = true;
+            T->bs = kNarrow;
+            if ((st = make_map(&T->tmA_bs, P->J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, P->Np, P->Np,
+                               kNarrow)))
                 return st;
             if ((st = dev_alloc(&T->counters, (size_t)nrb))) return st;
         } else if (grid_fits) {
@@ -1656,6 +1763,17 @@ gsb_status launch_persist(gsb_run_state* run, TcState* T, int m0, int n) {
                                         T->tmB[1], Np, Rp, run->x[0], run->y, run->p,
                                         (const float*)run->A, run->v8[0], run->v8[1], c, dt, ps, M,
                                         m0, n, (uint32_t*)nullptr, run->status));
+    } else if (T->bs != BM) {
+        const int nrb = run->Rp / BN;
+        GSB_CUDA_TRY(cudaMemsetAsync(T->counters, 0, sizeof(uint32_t) * nrb, run->stream));
+        dim3 grid(nrb, (run->N + T->bs - 1) / T->bs);
+        void* args[] = {(void*)&T->tmA_bs, (void*)&T->tmB[0], (void*)&T->tmB[1], &Np, &Rp,
+                        (void*)&run->x[0], (void*)&run->y, (void*)&run->p, (void*)&run->A,
+                        (void*)&run->v8[0], (void*)&run->v8[1], &c, &dt, (void*)&ps, &M, &m0, &n,
+                        (void*)&T->counters, (void*)&run->status};
+        GSB_CUDA_TRY(cudaLaunchCooperativeKernel(
+            (const void*)k_tc_persist<CONTROL, kFormGrid, 112>, grid, dim3(kThreadsP), args,
+            smem_bytes_persist(kFormGrid, 112), run->stream));
     } else {
         const int nrb = run->Rp / BN;
         GSB_CUDA_TRY(cudaMemsetAsync(T->counters, 0, sizeof(uint32_t) * nrb, run->stream));

@@ -505,17 +505,18 @@ def test_lambda_extremes_match_dense_eigensolver(case):
 @pytest.mark.parametrize("variant", ["dsb", "gdsb"])
 @pytest.mark.parametrize("N,R,form", [(100, 130, "cluster"), (300, 200, "cluster"),
                                       (2000, 128, "cluster"), (2100, 129, "pair"),
-                                      (2100, 129, "grid"), (2000, 1024, "pair"),
-                                      (2000, 1024, "grid")])
+                                      (2100, 129, "grid112"), (2000, 1024, "pair"),
+                                      (2000, 1024, "grid112"), (2000, 1152, "grid")])
 def test_fp8_persistent_matches_per_step_launches_bit_exact(variant, N, R, form):
     """The persistent FP8 kernel (state in TMEM, many steps per launch; 1, 3,
-    16 and 17 K atoms per step, so ring stages of two atoms and a last stage of
-    one; clusters of 1, 3 and 16 CTAs per replica block, the cooperative grid
-    form above 16 spin blocks, and that form on SM pairs (two replica blocks
-    per MMA, asked for with sm_pairs on an even number of replica blocks) and
-    the one-step-per-launch FP8 kernel do the same arithmetic: identical bits.
-    N = 2000, R = 1024 is the timed shape (8 replica blocks of 16 spin blocks:
-    the grid form)."""
+    16 and 17 K atoms per step, so ring stages of three atoms and a shorter
+    last one; clusters of 1, 3 and 16 CTAs per replica block; the cooperative
+    grid form above 16 spin blocks, with spin blocks of 112 (grid112: 18 or 19
+    of them, the last one short of N_p) where the extra CTAs still fit and of
+    128 where they do not (R = 1152: 9 replica blocks); and that form on SM
+    pairs, asked for with sm_pairs) and the one-step-per-launch FP8 kernel do
+    the same arithmetic: identical bits. N = 2000, R = 1024 is the timed shape
+    (8 replica blocks of 18 spin blocks of 112)."""
     M = 120
     J = I.sk_pm1(N, 41)
     P = gsb.Problem.dense(J)
