@@ -895,16 +895,26 @@ __host__ __device__ constexpr int smem_bytes_fx16() {
 }
 
 // e4m3 bytes of two small integers of at most four significant bits (exact).
+// (float)n for |n| < 2^22 without a conversion instruction: 1.5 2^23 + n lies
+// in [2^23, 2^24), where the float's last mantissa bit is worth 1, so its bit
+// pattern is that of 1.5 2^23 plus n, and subtracting 1.5 2^23 leaves n exactly.
+__device__ __forceinline__ float small_int_to_float(int n) {
+    return __fsub_rn(__int_as_float(0x4B400000 + n), 12582912.0f);
+}
 __device__ __forceinline__ uint32_t e4m3x2(int lo, int hi) {
-    return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2((float)lo, (float)hi), __NV_SATFINITE,
-                                              __NV_E4M3);
+    return (uint32_t)__nv_cvt_float2_to_fp8x2(
+        make_float2(small_int_to_float(lo), small_int_to_float(hi)), __NV_SATFINITE, __NV_E4M3);
 }
 
 // The four digit-plane bytes of x: d0, 16 d1, d2, 16 d3 of q = rint(x 2^15).
 // With u = q + 0x888 (8 (1 + 16 + 256)), d_k = nibble_k(u) - 8 for k < 3 and
-// d3 = u >> 12 (arithmetic), in [-8, 8] for |x| <= 1.
+// d3 = u >> 12 (arithmetic), in [-8, 8] for |x| <= 1. q is rounded by adding
+// 1.5 2^23 (x 2^15 is exact, |x 2^15| <= 2^15 < 2^22, so the sum's last
+// mantissa bits hold the integer, rounded to nearest even like rint) -- an
+// FP32 add instead of a conversion instruction.
 __device__ __forceinline__ void fx16_digits(float x, int (&d)[4]) {
-    const int u = __float2int_rn(x * 32768.0f) + 0x888;
+    const float t = __fadd_rn(x * 32768.0f, 12582912.0f);
+    const int u = __float_as_int(t) - 0x4B400000 + 0x888;
     d[0] = (u & 15) - 8;
     d[1] = 16 * (((u >> 4) & 15) - 8);
     d[2] = ((u >> 8) & 15) - 8;
@@ -1102,11 +1112,11 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     tmem_wait_ld(ry);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        // exact integers below 2^24 in FP32; their int32 combination
-                        // is exact, rounded once to FP32 (2^-15 is exact)
-                        const int q = __float2int_rn(__uint_as_float(ra[k])) +
-                                      256 * __float2int_rn(__uint_as_float(rb2[k]));
-                        f[k] = __int2float_rn(q) * 3.0517578125e-05f;
+                        // A0, A1: exact integers below 2^24 in FP32. f = 2^-15 (A0 +
+                        // 256 A1) rounded once: one FMA of the exactly scaled terms
+                        // (2^-15 A0 and 2^-7 are exact), no conversion instruction
+                        f[k] = __fmaf_rn(__uint_as_float(rb2[k]), 0.0078125f,
+                                         __uint_as_float(ra[k]) * 3.0517578125e-05f);
                         xs[k] = __uint_as_float(rx[k]);
                         ys[k] = __uint_as_float(ry[k]);
                     }
