@@ -1,6 +1,7 @@
 // gsb_internal.cuh -- types and helpers shared by the libgsb translation units.
 #pragma once
 
+#include <atomic>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -143,6 +144,17 @@ struct gsb_run_state {
 };
 
 namespace gsb {
+
+// Kernel attributes (the dynamic shared-memory limit) are set per device: a
+// call site keeps one bit per device it has set them on, so a process using
+// several GPUs sets them on each. True the first time the current device
+// reaches the site.
+inline bool first_on_device(std::atomic<uint64_t>& seen) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+    const uint64_t bit = 1ull << dev;
+    return !(seen.fetch_or(bit) & bit);
+}
 
 // Error reporting (thread-local message, set by the API layer).
 gsb_status set_error(gsb_status st, const std::string& msg);

@@ -458,12 +458,10 @@ int device_sms() {
 }
 
 gsb_status set_smem_attr() {
-    static bool done = false;
-    if (!done) {
+    static std::atomic<uint64_t> seen{0};
+    if (first_on_device(seen))
         GSB_CUDA_TRY(cudaFuncSetAttribute(k_bf16_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kSmemM));
-        done = true;
-    }
     return GSB_OK;
 }
 

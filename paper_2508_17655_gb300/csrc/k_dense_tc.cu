@@ -1483,26 +1483,22 @@ __global__ void __launch_bounds__(kThreadsF, 1)
 template <int KIND, bool CONTROL>
 gsb_status launch_step(gsb_run_state* run, TcState* T, float p_shared, float inv_rem) {
     dim3 grid(run->Rp / BN, run->Np / BM);
-    static bool attr_set = false;
+    static std::atomic<uint64_t> attr_seen{0};
     if constexpr (KIND == 1) {
-        if (!attr_set) {
+        if (first_on_device(attr_seen))
             GSB_CUDA_TRY(cudaFuncSetAttribute(k_fx32_step<CONTROL>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               smem_bytes_fx32()));
-            attr_set = true;
-        }
         GSB_CUDA_TRY(launch_pdl(k_fx32_step<CONTROL>, grid, dim3(kThreadsF), smem_bytes_fx32(),
                                 run->stream, T->tmA, T->tmB[T->vcur], run->Np, run->Rp,
                                 run->x[0], run->y, run->p, run->A, run->v16[T->vcur ^ 1], run->c,
                                 run->dt, p_shared, inv_rem, run->status));
         GSB_LAUNCH_CHECK("k_fx32_step");
     } else {
-        if (!attr_set) {
+        if (first_on_device(attr_seen))
             GSB_CUDA_TRY(cudaFuncSetAttribute(k_tc_step<CONTROL>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               smem_bytes_step()));
-            attr_set = true;
-        }
         k_tc_step<CONTROL><<<grid, kThreads, smem_bytes_step(), run->stream>>>(
             T->tmA, T->tmB[T->vcur], run->Np, run->Rp, run->x[0], run->y, run->p, run->A,
             run->v8[T->vcur ^ 1], run->c, run->dt, p_shared, inv_rem, run->status);
@@ -1876,12 +1872,10 @@ gsb_status tc_energy(gsb_run_state* run, int step) {
     if (run->path == kPathTcFp8 && T) {
         // sgn x(t_step) is the e4m3 operand the steps left in buffer step & 1
         const int b = step & 1;
-        static bool attr_set = false;
-        if (!attr_set) {
+        static std::atomic<uint64_t> attr_seen{0};
+        if (first_on_device(attr_seen))
             GSB_CUDA_TRY(cudaFuncSetAttribute(k_tc_energy, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               smem_bytes_step()));
-            attr_set = true;
-        }
         dim3 grid(run->Rp / BN, run->Np / BM);
         k_tc_energy<<<grid, kThreads, smem_bytes_step(), run->stream>>>(
             T->tmA, T->tmB[b], run->v8[b], run->Np, run->e_acc, run->status);
