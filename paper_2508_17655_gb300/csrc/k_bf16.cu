@@ -288,28 +288,29 @@ __global__ void __launch_bounds__(kThreadsM, 1)
             const size_t plane = (size_t)Rp * Np;
             uint16_t* vrow = reinterpret_cast<uint16_t*>(vout) + (size_t)r * Np + T.i0;
             const uint32_t ta = tl + 128u * b;
-            // chunks of 8 spins; the state of the next chunk is loaded while this
-            // one is processed, so the L2 latency of the loads overlaps the work
+            // chunks of 8 spins; the state is loaded two chunks ahead (two register
+            // buffers in turn), so the L2 latency of the loads -- the epilogue's
+            // bound when only one chunk was in flight -- overlaps the work
             constexpr int CW = 8;
-            float xn[CW], yn[CW], pn[CW];
-            auto load_state = [&](int cb) {
+            float xa[CW], ya[CW], pa[CW], xb[CW], yb[CW], pb[CW];
+            auto load_state = [&](int cb, float (&xq)[CW], float (&yq)[CW], float (&pq)[CW]) {
                 const size_t o = (size_t)(T.i0 + cb) * Rp + r;
 #pragma unroll
                 for (int k = 0; k < CW; ++k) {
-                    xn[k] = x[o + (size_t)k * Rp];
-                    yn[k] = y[o + (size_t)k * Rp];
-                    pn[k] = control ? p[o + (size_t)k * Rp] : 0.f;
+                    xq[k] = x[o + (size_t)k * Rp];
+                    yq[k] = y[o + (size_t)k * Rp];
+                    pq[k] = control ? p[o + (size_t)k * Rp] : 0.f;
                 }
             };
-            load_state(c0);
-#pragma unroll 1
-            for (int cb = c0; cb < c0 + 64; cb += CW) {
+            load_state(c0, xa, ya, pa);
+            load_state(c0 + CW, xb, yb, pb);
+            auto chunk = [&](int cb, float (&xq)[CW], float (&yq)[CW], float (&pq)[CW]) {
                 uint32_t rf[CW];
                 tmem_ld8_async(ta + cb, rf);
                 float xs[CW], ys[CW], ps[CW];
 #pragma unroll
-                for (int k = 0; k < CW; ++k) xs[k] = xn[k], ys[k] = yn[k], ps[k] = pn[k];
-                if (cb + CW < c0 + 64) load_state(cb + CW);
+                for (int k = 0; k < CW; ++k) xs[k] = xq[k], ys[k] = yq[k], ps[k] = pq[k];
+                if (cb + 2 * CW < c0 + 64) load_state(cb + 2 * CW, xq, yq, pq);
                 tmem_wait_ld8(rf);
 #pragma unroll
                 for (int k = 0; k < CW; k += 2) {
@@ -352,6 +353,11 @@ __global__ void __launch_bounds__(kThreadsM, 1)
                 if (!sign)
                     *reinterpret_cast<uint4*>(vrow + plane + cb) =
                         make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            };
+#pragma unroll 1
+            for (int cb = c0; cb < c0 + 64; cb += 2 * CW) {
+                chunk(cb, xa, ya, pa);
+                chunk(cb + CW, xb, yb, pb);
             }
             // the block barrier orders every thread's F reads and its state and V
             // stores before the one release; readers acquire the counter
