@@ -75,10 +75,176 @@ struct MTile {
     int inst, i0, r0, pad;
 };
 
-__device__ __forceinline__ uint16_t bf16_bits(float v) {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+// bf16 bits of a finite v rounded to nearest even, by integer operations (no
+// conversion instruction): add just under half a bf16 ulp (0x7FFF), plus one
+// when the kept part is odd so that ties go to the even neighbour, and keep
+// the top 16 bits. A carry out of the mantissa moves into the exponent, as the
+// rounding requires.
+__device__ __forceinline__ uint32_t bf16_rne_bits(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
+}
+// x = x_hi + x_lo with x_hi = bf16(x) and x_lo = bf16(x - x_hi) (x - x_hi is
+// exact in FP32: the two agree in their top 8 bits); both as bf16 bits.
+__device__ __forceinline__ void bf16_split_bits(float v, uint32_t& hi, uint32_t& lo) {
+    hi = bf16_rne_bits(v);
+    lo = bf16_rne_bits(v - __uint_as_float(hi << 16));
 }
 
+// The epilogue of the resident form: this CTA's one tile, its state in TMEM.
+// Per step: F from TMEM, Eqs. 7, 3, 4, 5 in the order of sb_update2, x, y, p
+// back to TMEM, the next step's operand planes to global memory; then the
+// accumulator is released and the instance's counter advanced.
+__device__ __forceinline__ void bf16_res_epilogue(const MInst* __restrict__ insts,
+                                                  const MTile* __restrict__ tiles, int ntiles,
+                                                  long nitems, long G, uint32_t* counters,
+                                                  int* status, uint32_t tmem, uint32_t* tmem_slot,
+                                                  uint64_t* accf, uint64_t* acce, int warp,
+                                                  int lane) {
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int c0 = (ew >> 2) * 64;
+    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+    volatile uint32_t* abort_flag = tmem_slot + 1;
+    const MTile T = tiles[blockIdx.x % ntiles];
+    const MInst* I = insts + T.inst;
+    const int Np = I->Np, Rp = I->Rp;
+    const bool sign = I->flags & 1, control = I->flags & 2;
+    const float c = I->c, dt = I->dt;
+    float* __restrict__ x = I->x;
+    float* __restrict__ y = I->y;
+    float* __restrict__ p = I->p;
+    const int r = T.r0 + quarter * 32 + lane;
+    const float a_r = control ? I->A[r] : 0.f;
+    const size_t plane = (size_t)Rp * Np;
+    // the tile's state into TMEM
+#pragma unroll 1
+    for (int cb = c0; cb < c0 + 64; cb += 16) {
+        const size_t o = (size_t)(T.i0 + cb) * Rp + r;
+        float v[16], w[16], q[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            v[k] = x[o + (size_t)k * Rp];
+            w[k] = y[o + (size_t)k * Rp];
+            q[k] = control ? p[o + (size_t)k * Rp] : 0.f;
+        }
+        tmem_st32(tl + 128 + 2 * cb, v, w);
+        tmem_st16(tl + 384 + cb, q);
+    }
+    tmem_wait_st();
+    uint32_t n = 0;
+    for (long j = blockIdx.x; j < nitems; j += G) {
+        const int s = (int)(j / ntiles);
+        const int m = I->m0 + s;
+        if (m >= I->stop) continue;
+        bool ok = *abort_flag == 0u;
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&accf[0], n & 1u, status));
+        if (!ok) {
+            *abort_flag = 1u;
+            named_barrier_sync(1, kEpiThreadsM);
+            break;
+        }
+        fence_after_sync();
+        const float inv_rem = __frcp_rn((float)(I->M - m));
+        const float p_shared = control ? 0.f : I->p_sched[m];
+        uint16_t* vrow = reinterpret_cast<uint16_t*>(I->v[(m + 1) & 1]) + (size_t)r * Np + T.i0;
+#pragma unroll 1
+        for (int cb = c0; cb < c0 + 64; cb += 16) {
+            float f[16], xs[16], ys[16], ps[16];
+            {
+                uint32_t rf[16], rx[16], ry[16], rq[16];
+                tmem_ld16_async(tl + cb, rf);
+                tmem_ld32_async(tl + 128 + 2 * cb, rx, ry);
+                tmem_ld16_async(tl + 384 + cb, rq);
+                tmem_wait_ld(rf);
+                tmem_wait_ld(rx);
+                tmem_wait_ld(ry);
+                tmem_wait_ld(rq);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    f[k] = __uint_as_float(rf[k]);
+                    xs[k] = __uint_as_float(rx[k]);
+                    ys[k] = __uint_as_float(ry[k]);
+                    ps[k] = __uint_as_float(rq[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+                float2 x2 = make_float2(xs[k], xs[k + 1]), y2 = make_float2(ys[k], ys[k + 1]);
+                float2 p2 = make_float2(ps[k], ps[k + 1]);
+                const float2 f2 = make_float2(f[k], f[k + 1]);
+                if (control)
+                    sb_update2<true>(x2, y2, p2, f2, a_r, c, dt, p_shared, inv_rem);
+                else
+                    sb_update2<false>(x2, y2, p2, f2, a_r, c, dt, p_shared, inv_rem);
+                xs[k] = x2.x, xs[k + 1] = x2.y, ys[k] = y2.x, ys[k + 1] = y2.y;
+                ps[k] = p2.x, ps[k + 1] = p2.y;
+            }
+            tmem_st32(tl + 128 + 2 * cb, xs, ys);
+            tmem_st16(tl + 384 + cb, ps);
+            // next step's operand planes, 16 bf16 (32 bytes) of the replica's row each
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+                if (sign) {
+                    hi[k / 2] = (xs[k] >= 0.f ? 0x3F80u : 0xBF80u) |
+                                ((xs[k + 1] >= 0.f ? 0x3F80u : 0xBF80u) << 16);
+                    lo[k / 2] = 0u;
+                } else {
+                    uint32_t h0, l0, h1, l1;
+                    bf16_split_bits(xs[k], h0, l0);
+                    bf16_split_bits(xs[k + 1], h1, l1);
+                    hi[k / 2] = h0 | (h1 << 16);
+                    lo[k / 2] = l0 | (l1 << 16);
+                }
+            }
+            *reinterpret_cast<uint4*>(vrow + cb) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(vrow + cb + 8) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+            if (!sign) {
+                *reinterpret_cast<uint4*>(vrow + plane + cb) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                *reinterpret_cast<uint4*>(vrow + plane + cb + 8) =
+                    make_uint4(lo[4], lo[5], lo[6], lo[7]);
+            }
+        }
+        // the block barrier orders every thread's F reads and V stores before
+        // the one release; readers acquire the counter
+        tmem_wait_st();
+        fence_before_sync();
+        named_barrier_sync(1, kEpiThreadsM);
+        if (*abort_flag) break;
+        if (ew == 0 && lane == 0) {
+            mbar_arrive(&acce[0]);
+            red_release_add(counters + T.inst, 1u);
+        }
+        ++n;
+    }
+    // state back to global memory
+#pragma unroll 1
+    for (int cb = c0; cb < c0 + 64; cb += 16) {
+        const size_t o = (size_t)(T.i0 + cb) * Rp + r;
+        float v[16];
+        tmem_ld16(tl + 128 + 2 * cb, v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[o + (size_t)k * Rp] = v[k];
+        tmem_ld16(tl + 128 + 2 * cb + 16, v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) y[o + (size_t)k * Rp] = v[k];
+        if (control) {
+            tmem_ld16(tl + 384 + cb, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) p[o + (size_t)k * Rp] = v[k];
+        }
+    }
+}
+
+// RES (resident form): launched with one CTA per tile (grid == ntiles), so the
+// item loop gives every CTA the same tile each step; its x, y, p stay in TMEM
+// for the whole launch (columns 128..383 x and y of each 16 spins side by
+// side, 384..511 p; one accumulator at 0..127) and cross global memory only at
+// the launch's start and end. Without RES the tiles of a step are spread over
+// the CTAs round robin and the state goes through L2 every step (two
+// accumulators for overlap across items).
+template <bool RES>
 __global__ void __launch_bounds__(kThreadsM, 1)
     k_bf16_multi(const MInst* __restrict__ insts, const MTile* __restrict__ tiles, int ntiles,
                  int nsteps, uint32_t* __restrict__ counters, int ninst, int* __restrict__ status) {
@@ -135,7 +301,7 @@ __global__ void __launch_bounds__(kThreadsM, 1)
         tmem_slot[1] = 0u;  // epilogue abort flag
         fence_barrier_init();
     }
-    if (warp == 1) tmem_alloc(tmem_slot, 256);
+    if (warp == 1) tmem_alloc(tmem_slot, RES ? 512 : 256);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -213,9 +379,11 @@ __global__ void __launch_bounds__(kThreadsM, 1)
                 if (I->m0 + s >= I->stop) continue;
                 const int nk = I->Np / kElems;
                 const bool xc = !(I->flags & 1);
-                const uint32_t b = n & 1u;
+                const uint32_t b = RES ? 0u : n & 1u;
                 // the epilogue has read this accumulator's previous item
-                if (n >= 2 && !mbar_wait(&acce[b], ((n - 2) >> 1) & 1u, status)) break;
+                if (RES ? (n >= 1 && !mbar_wait(&acce[0], (n - 1) & 1u, status))
+                        : (n >= 2 && !mbar_wait(&acce[b], ((n - 2) >> 1) & 1u, status)))
+                    break;
                 fence_after_sync();
                 const uint32_t d = tmem + 128u * b;
                 for (int u = 0; u < nk; ++u, ++g) {
@@ -244,6 +412,9 @@ __global__ void __launch_bounds__(kThreadsM, 1)
             mma_commit(drain);
             mbar_wait(drain, 0, status, kDrainLimitCycles);
         }
+    } else if (RES) {
+        bf16_res_epilogue(insts, tiles, ntiles, nitems, G, counters, status, tmem, tmem_slot, accf,
+                          acce, warp, lane);
     } else {
         const int ew = warp - 2;
         const int quarter = warp & 3;
@@ -340,13 +511,11 @@ __global__ void __launch_bounds__(kThreadsM, 1)
                                     ((xs[k + 1] >= 0.f ? 0x3F80u : 0xBF80u) << 16);
                         lo[k / 2] = 0u;
                     } else {
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(xs[k]);
-                        const __nv_bfloat16 h1 = __float2bfloat16_rn(xs[k + 1]);
-                        hi[k / 2] = (uint32_t)__bfloat16_as_ushort(h0) |
-                                    ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                        // x - x_hi is exact in FP32 (the two agree in their top 8 bits)
-                        lo[k / 2] = (uint32_t)bf16_bits(xs[k] - __bfloat162float(h0)) |
-                                    ((uint32_t)bf16_bits(xs[k + 1] - __bfloat162float(h1)) << 16);
+                        uint32_t h0, l0, h1, l1;
+                        bf16_split_bits(xs[k], h0, l0);
+                        bf16_split_bits(xs[k + 1], h1, l1);
+                        hi[k / 2] = h0 | (h1 << 16);
+                        lo[k / 2] = l0 | (l1 << 16);
                     }
                 }
                 *reinterpret_cast<uint4*>(vrow + cb) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -375,7 +544,7 @@ __global__ void __launch_bounds__(kThreadsM, 1)
     __syncthreads();
     if (warp == 1) {
         fence_after_sync();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, RES ? 512 : 256);
     }
 }
 
@@ -407,9 +576,10 @@ __global__ void k_bf16_prep(const float* __restrict__ x, __nv_bfloat16* __restri
         if (sign) {
             v[vo] = __ushort_as_bfloat16(xv >= 0.f ? (uint16_t)0x3F80 : (uint16_t)0xBF80);
         } else {
-            const __nv_bfloat16 h = __float2bfloat16_rn(xv);
-            v[vo] = h;
-            v[plane + vo] = __float2bfloat16_rn(xv - __bfloat162float(h));
+            uint32_t h, l;
+            bf16_split_bits(xv, h, l);
+            v[vo] = __ushort_as_bfloat16((uint16_t)h);
+            v[plane + vo] = __ushort_as_bfloat16((uint16_t)l);
         }
     }
 }
@@ -465,9 +635,12 @@ int device_sms() {
 
 gsb_status set_smem_attr() {
     static std::atomic<uint64_t> seen{0};
-    if (first_on_device(seen))
-        GSB_CUDA_TRY(cudaFuncSetAttribute(k_bf16_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kSmemM));
+    if (first_on_device(seen)) {
+        GSB_CUDA_TRY(cudaFuncSetAttribute(k_bf16_multi<false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemM));
+        GSB_CUDA_TRY(cudaFuncSetAttribute(k_bf16_multi<true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemM));
+    }
     return GSB_OK;
 }
 
@@ -477,16 +650,20 @@ gsb_status coop_grid(long items, int* grid) {
     gsb_status st = set_smem_attr();
     if (st != GSB_OK) return st;
     int per_sm = 0;
-    GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bf16_multi, kThreadsM,
-                                                               kSmemM));
+    GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bf16_multi<false>,
+                                                               kThreadsM, kSmemM));
     const long cap = (long)std::max(per_sm, 0) * device_sms();
     if (cap < 1) return set_error(GSB_ECUDA, "k_bf16_multi cannot be resident");
     *grid = (int)std::max(1L, std::min(cap, items));
     return GSB_OK;
 }
 
+// grid: the CTAs the launch may take. When every tile can have its own CTA
+// (grid >= ntiles) the launch takes exactly one per tile and the resident form.
 gsb_status launch_multi(const MInst* insts, const MTile* tiles, int ntiles, int nsteps,
                         uint32_t* counters, int ninst, int* status, int grid, cudaStream_t s) {
+    const bool res = grid >= ntiles;
+    if (res) grid = ntiles;
     GSB_CUDA_TRY(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * ninst, s));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -498,8 +675,12 @@ gsb_status launch_multi(const MInst* insts, const MTile* tiles, int ntiles, int 
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    GSB_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_bf16_multi, insts, tiles, ntiles, nsteps, counters,
-                                    ninst, status));
+    if (res)
+        GSB_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_bf16_multi<true>, insts, tiles, ntiles, nsteps,
+                                        counters, ninst, status));
+    else
+        GSB_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_bf16_multi<false>, insts, tiles, ntiles, nsteps,
+                                        counters, ninst, status));
     count_launch();
     return GSB_OK;
 }
@@ -640,7 +821,7 @@ gsb_status bf16_batch(gsb_run_state* const* runs, int n, const int* stop, int pe
     gsb_status st = set_smem_attr();
     if (st != GSB_OK) return st;
     int per_sm = 0;
-    GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bf16_multi, kThreadsM,
+    GSB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bf16_multi<false>, kThreadsM,
                                                                kSmemM));
     const int G = std::max(per_sm, 0) * device_sms();
     if (G < 1) return set_error(GSB_ECUDA, "k_bf16_multi cannot be resident");
