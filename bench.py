@@ -447,7 +447,8 @@ def _events(torch, stream):
     return e0, e1
 
 
-LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "adjoint", "fx32", "fx16",
+LEGS = ("sparse_N2000", "sparse_N20000", "batched_256", "lyapunov", "lyapunov_bf16x3",
+        "adjoint", "fx32", "fx16",
         "twin_delta", "grid", "twin_valley")
 
 
@@ -646,7 +647,7 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
             "mean_delta_tM": g["delta_mean"].tolist()}
         P.close()
         return out
-    if only is not None and only not in ("batched_256", "lyapunov", "adjoint"):
+    if only is not None and only not in ("batched_256", "lyapunov", "lyapunov_bf16x3", "adjoint"):
         return out
     # --- 256 batched uneven SK instances, N ~ U{64..1024}, R ~ U{32..256}, M = 1000:
     # the split-bf16 tensor-core form (persistent launches over windows of
@@ -710,37 +711,48 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (derived)"}}
     for P in probs:
         P.close()
-    if only is not None and only not in ("lyapunov", "adjoint"):
+    if only is not None and only not in ("lyapunov", "lyapunov_bf16x3", "adjoint"):
         return out
     # --- Lyapunov exponents: N = 2000 SK, 16 control strengths x 256 replicas
     J5 = I.sk_gauss(2000, 0)
     P5 = gsb.Problem.dense(J5, stream=stream.cuda_stream)
-    if not want("lyapunov"):
+    if not (want("lyapunov") or only == "lyapunov_bf16x3"):
         return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak)
     A16 = [0.025 * k for k in range(16)]
     steps = 200
-    P5.lyapunov("gbsb", 2000, 256, A16, c=0.5, dt=1.25, renorm_every=10, nsteps=20)
-    t = time.perf_counter()
-    mle = P5.lyapunov("gbsb", 2000, 256, A16, c=0.5, dt=1.25, renorm_every=10, nsteps=steps)
-    el = time.perf_counter() - t
-    gsb.set_call_profiling(True)
-    P5.lyapunov("gbsb", 2000, 256, A16, c=0.5, dt=1.25, renorm_every=10, nsteps=steps)
-    kms, kn, _ = gsb.last_call_profile()
-    gsb.set_call_profiling(False)
     # J over [X | dX]: 2 N^2 flop for each of the 2 x 16 x 256 columns per step
     flop = 2.0 * 2000 ** 2 * (2 * 16 * 256) * steps
-    ach = flop / (kms * 1e-3) / 1e12
-    out["lyapunov"] = {
-        "workload": "N=2000 SK N(0,1/N), R=256 x 16 A in [0, 0.375], first 200 of M=2000 steps, renorm 10",
-        "value": 16 * 256 * steps / el, "unit": "replica-steps/s (with tangents)",
-        "how": "value: host wall clock around gsb_lyapunov",
-        "kernel_ms": kms, "kernel_launches": kn,
-        "mean_mle_by_A": [float(np.mean(mle[k][np.isfinite(mle[k])])) if np.isfinite(mle[k]).any()
-                          else None for k in range(16)],
-        "roofline": {"bound": "alu", "kernel": "k_tangent_step", "achieved": ach,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                     "how": "algorithmic flop / CUDA-event time of the step-kernel launches"}}
-    if only == "lyapunov":
+    # (--leg lyapunov_bf16x3: the tensor-core form alone, for profiling)
+    for form in ("bf16x3",) if only == "lyapunov_bf16x3" else ("fp32", "bf16x3"):
+        kw = dict(c=0.5, dt=1.25, renorm_every=10, precision=form)
+        P5.lyapunov("gbsb", 2000, 256, A16, nsteps=20, **kw)
+        t = time.perf_counter()
+        mle = P5.lyapunov("gbsb", 2000, 256, A16, nsteps=steps, **kw)
+        el = time.perf_counter() - t
+        gsb.set_call_profiling(True)
+        P5.lyapunov("gbsb", 2000, 256, A16, nsteps=steps, **kw)
+        kms, kn, _ = gsb.last_call_profile()
+        gsb.set_call_profiling(False)
+        ach = flop / (kms * 1e-3) / 1e12
+        if form == "fp32":
+            roof = {"bound": "alu", "kernel": "k_tangent_step", "achieved": ach,
+                    "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak}
+        else:
+            roof = {"bound": "tensor", "kernel": "k_tangent_tc", "achieved": ach,
+                    "peak": Pk["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / Pk["bf16_tflops"],
+                    "peak_source": how + " (bf16 burst; the J x and J dx products counted once, "
+                                         "the split runs three bf16 MMAs for each)"}
+        roof["how"] = "algorithmic flop / CUDA-event time of the step-kernel launches"
+        out["lyapunov" if form == "fp32" else "lyapunov_bf16x3"] = {
+            "workload": "N=2000 SK N(0,1/N), R=256 x 16 A in [0, 0.375], first 200 of M=2000 "
+                        f"steps, renorm 10, coupling {form}",
+            "value": 16 * 256 * steps / el, "unit": "replica-steps/s (with tangents)",
+            "how": "value: host wall clock around gsb_lyapunov",
+            "kernel_ms": kms, "kernel_launches": kn,
+            "mean_mle_by_A": [float(np.mean(mle[k][np.isfinite(mle[k])]))
+                              if np.isfinite(mle[k]).any() else None for k in range(16)],
+            "roofline": roof}
+    if only in ("lyapunov", "lyapunov_bf16x3"):
         P5.close()
         return out
     return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak)

@@ -285,8 +285,11 @@ gsb_status gsb_run_destroy(gsb_run_state* run);
  * tangent starts as dx uniform in [-1, 1) (Philox stream 4), dy = dp = 0, unit
  * norm, and is renormalised every renorm_every steps and after the last of the
  * first nsteps steps (0 = all M) of the Eq. 6 schedule. mle_out (host, nA x R)
- * receives sum(log norms) / (nsteps dt), accumulated in FP64. Dense problems,
- * FP32 coupling. Blocks on `stream`. */
+ * receives sum(log norms) / (nsteps dt), accumulated in FP64. Dense problems.
+ * params->precision: GSB_PREC_AUTO or GSB_PREC_FP32, the FP32 coupling on CUDA
+ * cores; GSB_PREC_BF16X3, J x and J dx on the tensor cores in the split-bf16
+ * form (error against FP64 at the 2^-16 level of the coupling's magnitude);
+ * any other: GSB_EUNSUPPORTED. Blocks on `stream`. */
 gsb_status gsb_lyapunov(gsb_problem* problem, const gsb_params* params, int32_t nA,
                         const float* A_values, int32_t renorm_every, int32_t nsteps,
                         double* mle_out, void* stream);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <atomic>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -265,6 +266,14 @@ void tc_free(gsb_run_state* run);
 const char* tc_kernel_name(const gsb_run_state* run);
 // split-bf16 path (k_bf16.cu)
 gsb_status bf16_ensure_planes(gsb_problem* P, cudaStream_t s);
+// TMA map of a bf16 [outer][inner] array (inner contiguous): boxes of one
+// 128-byte K atom (64 elements) x 128 rows, 128-byte swizzle.
+gsb_status bf16_tensor_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer);
+// gsb_lyapunov's tangent-linear steps with J x and J dx on the tensor cores
+// (split bf16): R replicas (A_rep[r] each), log-norm sums into log_sum[R].
+gsb_status tangent_bf16x3(gsb_problem* P, bool sign, bool control, int R, const float* A_rep,
+                          float c, float dt, int M, int nsteps, int renorm_every, uint64_t seed,
+                          float x0_range, bool y0_uniform, double* log_sum, cudaStream_t s);
 gsb_status bf16_setup(gsb_run_state* run);
 gsb_status bf16_prepare(gsb_run_state* run);
 gsb_status bf16_steps(gsb_run_state* run, int m0, int nsteps);

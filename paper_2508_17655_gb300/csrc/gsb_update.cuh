@@ -76,4 +76,58 @@ __device__ __forceinline__ void sb_update2(float2& x, float2& y, float2& p, floa
     p = pn;
 }
 
+// Tangent-linear form of sb_update (the step linearised in (x, y, p)):
+//   dp' = dp - [(1 - A x^2) dp - 2 A x dx p] / (M - m)   (individual control; 0 otherwise)
+//   dy' = dy - [dp' x + p' dx - c df] dt                 (df = (J dx)_i; none for sgn coupling)
+//   dx' = dx + dy' dt;  where Eq. 5 clamps x', also dx' = dy' = 0.
+template <bool CONTROL, bool SIGN>
+__device__ __forceinline__ void sb_tangent_update(float& x, float& y, float& p, float& dx,
+                                                  float& dy, float& dp, float f, float df,
+                                                  float a, float c, float dt, float p_shared,
+                                                  float inv_rem) {
+    const float xo = x, dxo = dx;
+    float pn, dpn;
+    if (CONTROL) {
+        const float g = 1.f - a * xo * xo;
+        dpn = dp - (g * dp - 2.f * a * xo * dxo * p) * inv_rem;
+        pn = p - g * p * inv_rem;
+    } else {
+        pn = p_shared;
+        dpn = 0.f;
+    }
+    const float dfi = SIGN ? 0.f : df;
+    float dyn = dy - (dpn * xo + pn * dxo - c * dfi) * dt;
+    float yn = y - (pn * xo - c * f) * dt;
+    float xn = xo + yn * dt;
+    float dxn = dxo + dyn * dt;
+    if (fabsf(xn) > 1.f) {
+        xn = sgnf(xn);
+        yn = 0.f;
+        dxn = 0.f;
+        dyn = 0.f;
+    }
+    x = xn;
+    y = yn;
+    p = pn;
+    dx = dxn;
+    dy = dyn;
+    dp = dpn;
+}
+
+// bf16 bits of a finite v rounded to nearest even, by integer operations (no
+// conversion instruction): add just under half a bf16 ulp (0x7FFF), plus one
+// when the kept part is odd so that ties go to the even neighbour, and keep
+// the top 16 bits. A carry out of the mantissa moves into the exponent, as the
+// rounding requires.
+__device__ __forceinline__ uint32_t bf16_rne_bits(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
+}
+// x = x_hi + x_lo with x_hi = bf16(x) and x_lo = bf16(x - x_hi) (x - x_hi is
+// exact in FP32: the two agree in their top 8 bits); both as bf16 bits.
+__device__ __forceinline__ void bf16_split_bits(float v, uint32_t& hi, uint32_t& lo) {
+    hi = bf16_rne_bits(v);
+    lo = bf16_rne_bits(v - __uint_as_float(hi << 16));
+}
+
 }  // namespace gsb

@@ -75,22 +75,6 @@ struct MTile {
     int inst, i0, r0, pad;
 };
 
-// bf16 bits of a finite v rounded to nearest even, by integer operations (no
-// conversion instruction): add just under half a bf16 ulp (0x7FFF), plus one
-// when the kept part is odd so that ties go to the even neighbour, and keep
-// the top 16 bits. A carry out of the mantissa moves into the exponent, as the
-// rounding requires.
-__device__ __forceinline__ uint32_t bf16_rne_bits(float v) {
-    const uint32_t b = __float_as_uint(v);
-    return (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
-}
-// x = x_hi + x_lo with x_hi = bf16(x) and x_lo = bf16(x - x_hi) (x - x_hi is
-// exact in FP32: the two agree in their top 8 bits); both as bf16 bits.
-__device__ __forceinline__ void bf16_split_bits(float v, uint32_t& hi, uint32_t& lo) {
-    hi = bf16_rne_bits(v);
-    lo = bf16_rne_bits(v - __uint_as_float(hi << 16));
-}
-
 // The epilogue of the resident form: this CTA's one tile, its state in TMEM.
 // Per step: F from TMEM, Eqs. 7, 3, 4, 5 in the order of sb_update2, x, y, p
 // back to TMEM, the next step's operand planes to global memory; then the
@@ -686,6 +670,10 @@ gsb_status launch_multi(const MInst* insts, const MTile* tiles, int ntiles, int 
 }
 
 }  // namespace
+
+gsb_status bf16_tensor_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer) {
+    return bf16_map(map, base, inner, outer);
+}
 
 // J_hi / J_lo of a dense problem, made on first use.
 gsb_status bf16_ensure_planes(gsb_problem* P, cudaStream_t s) {

@@ -10,6 +10,8 @@
 // the same thread, and the epilogue advances both. Every renorm_every steps
 // (and at the end) the tangent is renormalised; the log of its norm is
 // accumulated in FP64 per replica.
+#include "gsb_update.cuh"
+#include "philox.cuh"
 #include "sgemm_f32.cuh"
 
 namespace gsb {
@@ -17,40 +19,6 @@ namespace gsb {
 namespace {
 
 using namespace f32;
-
-template <bool CONTROL, bool SIGN>
-__device__ __forceinline__ void sb_tangent_update(float& x, float& y, float& p, float& dx,
-                                                  float& dy, float& dp, float f, float df,
-                                                  float a, float c, float dt, float p_shared,
-                                                  float inv_rem) {
-    const float xo = x, dxo = dx;
-    float pn, dpn;
-    if (CONTROL) {
-        const float g = 1.f - a * xo * xo;
-        dpn = dp - (g * dp - 2.f * a * xo * dxo * p) * inv_rem;
-        pn = p - g * p * inv_rem;
-    } else {
-        pn = p_shared;
-        dpn = 0.f;
-    }
-    const float dfi = SIGN ? 0.f : df;
-    float dyn = dy - (dpn * xo + pn * dxo - c * dfi) * dt;
-    float yn = y - (pn * xo - c * f) * dt;
-    float xn = xo + yn * dt;
-    float dxn = dxo + dyn * dt;
-    if (fabsf(xn) > 1.f) {
-        xn = sgnf(xn);
-        yn = 0.f;
-        dxn = 0.f;
-        dyn = 0.f;
-    }
-    x = xn;
-    y = yn;
-    p = pn;
-    dx = dxn;
-    dy = dyn;
-    dp = dpn;
-}
 
 // State [Np][C] with C = 2 Rq columns, column 2r = replica r, 2r+1 = its tangent.
 template <bool SIGN, bool CONTROL>
@@ -97,23 +65,6 @@ __global__ void __launch_bounds__(256) k_tangent_step(const float* __restrict__ 
 // Initial state: replica r of the run draws x(0) (and y(0)) exactly as gsb_run
 // does for replica r; its tangent starts at dx uniform in [-1, 1) (Philox
 // stream 4), dy = dp = 0, normalised before the first step.
-__device__ __forceinline__ uint4 philox(uint4 ctr, uint2 key) {
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        if (round) {
-            key.x += 0x9E3779B9u;
-            key.y += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * ctr.x, hi0 = __umulhi(0xD2511F53u, ctr.x);
-        const uint32_t lo1 = 0xCD9E8D57u * ctr.z, hi1 = __umulhi(0xCD9E8D57u, ctr.z);
-        ctr = make_uint4(hi1 ^ ctr.y ^ key.x, lo1, hi0 ^ ctr.w ^ key.y, lo0);
-    }
-    return ctr;
-}
-__device__ __forceinline__ float draw(int i, int r, uint32_t stream, uint2 key, float scale) {
-    const uint4 w = philox(make_uint4((uint32_t)i, (uint32_t)r, stream, 0u), key);
-    return __fmul_rn((float)((int)(w.x >> 8) - 8388608), scale);
-}
 
 __global__ void k_tangent_init(float* x, float* y, float* p, int N, int R, int Np, int C,
                                uint2 key, float scale, int y_uniform) {
@@ -126,10 +77,10 @@ __global__ void k_tangent_init(float* x, float* y, float* p, int N, int R, int N
     float xv = 0.f, yv = 0.f;
     if (i < N && r < R) {
         if (tangent) {
-            xv = draw(i, r, 4u, key, 1.1920928955078125e-07f);  // uniform [-1, 1)
+            xv = uniform_draw(i, r, 4u, key, 1.1920928955078125e-07f);  // uniform [-1, 1)
         } else {
-            xv = draw(i, r, 0u, key, scale);
-            if (y_uniform) yv = draw(i, r, 1u, key, scale);
+            xv = uniform_draw(i, r, 0u, key, scale);
+            if (y_uniform) yv = uniform_draw(i, r, 1u, key, scale);
         }
     }
     x[o] = xv;
@@ -229,6 +180,23 @@ extern "C" gsb_status gsb_lyapunov(gsb_problem* P, const gsb_params* prm, int32_
     const bool sign = Q.variant == GSB_DSB || Q.variant == GSB_GDSB;
     const bool control = Q.variant == GSB_GBSB || Q.variant == GSB_GDSB;
     const int R = (int)Rtot;
+    const float range = Q.x0_range > 0.f ? Q.x0_range : 0.1f;
+    if (Q.precision == GSB_PREC_BF16X3) {
+        // J x and J dx on the tensor cores (split bf16)
+        std::vector<float> Ar((size_t)R);
+        for (int k = 0; k < nA; ++k)
+            for (int r = 0; r < Q.R; ++r) Ar[(size_t)k * Q.R + r] = A_values[k];
+        std::vector<double> ls((size_t)R);
+        gsb_status st = tangent_bf16x3(P, sign, control, R, Ar.data(), (float)c, (float)dt, Q.M,
+                                       nsteps, renorm_every, Q.seed, range, Q.y0_uniform != 0,
+                                       ls.data(), s);
+        if (st != GSB_OK) return st;
+        const double T = (double)nsteps * (double)(float)dt;
+        for (int r = 0; r < R; ++r) mle_out[r] = ls[r] / T;
+        return GSB_OK;
+    }
+    if (Q.precision != GSB_PREC_AUTO && Q.precision != GSB_PREC_FP32)
+        return set_error(GSB_EUNSUPPORTED, "gsb_lyapunov takes FP32 or BF16X3 coupling");
     const int Rq = round_up(R, BN / 2);  // pairs, padded so 2 Rq is a multiple of the tile
     const int C = 2 * Rq;
     const int Np = P->Np;
@@ -248,7 +216,6 @@ extern "C" gsb_status gsb_lyapunov(gsb_problem* P, const gsb_params* prm, int32_
     GSB_CUDA_TRY(cudaMemcpyAsync(B.A, Ah.data(), Rq * sizeof(float), cudaMemcpyHostToDevice, s));
     GSB_CUDA_TRY(cudaMemsetAsync(B.nrm2, 0, Rq * sizeof(double), s));
     GSB_CUDA_TRY(cudaMemsetAsync(B.log_sum, 0, Rq * sizeof(double), s));
-    const float range = Q.x0_range > 0.f ? Q.x0_range : 0.1f;
     const uint2 key = make_uint2((uint32_t)Q.seed, (uint32_t)(Q.seed >> 32));
     k_tangent_init<<<dim3((C + 127) / 128, Np), 128, 0, s>>>(
         B.x[0], B.y, B.p, P->N, R, Np, C, key, range * 1.1920928955078125e-07f, Q.y0_uniform);

@@ -417,10 +417,13 @@ class Problem:
                    fused_csr=fused_csr)
 
     def lyapunov(self, variant, M, R, A_values, *, c=0.0, dt=0.0, seed=0, renorm_every=10,
-                 nsteps=0, y0_uniform=False, x0_range=0.0, stream=None):
+                 nsteps=0, y0_uniform=False, x0_range=0.0, precision="fp32", stream=None):
         """Largest Lyapunov exponent per replica (len(A_values) x R), from the
-        tangent-linear kernel; see gsb_lyapunov in include/gsb.h."""
+        tangent-linear kernel; precision "fp32" (CUDA cores) or "bf16x3" (J x
+        and J dx on the tensor cores, split bf16); see gsb_lyapunov in
+        include/gsb.h."""
         prm = gsb_params()
+        prm.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
         prm.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
         prm.M = int(M)
         prm.R = int(R)

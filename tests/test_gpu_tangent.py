@@ -35,22 +35,53 @@ def _oracle_mle(J, variant, R_tot, N, seed, A_rep, c, dt, M, nsteps, renorm, y0_
     return t["log_sum"] / (nsteps * f32(dt)), margin
 
 
+PRECISIONS = ["fp32", "bf16x3"]
+# Decision margin (distance of a wall or sign test from its threshold in the
+# oracle's trajectory) below which a replica is excused: a GPU trajectory may
+# take the other branch there. FP32 coupling: 2e-6. Split bf16: the coupling
+# error per step is up to 2^-18 max_i sum_j |J_ij| (about 6e-5 for these
+# N(0, 1/N) matrices: the residue of J_lo and of x_lo), x moves by c dt^2
+# times that, and it builds up over the window, so 1e-3.
+NEAR_TIE = {"fp32": 2e-6, "bf16x3": 1e-3}
+
+
+def bf16_split_sum(J):
+    """J_hi + J_lo in FP64, J_hi = bf16(J) and J_lo = bf16(J - J_hi) rounded to
+    nearest even (the split-bf16 form's matrix, from the rounding's
+    definition). With the sgn coupling the form's products J_hi s + J_lo s
+    are exact, so the oracle on this matrix differs from the kernel by FP32
+    accumulation alone and the FP32 near-tie bar applies."""
+    def rne(a):
+        b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+        r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+        return r.astype(np.uint32).view(np.float32)
+    hi = rne(J)
+    lo = rne(J.astype(np.float32) - hi)
+    return hi.astype(np.float64) + lo.astype(np.float64)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("variant", ["gbsb", "bsb", "gdsb", "dsb"])
-def test_lyapunov_short_window_matches_oracle(variant):
+def test_lyapunov_short_window_matches_oracle(variant, precision):
     """First 50 steps of a 2000-step schedule, renormalised every 10 steps, two
-    control strengths x 65 replicas (ragged), SK Gaussian couplings (FP32):
-    per-replica exponent within 1e-4 (absolute, per unit time) of the oracle,
-    replicas with a wall or sign near-tie excused."""
+    control strengths x 65 replicas (ragged: three spin tiles, two replica
+    tiles of the tensor-core form), SK Gaussian couplings (FP32 J; bf16x3
+    splits it): per-replica exponent within 1e-4 (absolute, per unit time) of
+    the oracle, replicas with a wall or sign near-tie excused."""
     N, R, M, n, renorm = 300, 65, 2000, 50, 10
     J = I.sk_gauss(N, 7)
     A_vals = [0.1, 0.3]
     c, dt = 0.5, f32(1.25)
     got = gsb.Problem.dense(J).lyapunov(variant, M, R, A_vals, c=c, dt=dt, seed=21,
-                                        renorm_every=renorm, nsteps=n)
+                                        renorm_every=renorm, nsteps=n, precision=precision)
     A_rep = np.repeat(A_vals, R)
-    want, margin = _oracle_mle(J.astype(np.float64), variant, 2 * R, N, 21, A_rep, c, dt, M, n,
-                               renorm)
-    ok = margin >= 2e-6
+    sign = variant in ("dsb", "gdsb")
+    # the split form against the oracle on its own matrix J_hi + J_lo; with the
+    # sgn coupling that is exact up to FP32 accumulation (the FP32 bar), with
+    # the x coupling the split of x remains (the wider bar)
+    Jo = bf16_split_sum(J) if precision == "bf16x3" else J.astype(np.float64)
+    want, margin = _oracle_mle(Jo, variant, 2 * R, N, 21, A_rep, c, dt, M, n, renorm)
+    ok = margin >= (NEAR_TIE["fp32"] if sign else NEAR_TIE[precision])
     assert ok.mean() > 0.5
     g, w = got.ravel()[ok], want[ok]
     # the inelastic walls can zero a tangent (every oscillator clamped): -inf on both sides
@@ -61,7 +92,8 @@ def test_lyapunov_short_window_matches_oracle(variant):
     assert err.size == 0 or np.all(err <= 1e-4), f"max |mle gpu - oracle| {err.max():.2e}"
 
 
-def test_lyapunov_config5_shape_sampled():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_lyapunov_config5_shape_sampled(precision):
     """The chaos configuration as the bench runs it (N = 2000 SK Gaussian,
     16 control strengths x 256 replicas in one call, c = 0.5, dt = 1.25,
     M = 2000, renormalised every 10 steps), first 50 steps: 16 sampled replicas
@@ -71,7 +103,8 @@ def test_lyapunov_config5_shape_sampled():
     J = I.sk_gauss(N, 0)
     c, dt = 0.5, f32(1.25)
     got = gsb.Problem.dense(J).lyapunov("gbsb", M, R, A16, c=c, dt=dt, seed=3,
-                                        renorm_every=renorm, nsteps=n).ravel()
+                                        renorm_every=renorm, nsteps=n,
+                                        precision=precision).ravel()
     pick = np.array([k * R + (37 * k) % R for k in range(16)])
     x0 = O.init_uniform(16 * R, N, 3)[pick]
     dx0 = O.init_uniform(16 * R, N, 3, stream=4, rng=1.0)[pick]
@@ -82,13 +115,14 @@ def test_lyapunov_config5_shape_sampled():
                       renorm_every=renorm)
     want = t["log_sum"] / (n * dt)
     margin = O.run(Jo, "gbsb", x0, 0 * x0, c=c, dt=dt, M=M, A=A_rep, nsteps=n)["margin"]
-    ok = margin >= 2e-6
-    assert ok.sum() >= 12
+    ok = margin >= NEAR_TIE[precision]
+    assert ok.sum() >= 10
     err = np.abs(got[pick] - want)[ok]
     assert np.all(err <= 1e-4), f"max |mle gpu - oracle| {err.max():.2e}"
 
 
-def test_lyapunov_unstable_equilibrium_growth_rate():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_lyapunov_unstable_equilibrium_growth_rate(precision):
     """Near the x = 0 equilibrium of a ferromagnet (J = 1 - I) with p ~ 1, the
     uniform mode grows by mu per step, mu^2 - (2 - k dt^2) mu + 1 = 0,
     k = p - c (N - 1): GPU exponent equals the oracle's and approaches ln(mu)/dt."""
@@ -97,7 +131,7 @@ def test_lyapunov_unstable_equilibrium_growth_rate():
     c, dt = f32(0.02), f32(0.3)
     got = gsb.Problem.dense(J, validate=True).lyapunov("bsb", M, R, [0.0], c=c, dt=dt, seed=3,
                                                        renorm_every=10, nsteps=n,
-                                                       x0_range=1e-30)[0]
+                                                       x0_range=1e-30, precision=precision)[0]
     want, _ = _oracle_mle(J.astype(np.float64), "bsb", R, N, 3, np.zeros(R), c, dt, M, n, 10,
                           x0_range=1e-30)
     np.testing.assert_allclose(got, want, rtol=1e-4)
@@ -111,8 +145,9 @@ def test_lyapunov_unstable_equilibrium_growth_rate():
     assert np.all(got <= rate * 1.01) and np.all(got >= rate * 0.88)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("variant", ["gbsb", "gdsb"])
-def test_lyapunov_long_window_statistics(variant):
+def test_lyapunov_long_window_statistics(variant, precision):
     """The first 300 steps of 600-step runs (long enough for the trajectories
     to decorrelate, before the end of the schedule pins every oscillator to a
     wall and zeroes every tangent), 4 control strengths x 64 replicas: mean
@@ -122,7 +157,7 @@ def test_lyapunov_long_window_statistics(variant):
     A_vals = [0.0, 0.2, 0.4, 0.6]
     c, dt = 0.5, f32(1.0)
     got = gsb.Problem.dense(J).lyapunov(variant, M, R, A_vals, c=c, dt=dt, seed=5, renorm_every=10,
-                                        nsteps=n)
+                                        nsteps=n, precision=precision)
     want, _ = _oracle_mle(J.astype(np.float64), variant, 4 * R, N, 5, np.repeat(A_vals, R), c, dt,
                           M, n, 10)
     want = want.reshape(4, R)
@@ -137,3 +172,30 @@ def test_lyapunov_long_window_statistics(variant):
             continue
         bound = Z99 * math.sqrt(np.var(g, ddof=1) / len(g) + np.var(w, ddof=1) / len(w)) + 1e-6
         assert abs(g.mean() - w.mean()) <= bound, (A_vals[k], g.mean(), w.mean(), bound)
+
+
+def test_lyapunov_bf16x3_agrees_with_fp32_and_rejects_other_forms():
+    """The two coupling forms on the same runs (N = 257: a ragged third spin
+    tile; 3 x 50 replicas), 40 steps: exponents within 1e-4 of each other
+    wherever the oracle's trajectory has no near-tie decision (margin 1e-3, as
+    for the split form above); a form the tangent path does not have is
+    refused."""
+    N, R, M, n = 257, 50, 1000, 40
+    J = I.sk_gauss(N, 4)
+    A_vals = [0.0, 0.2, 0.4]
+    P = gsb.Problem.dense(J)
+    kw = dict(c=0.5, dt=f32(1.25), seed=8, renorm_every=10, nsteps=n)
+    a = P.lyapunov("gbsb", M, R, A_vals, precision="fp32", **kw).ravel()
+    b = P.lyapunov("gbsb", M, R, A_vals, precision="bf16x3", **kw).ravel()
+    x0 = O.init_uniform(3 * R, N, 8)
+    margin = O.run(J.astype(np.float64), "gbsb", x0, 0 * x0, c=0.5, dt=f32(1.25), M=M,
+                   A=np.repeat(A_vals, R), nsteps=n)["margin"]
+    ok = margin >= NEAR_TIE["bf16x3"]
+    assert ok.mean() > 0.5
+    a, b = a[ok], b[ok]
+    assert np.array_equal(np.isneginf(a), np.isneginf(b))
+    fin = np.isfinite(a)
+    assert np.max(np.abs(a[fin] - b[fin])) <= 1e-4
+    with pytest.raises(gsb.GsbError) as e:
+        P.lyapunov("gbsb", M, R, [0.0], precision="fp8", **kw)
+    assert e.value.status == gsb.EUNSUPPORTED
