@@ -13,19 +13,30 @@
 // One launch per time step. The tiles of a step (128 spins x 128 replicas)
 // do not wait on one another -- each reads the step's operand planes and
 // writes only its own state and its part of the next step's planes -- so CTA
-// b of G takes tiles b, b + G, ..., and two accumulator pairs in TMEM let one
-// tile's MMAs run while the previous tile's epilogue reads its F and G.
+// b of G takes tiles b, b + G, ..., and two accumulators in TMEM let one
+// tile's MMAs run while the previous tile's epilogue reads the other.
 //
-// Layout: state x, y, p, dx, dy, dp in FP32, spin-major [Np][Rp] (a warp's 32
-// replicas at one spin are 128 contiguous bytes); operand planes bf16,
+// The MMAs take J as the A operand (M = 128 spins: TMEM lane = spin) and the
+// planes as B with x and dx side by side (N = 256: the tile's 128 replicas,
+// then their 128 tangents), so one MMA serves both products:
+//   D = J_hi [x_hi | dx_hi] + J_lo [x_hi | dx_hi] + J_hi [x_lo | dx_lo],
+// F = D[:, 0:128], G = D[:, 128:256]. Three MMAs per 16 K elements, each
+// reading 12 KB of shared memory for 128 x 256 x 16 -- a third less operand
+// traffic than six 128 x 128 MMAs; shared-memory bandwidth (128 bytes a
+// cycle per SM) is what bounds this loop. The sgn coupling: D = J_hi s +
+// J_lo s, N = 128.
+//
+// Layout: state x, y, p, dx, dy, dp in FP32, replica-major [Rp][Np] (a warp's
+// 32 spins of one replica are 128 contiguous bytes); operand planes bf16,
 // replica-major [planes][Rp][Np] -- x_hi, x_lo, dx_hi, dx_lo, or sgn x alone
 // for the sgn coupling -- double-buffered by the parity of the step.
-// TMEM (512 columns): accumulator pair b at 256 b, F at +0 and G at +128.
-// Shared memory: 2 stages x (J_hi, J_lo and the planes' atoms: 6, or 3 for
-// the sgn coupling), each atom 64 K elements x 128 rows, 128-byte swizzled.
+// TMEM (512 columns): accumulator b at 256 b (F at +0, G at +128).
+// Shared memory: 2 stages x (J_hi, J_lo, x_hi, dx_hi, x_lo, dx_lo atoms; J_hi,
+// J_lo, s for the sgn coupling), each atom 64 K elements x 128 rows, 128-byte
+// swizzled; x_hi, dx_hi (and x_lo, dx_lo) are adjacent, one 256-row operand.
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2-9 epilogue (warp w
-// reads TMEM lanes 32 (w % 4).. -- its 32 replicas -- and columns
-// 64 ((w - 2) / 4) .. +63 of F and G -- 64 spins of the tile).
+// reads TMEM lanes 32 (w % 4).. -- its 32 spins -- and columns
+// 64 ((w - 2) / 4) .. +63 of F and of G -- 64 replicas of the tile).
 #include <cudaTypedefs.h>
 #include <string.h>
 
@@ -130,9 +141,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
                     mbar_arrive_expect_tx(&full[st], kStageTx);
                     tma_load_2d(atom(st, 0), &P.tmJ[0], &full[st], u * kElems, i0);
                     tma_load_2d(atom(st, 1), &P.tmJ[1], &full[st], u * kElems, i0);
+                    // atoms 2.. hold the planes x_hi, dx_hi, x_lo, dx_lo (stored as
+                    // x_hi, x_lo, dx_hi, dx_lo), so that each hi and each lo pair
+                    // is one 256-row B operand
 #pragma unroll
                     for (int q = 0; q < NPLANE; ++q)
-                        tma_load_2d(atom(st, 2 + q), tv, &full[st], u * kElems, q * P.Rp + r0);
+                        tma_load_2d(atom(st, 2 + q), tv, &full[st], u * kElems,
+                                    ((q >> 1) | ((q & 1) << 1)) * P.Rp + r0);
                 }
             }
             // no copy is in flight when the CTA leaves
@@ -141,12 +156,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_make(1u, kT, kT);
+            constexpr uint32_t idesc = idesc_make(1u, kT, SIGN ? kT : 2 * kT);
             uint32_t g = 0, n = 0;
             bool ok = true;
             for (int j = blockIdx.x; j < ntiles && ok; j += gridDim.x, ++n) {
                 const uint32_t b = n & 1u;
-                // the epilogue has read this pair's previous tile
+                // the epilogue has read this accumulator's previous tile
                 if (n >= 2 && !mbar_wait(&acce[b], ((n - 2) >> 1) & 1u, P.status)) break;
                 fence_after_sync();
                 const uint32_t d = tmem + 256u * b;
@@ -158,23 +173,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
                     }
                     fence_after_sync();
                     const uint32_t jh = smem_u32(atom(st, 0)), jl = smem_u32(atom(st, 1));
-                    const uint32_t xh = smem_u32(atom(st, 2));
+                    const uint32_t vh = smem_u32(atom(st, 2)), vl = smem_u32(atom(st, 4));
 #pragma unroll
                     for (int k = 0; k < kKB / 32; ++k) {  // 16 bf16 of K per MMA
                         const uint32_t acc = (u | k) != 0;
-                        const uint64_t bh = sdesc_sw128(jh + k * 32), bl = sdesc_sw128(jl + k * 32);
-                        const uint64_t ah = sdesc_sw128(xh + k * 32);
+                        const uint64_t ah = sdesc_sw128(jh + k * 32), al = sdesc_sw128(jl + k * 32);
+                        const uint64_t bh = sdesc_sw128(vh + k * 32);
                         mma_f16(d, ah, bh, idesc, acc);
-                        mma_f16(d, ah, bl, idesc, 1u);
-                        if (!SIGN) {
-                            const uint32_t xl = smem_u32(atom(st, 3));
-                            const uint32_t dh = smem_u32(atom(st, 4)), dl = smem_u32(atom(st, 5));
-                            mma_f16(d, sdesc_sw128(xl + k * 32), bh, idesc, 1u);
-                            const uint64_t gh = sdesc_sw128(dh + k * 32);
-                            mma_f16(d + 128u, gh, bh, idesc, acc);
-                            mma_f16(d + 128u, gh, bl, idesc, 1u);
-                            mma_f16(d + 128u, sdesc_sw128(dl + k * 32), bh, idesc, 1u);
-                        }
+                        mma_f16(d, al, bh, idesc, 1u);
+                        if (!SIGN) mma_f16(d, ah, sdesc_sw128(vl + k * 32), idesc, 1u);
                     }
                     mma_commit(&empty[st]);
                 }
@@ -191,8 +198,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
         const int c0 = (ew >> 2) * 64;
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         volatile uint32_t* abort_flag = tmem_slot + 1;
-        const int Rp = P.Rp;
-        const size_t plane = (size_t)Rp * P.Np;
+        const int Np = P.Np;
+        const size_t plane = (size_t)P.Rp * Np;
         const float c = P.c, dt = P.dt, p_shared = P.p_shared, inv_rem = P.inv_rem;
         float* __restrict__ x = P.x;
         float* __restrict__ y = P.y;
@@ -200,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
         float* __restrict__ dx = P.dx;
         float* __restrict__ dy = P.dy;
         float* __restrict__ dp = P.dp;
+        uint16_t* __restrict__ vout = reinterpret_cast<uint16_t*>(P.v[(P.m + 1) & 1]);
         uint32_t n = 0;
         for (int j = blockIdx.x; j < ntiles; j += gridDim.x, ++n) {
             const int i0 = (j % nsb) * kT, r0 = (j / nsb) * kT;
@@ -212,21 +220,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
                 break;
             }
             fence_after_sync();
-            const int r = r0 + quarter * 32 + lane;
-            const float a_r = CONTROL ? P.A[r] : 0.f;
-            uint16_t* vrow = reinterpret_cast<uint16_t*>(P.v[(P.m + 1) & 1]) + (size_t)r * P.Np + i0;
+            const int i = i0 + quarter * 32 + lane;  // this thread's spin (TMEM lane)
             const uint32_t ta = tl + 256u * b;
-            // chunks of 8 spins in two register buffers taken in turn: while one
-            // chunk is updated in place, the next one's state (six arrays, from
-            // HBM) is in flight; the state is read and written with the
+            // chunks of 8 replicas in two register buffers taken in turn: while
+            // one chunk is updated in place, the next one's state (six arrays,
+            // from HBM) is in flight; the state is read and written with the
             // evict-first hint, so that it streams past the planes and J in L2
             constexpr int CW = 8;
             float qa[6][CW], qb[6][CW];
             auto load_state = [&](int cb, float (&q)[6][CW]) {
-                const size_t o = (size_t)(i0 + cb) * Rp + r;
+                const size_t o = (size_t)(r0 + cb) * Np + i;
 #pragma unroll
                 for (int k = 0; k < CW; ++k) {
-                    const size_t e = o + (size_t)k * Rp;
+                    const size_t e = o + (size_t)k * Np;
                     q[0][k] = __ldcs(x + e);
                     q[1][k] = __ldcs(y + e);
                     q[2][k] = CONTROL ? __ldcs(p + e) : 0.f;
@@ -241,51 +247,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
                 uint32_t rf[CW], rg[CW];
                 tmem_ld8_async(ta + cb, rf);
                 if (!SIGN) tmem_ld8_async(ta + 128u + cb, rg);
+                float a_r[CW];
+#pragma unroll
+                for (int k = 0; k < CW; ++k) a_r[k] = CONTROL ? __ldg(P.A + r0 + cb + k) : 0.f;
                 tmem_wait_ld8(rf);
                 if (!SIGN) tmem_wait_ld8(rg);
 #pragma unroll
                 for (int k = 0; k < CW; ++k)
                     sb_tangent_update<CONTROL, SIGN>(s[0][k], s[1][k], s[2][k], s[3][k], s[4][k],
                                                      s[5][k], __uint_as_float(rf[k]),
-                                                     SIGN ? 0.f : __uint_as_float(rg[k]), a_r, c, dt,
-                                                     p_shared, inv_rem);
-                const size_t o = (size_t)(i0 + cb) * Rp + r;
+                                                     SIGN ? 0.f : __uint_as_float(rg[k]), a_r[k], c,
+                                                     dt, p_shared, inv_rem);
+                const size_t o = (size_t)(r0 + cb) * Np + i;
 #pragma unroll
                 for (int k = 0; k < CW; ++k) {
-                    const size_t e = o + (size_t)k * Rp;
+                    const size_t e = o + (size_t)k * Np;
                     __stcs(x + e, s[0][k]);
                     __stcs(y + e, s[1][k]);
                     if (CONTROL) __stcs(p + e, s[2][k]);
                     __stcs(dx + e, s[3][k]);
                     __stcs(dy + e, s[4][k]);
                     if (CONTROL) __stcs(dp + e, s[5][k]);
-                }
-                // next step's operand planes, 8 bf16 (16 bytes) of the replica's row each
-                uint32_t xh[CW / 2], xl[CW / 2], dh[CW / 2], dl[CW / 2];
-#pragma unroll
-                for (int k = 0; k < CW; k += 2) {
+                    // next step's operand planes (a warp writes 64 contiguous bytes of each)
                     if (SIGN) {
-                        xh[k / 2] = (s[0][k] >= 0.f ? 0x3F80u : 0xBF80u) |
-                                    ((s[0][k + 1] >= 0.f ? 0x3F80u : 0xBF80u) << 16);
+                        vout[e] = s[0][k] >= 0.f ? (uint16_t)0x3F80 : (uint16_t)0xBF80;
                     } else {
-                        uint32_t h0, l0, h1, l1;
-                        bf16_split_bits(s[0][k], h0, l0);
-                        bf16_split_bits(s[0][k + 1], h1, l1);
-                        xh[k / 2] = h0 | (h1 << 16);
-                        xl[k / 2] = l0 | (l1 << 16);
-                        bf16_split_bits(s[3][k], h0, l0);
-                        bf16_split_bits(s[3][k + 1], h1, l1);
-                        dh[k / 2] = h0 | (h1 << 16);
-                        dl[k / 2] = l0 | (l1 << 16);
+                        uint32_t h, l;
+                        bf16_split_bits(s[0][k], h, l);
+                        vout[e] = (uint16_t)h;
+                        vout[plane + e] = (uint16_t)l;
+                        bf16_split_bits(s[3][k], h, l);
+                        vout[2 * plane + e] = (uint16_t)h;
+                        vout[3 * plane + e] = (uint16_t)l;
                     }
-                }
-                *reinterpret_cast<uint4*>(vrow + cb) = make_uint4(xh[0], xh[1], xh[2], xh[3]);
-                if (!SIGN) {
-                    *reinterpret_cast<uint4*>(vrow + plane + cb) = make_uint4(xl[0], xl[1], xl[2], xl[3]);
-                    *reinterpret_cast<uint4*>(vrow + 2 * plane + cb) =
-                        make_uint4(dh[0], dh[1], dh[2], dh[3]);
-                    *reinterpret_cast<uint4*>(vrow + 3 * plane + cb) =
-                        make_uint4(dl[0], dl[1], dl[2], dl[3]);
                 }
                 if (cb + 2 * CW < c0 + 64) load_state(cb + 2 * CW, s);
             };
@@ -294,7 +288,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
                 chunk(cb, qa);
                 chunk(cb + CW, qb);
             }
-            // every epilogue thread has read F and G before the pair is handed back
+            // every epilogue thread has read its F and G before the accumulator
+            // is handed back
             fence_before_sync();
             named_barrier_sync(1, kEpiThreads);
             if (*abort_flag) break;
@@ -310,14 +305,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tangent_tc(const __grid_constan
 }
 
 // x(0), y(0), p(0) = 1 as gsb_run draws them for replica r, and the tangent's
-// dx(0) uniform in [-1, 1) (Philox stream 4), dy = dp = 0; spin-major
-// [Np][Rp], padded spins and replicas at zero (p = 1).
+// dx(0) uniform in [-1, 1) (Philox stream 4), dy = dp = 0; replica-major
+// [Rp][Np], padded spins and replicas at zero (p = 1).
 __global__ void k_tan_tc_init(float* x, float* y, float* p, float* dx, float* dy, float* dp, int N,
-                              int R, int Rp, uint2 key, float scale, int y_uniform) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y;
-    if (r >= Rp) return;
-    const size_t o = (size_t)i * Rp + r;
+                              int R, int Np, uint2 key, float scale, int y_uniform) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i >= Np) return;
+    const size_t o = (size_t)r * Np + i;
     const bool real = i < N && r < R;
     x[o] = real ? uniform_draw(i, r, 0u, key, scale) : 0.f;
     y[o] = real && y_uniform ? uniform_draw(i, r, 1u, key, scale) : 0.f;
@@ -329,71 +324,60 @@ __global__ void k_tan_tc_init(float* x, float* y, float* p, float* dx, float* dy
     }
 }
 
-// nrm2[r] += sum over a block of spins of dx^2 + dy^2 + dp^2 (FP64).
-constexpr int kNormRows = 64;
+// nrm2[r] = sum over the spins of dx^2 + dy^2 + dp^2 (FP64), one warp per
+// replica, partial sums added in a fixed order (deterministic).
 __global__ void k_tan_tc_norm(const float* __restrict__ dx, const float* __restrict__ dy,
-                              const float* __restrict__ dp, int N, int R, int Rp,
+                              const float* __restrict__ dp, int N, int R, int Np,
                               double* __restrict__ nrm2) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (r >= R) return;
-    const int i0 = blockIdx.y * kNormRows;
-    const int i1 = min(N, i0 + kNormRows);
+    const size_t o = (size_t)r * Np;
     double s = 0.0;
-    for (int i = i0; i < i1; ++i) {
-        const size_t o = (size_t)i * Rp + r;
-        const double a = dx[o], b = dy[o], d = dp ? dp[o] : 0.f;
+    for (int i = lane; i < N; i += 32) {
+        const double a = dx[o + i], b = dy[o + i], d = dp ? dp[o + i] : 0.f;
         s += a * a + b * b + d * d;
     }
-    atomicAdd(&nrm2[r], s);
+    for (int k = 16; k; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+    if (lane == 0) nrm2[r] = s;
 }
 
 // log_sum[r] += log |delta| (when accumulating); scale[r] = 1 / |delta|.
-__global__ void k_tan_tc_log(double* __restrict__ nrm2, double* __restrict__ log_sum,
+__global__ void k_tan_tc_log(const double* __restrict__ nrm2, double* __restrict__ log_sum,
                              float* __restrict__ scale, int R, int accumulate) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const double s2 = nrm2[r];
     if (accumulate) log_sum[r] += 0.5 * log(s2);
     scale[r] = s2 > 0.0 ? (float)(1.0 / sqrt(s2)) : 0.f;
-    nrm2[r] = 0.0;
 }
 
 // The tangent of every replica scaled by scale[r] (scale[r] = 0 on padded
-// replicas), then the step's operand planes written from x and dx (32 x 32
-// tiles through shared memory: state spin-major, planes replica-major).
+// replicas), then the step's operand planes written from x and dx.
 __global__ void k_tan_tc_planes(const float* __restrict__ x, float* __restrict__ dx,
                                 float* __restrict__ dy, float* __restrict__ dp,
-                                const float* __restrict__ scale, __nv_bfloat16* __restrict__ v,
-                                int Np, int Rp, int sign) {
-    __shared__ float tx[32][33], td[32][33];
-    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const size_t o = (size_t)(i0 + k) * Rp + r0 + threadIdx.x;
-        const float s = scale[r0 + threadIdx.x];
-        const float d = dx[o] * s;
-        dx[o] = d;
-        dy[o] *= s;
-        if (dp) dp[o] *= s;
-        tx[k][threadIdx.x] = x[o];
-        td[k][threadIdx.x] = d;
-    }
-    __syncthreads();
-    const size_t plane = (size_t)Rp * Np;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int r = r0 + k, i = i0 + threadIdx.x;
-        const size_t vo = (size_t)r * Np + i;
-        const float xv = tx[threadIdx.x][k];
-        if (sign) {
-            v[vo] = __ushort_as_bfloat16(xv >= 0.f ? (uint16_t)0x3F80 : (uint16_t)0xBF80);
-        } else {
-            uint32_t h, l;
-            bf16_split_bits(xv, h, l);
-            v[vo] = __ushort_as_bfloat16((uint16_t)h);
-            v[plane + vo] = __ushort_as_bfloat16((uint16_t)l);
-            bf16_split_bits(td[threadIdx.x][k], h, l);
-            v[2 * plane + vo] = __ushort_as_bfloat16((uint16_t)h);
-            v[3 * plane + vo] = __ushort_as_bfloat16((uint16_t)l);
-        }
+                                const float* __restrict__ scale, uint16_t* __restrict__ v, int Np,
+                                int Rp, int sign) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i >= Np || r >= Rp) return;
+    const size_t o = (size_t)r * Np + i, plane = (size_t)Rp * Np;
+    const float s = scale[r];
+    const float d = dx[o] * s;
+    dx[o] = d;
+    dy[o] *= s;
+    if (dp) dp[o] *= s;
+    const float xv = x[o];
+    if (sign) {
+        v[o] = xv >= 0.f ? (uint16_t)0x3F80 : (uint16_t)0xBF80;
+    } else {
+        uint32_t h, l;
+        bf16_split_bits(xv, h, l);
+        v[o] = (uint16_t)h;
+        v[plane + o] = (uint16_t)l;
+        bf16_split_bits(d, h, l);
+        v[2 * plane + o] = (uint16_t)h;
+        v[3 * plane + o] = (uint16_t)l;
     }
 }
 
@@ -460,7 +444,6 @@ gsb_status tangent_bf16x3(gsb_problem* P, bool sign, bool control, int R, const 
     std::vector<float> Ah(Rp, 0.f);
     std::copy(A_rep, A_rep + R, Ah.begin());
     GSB_CUDA_TRY(cudaMemcpyAsync(B.A, Ah.data(), Rp * sizeof(float), cudaMemcpyHostToDevice, s));
-    GSB_CUDA_TRY(cudaMemsetAsync(B.nrm2, 0, Rp * sizeof(double), s));
     GSB_CUDA_TRY(cudaMemsetAsync(B.log_sum, 0, Rp * sizeof(double), s));
     GSB_CUDA_TRY(cudaMemsetAsync(B.scale, 0, Rp * sizeof(float), s));
     GSB_CUDA_TRY(cudaMemsetAsync(B.status, 0, sizeof(int), s));
@@ -488,20 +471,20 @@ gsb_status tangent_bf16x3(gsb_problem* P, bool sign, bool control, int R, const 
     a.dt = dt;
 
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    k_tan_tc_init<<<dim3((Rp + 127) / 128, Np), 128, 0, s>>>(
-        a.x, a.y, a.p, a.dx, a.dy, a.dp, N, R, Rp, key, x0_range * 1.1920928955078125e-07f,
+    k_tan_tc_init<<<dim3(Np / 128, Rp), 128, 0, s>>>(
+        a.x, a.y, a.p, a.dx, a.dy, a.dp, N, R, Np, key, x0_range * 1.1920928955078125e-07f,
         y0_uniform ? 1 : 0);
     GSB_LAUNCH_CHECK("k_tan_tc_init");
     // the tangents renormalised (the log of the norm accumulated when asked)
     // and the operand planes of step m written into buffer m & 1
     auto renorm = [&](int m, int accumulate) -> gsb_status {
-        k_tan_tc_norm<<<dim3((R + 127) / 128, (N + kNormRows - 1) / kNormRows), 128, 0, s>>>(
-            a.dx, a.dy, a.dp, N, R, Rp, B.nrm2);
+        k_tan_tc_norm<<<(R + 7) / 8, 256, 0, s>>>(a.dx, a.dy, a.dp, N, R, Np, B.nrm2);
         GSB_LAUNCH_CHECK("k_tan_tc_norm");
         k_tan_tc_log<<<(R + 255) / 256, 256, 0, s>>>(B.nrm2, B.log_sum, B.scale, R, accumulate);
         GSB_LAUNCH_CHECK("k_tan_tc_log");
-        k_tan_tc_planes<<<dim3(Np / 32, Rp / 32), dim3(32, 8), 0, s>>>(
-            a.x, a.dx, a.dy, a.dp, B.scale, B.v[m & 1], Np, Rp, sign ? 1 : 0);
+        k_tan_tc_planes<<<dim3(Np / 128, Rp), 128, 0, s>>>(
+            a.x, a.dx, a.dy, a.dp, B.scale, reinterpret_cast<uint16_t*>(B.v[m & 1]), Np, Rp,
+            sign ? 1 : 0);
         GSB_LAUNCH_CHECK("k_tan_tc_planes");
         return GSB_OK;
     };
