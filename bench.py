@@ -717,7 +717,7 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
     J5 = I.sk_gauss(2000, 0)
     P5 = gsb.Problem.dense(J5, stream=stream.cuda_stream)
     if not (want("lyapunov") or only == "lyapunov_bf16x3"):
-        return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak)
+        return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak, Pk, how)
     A16 = [0.025 * k for k in range(16)]
     steps = 200
     # J over [X | dX]: 2 N^2 flop for each of the 2 x 16 x 256 columns per step
@@ -755,7 +755,7 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
     if only in ("lyapunov", "lyapunov_bf16x3"):
         P5.close()
         return out
-    return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak)
+    return adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak, Pk, how)
 
 
 def batch_error_vs_oracle(gsb, probs, Js, Ns, Rs, stream, sample=256):
@@ -786,9 +786,10 @@ def batch_error_vs_oracle(gsb, probs, Js, Ns, Rs, stream, sample=256):
             "how": "first step from the same x(0): max |dy| / (c dt max_i sum_j |J_ij x_j|)"}
 
 
-def adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak):
+def adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak, Pk, how):
     """Adjoint gradient: N = 2000 SK (the problem P5), R = 256, 200-step
-    window, checkpoints every 20; closes P5."""
+    window, checkpoints every 20, with the products as FP32 SGEMMs and as
+    split-bf16 tensor-core partials; closes P5."""
     R5, W = 256, 200
     x0 = torch.from_numpy(I.uniform_state(R5, 2000, 1)).cuda()
     E = torch.empty(R5, dtype=torch.float64, device="cuda")
@@ -797,26 +798,48 @@ def adjoint_leg(gsb, I, np, torch, stream, P5, out, fp32_peak):
     gdt = torch.empty(R5, dtype=torch.float64, device="cuda")
     args = (x0.data_ptr(), R5, 0.2, 1.25, 0.5, E.data_ptr(), gx.data_ptr(), gA.data_ptr(),
             gdt.data_ptr())
-    P5.relaxed_energy_grad("gbsb", 21500, 20, *args, ckpt_every=20, stream=stream.cuda_stream)
-    t = time.perf_counter()
-    P5.relaxed_energy_grad("gbsb", 21500, W, *args, ckpt_every=20, stream=stream.cuda_stream)
-    el = time.perf_counter() - t
-    gsb.set_call_profiling(True)
-    P5.relaxed_energy_grad("gbsb", 21500, W, *args, ckpt_every=20, stream=stream.cuda_stream)
-    kms, kn, _ = gsb.last_call_profile()
-    gsb.set_call_profiling(False)
     # forward W + recompute W - K + the seed + reverse W products of 2 N^2 R flop
     flop = 2.0 * 2000 ** 2 * R5 * (3 * W - 20 + 1)
-    ach = flop / (kms * 1e-3) / 1e12
-    out["adjoint"] = {
-        "workload": "N=2000 SK N(0,1/N), R=256, gradient over a 200-step window, checkpoints every 20",
-        "value": R5 / el, "unit": "gradients/s (one per replica)", "ms_per_call": 1e3 * el,
-        "how": "value: host wall clock around gsb_relaxed_energy_grad",
-        "kernel_ms": kms, "kernel_launches": kn,
-        "roofline": {"bound": "alu", "kernel": "k_adj_fwd / k_adj_post (FP32 SGEMM)",
-                     "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": ach / fp32_peak,
-                     "how": "algorithmic flop / CUDA-event time of the step-kernel launches"}}
+    grads = {}
+    for form in ("fp32", "bf16x3"):
+        kw = dict(ckpt_every=20, precision=form, stream=stream.cuda_stream)
+        P5.relaxed_energy_grad("gbsb", 21500, 20, *args, **kw)
+        t = time.perf_counter()
+        P5.relaxed_energy_grad("gbsb", 21500, W, *args, **kw)
+        el = time.perf_counter() - t
+        grads[form] = (E.cpu().numpy().copy(), gA.cpu().numpy().copy(), gdt.cpu().numpy().copy())
+        gsb.set_call_profiling(True)
+        P5.relaxed_energy_grad("gbsb", 21500, W, *args, **kw)
+        kms, kn, _ = gsb.last_call_profile()
+        gsb.set_call_profiling(False)
+        ach = flop / (kms * 1e-3) / 1e12
+        if form == "fp32":
+            roof = {"bound": "alu", "kernel": "k_adj_fwd / k_adj_post (FP32 SGEMM)",
+                    "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak}
+        else:
+            roof = {"bound": "tensor", "kernel": "k_gemm_tc (split-bf16 K-split partials)",
+                    "achieved": ach, "peak": Pk["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / Pk["bf16_tflops"],
+                    "peak_source": how + " (bf16 burst; each product counted once, the split "
+                                         "runs three bf16 MMAs for it)"}
+        roof["how"] = "algorithmic flop / CUDA-event time of the step-kernel launches"
+        out["adjoint" if form == "fp32" else "adjoint_bf16x3"] = {
+            "workload": "N=2000 SK N(0,1/N), R=256, gradient over a 200-step window, checkpoints "
+                        f"every 20, products {form}",
+            "value": R5 / el, "unit": "gradients/s (one per replica)", "ms_per_call": 1e3 * el,
+            "how": "value: host wall clock around gsb_relaxed_energy_grad",
+            "kernel_ms": kms, "kernel_launches": kn, "roofline": roof}
+    # the two forms' results side by side: relative difference per replica, the
+    # scale floored at 5 % of the median magnitude (a gradient that cancels
+    # across its terms has no meaningful relative error)
+    a, b = grads["fp32"], grads["bf16x3"]
+    diff = {}
+    for k, x, y in zip(("E", "dE/dA", "dE/ddt"), a, b):
+        scale = np.maximum(np.abs(x), 0.05 * np.median(np.abs(x)))
+        d = np.abs(x - y) / np.maximum(scale, 1e-300)
+        diff[k] = {"median": float(np.median(d)), "max": float(np.max(d))}
+    out["adjoint_bf16x3"]["rel_diff_vs_fp32"] = diff
     P5.close()
     return out
 

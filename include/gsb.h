@@ -325,7 +325,11 @@ gsb_status gsb_twin_delta(gsb_run_state* run, double* delta_out);
  * variant, M, R, c (> 0), dt (> 0), A / A_per_replica. Device buffers owned by
  * the caller: x0 (R x N float, replica-major), energy (R doubles, written),
  * grad_x0 (R x N float), grad_A and grad_dt (R doubles each; nullable).
- * Dense problems without h, FP32 arithmetic. Blocks on `stream`. */
+ * Dense problems without h, FP32 arithmetic. params->precision: GSB_PREC_AUTO or
+ * GSB_PREC_FP32, the products J v as FP32 SGEMMs on CUDA cores; GSB_PREC_BF16X3,
+ * as K-split partial products on the tensor cores in the split-bf16 form (J and
+ * v split into bf16 hi + lo terms; error at the 2^-16 level of the coupling's
+ * magnitude); any other: GSB_EUNSUPPORTED. Blocks on `stream`. */
 gsb_status gsb_relaxed_energy_grad(gsb_problem* problem, const gsb_params* params,
                                    int32_t window, int32_t ckpt_every, const float* x0,
                                    double* energy, float* grad_x0, double* grad_A,

@@ -269,6 +269,15 @@ gsb_status bf16_ensure_planes(gsb_problem* P, cudaStream_t s);
 // TMA map of a bf16 [outer][inner] array (inner contiguous): boxes of one
 // 128-byte K atom (64 elements) x 128 rows, 128-byte swizzle.
 gsb_status bf16_tensor_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer);
+// K-split partial products Fp[s] = J[:, K_s] V[K_s, :] on the tensor cores
+// (split bf16; V and Fp[s] spin-major [Np][Rp] FP32), for the adjoint.
+struct SplitGemm;
+gsb_status split_gemm_create(gsb_problem* P, int Rp, SplitGemm** out, cudaStream_t s);
+gsb_status split_gemm_partials(SplitGemm* g, const float* V, bool sign, int nslices, float* Fp,
+                               cudaStream_t s);
+// synchronises s; GSB_ETIMEOUT / GSB_ECUDA when a kernel reported a failed wait or check
+gsb_status split_gemm_status(SplitGemm* g, cudaStream_t s);
+void split_gemm_destroy(SplitGemm* g);
 // gsb_lyapunov's tangent-linear steps with J x and J dx on the tensor cores
 // (split bf16): R replicas (A_rep[r] each), log-norm sums into log_sum[R].
 gsb_status tangent_bf16x3(gsb_problem* P, bool sign, bool control, int R, const float* A_rep,

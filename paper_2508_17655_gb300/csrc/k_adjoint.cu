@@ -18,7 +18,10 @@
 //                                   lp = lp' (1 - g / (M - m)), lg = -lp' p / (M - m),
 //                                   gA -= lg x^2, lx -= 2 A x lg
 // Each reverse step is an elementwise pass writing lf, then an SGEMM J lf whose
-// epilogue finishes the step and reduces gA, gdt per replica.
+// epilogue finishes the step and reduces gA, gdt per replica. Under
+// GSB_PREC_BF16X3 every product J v is taken as K-split partial sums from the
+// tensor cores (split bf16, k_gemm_tc.cu), which the same step kernels add in
+// their fixed order.
 #include <vector>
 
 #include "sgemm_f32.cuh"
@@ -280,6 +283,11 @@ __global__ void k_finish(const double* e_acc, double* E, const double* gA, doubl
     if (gdt_out) gdt_out[r] = gdt[r];
 }
 
+struct SplitGemmGuard {
+    SplitGemm* g = nullptr;
+    ~SplitGemmGuard() { split_gemm_destroy(g); }
+};
+
 struct DevBuf {
     std::vector<void*> ptrs;
     ~DevBuf() {
@@ -315,6 +323,9 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
     if (ckpt_every < 1) return set_error(GSB_EINVAL, "ckpt_every must be >= 1");
     if (!(Q.c > 0.0) || !(Q.dt > 0.0)) return set_error(GSB_EINVAL, "c and dt must be > 0");
     if (Q.schedule) return set_error(GSB_EUNSUPPORTED, "the Eq. 6 schedule only");
+    if (Q.precision != GSB_PREC_AUTO && Q.precision != GSB_PREC_FP32 &&
+        Q.precision != GSB_PREC_BF16X3)
+        return set_error(GSB_EUNSUPPORTED, "gsb_relaxed_energy_grad takes FP32 or BF16X3 coupling");
     cudaStream_t s = (cudaStream_t)stream;
     const bool sign = Q.variant == GSB_DSB || Q.variant == GSB_GDSB;
     const bool control = Q.variant == GSB_GBSB || Q.variant == GSB_GDSB;
@@ -358,13 +369,20 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
     GSB_CUDA_TRY(cudaGetDevice(&dev));
     GSB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const long tiles64 = (long)(Rp / 64) * (Np / 64);
-    const int mode = (long)(Rp / 128) * (Np / 128) >= sms ? 128 : (tiles64 >= 2L * sms ? 64 : kSplitK);
+    // the split-bf16 form takes its partial products from the tensor cores
+    const bool tensor = Q.precision == GSB_PREC_BF16X3;
+    const int mode = tensor ? kSplitK
+                            : (long)(Rp / 128) * (Np / 128) >= sms ? 128
+                                                                   : (tiles64 >= 2L * sms ? 64 : kSplitK);
     const int T = mode == 128 ? 128 : 64;
     const dim3 grid(Rp / T, Np / T);
     float* Fp = nullptr;  // split-K partial sums
     if (mode == kSplitK && (st = B.alloc(&Fp, kSplitK * nst))) return st;
+    SplitGemmGuard tg;
+    if (tensor && (st = split_gemm_create(P, Rp, &tg.g, s))) return st;
     // the partial sums of J X for a kernel in the split mode
     auto gemm_part = [&](const float* X, bool sgn) -> gsb_status {
+        if (tensor) return split_gemm_partials(tg.g, X, sgn, kSplitK, Fp, s);
         const dim3 g(Rp / 64, Np / 64, kSplitK);
         if (sgn)
             k_adj_gemm_part<true><<<g, 256, 0, s>>>(P->J32, X, Np, Rp, Fp);
@@ -497,5 +515,6 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
         if (st != GSB_OK) return st;
     }
     GSB_CUDA_TRY(cudaStreamSynchronize(s));  // buffers are freed on return
+    if (tensor && (st = split_gemm_status(tg.g, s))) return st;
     return call_prof_collect();
 }

@@ -471,9 +471,12 @@ class Problem:
 
     def relaxed_energy_grad(self, variant, M, window, x0_ptr, R, A, dt, c, energy_ptr,
                             grad_x0_ptr=None, grad_A_ptr=None, grad_dt_ptr=None,
-                            ckpt_every=20, stream=None):
-        """gsb_relaxed_energy_grad on caller device buffers (raw pointers)."""
+                            ckpt_every=20, precision="fp32", stream=None):
+        """gsb_relaxed_energy_grad on caller device buffers (raw pointers);
+        precision "fp32" (SGEMMs on CUDA cores) or "bf16x3" (the products on
+        the tensor cores, split bf16)."""
         prm = gsb_params()
+        prm.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
         prm.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
         prm.M = int(M)
         prm.R = int(R)

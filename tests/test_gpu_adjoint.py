@@ -21,7 +21,7 @@ def _built():
     build.build()
 
 
-def _gpu_grad(P, variant, M, W, x0, A, dt, c, K=20):
+def _gpu_grad(P, variant, M, W, x0, A, dt, c, K=20, precision="fp32"):
     torch = pytest.importorskip("torch")
     R, N = x0.shape
     xd = torch.from_numpy(np.ascontiguousarray(x0, dtype=np.float32)).cuda()
@@ -30,7 +30,7 @@ def _gpu_grad(P, variant, M, W, x0, A, dt, c, K=20):
     gA = torch.empty(R, dtype=torch.float64, device="cuda")
     gdt = torch.empty(R, dtype=torch.float64, device="cuda")
     P.relaxed_energy_grad(variant, M, W, xd.data_ptr(), R, A, dt, c, E.data_ptr(), gx.data_ptr(),
-                          gA.data_ptr(), gdt.data_ptr(), ckpt_every=K,
+                          gA.data_ptr(), gdt.data_ptr(), ckpt_every=K, precision=precision,
                           stream=torch.cuda.current_stream())
     torch.cuda.synchronize()
     return E.cpu().numpy(), gx.cpu().numpy().astype(np.float64), gA.cpu().numpy(), gdt.cpu().numpy()
@@ -78,7 +78,7 @@ def _check(got, want, sens, ok, what, base=1e-4, factor=200.0):
             # relative error: floor the scale at 5 % of the median magnitude
             scale = np.maximum(np.abs(w), 0.05 * np.median(np.abs(w)))
             err = np.abs(g - w) / np.maximum(scale, 1e-300)
-        tol = np.maximum(base, factor * sens[k])
+        tol = np.maximum(base[k] if isinstance(base, tuple) else base, factor * sens[k])
         # a NaN error or tolerance would pass the comparison below: it fails here
         assert not np.isnan(err[ok]).any(), f"{what} {name}: NaN error"
         assert not np.isnan(tol[ok]).any(), f"{what} {name}: NaN tolerance"
@@ -86,43 +86,98 @@ def _check(got, want, sens, ok, what, base=1e-4, factor=200.0):
         assert not bad.any(), (f"{what} {name}: errors {err[bad]} vs tolerances {tol[bad]}")
 
 
+def bf16_split_sum(J):
+    """J_hi + J_lo in FP64, J_hi = bf16(J) and J_lo = bf16(J - J_hi) rounded to
+    nearest even: the matrix whose products the split-bf16 form computes (its
+    sgn-coupled products exactly, up to FP32 accumulation)."""
+    def rne(a):
+        b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+        r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+        return r.astype(np.uint32).view(np.float32)
+    hi = rne(J)
+    lo = rne(J.astype(np.float32) - hi)
+    return hi.astype(np.float64) + lo.astype(np.float64)
+
+
+def _oracle_J(J, precision):
+    return bf16_split_sum(J) if precision == "bf16x3" else J.astype(np.float64)
+
+
+# The split form's x coupling: each product J x carries three residues of up
+# to 2^-18 of its magnitude sum_j |J_ij x_j| (x_lo and J_lo rounded, J_lo x_lo
+# dropped) where FP32 carries one rounding of 2^-24: 3 x 2^6 ~ 2^7.6, so 2^8
+# times the FP32 bars that scale with the rounding.
+SPLIT_RATIO = 2.0 ** 8
+
+
+def _energy_cancellation(Jd, x):
+    """kappa per replica: the magnitude 1/2 sum_i |x_i| sum_j |J_ij x_j| of the
+    energy's terms over |E|. A product error that is relative to the terms'
+    magnitude is kappa times larger relative to E."""
+    mag = 0.5 * np.einsum("ri,ri->r", np.abs(x), np.abs(x) @ np.abs(Jd).T)
+    E = -0.5 * np.einsum("ri,ri->r", x, x @ Jd.T)
+    return mag / np.maximum(np.abs(E), 1e-300)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("variant", ["gbsb", "bsb", "gdsb", "dsb"])
-def test_adjoint_well_conditioned_within_1e4(variant):
+def test_adjoint_well_conditioned_within_1e4(variant, precision):
     """A short window from small x0 (no wall events, little amplification):
-    every replica's E, dE/dx0, dE/dA, dE/ddt within 1e-4 relative of FP64."""
+    every replica's E, dE/dx0, dE/dA, dE/ddt within 1e-4 relative of FP64 (for
+    the split-bf16 form, of the oracle on its matrix J_hi + J_lo)."""
     N, R, M, W = 300, 96, 400, 12
     J = I.sk_gauss(N, 13)
     c, dt = 0.5, f32(0.8)
     A = np.linspace(0.1, 0.4, R).astype(np.float32)
     x0 = O.init_uniform(R, N, 18, rng=0.02)
-    got = _gpu_grad(gsb.Problem.dense(J), variant, M, W, x0, A, dt, c)
-    Jd = J.astype(np.float64)
+    got = _gpu_grad(gsb.Problem.dense(J), variant, M, W, x0, A, dt, c, precision=precision)
+    Jd = _oracle_J(J, precision)
     Ad = A.astype(np.float64)
     want = O.relaxed_energy_grad(Jd, variant, x0, c=c, dt=dt, M=M, W=W, A=Ad)
-    margin = O.run(Jd, variant, x0, 0 * x0, c=c, dt=dt, M=M, A=Ad, nsteps=W)["margin"]
-    ok = margin >= (2e-6 if variant in ("dsb", "gdsb") else 0.5)
+    run = O.run(Jd, variant, x0, 0 * x0, c=c, dt=dt, M=M, A=Ad, nsteps=W)
+    sign = variant in ("dsb", "gdsb")
+    ok = run["margin"] >= (2e-6 if sign else 0.5)
     assert ok.mean() >= 0.9
     zero = (np.zeros(R),) * 4
-    _check(got, want, zero, ok, variant, base=1e-4, factor=0.0)
+    base = 1e-4
+    if precision == "bf16x3" and not sign:
+        # the split's residues (up to 3 x 2^-18 of each product's magnitude) in
+        # each of the W forward, W recomputed and W reverse products: W 2^-15
+        # for the gradients; E, one product of x(t_W) with J x(t_W), within
+        # 2^-14 of its terms' magnitude (kappa x 2^-14 of E). The sgn
+        # coupling is exact on J_hi + J_lo: the FP32 bar.
+        kappa = _energy_cancellation(Jd, run["x"])
+        base = (np.maximum(1e-4, kappa * 2.0 ** -14),) + (W * 2.0 ** -15,) * 3
+    _check(got, want, zero, ok, f"{variant} {precision}", base=base, factor=0.0)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("variant", ["gbsb", "bsb", "gdsb", "dsb"])
-def test_adjoint_matches_oracle_small(variant):
+def test_adjoint_matches_oracle_small(variant, precision):
+    """60 steps with wall events: per replica within max(1e-4, 200 x the FP64
+    gradient's sensitivity to a 2^-24 relative perturbation of x0); the
+    split-bf16 form against the oracle on J_hi + J_lo, its x coupling also
+    splitting x, so SPLIT_RATIO x the sensitivity term and a floor of
+    W 2^-15 (as in the well-conditioned test)."""
     N, R, M, W = 300, 70, 400, 60
     J = I.sk_gauss(N, 13)
     c, dt = 0.5, f32(0.8)
     A = np.linspace(0.1, 0.4, R).astype(np.float32)
     x0 = O.init_uniform(R, N, 17)
-    got = _gpu_grad(gsb.Problem.dense(J), variant, M, W, x0, A, dt, c)
-    Jd = J.astype(np.float64)
+    got = _gpu_grad(gsb.Problem.dense(J), variant, M, W, x0, A, dt, c, precision=precision)
+    Jd = _oracle_J(J, precision)
     Ad = A.astype(np.float64)
     want, sens = _sensitivity(
         lambda x: O.relaxed_energy_grad(Jd, variant, x, c=c, dt=dt, M=M, W=W, A=Ad), x0)
     margin = O.run(Jd, variant, x0, 0 * x0, c=c, dt=dt, M=M, A=Ad, nsteps=W)["margin"]
     # a different wall or sign decision changes the gradient by O(1)
-    ok = margin >= (1e-5 if variant in ("dsb", "gdsb") else 1e-4)
+    sign = variant in ("dsb", "gdsb")
+    ok = margin >= (1e-5 if sign else 1e-4)
     assert ok.sum() >= 2
-    _check(got, want, sens, ok, variant)
+    split_x = precision == "bf16x3" and not sign
+    factor = 200.0 * (SPLIT_RATIO if split_x else 1.0)
+    _check(got, want, sens, ok, f"{variant} {precision}", base=W * 2.0 ** -15 if split_x else 1e-4,
+           factor=factor)
 
 
 def test_adjoint_config5_shape_against_fp64():
@@ -164,12 +219,14 @@ def test_adjoint_config5_shape_against_fp64():
     assert abs(want[2][0] - fdA[0]) <= 1e-4 * abs(fdA[0]) + 1e-8
 
 
-def test_checkpoint_interval_does_not_change_the_gradient():
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_checkpoint_interval_does_not_change_the_gradient(precision):
     N, R, M, W = 256, 128, 500, 45
     J = I.sk_gauss(N, 19)
     x0 = O.init_uniform(R, N, 23)
     P = gsb.Problem.dense(J)
-    outs = [_gpu_grad(P, "gbsb", M, W, x0, 0.3, 0.9, 0.5, K=K) for K in (1, 7, 20, 45)]
+    outs = [_gpu_grad(P, "gbsb", M, W, x0, 0.3, 0.9, 0.5, K=K, precision=precision)
+            for K in (1, 7, 20, 45)]
     for o in outs[1:]:
         for a, b in zip(o, outs[0]):
             assert np.array_equal(a, b)
@@ -196,3 +253,35 @@ def test_torch_autograd_function():
     np.testing.assert_allclose(A.grad.numpy(), (wn * gA).astype(np.float32), rtol=1e-6)
     np.testing.assert_allclose(float(dt.grad), float(np.sum(wn * gdt)), rtol=1e-5)
     assert A.grad.device.type == "cpu" and x0.grad.device.type == "cuda"
+
+
+def test_adjoint_bf16x3_config5_shape():
+    """The configuration-5 shape (N = 2000 SK, R = 256, 200 steps of M = 21,500,
+    checkpoints every 20) with the products on the tensor cores: sampled
+    replicas against the FP64 oracle on J_hi + J_lo within max(1e-4, 5 x the
+    FP32-storage drift x SPLIT_RATIO) -- the x split perturbs each step about
+    that many times more than FP32 rounding of the state."""
+    N, R, M, W = 2000, 256, 21500, 200
+    J = I.sk_gauss(N, 0)
+    Jd = bf16_split_sum(J)
+    c, dt, A = 0.5, 1.25, 0.2
+    x0 = O.init_uniform(R, N, 1)
+    got = _gpu_grad(gsb.Problem.dense(J), "gbsb", M, W, x0, A, dt, c, precision="bf16x3")
+    pick = np.linspace(0, R - 1, 6).astype(int)
+    want = O.relaxed_energy_grad(Jd, "gbsb", x0[pick], c=c, dt=dt, M=M, W=W, A=A)
+    store = O.relaxed_energy_grad(Jd, "gbsb", x0[pick], c=c, dt=dt, M=M, W=W, A=A, f32_state=True)
+    rel = lambda a, b: np.abs(a - b) / np.abs(a)
+    drift = (rel(want[0], store[0]),
+             np.linalg.norm(want[1] - store[1], axis=1) / np.linalg.norm(want[1], axis=1),
+             rel(want[2], store[2]), rel(want[3], store[3]))
+    _check(tuple(g[pick] for g in got), want, drift, np.ones(len(pick), bool), "config 5 bf16x3",
+           base=1e-4, factor=5.0 * SPLIT_RATIO)
+
+
+def test_adjoint_rejects_other_forms():
+    torch = pytest.importorskip("torch")
+    J = I.sk_gauss(64, 2)
+    x0 = O.init_uniform(4, 64, 1)
+    with pytest.raises(gsb.GsbError) as e:
+        _gpu_grad(gsb.Problem.dense(J), "gbsb", 100, 5, x0, 0.2, 0.9, 0.5, precision="fp8")
+    assert e.value.status == gsb.EUNSUPPORTED
