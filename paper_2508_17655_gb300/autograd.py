@@ -12,7 +12,7 @@ from . import gsb
 
 class GsbRelaxedEnergy(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x0, A, dt, problem, variant, M, window, c, ckpt_every):
+    def forward(ctx, x0, A, dt, problem, variant, M, window, c, ckpt_every, precision):
         if not (x0.is_cuda and x0.dtype == torch.float32 and x0.is_contiguous()):
             raise ValueError("x0 must be a contiguous float32 CUDA tensor (R x N)")
         R = x0.shape[0]
@@ -25,7 +25,7 @@ class GsbRelaxedEnergy(torch.autograd.Function):
         stream = torch.cuda.current_stream(dev)
         problem.relaxed_energy_grad(variant, M, window, x0.data_ptr(), R, A_host, float(dt), c,
                                     E.data_ptr(), gx.data_ptr(), gA.data_ptr(), gdt.data_ptr(),
-                                    ckpt_every=ckpt_every, stream=stream)
+                                    ckpt_every=ckpt_every, precision=precision, stream=stream)
         ctx.save_for_backward(gx, gA, gdt)
         ctx.A_shape = A.shape
         ctx.A_device = A.device
@@ -46,9 +46,13 @@ class GsbRelaxedEnergy(torch.autograd.Function):
         if ctx.dt_shape is not None:
             grad_dt = (gE * gdt).sum().reshape(ctx.dt_shape).to(device=ctx.dt_device,
                                                                   dtype=torch.float32)
-        return grad_x0, grad_A, grad_dt, None, None, None, None, None, None
+        return grad_x0, grad_A, grad_dt, None, None, None, None, None, None, None
 
 
-def relaxed_energy(x0, A, dt, problem, variant="gbsb", M=2000, window=200, c=0.5, ckpt_every=20):
-    """E per replica; differentiable in x0 (R x N), A (R or scalar) and dt (scalar tensor)."""
-    return GsbRelaxedEnergy.apply(x0, A, dt, problem, variant, M, window, c, ckpt_every)
+def relaxed_energy(x0, A, dt, problem, variant="gbsb", M=2000, window=200, c=0.5, ckpt_every=20,
+                   precision="fp32"):
+    """E per replica; differentiable in x0 (R x N), A (R or scalar) and dt (scalar tensor).
+    precision: "fp32" (the products as FP32 SGEMMs) or "bf16x3" (on the tensor cores,
+    split bf16)."""
+    return GsbRelaxedEnergy.apply(x0, A, dt, problem, variant, M, window, c, ckpt_every,
+                                  precision)
