@@ -505,6 +505,10 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
         mkf = lambda m, prof: P.run("gbsb", M=m, R=R, c=0.0, dt=0.0, A=0.2, seed=1, defer=True,
                                     profile=prof, stream=stream.cuda_stream, fused_csr=True)
         us_fused = kernel_us(mkf, min(M, 1000))
+        # FP32 sums in the nonzeros' order instead of the exact fixed-point form
+        mk32 = lambda m, prof: P.run("gbsb", M=m, R=R, c=0.0, dt=0.0, A=0.2, seed=1, defer=True,
+                                     profile=prof, stream=stream.cuda_stream, precision="fp32")
+        us_fp32 = kernel_us(mk32, min(M, 1000))
         nnz = len(col)
         # algorithmic bytes per step: x, y, p read and written (24 B per spin and
         # replica), x gathered once (4 B), CSR indices and values (8 B per nonzero)
@@ -518,7 +522,11 @@ def other_legs(gsb, I, np, torch, stream, Pk, how, only=None, leg_M=0):
                          "peak": hbm, "unit": "GB/s",
                          "frac": bytes_step / (us * 1e-6) / 1e9 / hbm, "us_per_step": us,
                          "algorithmic_bytes_per_step": bytes_step, "peak_source": how},
-            "fused_multistep_us_per_step": us_fused}
+            "fused_multistep_us_per_step": us_fused,
+            "fp32_sums": {"us_per_step": us_fp32,
+                          "frac": bytes_step / (us_fp32 * 1e-6) / 1e9 / hbm,
+                          "how": "precision fp32: FP32 sums in the nonzeros' order (the default "
+                                 "for integer J is the exact fixed-point sum)"}}
         run.close()
         P.close()
     # --- FX32 (GbSB, J.x exact on bf16 digit planes), the headline shape, one run

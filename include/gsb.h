@@ -65,8 +65,11 @@ typedef enum gsb_variant { GSB_BSB = 0, GSB_GBSB = 1, GSB_DSB = 2, GSB_GDSB = 3 
 typedef enum gsb_precision {
     GSB_PREC_AUTO = 0,   /* FP8 for sgn-x coupling with integer |J| <= 16, FX32 for x coupling
                             with integer J (128 max_i sum_j |J_ij| < 2^24), BF16X3 for
-                            real-valued J, FP32 otherwise; CSR problems always use CSR */
-    GSB_PREC_FP32 = 1,   /* FP32 on CUDA cores (the plain form) */
+                            real-valued J, FP32 otherwise; CSR problems always use CSR,
+                            with the exact fixed-point x coupling (int64 sums of
+                            J_ij rint(2^30 x_j)) for integer J */
+    GSB_PREC_FP32 = 1,   /* FP32 on CUDA cores (the plain form); for CSR problems, FP32 sums
+                            in the nonzeros' order for any J (no fixed-point form) */
     GSB_PREC_FP8 = 2,    /* tcgen05 kind::f8f6f4, e4m3 J and sgn x, FP32 accumulate: exact for
                             integer |J| <= 16; sgn-x coupling (dSB, GdSB) only */
     GSB_PREC_FX32 = 3,   /* tcgen05 kind::f16 with integer J in bf16 and x as 32-bit fixed point

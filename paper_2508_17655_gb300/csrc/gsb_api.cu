@@ -778,8 +778,9 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
         return set_error(GSB_EINVAL, "a schedule applies to bSB / dSB only (GbSB uses Eq. 7)");
     int path = kPathDenseF32;
     if (P->csr) {
-        if (Q.precision != GSB_PREC_AUTO)
-            return set_error(GSB_EUNSUPPORTED, "CSR problems run on the CSR path only");
+        if (Q.precision != GSB_PREC_AUTO && Q.precision != GSB_PREC_FP32)
+            return set_error(GSB_EUNSUPPORTED,
+                             "CSR problems take GSB_PREC_AUTO or GSB_PREC_FP32 (the CSR path)");
         path = kPathCsr;
     } else {
         switch (Q.precision) {

@@ -323,8 +323,10 @@ gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc) {
                             (const int8_t*)run->s8[cur], run->x[cur ^ 1], run->s8[cur ^ 1],  \
                             run->y, run->p, (const float*)run->A, sc.c, sc.dt, sc.p_next,    \
                             inv_rem, run->status))
-    // exact fixed-point x coupling when J is integer and 2^30 sum_k |J_ik| fits in int64
-    const bool exact = P->integer_J && P->max_row_abs < 4294967296.0;
+    // exact fixed-point x coupling when J is integer and 2^30 sum_k |J_ik| fits in
+    // int64, unless FP32 sums were asked for
+    const bool exact = P->integer_J && P->max_row_abs < 4294967296.0 &&
+                       run->params.precision != GSB_PREC_FP32;
     if (run->sign_coupling) {
         if (run->control) GSB_CSR_LAUNCH(true, true, false); else GSB_CSR_LAUNCH(true, false, false);
     } else if (exact) {
@@ -343,7 +345,8 @@ namespace {
 // The fused kernel for the run's coupling, control and exactness.
 const void* csr_persist_kernel(const gsb_run_state* run) {
     const gsb_problem* P = run->prob;
-    const bool exact = P->integer_J && P->max_row_abs < 4294967296.0;
+    const bool exact = P->integer_J && P->max_row_abs < 4294967296.0 &&
+                       run->params.precision != GSB_PREC_FP32;
     if (run->sign_coupling)
         return run->control ? (const void*)k_csr_persist<true, true, false>
                             : (const void*)k_csr_persist<true, false, false>;

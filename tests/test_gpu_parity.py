@@ -200,15 +200,19 @@ def test_dense_one_step_parity(variant, N, R, precision):
         _one_step_resync(P, J.astype(np.float64), variant, N, R, 400, m, **kw)
 
 
+@pytest.mark.parametrize("precision", ["auto", "fp32"])
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("weights", ["+1", "pm1"])
-def test_csr_one_step_parity(variant, weights):
+def test_csr_one_step_parity(variant, weights, precision):
+    """Integer weights: the exact fixed-point coupling ("auto") and FP32 sums
+    in the nonzeros' order ("fp32"), each step against the oracle."""
     N, R, M = 1000, 130, 500
     rp, col, val = I.er_graph(N, 20, weights, 5)
     C = O.Coupling(N, rowptr=rp, col=col, val=val)
     lmax, lmin = O.lambda_extremes(C)
     P = gsb.Problem.csr(N, rp, col, val)
-    kw = dict(c=f32(1 / lmax), dt=f32(O.dt_from_lambda(lmax, lmin)), A=0.2, seed=3)
+    kw = dict(c=f32(1 / lmax), dt=f32(O.dt_from_lambda(lmax, lmin)), A=0.2, seed=3,
+              precision=precision)
     for m in (0, 60, 499):
         _one_step_resync(P, C, variant, N, R, M, m, **kw)
 
@@ -237,7 +241,7 @@ def test_csr_trajectory_50_steps(variant, weights):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("weights", ["+1", "pm1", "real"])
+@pytest.mark.parametrize("weights", ["+1", "pm1", "real", "+1 fp32"])
 def test_csr_fused_steps_match_one_step_launches_bit_exact(variant, weights):
     """The fused multi-step CSR kernel (GSB_RUN_FUSED_CSR: one cooperative
     launch per stretch of steps, a grid barrier between steps, gathered rows
@@ -246,13 +250,15 @@ def test_csr_fused_steps_match_one_step_launches_bit_exact(variant, weights):
     ER N = 2000, mean degree 20 (more tasks than resident warps), R = 200 (a
     ragged second replica block), energies every 25 steps (launches cut
     there) and stretches of at most 7 steps; "real" scales the +-1 weights by
-    0.37 (no exact fixed-point form)."""
+    0.37 (no exact fixed-point form); "+1 fp32" asks for FP32 sums with
+    integer weights."""
     N, R, M = 2000, 200, 120
-    rp, col, val = I.er_graph(N, 20, "+1" if weights == "+1" else "pm1", 6)
+    rp, col, val = I.er_graph(N, 20, "pm1" if weights in ("pm1", "real") else "+1", 6)
     if weights == "real":
         val = (val * np.float32(0.37)).astype(np.float32)
     P = gsb.Problem.csr(N, rp, col, val)
-    kw = dict(M=M, R=R, c=0.08, dt=0.9, A=0.25, seed=4, eval_every=25)
+    kw = dict(M=M, R=R, c=0.08, dt=0.9, A=0.25, seed=4, eval_every=25,
+              precision="fp32" if weights.endswith("fp32") else "auto")
     outs = []
     for spl, fused in ((1, False), (0, True), (7, True)):
         run = P.run(variant, steps_per_launch=spl, fused_csr=fused, **kw)
