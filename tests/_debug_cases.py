@@ -59,6 +59,30 @@ def run_cases():
             C.close()
         P.close()
         G.close()
+    # Lyapunov exponents and adjoint gradients, both coupling forms (the split
+    # form's tangent step and K-split partial products included), at a ragged
+    # shape: N = 129 (two spin tiles), 2 x 67 replicas (two replica tiles)
+    import torch
+    Jg = I.sk_gauss(129, 5)
+    G = gsb.Problem.dense(Jg)
+    x0 = I.uniform_state(67, 129, 4)
+    xd = torch.from_numpy(np.ascontiguousarray(x0, dtype=np.float32)).cuda()
+    for prec in ("fp32", "bf16x3"):
+        for variant in ("gbsb", "gdsb"):
+            out[f"lyap/{prec}/{variant}"] = np.asarray(
+                G.lyapunov(variant, 400, 67, [0.1, 0.3], c=0.5, dt=0.9, seed=6, renorm_every=5,
+                           nsteps=20, precision=prec))
+            E = torch.empty(67, dtype=torch.float64, device="cuda")
+            gx = torch.empty_like(xd)
+            gA = torch.empty(67, dtype=torch.float64, device="cuda")
+            gdt = torch.empty(67, dtype=torch.float64, device="cuda")
+            G.relaxed_energy_grad(variant, 400, 9, xd.data_ptr(), 67, 0.2, 0.9, 0.5, E.data_ptr(),
+                                  gx.data_ptr(), gA.data_ptr(), gdt.data_ptr(), ckpt_every=4,
+                                  precision=prec)
+            torch.cuda.synchronize()
+            for k, t in (("E", E), ("gx", gx), ("gA", gA), ("gdt", gdt)):
+                out[f"adj/{prec}/{variant}/{k}"] = t.cpu().numpy()
+    G.close()
     # batched runs of uneven instances, both forms
     Ns, Rs = [17, 129, 64, 2], [3, 130, 1, 5]
     for form in ("fp32", "bf16x3"):

@@ -8,8 +8,9 @@ and sets a bit in the status word, so nothing traps. Here:
   access; a run afterwards works (the context survives);
 * on valid inputs no check fires and the results are the release build's, bit
   for bit, over every path (dense FP8 persistent and per-step, FX32, FX16, split
-  bf16, FP32, CSR per-step and fused, batched in both forms) at the tiling's
-  edge sizes (N = 1, 2, 17, 127, 129; R = 1, 3, 130).
+  bf16, FP32, CSR per-step and fused, batched in both forms, Lyapunov and
+  adjoint in both coupling forms) at the tiling's edge sizes (N = 1, 2, 17,
+  127, 129; R = 1, 3, 130; 134 replicas with tangents).
 
 The debug library runs in a child process (GSB_LIBRARY=debug); the release
 results come from this process."""
