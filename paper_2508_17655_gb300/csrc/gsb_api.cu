@@ -428,6 +428,7 @@ void free_run(gsb_run_state* r) {
     dev_free(r->e_acc);
     dev_free(r->best_e);
     dev_free(r->best_step);
+    dev_free(r->e_part);
     dev_free(r->best_s);
     dev_free(r->best_out);
     dev_free(r->flag);
@@ -447,7 +448,7 @@ gsb_status evaluate(gsb_run_state* run, int step) {
                         ? launch_csr_energy(run->prob, run->x[run->cur], run->Rp, run->e_acc,
                                             run->stream, run->status)
                         : launch_dense_f32_energy(run->prob, run->x[run->cur], run->Rp,
-                                                  run->e_acc, run->stream);
+                                                  run->e_acc, run->e_part, run->stream);
     if (st != GSB_OK) return st;
     return launch_best_keep(run, step);
 }
@@ -864,6 +865,8 @@ gsb_status gsb_run(gsb_problem* P, const gsb_params* prm, gsb_run_state** out, v
     if (path == kPathCsr && sign)
         if ((st = dev_alloc(&run->s8[0], nst)) || (st = dev_alloc(&run->s8[1], nst)))
             return fail(st);
+    if (!P->csr && (st = dev_alloc(&run->e_part, (size_t)(run->Np / kTile) * run->Rp)))
+        return fail(st);
     if ((st = dev_alloc(&run->A, run->Rp)) || (st = dev_alloc(&run->e_acc, run->Rp)) ||
         (st = dev_alloc(&run->best_e, run->Rp)) || (st = dev_alloc(&run->best_step, run->Rp)) ||
         (st = dev_alloc(&run->flag, run->Rp)) || (st = dev_alloc(&run->best_s, nst)) ||
@@ -1114,8 +1117,9 @@ gsb_status gsb_energy(gsb_problem* P, int32_t R, const int8_t* spins, double* en
     float* xd = nullptr;
     double* acc = nullptr;
     gsb_status st = GSB_OK;
+    // acc: the Rp sums, then (dense) the per-row-block partials they are made from
     if ((st = dev_alloc(&sd, (size_t)R * P->N)) || (st = dev_alloc(&xd, nst)) ||
-        (st = dev_alloc(&acc, Rp))) {
+        (st = dev_alloc(&acc, (size_t)Rp * (1 + P->Np / kTile)))) {
         dev_free(sd);
         dev_free(xd);
         dev_free(acc);
@@ -1133,7 +1137,7 @@ gsb_status gsb_energy(gsb_problem* P, int32_t R, const int8_t* spins, double* en
             break;
         }
         st = P->csr ? launch_csr_energy(P, xd, Rp, acc, s)
-                    : launch_dense_f32_energy(P, xd, Rp, acc, s);
+                    : launch_dense_f32_energy(P, xd, Rp, acc, acc + Rp, s);
         if (st != GSB_OK) break;
         if (cudaMemcpyAsync(h.data(), acc, sizeof(double) * R, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||

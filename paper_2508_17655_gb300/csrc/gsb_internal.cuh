@@ -130,6 +130,7 @@ struct gsb_run_state {
                                                  // split bf16: [planes][Rp][Np], V(t_m) in [m & 1]
     // energy bookkeeping
     double* e_acc = nullptr;    // [Rp] sum_i s_i (J s)_i
+    double* e_part = nullptr;   // [Np / 128][Rp] partials of the FP32 energy kernel (dense runs)
     double* best_e = nullptr;   // [Rp]
     int32_t* best_step = nullptr;
     int8_t* best_s = nullptr;   // [Np][Rp]
@@ -240,8 +241,10 @@ gsb_status launch_spins_to_state(const int8_t* spins_rm, float* x_sm, int N, int
                                  int Rp, cudaStream_t s);
 // dense FP32 path
 gsb_status launch_dense_f32_step(gsb_run_state* run, const StepScalars& sc);
+// e_acc[r] += sum_i s_i (J s)_i; e_part: scratch of Np / 128 x Rp doubles, for
+// per-row-block partials added in a fixed order (the same bits every run)
 gsb_status launch_dense_f32_energy(const gsb_problem* prob, const float* x_sm, int Rp,
-                                   double* e_acc, cudaStream_t s);
+                                   double* e_acc, double* e_part, cudaStream_t s);
 // CSR path
 gsb_status launch_csr_step(gsb_run_state* run, const StepScalars& sc);
 gsb_status launch_csr_energy(const gsb_problem* prob, const float* x_sm, int Rp, double* e_acc,

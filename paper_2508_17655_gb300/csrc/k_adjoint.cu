@@ -130,7 +130,9 @@ __global__ void __launch_bounds__(256) k_adj_fwd(const float* __restrict__ J, in
     }
 }
 
-// Seed: G = J x(t_W); lx = -G, ly = lp = 0, e_acc[r] += sum_i x_i G_i.
+// Seed: G = J x(t_W); lx = -G, ly = lp = 0, e_acc[b][r] += sum_i x_i G_i over the
+// rows of block row b. Per-replica sums are kept per block row (one writer a
+// slot) and added in order by k_finish, so every run gives the same bits.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_adj_seed(const float* __restrict__ J, int Np, int Rp,
                                                   const float* __restrict__ x, float* __restrict__ lx,
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(256) k_adj_seed(const float* __restrict__ J, i
     if (threadIdx.x < T) {
         double s = 0.0;
         for (int t = 0; t < 16; ++t) s += (double)red[t][threadIdx.x];
-        atomicAdd(&e_acc[r0 + threadIdx.x], s);
+        e_acc[(size_t)blockIdx.y * Rp + r0 + threadIdx.x] += s;
     }
 }
 
@@ -250,8 +252,11 @@ __global__ void __launch_bounds__(256) k_adj_post(const float* __restrict__ J, i
             a += (double)redA[k][threadIdx.x];
             t += (double)redT[k][threadIdx.x];
         }
-        if (CONTROL) atomicAdd(&gA[r0 + threadIdx.x], a);
-        atomicAdd(&gdt[r0 + threadIdx.x], t);
+        // one slot per block row and replica, each written by one block a step
+        // (stream order between steps): no atomics, a fixed order of additions
+        const size_t slot = (size_t)blockIdx.y * Rp + r0 + threadIdx.x;
+        if (CONTROL) gA[slot] += a;
+        gdt[slot] += t;
     }
 }
 
@@ -274,13 +279,21 @@ __global__ void k_fill(float* p, float v, size_t n) {
     if (k < n) p[k] = v;
 }
 
+// The per-block-row sums added in block-row order.
 __global__ void k_finish(const double* e_acc, double* E, const double* gA, double* gA_out,
-                         const double* gdt, double* gdt_out, int R) {
+                         const double* gdt, double* gdt_out, int R, int Rp, int nby) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    E[r] = -0.5 * e_acc[r];
-    if (gA_out) gA_out[r] = gA[r];
-    if (gdt_out) gdt_out[r] = gdt[r];
+    double e = 0.0, a = 0.0, t = 0.0;
+    for (int b = 0; b < nby; ++b) {
+        const size_t o = (size_t)b * Rp + r;
+        e += e_acc[o];
+        a += gA[o];
+        t += gdt[o];
+    }
+    E[r] = -0.5 * e;
+    if (gA_out) gA_out[r] = a;
+    if (gdt_out) gdt_out[r] = t;
 }
 
 struct SplitGemmGuard {
@@ -344,8 +357,8 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
         (st = B.alloc(&sy, nst * (K + 1))) || (st = B.alloc(&sp, nst * (K + 1))) ||
         (st = B.alloc(&syt, nst * K)) || (st = B.alloc(&lx, nst)) || (st = B.alloc(&ly, nst)) ||
         (st = B.alloc(&lp, nst)) || (st = B.alloc(&lf, nst)) || (st = B.alloc(&Ad, Rp)) ||
-        (st = B.alloc(&tmp, nst)) || (st = B.alloc(&e_acc, Rp)) || (st = B.alloc(&gA, Rp)) ||
-        (st = B.alloc(&gdt, Rp)))
+        (st = B.alloc(&tmp, nst)) || (st = B.alloc(&e_acc, (size_t)Np / 64 * Rp)) ||
+        (st = B.alloc(&gA, (size_t)Np / 64 * Rp)) || (st = B.alloc(&gdt, (size_t)Np / 64 * Rp)))
         return st;
     {
         std::vector<float> Ah(Rp, 0.f);
@@ -354,9 +367,10 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
         GSB_CUDA_TRY(cudaStreamSynchronize(s));
     }
     call_prof_reset();
-    GSB_CUDA_TRY(cudaMemsetAsync(e_acc, 0, sizeof(double) * Rp, s));
-    GSB_CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * Rp, s));
-    GSB_CUDA_TRY(cudaMemsetAsync(gdt, 0, sizeof(double) * Rp, s));
+    // per-block-row sums: at most Np / 64 block rows (64-row tiles)
+    GSB_CUDA_TRY(cudaMemsetAsync(e_acc, 0, sizeof(double) * Rp * (Np / 64), s));
+    GSB_CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * Rp * (Np / 64), s));
+    GSB_CUDA_TRY(cudaMemsetAsync(gdt, 0, sizeof(double) * Rp * (Np / 64), s));
     // initial state into segment slot 0
     k_rm_to_sm<<<dim3(Np / 32, Rp / 32), dim3(32, 8), 0, s>>>(x0, sx, N, R, Rp);
     GSB_LAUNCH_CHECK("k_rm_to_sm");
@@ -508,7 +522,8 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
             if ((st = call_prof_end(s, 1))) return st;
         }
     }
-    k_finish<<<(R + 255) / 256, 256, 0, s>>>(e_acc, energy, gA, grad_A, gdt, grad_dt, R);
+    k_finish<<<(R + 255) / 256, 256, 0, s>>>(e_acc, energy, gA, grad_A, gdt, grad_dt, R, Rp,
+                                             (int)grid.y);
     GSB_LAUNCH_CHECK("k_finish");
     if (grad_x0) {
         st = launch_transpose_to_host_layout(lx, grad_x0, Np, Rp, N, R, s);

@@ -60,10 +60,10 @@ __global__ void __launch_bounds__(256) k_dense_f32_step(
     }
 }
 
-// e_acc[r] += sum_i s_i (J s)_i over this tile's 128 spins (s = sgn x).
+// part[b][r] = sum_i s_i (J s)_i over the 128 spins of row block b (s = sgn x).
 __global__ void __launch_bounds__(256) k_dense_f32_energy(const float* __restrict__ J, int Np,
                                                           int Rp, const float* __restrict__ x,
-                                                          double* __restrict__ e_acc) {
+                                                          double* __restrict__ part) {
     __shared__ __align__(16) F32Smem sm;
     __shared__ float red[16][BN + 1];
     const int i0 = blockIdx.y * BM, r0 = blockIdx.x * BN;
@@ -85,8 +85,18 @@ __global__ void __launch_bounds__(256) k_dense_f32_energy(const float* __restric
     if (threadIdx.x < BN) {
         double s = 0.0;
         for (int t = 0; t < 16; ++t) s += (double)red[t][threadIdx.x];
-        atomicAdd(&e_acc[r0 + threadIdx.x], s);
+        part[(size_t)blockIdx.y * Rp + r0 + threadIdx.x] = s;
     }
+}
+
+// e_acc[r] += the row blocks' partials, in row-block order.
+__global__ void k_energy_parts_sum(const double* __restrict__ part, int nblk, int Rp,
+                                   double* __restrict__ e_acc) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Rp) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * Rp + r];
+    e_acc[r] += s;
 }
 
 }  // namespace
@@ -113,10 +123,12 @@ gsb_status launch_dense_f32_step(gsb_run_state* run, const StepScalars& sc) {
 }
 
 gsb_status launch_dense_f32_energy(const gsb_problem* P, const float* x, int Rp, double* e_acc,
-                                   cudaStream_t s) {
+                                   double* e_part, cudaStream_t s) {
     dim3 grid(Rp / BN, P->Np / BM);
-    k_dense_f32_energy<<<grid, 256, 0, s>>>(P->J32, P->Np, Rp, x, e_acc);
+    k_dense_f32_energy<<<grid, 256, 0, s>>>(P->J32, P->Np, Rp, x, e_part);
     GSB_LAUNCH_CHECK("k_dense_f32_energy");
+    k_energy_parts_sum<<<(Rp + 255) / 256, 256, 0, s>>>(e_part, P->Np / BM, Rp, e_acc);
+    GSB_LAUNCH_CHECK("k_energy_parts_sum");
     return GSB_OK;
 }
 

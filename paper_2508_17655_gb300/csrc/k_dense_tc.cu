@@ -1882,7 +1882,8 @@ gsb_status tc_energy(gsb_run_state* run, int step) {
         GSB_LAUNCH_CHECK("k_tc_energy");
         return GSB_OK;
     }
-    return launch_dense_f32_energy(run->prob, run->x[0], run->Rp, run->e_acc, run->stream);
+    return launch_dense_f32_energy(run->prob, run->x[0], run->Rp, run->e_acc, run->e_part,
+                                   run->stream);
 }
 
 void tc_free(gsb_run_state* run) {

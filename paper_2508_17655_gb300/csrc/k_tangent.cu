@@ -88,11 +88,12 @@ __global__ void k_tangent_init(float* x, float* y, float* p, int N, int R, int N
     if (p) p[o] = tangent ? 0.f : 1.f;
 }
 
-// nrm2[r] += sum over a block of rows of dx^2 + dy^2 + dp^2.
+// part[b][r] = sum over row block b (kNormRows rows) of dx^2 + dy^2 + dp^2, in
+// FP64; the blocks are added in order by k_tangent_log (deterministic).
 constexpr int kNormRows = 64;
 __global__ void k_tangent_norm(const float* __restrict__ x, const float* __restrict__ y,
                                const float* __restrict__ p, int N, int C, int R,
-                               double* __restrict__ nrm2) {
+                               double* __restrict__ part) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const int i0 = blockIdx.y * kNormRows;
@@ -103,17 +104,18 @@ __global__ void k_tangent_norm(const float* __restrict__ x, const float* __restr
         const double a = x[o], b = y[o], d = p ? p[o] : 0.f;
         s += a * a + b * b + d * d;
     }
-    atomicAdd(&nrm2[r], s);
+    part[(size_t)blockIdx.y * R + r] = s;
 }
 
-__global__ void k_tangent_log(double* __restrict__ nrm2, double* __restrict__ log_sum,
-                              float* __restrict__ scale, int R, int accumulate) {
+__global__ void k_tangent_log(const double* __restrict__ part, int nblk,
+                              double* __restrict__ log_sum, float* __restrict__ scale, int R,
+                              int accumulate) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    const double s2 = nrm2[r];
+    double s2 = 0.0;
+    for (int b = 0; b < nblk; ++b) s2 += part[(size_t)b * R + r];
     if (accumulate) log_sum[r] += 0.5 * log(s2);
     scale[r] = s2 > 0.0 ? (float)(1.0 / sqrt(s2)) : 0.f;
-    nrm2[r] = 0.0;
 }
 
 __global__ void k_tangent_scale(float* x, float* y, float* p, int N, int C, int R,
@@ -207,24 +209,25 @@ extern "C" gsb_status gsb_lyapunov(gsb_problem* P, const gsb_params* prm, int32_
     GSB_CUDA_TRY(cudaMalloc(&B.y, nst * sizeof(float)));
     if (control) GSB_CUDA_TRY(cudaMalloc(&B.p, nst * sizeof(float)));
     GSB_CUDA_TRY(cudaMalloc(&B.A, Rq * sizeof(float)));
-    GSB_CUDA_TRY(cudaMalloc(&B.nrm2, Rq * sizeof(double)));
+    const int nblk = (P->N + kNormRows - 1) / kNormRows;
+    GSB_CUDA_TRY(cudaMalloc(&B.nrm2, (size_t)nblk * R * sizeof(double)));
     GSB_CUDA_TRY(cudaMalloc(&B.log_sum, Rq * sizeof(double)));
     GSB_CUDA_TRY(cudaMalloc(&B.scale, Rq * sizeof(float)));
     std::vector<float> Ah(Rq, 0.f);
     for (int k = 0; k < nA; ++k)
         for (int r = 0; r < Q.R; ++r) Ah[(size_t)k * Q.R + r] = A_values[k];
     GSB_CUDA_TRY(cudaMemcpyAsync(B.A, Ah.data(), Rq * sizeof(float), cudaMemcpyHostToDevice, s));
-    GSB_CUDA_TRY(cudaMemsetAsync(B.nrm2, 0, Rq * sizeof(double), s));
     GSB_CUDA_TRY(cudaMemsetAsync(B.log_sum, 0, Rq * sizeof(double), s));
     const uint2 key = make_uint2((uint32_t)Q.seed, (uint32_t)(Q.seed >> 32));
     k_tangent_init<<<dim3((C + 127) / 128, Np), 128, 0, s>>>(
         B.x[0], B.y, B.p, P->N, R, Np, C, key, range * 1.1920928955078125e-07f, Q.y0_uniform);
     GSB_LAUNCH_CHECK("k_tangent_init");
     auto renorm = [&](int cur, int accumulate) -> gsb_status {
-        k_tangent_norm<<<dim3((R + 127) / 128, (P->N + kNormRows - 1) / kNormRows), 128, 0, s>>>(
-            B.x[cur], B.y, B.p, P->N, C, R, B.nrm2);
+        k_tangent_norm<<<dim3((R + 127) / 128, nblk), 128, 0, s>>>(B.x[cur], B.y, B.p, P->N, C, R,
+                                                                  B.nrm2);
         GSB_LAUNCH_CHECK("k_tangent_norm");
-        k_tangent_log<<<(R + 255) / 256, 256, 0, s>>>(B.nrm2, B.log_sum, B.scale, R, accumulate);
+        k_tangent_log<<<(R + 255) / 256, 256, 0, s>>>(B.nrm2, nblk, B.log_sum, B.scale, R,
+                                                      accumulate);
         GSB_LAUNCH_CHECK("k_tangent_log");
         k_tangent_scale<<<dim3((R + 127) / 128, P->N), 128, 0, s>>>(B.x[cur], B.y, B.p, P->N, C,
                                                                     R, B.scale);
