@@ -53,7 +53,7 @@ constexpr int kStagesM = 3;
 constexpr int kStageBytesM = 4 * kAtom;  // J_hi, J_lo, V_hi, V_lo
 constexpr int kSmemM = 1024 + kStagesM * kStageBytesM + 256;
 
-struct alignas(64) MInst {
+struct MInst {  // aligned as its CUtensorMap members require
     CUtensorMap tmJ[2];  // J_hi, J_lo: [Np][Np] bf16, boxes of 64 elements x 128 rows
     CUtensorMap tmV[2];  // V(t_m), m even / odd: [planes x Rp][Np] bf16, same boxes
     float* x;
