@@ -143,11 +143,11 @@ def test_adjoint_well_conditioned_within_1e4(variant, precision):
     if precision == "bf16x3" and not sign:
         # the split's residues (up to 3 x 2^-18 of each product's magnitude) in
         # each of the W forward, W recomputed and W reverse products: W 2^-15
-        # for the gradients; E, one product of x(t_W) with J x(t_W), within
-        # 2^-14 of its terms' magnitude (kappa x 2^-14 of E). The sgn
-        # coupling is exact on J_hi + J_lo: the FP32 bar.
+        # for the gradients and for E's trajectory; E's last product of x(t_W)
+        # with J x(t_W) also within 2^-14 of its terms' magnitude (kappa x
+        # 2^-14 of E). The sgn coupling is exact on J_hi + J_lo: the FP32 bar.
         kappa = _energy_cancellation(Jd, run["x"])
-        base = (np.maximum(1e-4, kappa * 2.0 ** -14),) + (W * 2.0 ** -15,) * 3
+        base = (np.maximum(W * 2.0 ** -15, kappa * 2.0 ** -14),) + (W * 2.0 ** -15,) * 3
     _check(got, want, zero, ok, f"{variant} {precision}", base=base, factor=0.0)
 
 
@@ -285,3 +285,30 @@ def test_adjoint_rejects_other_forms():
     with pytest.raises(gsb.GsbError) as e:
         _gpu_grad(gsb.Problem.dense(J), "gbsb", 100, 5, x0, 0.2, 0.9, 0.5, precision="fp8")
     assert e.value.status == gsb.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("N", [1, 2, 129])
+def test_adjoint_degenerate_and_edge_sizes(N, precision):
+    """N = 1 (no coupling), N = 2 and N = 129 (one spin past a tile), 5
+    replicas, a 10-step window from small x0 (no wall event): E, dE/dx0,
+    dE/dA, dE/ddt within 1e-4 relative of the FP64 oracle (the split form
+    against the oracle on J_hi + J_lo, with its W 2^-15 floor for the x
+    coupling)."""
+    J = I.sk_gauss(N, 6) if N > 1 else np.zeros((1, 1), np.float32)
+    R, M, W = 5, 300, 10
+    c, dt = 0.5, f32(0.8)
+    A = np.linspace(0.1, 0.3, R).astype(np.float32)
+    x0 = O.init_uniform(R, N, 7, rng=0.02)
+    got = _gpu_grad(gsb.Problem.dense(J), "gbsb", M, W, x0, A, dt, c, precision=precision)
+    Jd = _oracle_J(J, precision)
+    want = O.relaxed_energy_grad(Jd, "gbsb", x0, c=c, dt=dt, M=M, W=W, A=A.astype(np.float64))
+    base = W * 2.0 ** -15 if precision == "bf16x3" else 1e-4
+    if N > 1 and precision == "bf16x3":
+        # as in the well-conditioned test: W 2^-15 for the trajectory, kappa
+        # 2^-14 for E's last product
+        run = O.run(Jd, "gbsb", x0, 0 * x0, c=c, dt=dt, M=M, A=A.astype(np.float64), nsteps=W)
+        kappa = _energy_cancellation(Jd, run["x"])
+        base = (np.maximum(base, kappa * 2.0 ** -14),) + (base,) * 3
+    _check(got, want, (np.zeros(R),) * 4, np.ones(R, bool), f"N={N} {precision}", base=base,
+           factor=0.0)

@@ -199,3 +199,23 @@ def test_lyapunov_bf16x3_agrees_with_fp32_and_rejects_other_forms():
     with pytest.raises(gsb.GsbError) as e:
         P.lyapunov("gbsb", M, R, [0.0], precision="fp8", **kw)
     assert e.value.status == gsb.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("N", [1, 2, 129])
+def test_lyapunov_degenerate_and_edge_sizes(N, precision):
+    """N = 1 (no coupling at all), N = 2 and N = 129 (one spin past a tile),
+    3 replicas, 30 steps: the exponents match the oracle's within 1e-4 (the
+    split form against the oracle on J_hi + J_lo), replicas with a near-tie
+    decision excused."""
+    J = I.sk_gauss(N, 3) if N > 1 else np.zeros((1, 1), np.float32)
+    R, M, n = 3, 500, 30
+    c, dt = 0.5, f32(0.9)
+    got = gsb.Problem.dense(J).lyapunov("gbsb", M, R, [0.2], c=c, dt=dt, seed=5, renorm_every=10,
+                                        nsteps=n, precision=precision).ravel()
+    Jo = bf16_split_sum(J) if precision == "bf16x3" else J.astype(np.float64)
+    want, margin = _oracle_mle(Jo, "gbsb", R, N, 5, np.full(R, 0.2), c, dt, M, n, 10)
+    ok = margin >= NEAR_TIE[precision]
+    assert np.array_equal(np.isneginf(got[ok]), np.isneginf(want[ok]))
+    fin = ok & np.isfinite(want)
+    assert np.all(np.abs(got[fin] - want[fin]) <= 1e-4), (got, want)
