@@ -33,13 +33,15 @@ namespace {
 using namespace f32;
 
 // MODE selects how a kernel gets its SGEMM: 128 or 64 -- a fused T x T tile;
-// kSplitK -- 64 x 64 tiles whose K is split kSplitK ways by k_adj_gemm_part
-// (more CTAs when few replicas leave SMs idle), the kernel adding the partial
-// sums in a fixed order (deterministic: a recomputed step is bit-identical).
+// kSplitK -- the products' K split kSplitK ways (by k_adj_gemm_part on CUDA
+// cores or k_gemm_tc on the tensor cores; more CTAs when few replicas leave
+// SMs idle), the step kernel adding the partial sums in a fixed order
+// (deterministic: a recomputed step is bit-identical) over 32 x 32 tiles,
+// four times as many blocks as 64 x 64 ones (the kernel only streams memory).
 constexpr int kSplitK = 4;
 template <int MODE>
 struct Mode {
-    static constexpr int T = MODE == 128 ? 128 : 64;
+    static constexpr int T = MODE == 128 ? 128 : (MODE == 64 ? 64 : 32);
     static constexpr bool split = MODE == kSplitK;
 };
 
@@ -72,18 +74,19 @@ __device__ __forceinline__ void adj_gemm(const float* J, const float* X, int Np,
     if constexpr (!Mode<MODE>::split) {
         TT::template gemm<SIGN>(J, X, Np, Rp, i0, r0, acc, sm);
     } else {
+        static_assert(TT::NB == 2, "the split mode's tile holds two replicas a thread");
         const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
         const size_t nst = (size_t)Np * Rp;
 #pragma unroll
         for (int a = 0; a < TT::NA; ++a) {
             const size_t o = (size_t)(i0 + TT::row(a, ty)) * Rp + r0 + TT::col(0, tx);
-            float4 v = *reinterpret_cast<const float4*>(Fp + o);
+            float2 v = *reinterpret_cast<const float2*>(Fp + o);
 #pragma unroll
             for (int sl = 1; sl < kSplitK; ++sl) {
-                const float4 w = *reinterpret_cast<const float4*>(Fp + sl * nst + o);
-                v.x += w.x, v.y += w.y, v.z += w.z, v.w += w.w;
+                const float2 w = *reinterpret_cast<const float2*>(Fp + sl * nst + o);
+                v.x += w.x, v.y += w.y;
             }
-            acc[a][0] = v.x, acc[a][1] = v.y, acc[a][2] = v.z, acc[a][3] = v.w;
+            acc[a][0] = v.x, acc[a][1] = v.y;
         }
     }
 }
@@ -357,8 +360,8 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
         (st = B.alloc(&sy, nst * (K + 1))) || (st = B.alloc(&sp, nst * (K + 1))) ||
         (st = B.alloc(&syt, nst * K)) || (st = B.alloc(&lx, nst)) || (st = B.alloc(&ly, nst)) ||
         (st = B.alloc(&lp, nst)) || (st = B.alloc(&lf, nst)) || (st = B.alloc(&Ad, Rp)) ||
-        (st = B.alloc(&tmp, nst)) || (st = B.alloc(&e_acc, (size_t)Np / 64 * Rp)) ||
-        (st = B.alloc(&gA, (size_t)Np / 64 * Rp)) || (st = B.alloc(&gdt, (size_t)Np / 64 * Rp)))
+        (st = B.alloc(&tmp, nst)) || (st = B.alloc(&e_acc, (size_t)Np / 32 * Rp)) ||
+        (st = B.alloc(&gA, (size_t)Np / 32 * Rp)) || (st = B.alloc(&gdt, (size_t)Np / 32 * Rp)))
         return st;
     {
         std::vector<float> Ah(Rp, 0.f);
@@ -367,10 +370,10 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
         GSB_CUDA_TRY(cudaStreamSynchronize(s));
     }
     call_prof_reset();
-    // per-block-row sums: at most Np / 64 block rows (64-row tiles)
-    GSB_CUDA_TRY(cudaMemsetAsync(e_acc, 0, sizeof(double) * Rp * (Np / 64), s));
-    GSB_CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * Rp * (Np / 64), s));
-    GSB_CUDA_TRY(cudaMemsetAsync(gdt, 0, sizeof(double) * Rp * (Np / 64), s));
+    // per-block-row sums: at most Np / 32 block rows (32-row tiles)
+    GSB_CUDA_TRY(cudaMemsetAsync(e_acc, 0, sizeof(double) * Rp * (Np / 32), s));
+    GSB_CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * Rp * (Np / 32), s));
+    GSB_CUDA_TRY(cudaMemsetAsync(gdt, 0, sizeof(double) * Rp * (Np / 32), s));
     // initial state into segment slot 0
     k_rm_to_sm<<<dim3(Np / 32, Rp / 32), dim3(32, 8), 0, s>>>(x0, sx, N, R, Rp);
     GSB_LAUNCH_CHECK("k_rm_to_sm");
@@ -388,7 +391,7 @@ extern "C" gsb_status gsb_relaxed_energy_grad(gsb_problem* P, const gsb_params* 
     const int mode = tensor ? kSplitK
                             : (long)(Rp / 128) * (Np / 128) >= sms ? 128
                                                                    : (tiles64 >= 2L * sms ? 64 : kSplitK);
-    const int T = mode == 128 ? 128 : 64;
+    const int T = mode == 128 ? 128 : (mode == 64 ? 64 : 32);
     const dim3 grid(Rp / T, Np / T);
     float* Fp = nullptr;  // split-K partial sums
     if (mode == kSplitK && (st = B.alloc(&Fp, kSplitK * nst))) return st;

@@ -175,5 +175,16 @@ struct Tile<64> {
     }
 };
 
+// 32 x 32 elementwise tile (no SGEMM of its own: for kernels whose products
+// come precomputed, e.g. as K-split partial sums): 16 x 16 threads, 2 x 2
+// elements each (two consecutive replicas of two consecutive rows).
+template <>
+struct Tile<32> {
+    static constexpr int NA = 2, NB = 2;
+    struct Smem {};
+    __device__ static int row(int a, int ty) { return ty * 2 + a; }
+    __device__ static int col(int b, int tx) { return tx * 2 + b; }
+};
+
 }  // namespace f32
 }  // namespace gsb
