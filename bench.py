@@ -48,7 +48,7 @@ KNOWN_TRAFFIC = {
     # profiles/k_tc_persist_N2000_R1024_M100.md (the 112-spin grid form, 144 CTAs)
     "k_tc_persist<grid112>": 31082752 + 1356288,
     # profiles/k_fx16_persist_N2000_R1024_M100.md
-    "k_fx16_persist": 37800192 + 2225152,
+    "k_fx16_persist": 37800960 + 2204160,
 }
 
 
