@@ -29,6 +29,24 @@ def spins(x):
     return np.where(np.asarray(x) >= 0, 1, -1).astype(np.int8)
 
 
+def bf16_rne(a):
+    """FP32 values rounded to bf16 (8 significant bits) to nearest, ties to even,
+    returned as FP32: add just under half an ulp plus the kept part's lowest
+    bit to the bit pattern and clear the low 16 bits (finite inputs)."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).reshape(np.shape(a))
+
+
+def bf16_split_sum(J):
+    """J_hi + J_lo in FP64 with J_hi = bf16(J) and J_lo = bf16(J - J_hi): the
+    matrix whose products the split-bf16 form computes (its sgn-coupled
+    products exactly, up to FP32 accumulation)."""
+    hi = bf16_rne(J)
+    lo = bf16_rne(np.asarray(J, dtype=np.float32) - hi)
+    return hi.astype(np.float64) + lo.astype(np.float64)
+
+
 # A replica whose oracle trajectory put a wall test or a sign within this
 # distance of its threshold may legitimately take the other branch in FP32.
 TIE_MARGIN = 2e-6

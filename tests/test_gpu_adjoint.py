@@ -7,6 +7,7 @@ import pytest
 
 import oracle as O
 from paper_2508_17655_gb300 import gsb, inputs as I
+from tests._parity import bf16_split_sum
 
 pytestmark = pytest.mark.gpu
 
@@ -86,28 +87,15 @@ def _check(got, want, sens, ok, what, base=1e-4, factor=200.0):
         assert not bad.any(), (f"{what} {name}: errors {err[bad]} vs tolerances {tol[bad]}")
 
 
-def bf16_split_sum(J):
-    """J_hi + J_lo in FP64, J_hi = bf16(J) and J_lo = bf16(J - J_hi) rounded to
-    nearest even: the matrix whose products the split-bf16 form computes (its
-    sgn-coupled products exactly, up to FP32 accumulation)."""
-    def rne(a):
-        b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
-        r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
-        return r.astype(np.uint32).view(np.float32)
-    hi = rne(J)
-    lo = rne(J.astype(np.float32) - hi)
-    return hi.astype(np.float64) + lo.astype(np.float64)
-
-
 def _oracle_J(J, precision):
     return bf16_split_sum(J) if precision == "bf16x3" else J.astype(np.float64)
 
 
-# The split form's x coupling: each product J x carries three residues of up
-# to 2^-18 of its magnitude sum_j |J_ij x_j| (x_lo and J_lo rounded, J_lo x_lo
-# dropped) where FP32 carries one rounding of 2^-24: 3 x 2^6 ~ 2^7.6, so 2^8
-# times the FP32 bars that scale with the rounding.
-SPLIT_RATIO = 2.0 ** 8
+# The split form's x coupling against the oracle on J_hi + J_lo: each product
+# J x differs by J_hi (x - x_hi - x_lo) + J_lo x_lo + ..., at most about
+# 2^-17 + 2^-16 < 2^-15 of its magnitude sum_j |J_ij x_j|, where FP32 carries
+# one rounding of 2^-24: 2^9 times the FP32 bars that scale with the rounding.
+SPLIT_RATIO = 2.0 ** 9
 
 
 def _energy_cancellation(Jd, x):
@@ -141,13 +129,14 @@ def test_adjoint_well_conditioned_within_1e4(variant, precision):
     zero = (np.zeros(R),) * 4
     base = 1e-4
     if precision == "bf16x3" and not sign:
-        # the split's residues (up to 3 x 2^-18 of each product's magnitude) in
-        # each of the W forward, W recomputed and W reverse products: W 2^-15
-        # for the gradients and for E's trajectory; E's last product of x(t_W)
-        # with J x(t_W) also within 2^-14 of its terms' magnitude (kappa x
-        # 2^-14 of E). The sgn coupling is exact on J_hi + J_lo: the FP32 bar.
+        # each product carries up to 2^-15 of its magnitude (SPLIT_RATIO): the
+        # gradients W 2^-14 (W forward and W reverse products; the recompute
+        # repeats the forward bit for bit); E its trajectory's W 2^-15 plus its
+        # last product's 2^-15 of its terms' magnitude (kappa 2^-15 of E),
+        # bounded by 2^-14 max(W, kappa). The sgn coupling is exact on
+        # J_hi + J_lo: the FP32 bar.
         kappa = _energy_cancellation(Jd, run["x"])
-        base = (np.maximum(W * 2.0 ** -15, kappa * 2.0 ** -14),) + (W * 2.0 ** -15,) * 3
+        base = (2.0 ** -14 * np.maximum(W, kappa),) + (W * 2.0 ** -14,) * 3
     _check(got, want, zero, ok, f"{variant} {precision}", base=base, factor=0.0)
 
 
@@ -158,7 +147,7 @@ def test_adjoint_matches_oracle_small(variant, precision):
     gradient's sensitivity to a 2^-24 relative perturbation of x0); the
     split-bf16 form against the oracle on J_hi + J_lo, its x coupling also
     splitting x, so SPLIT_RATIO x the sensitivity term and a floor of
-    W 2^-15 (as in the well-conditioned test)."""
+    W 2^-14 (as in the well-conditioned test)."""
     N, R, M, W = 300, 70, 400, 60
     J = I.sk_gauss(N, 13)
     c, dt = 0.5, f32(0.8)
@@ -176,7 +165,7 @@ def test_adjoint_matches_oracle_small(variant, precision):
     assert ok.sum() >= 2
     split_x = precision == "bf16x3" and not sign
     factor = 200.0 * (SPLIT_RATIO if split_x else 1.0)
-    _check(got, want, sens, ok, f"{variant} {precision}", base=W * 2.0 ** -15 if split_x else 1e-4,
+    _check(got, want, sens, ok, f"{variant} {precision}", base=W * 2.0 ** -14 if split_x else 1e-4,
            factor=factor)
 
 
@@ -293,8 +282,8 @@ def test_adjoint_degenerate_and_edge_sizes(N, precision):
     """N = 1 (no coupling), N = 2 and N = 129 (one spin past a tile), 5
     replicas, a 10-step window from small x0 (no wall event): E, dE/dx0,
     dE/dA, dE/ddt within 1e-4 relative of the FP64 oracle (the split form
-    against the oracle on J_hi + J_lo, with its W 2^-15 floor for the x
-    coupling)."""
+    against the oracle on J_hi + J_lo, with the bars of the well-conditioned
+    test)."""
     J = I.sk_gauss(N, 6) if N > 1 else np.zeros((1, 1), np.float32)
     R, M, W = 5, 300, 10
     c, dt = 0.5, f32(0.8)
@@ -303,12 +292,11 @@ def test_adjoint_degenerate_and_edge_sizes(N, precision):
     got = _gpu_grad(gsb.Problem.dense(J), "gbsb", M, W, x0, A, dt, c, precision=precision)
     Jd = _oracle_J(J, precision)
     want = O.relaxed_energy_grad(Jd, "gbsb", x0, c=c, dt=dt, M=M, W=W, A=A.astype(np.float64))
-    base = W * 2.0 ** -15 if precision == "bf16x3" else 1e-4
+    base = W * 2.0 ** -14 if precision == "bf16x3" else 1e-4
     if N > 1 and precision == "bf16x3":
-        # as in the well-conditioned test: W 2^-15 for the trajectory, kappa
-        # 2^-14 for E's last product
+        # the bars of the well-conditioned test
         run = O.run(Jd, "gbsb", x0, 0 * x0, c=c, dt=dt, M=M, A=A.astype(np.float64), nsteps=W)
         kappa = _energy_cancellation(Jd, run["x"])
-        base = (np.maximum(base, kappa * 2.0 ** -14),) + (base,) * 3
+        base = (2.0 ** -14 * np.maximum(W, kappa),) + (base,) * 3
     _check(got, want, (np.zeros(R),) * 4, np.ones(R, bool), f"N={N} {precision}", base=base,
            factor=0.0)
