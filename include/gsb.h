@@ -84,8 +84,9 @@ typedef enum gsb_precision {
                             coupling accumulated in FP32 as J_hi x_hi + J_hi x_lo +
                             J_lo x_hi (J_hi s + J_lo s for sgn x, which is exact in
                             bf16). Each product is exact; the error against FP64 is
-                            the split's 2^-16-level residue (about 2^-15 of
-                            sum_j |J_ij v_j| at most) plus FP32 accumulation. One
+                            at most about 3 2^-16 of sum_j |J_ij v_j| (the two
+                            splits' residues, 2^-17 each, and the J_lo x_lo term
+                            left out, up to 2^-16) plus FP32 accumulation. One
                             persistent launch runs the steps between energy
                             evaluations. Not in the paper, whose machine computes J x
                             in 16-bit fixed point (Sec. VI) */
@@ -291,7 +292,7 @@ gsb_status gsb_run_destroy(gsb_run_state* run);
  * receives sum(log norms) / (nsteps dt), accumulated in FP64. Dense problems.
  * params->precision: GSB_PREC_AUTO or GSB_PREC_FP32, the FP32 coupling on CUDA
  * cores; GSB_PREC_BF16X3, J x and J dx on the tensor cores in the split-bf16
- * form (error against FP64 at the 2^-16 level of the coupling's magnitude);
+ * form (error against FP64 up to about 3 2^-16 of the coupling's magnitude);
  * any other: GSB_EUNSUPPORTED. Blocks on `stream`. */
 gsb_status gsb_lyapunov(gsb_problem* problem, const gsb_params* params, int32_t nA,
                         const float* A_values, int32_t renorm_every, int32_t nsteps,
@@ -331,7 +332,7 @@ gsb_status gsb_twin_delta(gsb_run_state* run, double* delta_out);
  * Dense problems without h, FP32 arithmetic. params->precision: GSB_PREC_AUTO or
  * GSB_PREC_FP32, the products J v as FP32 SGEMMs on CUDA cores; GSB_PREC_BF16X3,
  * as K-split partial products on the tensor cores in the split-bf16 form (J and
- * v split into bf16 hi + lo terms; error at the 2^-16 level of the coupling's
+ * v split into bf16 hi + lo terms; error up to about 3 2^-16 of the coupling's
  * magnitude); any other: GSB_EUNSUPPORTED. Blocks on `stream`. */
 gsb_status gsb_relaxed_energy_grad(gsb_problem* problem, const gsb_params* params,
                                    int32_t window, int32_t ckpt_every, const float* x0,

@@ -5,10 +5,11 @@
 // term the bf16 rounding of what the terms before it leave, so every pair
 // holds 16 significant bits. The coupling F = J v is accumulated in FP32 in
 // TMEM as J_hi x_hi + J_hi x_lo + J_lo x_hi (three tcgen05 kind::f16 MMAs per
-// K slice; the J_lo x_lo term is below the representation error of the
-// split), and J_hi s + J_lo s for the sgn coupling, whose +-1 operand is exact
-// in bf16. Each product is exact; the error against FP64 is the 2^-16-level
-// split residue plus the tensor core's FP32 accumulation.
+// K slice; the J_lo x_lo term, at most 2^-16 of |J_ij x_j|, is left out), and
+// J_hi s + J_lo s for the sgn coupling, whose +-1 operand is exact in bf16.
+// Each product is exact; the error against FP64 is at most about 3 2^-16 of
+// sum_j |J_ij v_j| (the two splits' residues, 2^-17 each, and the term left
+// out) plus the tensor core's FP32 accumulation.
 //
 // One kernel serves a single run and a batch of instances: it walks a work
 // list of items (step, tile), a tile being 128 spins x 128 replicas of one

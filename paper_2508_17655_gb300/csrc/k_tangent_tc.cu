@@ -7,8 +7,9 @@
 // before it leave), F = J x is accumulated in FP32 in TMEM as
 // J_hi x_hi + J_hi x_lo + J_lo x_hi (three tcgen05 kind::f16 MMAs per K
 // slice) and G = J dx alike; the sgn coupling takes J_hi s + J_lo s for F (s
-// is exact in bf16) and has no J dx term. The error against FP64 is the
-// 2^-16-level split residue plus the FP32 accumulation.
+// is exact in bf16) and has no J dx term. The error against FP64 is at most
+// about 3 2^-16 of each product's magnitude sum_j |J_ij v_j| (the splits'
+// residues and the J_lo v_lo term left out) plus the FP32 accumulation.
 //
 // One launch per time step. The tiles of a step (128 spins x 128 replicas)
 // do not wait on one another -- each reads the step's operand planes and
