@@ -82,6 +82,18 @@ def rank_seed(rank):
     return 1000 * rank
 
 
+def clocks_rejected(clocks):
+    """True when a timed region's clock record disqualifies its number: a
+    hardware or thermal slowdown was active, or the median SM clock sat well
+    below its maximum with no reason given (a clock lock left behind by
+    another user). sw_power_cap alone keeps the number (it is noted)."""
+    reasons = set(clocks.get("reasons", [])) - {"no samples"}
+    if reasons & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}:
+        return True
+    sm, mx = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    return sm is not None and bool(mx) and sm < 0.9 * mx and not reasons
+
+
 def job_time_and_value(total_ms, units_per_rank, world, device=None):
     """Whole-job figures from one rank's timed total: the slowest rank's time
     (max over ranks, the only collective) and all ranks' units over it."""
@@ -262,11 +274,23 @@ def gpu_arm(args, world, rank, local):
         run.close()
         return times, (kern_ms, kern_n, kern_steps), np.concatenate(energies), launches, kernel
 
-    # headline: GdSB on FP8 tensor cores
-    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0)) as clk:
-        times, (kern_ms, kern_n, kern_steps), energies, launches, kernel_name = timed_runs(
-            "gdsb", "fp8", args.steps, args.warmup, rank_seed(rank))
-    clocks = clk.summary()
+    # headline: GdSB on FP8 tensor cores; a measurement whose clock record
+    # disqualifies it (on any rank) is taken once more
+    first = None
+    for attempt in range(2):
+        with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0)) as clk:
+            times, (kern_ms, kern_n, kern_steps), energies, launches, kernel_name = timed_runs(
+                "gdsb", "fp8", args.steps, args.warmup, rank_seed(rank) + 17 * attempt)
+        clocks = clk.summary()
+        bad = torch.tensor([1.0 if clocks_rejected(clocks) else 0.0], device=dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(bad, op=dist.ReduceOp.MAX)
+        if attempt == 1 or bad.item() == 0.0:
+            break
+        first = clocks
+    if first is not None:
+        clocks["remeasured_after"] = first
     total_ms, value = job_time_and_value(sum(times), N_SPINS * R_REPLICAS * M_STEPS * args.steps,
                                          world, dev)
     ms_per_step = total_ms / args.steps
