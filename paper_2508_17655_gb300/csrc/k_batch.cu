@@ -204,8 +204,9 @@ gsb_status batch_bf16(int n, gsb_problem* const* problems, const gsb_params* par
     GSB_CUDA_TRY(cudaStreamSynchronize(s));
     call_prof_reset();
     const int force = info ? info->force_tiles_per_cta : 0;
-    // Window budgets the autotuner tries: tiles per CTA per step, and the MB of
-    // working set (J, state, V) a window may hold -- within the 129 MB L2 it
+    // Window budgets the autotuner tries, in this order until one is slower than
+    // the one before: tiles per CTA per step (1: the resident form), and the MB
+    // of working set (J, state, V) a window may hold -- within the 129 MB L2 it
     // stays resident across its steps, beyond it more tiles run at once.
     constexpr int kCands[4] = {1, 2, 4, 8};
     constexpr double kCandMB[4] = {80.0, 120.0, 160.0, 240.0};
@@ -238,6 +239,9 @@ gsb_status batch_bf16(int n, gsb_problem* const* problems, const gsb_params* par
                 best = ms_probe[w];
                 per_cta = kCands[w];
                 window_mb = kCandMB[w];
+            } else {
+                // larger windows only lengthened the step: stop probing
+                break;
             }
         }
         cudaEventDestroy(e0);
